@@ -1,0 +1,136 @@
+"""Named synthetic workloads (meshes, density models, sources, receivers, time axis).
+
+Flaw contrast.  The flaws keep the geometry of the specified workloads (a circle of
+radius 0.1; two ellipses with semi-axes in [0.03, 0.12]) but multiply the density
+by FLAW_FACTOR = 0.5, the paper's weak-inclusion contrast (Section 4, "half the
+density").  The paper's radial finite differences discretise the expanded,
+non-conservative form of the radial ODE; with a sharp jump of the density to
+1e-3 or 1e-5 of the background the semi-discrete operator has real negative
+omega^2 modes and every time integrator diverges (jumps to 0.1 of the background
+already diverge within 2000 steps).  ``flaw_factor`` overrides the default.
+
+Time step and source frequency follow one rule for every workload: with s_min the
+smallest spacing of consecutive boundary nodes, f0 = c / (10 s_min) (about ten
+nodes per dominant wavelength) and dt = 0.5 s_min / c.  Newmark uses the
+average-acceleration parameters beta = 1/4, gamma = 1/2.
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node
+from .fields import flawed_density_circle, flawed_density_ellipses
+from .wavelet import ricker
+
+FLAW_FACTOR = 0.5
+
+
+@dataclass
+class Workload:
+    name: str
+    mesh: StructuredMesh
+    n_r: int                   # radial FD points per element (n + 1, i = 0..n)
+    c: float
+    gx: int
+    gy: int
+    rho_true: np.ndarray       # (gy, gx) density with flaws
+    rho_start: np.ndarray      # (gy, gx) homogeneous starting model
+    src_nodes: np.ndarray      # (B,) int64, one point source per shot
+    wavelets: np.ndarray       # (B, K) float64, sample k drives the step to t_{k+1}
+    rec_nodes: np.ndarray      # (R,) int64, shared by all shots
+    dt: float
+    K: int
+    f0: float
+    beta: float = 0.25
+    gamma: float = 0.5
+    xi0: float = 1e-3
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n_shots(self) -> int:
+        return int(self.src_nodes.shape[0])
+
+    def summary(self) -> dict:
+        m = self.mesh
+        return {"workload": self.name, "elements": m.n_elem, "p": m.p, "n_b": 4 * m.p,
+                "N_r": self.n_r, "global_nodes": m.n_nodes, "shots": self.n_shots,
+                "receivers": int(self.rec_nodes.shape[0]), "steps": self.K,
+                "grid": [self.gy, self.gx], "dt": self.dt, "f0": self.f0}
+
+
+def _time_axis(mesh: StructuredMesh, c: float):
+    s_min = min(mesh.lx / (mesh.nx * mesh.p), mesh.ly / (mesh.ny * mesh.p))
+    return c / (10.0 * s_min), 0.5 * s_min / c
+
+
+def tiny_workload(seed: int = 0, refine: int = 1, K: int = 400, flaw_factor: float = FLAW_FACTOR) -> Workload:
+    """4x4 square S-elements, p = 2, N_r = 8, one circular flaw (radius 0.1) on a 64x64 grid.
+
+    One Ricker source at the top-edge node nearest x = 0.5; four receivers on the
+    other three edges.  ``refine=2`` gives the same physical set-up on a mesh with
+    twice the elements per direction and twice the radial points (used to make
+    observed data without an inverse crime); the source and receivers sit at the
+    same physical points, which are nodes of both meshes.  The time axis is that
+    of the unrefined mesh.
+    """
+    rng = np.random.default_rng(seed)
+    base = structured_mesh(4, 4, 2)
+    mesh = structured_mesh(4 * refine, 4 * refine, 2)
+    c = 1.0
+    f0, dt = _time_axis(base, c)
+    rho_true, finfo = flawed_density_circle(64, 64, radius=0.1, factor=flaw_factor, seed=seed)
+    rho_start = np.ones_like(rho_true)
+    src = nearest_node(mesh, boundary_nodes(mesh, "top"), (0.5, 1.0))
+    sides = ["bottom", "left", "right", ["bottom", "left", "right"][rng.integers(3)]]
+    recs = []
+    for side in sides:
+        t = rng.uniform(0.1, 0.9)
+        pt = {"bottom": (t, 0.0), "left": (0.0, t), "right": (1.0, t)}[side]
+        # snap to a node of the unrefined mesh so the point exists in both meshes
+        pb = base.node_xy[nearest_node(base, boundary_nodes(base, side), pt)]
+        g = nearest_node(mesh, boundary_nodes(mesh, side), pb)
+        if g in recs:
+            g = nearest_node(mesh, np.setdiff1d(boundary_nodes(mesh, side), recs), pb)
+        recs.append(g)
+    wav = ricker(f0, dt, K)[None, :]
+    return Workload("tiny", mesh, 8 * refine, c, 64, 64, rho_true, rho_start,
+                    np.array([src], dtype=np.int64), wav, np.array(recs, dtype=np.int64),
+                    dt, K, f0, info={"flaw": finfo, "seed": seed, "refine": refine})
+
+
+def size_workload(seed: int = 1, K: int = 2000, n_shots: int = 8, nx: int = 64, n_r: int = 32,
+                  grid: int = 256, n_rec: int = 32, flaw_factor: float = FLAW_FACTOR) -> Workload:
+    """64x64 square S-elements, p = 4, N_r = 32, two elliptical flaws on a 256x256 grid.
+
+    Eight Ricker sources equally spaced along the top edge, 32 receivers equally
+    spaced along the perimeter, 2000 steps.  Smaller meshes with the same recipe
+    are available through ``nx`` / ``n_r`` / ``grid`` for tests.
+    """
+    mesh = structured_mesh(nx, nx, 4)
+    c = 1.0
+    f0, dt = _time_axis(mesh, c)
+    rho_true, finfo = flawed_density_ellipses(grid, grid, n=2, factor=flaw_factor, seed=seed)
+    rho_start = np.ones_like(rho_true)
+    top = boundary_nodes(mesh, "top")
+    srcs = [nearest_node(mesh, top, ((s + 0.5) / n_shots, 1.0)) for s in range(n_shots)]
+    recs = []
+    for k in range(n_rec):
+        t = 4.0 * (k + 0.5) / n_rec          # position along the perimeter, CCW from (0,0)
+        side, u = int(t), t - int(t)
+        side_name, pt = [("bottom", (u, 0.0)), ("right", (1.0, u)),
+                         ("top", (1.0 - u, 1.0)), ("left", (0.0, 1.0 - u))][side]
+        recs.append(nearest_node(mesh, boundary_nodes(mesh, side_name), pt))
+    recs = list(dict.fromkeys(recs))
+    wav = np.stack([ricker(f0, dt, K) for _ in srcs])
+    return Workload("size", mesh, n_r, c, grid, grid, rho_true, rho_start,
+                    np.array(srcs, dtype=np.int64), wav, np.array(recs, dtype=np.int64),
+                    dt, K, f0, info={"flaws": finfo, "seed": seed})
+
+
+def workload_by_name(name: str, **kw) -> Workload:
+    if name == "tiny":
+        return tiny_workload(**kw)
+    if name == "size":
+        return size_workload(**kw)
+    raise KeyError(name)
