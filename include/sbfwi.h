@@ -1,0 +1,184 @@
+/*
+ * sbfwi.h -- C ABI of the GB300 library for the time-domain SBFEM full-waveform
+ * inversion hot path (forward solve, misfit, time-reversed adjoint and the
+ * velocity part of the Frechet kernel) of "Full-waveform inversion via the
+ * scaled boundary finite element method" (arXiv 2501.06748).
+ *
+ * Conventions for every call
+ * --------------------------
+ *  - Return value: SBFWI_OK (0) or a negative SBFWI_E* code.  The message of the
+ *    last failure on the calling thread is returned by sbfwi_last_error().
+ *  - Floating-point data are IEEE binary64, C-contiguous.  Integer ids are int64.
+ *  - Arrays are owned by the caller.  Handles (mesh, model, forward state) are
+ *    owned by the library and released with the matching sbfwi_destroy_* call.
+ *    A handle must not be used by two threads at once.
+ *  - `mem` tells where the floating-point arrays named in a call's description
+ *    live: SBFWI_MEM_HOST (ordinary or pinned host memory; the library stages
+ *    them through the device) or SBFWI_MEM_DEVICE (device memory of the current
+ *    CUDA device).  Id arrays (node ids) are always host memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work of a call is ordered on it; calls return after the work is
+ *    complete (host outputs are written, device outputs are ready).
+ *  - Nothing here falls back to the CPU: without a usable CUDA device the
+ *    compute calls return SBFWI_ECUDA.
+ *
+ * Nodal points (the parameters and the gradient live on them; Section 4 of the
+ * paper defines the density "at the nodal points" and uses the solution fields
+ * there directly):
+ *    interior point (e, i, j), element e, radial point i = 0..N_r-2, boundary
+ *    node j of the element (local numbering below), has index
+ *        e*(N_r-1)*n_b + i*n_b + j
+ *    and global boundary node g (radial point i = N_r-1, shared by the elements
+ *    meeting there) has index n_int + g, n_int = n_elem*(N_r-1)*n_b.
+ *    Its location is x0 + xi_i (x_j - x0) (Eq. (transformation)).
+ *  Local numbering of an element's boundary nodes: order of first appearance
+ *  when walking its line elements in the given (counter-clockwise) order.
+ */
+#ifndef SBFWI_H
+#define SBFWI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  SBFWI_OK = 0,
+  SBFWI_EINVAL = -1,       /* bad argument or malformed mesh */
+  SBFWI_ENOMEM = -2,       /* device or host allocation failed */
+  SBFWI_ECUDA = -3,        /* CUDA runtime error (message has the CUDA text) */
+  SBFWI_ETIMEOUT = -4,     /* a bounded device wait gave up */
+  SBFWI_ESTATE = -5,       /* handle used in the wrong state */
+  SBFWI_ESINGULAR = -6,    /* a pivot block or the global matrix is singular */
+  SBFWI_EUNSUPPORTED = -7  /* valid request outside what this build implements */
+};
+enum { SBFWI_MEM_HOST = 0, SBFWI_MEM_DEVICE = 1 };
+enum { SBFWI_RHO_GRID = 0, SBFWI_RHO_NODAL = 1 };
+enum { SBFWI_GRAD_KERNEL = 0, SBFWI_GRAD_EXACT = 1 };
+
+typedef struct sbfwi_mesh sbfwi_mesh;
+typedef struct sbfwi_model sbfwi_model;
+typedef struct sbfwi_fwdstate sbfwi_fwdstate;
+
+/* Message of the last failure on this thread ("" if none).  Owned by the library. */
+const char* sbfwi_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int sbfwi_version(void);
+
+/*
+ * sbfwi_build_mesh -- a mesh of 2-D scaled-boundary elements (Section 3: a
+ * star-convex polygon per element, boundary discretised by line elements of
+ * Lagrange order p, scaling centre (x0, y0), coordinate map
+ * x = x0 + xi (x_b(eta) - x0), Eq. (transformation)).
+ *
+ *   node_xy     [n_nodes][2]   node coordinates
+ *   elem_ptr    [n_elem+1]     element e owns line elements elem_ptr[e]..elem_ptr[e+1]-1
+ *   line_nodes  [n_lines][p+1] global node ids of each line element, in the direction
+ *                              of travel; an element's lines form a closed
+ *                              counter-clockwise loop (end of one = start of next)
+ *   centre_xy   [n_elem][2]    scaling centres
+ *   p           line order, 1..8 (nodes equally spaced along straight lines)
+ *   n_r         radial finite-difference points per element, N_r >= 3
+ *               (xi_i = xi0 + i h, h = (1-xi0)/(N_r-1), Section 3.3)
+ *   xi0         scaling-centre offset (the paper uses 1e-3)
+ *
+ * Checks: ids in range, closed CCW loops, straight lines with equally spaced
+ * nodes, det J_b > 0 (scaling centre sees every line from its left).  Returns
+ * SBFWI_EINVAL with the offending element in the message.  This build requires
+ * the same number of boundary nodes n_b (<= 24) for every element
+ * (SBFWI_EUNSUPPORTED otherwise).  All arrays are host memory, copied.
+ */
+int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes,
+                     const int64_t* elem_ptr, const int64_t* line_nodes, int64_t n_lines,
+                     const double* centre_xy, int64_t n_elem, int32_t p, int32_t n_r, double xi0);
+
+/* info[0..7] = n_elem, n_nodes, n_b, N_r, n_nodal (= n_int + n_nodes), n_int,
+ * levels of the global elimination tree, nonzeros kept by the global factors. */
+int sbfwi_mesh_info(const sbfwi_mesh* mesh, int64_t* info);
+void sbfwi_destroy_mesh(sbfwi_mesh* mesh);
+
+/*
+ * sbfwi_set_model -- set-up of the path for one density model and time step
+ * (per model, not per step; Section 3):
+ *   density on the nodal points; coefficient matrices E0, E1, E2, M0 at every
+ *   radial point (Eq. (Es)); radial derivatives of E0, E1; blocks of
+ *   Eq. (system); condensation (pivots, Thomas sweep, last-row elimination and
+ *   2x2 closure giving the element dynamic stiffness S and the effective-source
+ *   operator); assembly and factorisation of the global boundary matrix sum_e S_e.
+ *   The set-up runs in double-double arithmetic and rounds its results to FP64.
+ *
+ *   c        wave speed (constant, Section 3)
+ *   rho      SBFWI_RHO_GRID:  [gy][gx] cell-centred values on [0,lx]x[0,ly],
+ *                             mapped to nodal points by bilinear interpolation
+ *                             (clamped at the edges);
+ *            SBFWI_RHO_NODAL: [n_nodal] values on the nodal points (gx, gy, lx, ly unused).
+ *            All values must be > 0 (SBFWI_EINVAL).
+ *   dt, beta, gamma  Newmark parameters (Eq. (Newmark)); beta > 0.
+ *   mem      where rho lives.
+ * Errors: SBFWI_ESINGULAR if a pivot block or a separator block of the global
+ * matrix cannot be inverted.  The model keeps a reference to `mesh`, which must
+ * outlive it.
+ */
+int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho,
+                    int rho_kind, int64_t gx, int64_t gy, double lx, double ly,
+                    double dt, double beta, double gamma, int mem, void* stream);
+void sbfwi_destroy_model(sbfwi_model* model);
+
+/*
+ * sbfwi_forward -- forward solve of n_shots independent shots on the model
+ * (Section 2, Eq. (main); zero initial state), K Newmark steps.  Each step:
+ * residual sources (Eq. (ODE_Newmark)), forward condensation sweep and
+ * effective source of every element, global boundary solve, radial
+ * back-substitution and Newmark update (Section 3.3).
+ *
+ *   src_node    [n_shots]          host; node of shot s's point source
+ *   src_wavelet [n_shots][K]       sample k is added to the boundary right-hand
+ *                                  side at src_node[s] for the step that produces
+ *                                  the state at t_{k+1} = (k+1) dt
+ *   rec_node    [n_rec]            host; receiver nodes shared by all shots (distinct)
+ *   traces      [n_shots][n_rec][K] out: u at the receivers at t_{k+1}
+ *   keep        if not NULL, receives a forward state holding the nodal velocities
+ *               of every step (Section 4 stores the forward field for the adjoint);
+ *               it needs K * n_nodal * n_shots * 8 bytes of device memory
+ *               (SBFWI_ENOMEM if that is not available).
+ *   mem         where src_wavelet and traces live.
+ */
+int sbfwi_forward(sbfwi_model* model, int32_t n_shots, const int64_t* src_node,
+                  const double* src_wavelet, int32_t n_rec, const int64_t* rec_node, int64_t K,
+                  double* traces, sbfwi_fwdstate** keep, int mem, void* stream);
+
+/*
+ * sbfwi_misfit -- E = 1/2 sum_{shot,rec} int (d - u)^2 dt (Eq. (misfit)) with the
+ * rectangle rule over the n trace samples: E = 0.5 * dt * sum (observed - traces)^2.
+ *   traces, observed  [n]; residual_out [n] (nullable) receives observed - traces.
+ *   E_out  host pointer.  mem applies to traces, observed, residual_out.
+ */
+int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double dt,
+                 double* E_out, double* residual_out, int mem, void* stream);
+
+/*
+ * sbfwi_adjoint_gradient -- time-reversed adjoint solve and zero-lag
+ * cross-correlation (Section 2: adjoint equation and Frechet kernel; Section 4:
+ * the c^2 grad(lambda).grad(u) term is dropped and the nodal fields are used
+ * directly).  Adjoint step m (0-based) injects residual[s][r][K-1-m] at
+ * rec_node[r] (same sign slot as the forward source) and accumulates
+ *     g(node) += dt * sum_s udot_fwd[K-1-m](node, s) * lambdadot^{m+1}(node, s).
+ *
+ *   fwdstate  from sbfwi_forward(..., keep) on the same model; not consumed.
+ *   residual  [n_shots][n_rec][K] (d - u, as from sbfwi_misfit)
+ *   mode      SBFWI_GRAD_KERNEL (the paper's kernel).  SBFWI_GRAD_EXACT returns
+ *             SBFWI_EUNSUPPORTED in this build.
+ *   grad      out: [gy][gx] (model set with SBFWI_RHO_GRID, the transpose of the
+ *             bilinear map) or [n_nodal] (SBFWI_RHO_NODAL).
+ *   mem       where residual and grad live.
+ */
+int sbfwi_adjoint_gradient(sbfwi_model* model, sbfwi_fwdstate* fwdstate, const double* residual,
+                           int mode, double* grad, int mem, void* stream);
+void sbfwi_destroy_fwdstate(sbfwi_fwdstate* state);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBFWI_H */

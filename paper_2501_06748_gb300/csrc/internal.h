@@ -1,0 +1,152 @@
+// Internal data structures of libsbfwi (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sbfwi.h"
+
+namespace sbfwi {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SBFWI_CUDA(call)                                   \
+  do {                                                     \
+    cudaError_t err__ = (call);                            \
+    if (err__ != cudaSuccess) return cuda_fail(err__, #call); \
+  } while (0)
+
+// RAII device buffer
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t alloc(size_t nbytes) {
+    release();
+    if (nbytes == 0) nbytes = 16;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e == cudaSuccess) bytes = nbytes;
+    else p = nullptr;
+    return e;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---------------------------------------------------------------------------
+// elimination tree of the global boundary system (nested dissection by
+// recursive coordinate bisection of the elements)
+// ---------------------------------------------------------------------------
+struct TreeNodeDev {
+  int32_t s, b;            // separator size (eliminated here), boundary size (passed up)
+  int32_t child0, child1;  // -1 for leaves
+  int32_t elem;            // leaf: its element; -1 otherwise
+  int32_t pad;
+  int64_t sep_off;         // into sep_nodes (s ids) and ysep rows
+  int64_t bnd_off;         // into bnd_nodes (b ids) and ybnd rows
+  int64_t map_off;         // into map0/map1 (s+b entries)
+  int64_t X_off;           // factor storage: X (s*s) then G (s*b) then C (b*s)
+  int64_t F_off;           // set-up workspace: front (f*f)
+  int64_t U_off;           // set-up workspace: update matrix (b*b)
+};
+
+struct Task {               // a row range of one tree node
+  int32_t node;
+  int32_t r0, r1;
+  int32_t pad;
+};
+
+struct Tree {
+  std::vector<TreeNodeDev> nodes;      // post-order; root last
+  std::vector<int32_t> level_of;       // height: leaves 0
+  int levels = 0;
+  std::vector<int32_t> sep_nodes, bnd_nodes;
+  std::vector<int32_t> map0, map1;     // per front position: child0 / child1 bnd index, -1 if absent;
+                                       // leaves: map0 = local dof of the element
+  std::vector<std::vector<int32_t>> nodes_at_level;
+  int64_t X_total = 0, F_total = 0, U_total = 0, sep_rows = 0, bnd_rows = 0;
+  std::vector<int32_t> sep_owner;      // per global node: tree node that eliminates it
+};
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+struct Mesh {
+  int64_t n_elem = 0, n_nodes = 0, n_lines = 0;
+  int p = 0, n_r = 0, nb = 0, n = 0, L = 0;   // n = N_r - 1 intervals, L lines per element
+  double xi0 = 1e-3;
+  std::vector<double> node_xy, centre_xy;
+  std::vector<int64_t> elem_ptr, line_nodes;
+  std::vector<int32_t> dofs;        // [n_elem][nb] global node of each local dof
+  std::vector<int32_t> line_local;  // [n_elem][L][p+1] local dof of each line position
+  Tree tree;
+  int64_t n_int = 0, n_nodal = 0;
+};
+
+int build_tree(Mesh& m);
+
+// ---------------------------------------------------------------------------
+// model (device resident)
+// ---------------------------------------------------------------------------
+struct LevelTasks {
+  std::vector<int32_t> fwd_start, bwd_start;   // per level: first task index (levels+1 entries)
+  DevBuf fwd, bwd;                              // Task arrays
+  int rows_per_task = 0;
+};
+
+struct Model {
+  const Mesh* mesh = nullptr;
+  int nb = 0, n = 0;
+  int64_t E = 0, N = 0;
+  double c = 1, dt = 0, beta = 0.25, gamma = 0.5;
+  double a0 = 0, a1 = 0, a2 = 0, c1 = 0, c2 = 0;  // Newmark constants
+  int rho_kind = SBFWI_RHO_GRID;
+  int64_t gx = 0, gy = 0;
+  double lx = 1, ly = 1;
+  // element operators, FP64: per element and radial point i = 0..n-1: P_i, Q_i, H_i; then R, T
+  DevBuf mats;      // [E][n][3][nb][nb]
+  DevBuf rt;        // [E][2][nb][nb]
+  DevBuf S;         // [E][nb][nb]  dynamic stiffness (kept for tests/inspection)
+  DevBuf dofs;      // [E][nb] int32
+  DevBuf rho_nodal; // [n_nodal] FP64 (hi part of the set-up value)
+  // global elimination tree
+  DevBuf tree_nodes, sep_nodes, bnd_nodes, map0, map1, factors;
+  // fine-grid map (SBFWI_RHO_GRID)
+  DevBuf cell_of_point;  // [n_nodal] int32 base cell ix + gx*iy
+  DevBuf clamp_of_point; // [n_nodal] int8 bit0 x-low, bit1 x-high, bit2 y-low, bit3 y-high
+  DevBuf pts_hi, pts_lo; // [n_nodal][2] dd location of every nodal point
+  DevBuf cell_ptr, cell_list;   // CSR: grid cell -> (point*4 + corner)
+  LevelTasks tasks;        // built for tasks.rows_per_task
+};
+
+int build_level_tasks(Model& md, int rows_per_task);
+
+struct FwdState {
+  Model* model = nullptr;
+  int32_t B = 0, R = 0;
+  int64_t K = 0;
+  std::vector<int64_t> rec;
+  DevBuf store;      // [K][n_nodal][B] nodal velocities after every step
+};
+
+}  // namespace sbfwi
+
+// opaque handle types of the C ABI
+struct sbfwi_mesh : public sbfwi::Mesh {};
+struct sbfwi_model : public sbfwi::Model {};
+struct sbfwi_fwdstate : public sbfwi::FwdState {};

@@ -1,0 +1,279 @@
+// Mesh validation, element-local numbering and the elimination tree of the
+// global boundary system.
+//
+// The global system (sum over elements of the dynamic stiffness S_e, Section 3.3:
+// "the global algebraic system ... can then be assembled and solved"; the paper
+// leaves the solver open) is solved by a multifrontal factorisation ordered by
+// nested dissection: elements are split recursively in halves by the median of
+// their scaling centres along the longer extent of their bounding box.  A global
+// node is eliminated at the smallest subtree that contains every element
+// touching it (its separator); what a subtree still shares with the rest of the
+// mesh is its boundary and is passed to the parent.  This file builds that tree,
+// its separator/boundary lists and the index maps used to assemble fronts and
+// right-hand sides; the numerical work runs in CUDA kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+
+#include "internal.h"
+
+namespace sbfwi {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SBFWI_ENOMEM : SBFWI_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// elimination tree
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Builder {
+  const Mesh& m;
+  std::vector<int32_t> order;           // elements in tree order
+  std::vector<int32_t> lo, hi, c0, c1;  // per tree node
+  explicit Builder(const Mesh& mm) : m(mm) {}
+
+  int make(int32_t a, int32_t b) {
+    int32_t left = -1, right = -1;
+    if (b - a > 1) {
+      double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+      for (int32_t k = a; k < b; ++k) {
+        double x = m.centre_xy[2 * order[k]], y = m.centre_xy[2 * order[k] + 1];
+        xmin = std::min(xmin, x); xmax = std::max(xmax, x);
+        ymin = std::min(ymin, y); ymax = std::max(ymax, y);
+      }
+      int ax = (xmax - xmin >= ymax - ymin) ? 0 : 1;
+      std::stable_sort(order.begin() + a, order.begin() + b, [&](int32_t e1, int32_t e2) {
+        double p1 = m.centre_xy[2 * e1 + ax], p2 = m.centre_xy[2 * e2 + ax];
+        if (p1 != p2) return p1 < p2;
+        double q1 = m.centre_xy[2 * e1 + 1 - ax], q2 = m.centre_xy[2 * e2 + 1 - ax];
+        if (q1 != q2) return q1 < q2;
+        return e1 < e2;
+      });
+      int32_t mid = a + (b - a) / 2;
+      left = make(a, mid);
+      right = make(mid, b);
+    }
+    lo.push_back(a); hi.push_back(b); c0.push_back(left); c1.push_back(right);
+    return (int)lo.size() - 1;
+  }
+};
+
+}  // namespace
+
+int build_tree(Mesh& m) {
+  Tree& t = m.tree;
+  t = Tree();
+  Builder bd(m);
+  bd.order.resize(m.n_elem);
+  std::iota(bd.order.begin(), bd.order.end(), 0);
+  int root = bd.make(0, (int32_t)m.n_elem);
+  const int T = (int)bd.lo.size();
+  if (root != T - 1) return fail(SBFWI_EINVAL, "internal: tree root not last");
+  std::vector<int32_t> pos_of(m.n_elem);
+  for (int32_t k = 0; k < (int32_t)m.n_elem; ++k) pos_of[bd.order[k]] = k;
+
+  // smallest subtree containing all elements of each node
+  std::vector<int32_t> pmin(m.n_nodes, INT32_MAX), pmax(m.n_nodes, -1);
+  for (int64_t e = 0; e < m.n_elem; ++e)
+    for (int j = 0; j < m.nb; ++j) {
+      int32_t g = m.dofs[e * m.nb + j];
+      pmin[g] = std::min(pmin[g], pos_of[e]);
+      pmax[g] = std::max(pmax[g], pos_of[e]);
+    }
+  t.sep_owner.assign(m.n_nodes, -1);
+  std::vector<std::vector<int32_t>> sep(T), bnd(T);
+  for (int64_t g = 0; g < m.n_nodes; ++g) {
+    if (pmax[g] < 0) return fail(SBFWI_EINVAL, "node " + std::to_string(g) + " belongs to no element");
+    int nd = root;
+    while (bd.c0[nd] >= 0) {
+      int a = bd.c0[nd], b = bd.c1[nd];
+      if (pmax[g] < bd.hi[a]) nd = a;
+      else if (pmin[g] >= bd.lo[b]) nd = b;
+      else break;
+    }
+    t.sep_owner[g] = nd;
+    sep[nd].push_back((int32_t)g);
+  }
+  // boundary lists bottom-up (post-order: children before parents)
+  for (int nd = 0; nd < T; ++nd) {
+    std::vector<int32_t> cand;
+    if (bd.c0[nd] < 0) {
+      int32_t e = bd.order[bd.lo[nd]];
+      for (int j = 0; j < m.nb; ++j) cand.push_back(m.dofs[(int64_t)e * m.nb + j]);
+    } else {
+      cand = bnd[bd.c0[nd]];
+      cand.insert(cand.end(), bnd[bd.c1[nd]].begin(), bnd[bd.c1[nd]].end());
+    }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    for (int32_t g : cand)
+      if (t.sep_owner[g] != nd) bnd[nd].push_back(g);
+    std::sort(sep[nd].begin(), sep[nd].end());
+  }
+  if (!bnd[root].empty()) return fail(SBFWI_EINVAL, "internal: root of elimination tree has a boundary");
+
+  // node records, maps and offsets
+  t.nodes.resize(T);
+  t.level_of.assign(T, 0);
+  int64_t sep_off = 0, bnd_off = 0, map_off = 0, X_off = 0, F_off = 0, U_off = 0;
+  for (int nd = 0; nd < T; ++nd) {
+    TreeNodeDev& r = t.nodes[nd];
+    r.s = (int32_t)sep[nd].size();
+    r.b = (int32_t)bnd[nd].size();
+    r.child0 = bd.c0[nd];
+    r.child1 = bd.c1[nd];
+    r.elem = (bd.c0[nd] < 0) ? bd.order[bd.lo[nd]] : -1;
+    r.pad = 0;
+    r.sep_off = sep_off;
+    r.bnd_off = bnd_off;
+    r.map_off = map_off;
+    r.X_off = X_off;
+    r.F_off = F_off;
+    r.U_off = U_off;
+    const int64_t s = r.s, b = r.b, f = s + b;
+    sep_off += s; bnd_off += b; map_off += f;
+    X_off += s * s + 2 * s * b;
+    F_off += f * f;
+    U_off += b * b;
+    t.sep_nodes.insert(t.sep_nodes.end(), sep[nd].begin(), sep[nd].end());
+    t.bnd_nodes.insert(t.bnd_nodes.end(), bnd[nd].begin(), bnd[nd].end());
+    std::vector<int32_t> front = sep[nd];
+    front.insert(front.end(), bnd[nd].begin(), bnd[nd].end());
+    if (r.elem >= 0) {
+      std::map<int32_t, int32_t> local;
+      for (int j = 0; j < m.nb; ++j) local[m.dofs[(int64_t)r.elem * m.nb + j]] = j;
+      for (int32_t g : front) { t.map0.push_back(local.at(g)); t.map1.push_back(-1); }
+    } else {
+      std::map<int32_t, int32_t> in0, in1;
+      for (size_t k = 0; k < bnd[r.child0].size(); ++k) in0[bnd[r.child0][k]] = (int32_t)k;
+      for (size_t k = 0; k < bnd[r.child1].size(); ++k) in1[bnd[r.child1][k]] = (int32_t)k;
+      for (int32_t g : front) {
+        auto a = in0.find(g), b2 = in1.find(g);
+        t.map0.push_back(a == in0.end() ? -1 : a->second);
+        t.map1.push_back(b2 == in1.end() ? -1 : b2->second);
+      }
+      t.level_of[nd] = 1 + std::max(t.level_of[r.child0], t.level_of[r.child1]);
+    }
+  }
+  t.levels = t.level_of[root] + 1;
+  t.nodes_at_level.assign(t.levels, {});
+  for (int nd = 0; nd < T; ++nd) t.nodes_at_level[t.level_of[nd]].push_back(nd);
+  t.X_total = X_off;
+  t.F_total = F_off;
+  t.U_total = U_off;
+  t.sep_rows = sep_off;
+  t.bnd_rows = bnd_off;
+  if (sep_off != m.n_nodes) return fail(SBFWI_EINVAL, "internal: separators do not cover the nodes");
+  return SBFWI_OK;
+}
+
+}  // namespace sbfwi
+
+using namespace sbfwi;
+
+extern "C" {
+
+const char* sbfwi_last_error(void) { return g_last_error.c_str(); }
+int sbfwi_version(void) { return 100; }
+
+int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes, const int64_t* elem_ptr,
+                     const int64_t* line_nodes, int64_t n_lines, const double* centre_xy, int64_t n_elem,
+                     int32_t p, int32_t n_r, double xi0) {
+  if (!out) return fail(SBFWI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!node_xy || !elem_ptr || !line_nodes || !centre_xy) return fail(SBFWI_EINVAL, "NULL array");
+  if (n_nodes < 1 || n_elem < 1 || n_lines < 1) return fail(SBFWI_EINVAL, "empty mesh");
+  if (n_nodes > INT32_MAX / 2 || n_elem > INT32_MAX / 2) return fail(SBFWI_EINVAL, "mesh too large");
+  if (p < 1 || p > 8) return fail(SBFWI_EINVAL, "line order p must be in 1..8");
+  if (n_r < 3) return fail(SBFWI_EINVAL, "need at least 3 radial points");
+  if (!(xi0 > 0.0 && xi0 < 1.0)) return fail(SBFWI_EINVAL, "xi0 must be in (0, 1)");
+  if (elem_ptr[0] != 0 || elem_ptr[n_elem] != n_lines) return fail(SBFWI_EINVAL, "elem_ptr must start at 0 and end at n_lines");
+  auto m = new sbfwi_mesh();
+  m->n_elem = n_elem; m->n_nodes = n_nodes; m->n_lines = n_lines;
+  m->p = p; m->n_r = n_r; m->n = n_r - 1; m->xi0 = xi0;
+  m->node_xy.assign(node_xy, node_xy + 2 * n_nodes);
+  m->centre_xy.assign(centre_xy, centre_xy + 2 * n_elem);
+  m->elem_ptr.assign(elem_ptr, elem_ptr + n_elem + 1);
+  m->line_nodes.assign(line_nodes, line_nodes + n_lines * (p + 1));
+  auto bad = [&](int code, const std::string& msg) { delete m; return fail(code, msg); };
+  for (int64_t k = 0; k < n_lines * (p + 1); ++k)
+    if (line_nodes[k] < 0 || line_nodes[k] >= n_nodes) return bad(SBFWI_EINVAL, "line node id out of range");
+  int nb_all = -1, L_all = -1;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    const int64_t l0 = elem_ptr[e], l1 = elem_ptr[e + 1];
+    const std::string tag = "element " + std::to_string(e) + ": ";
+    if (l1 - l0 < 2) return bad(SBFWI_EINVAL, tag + "needs at least two line elements");
+    const double x0 = centre_xy[2 * e], y0 = centre_xy[2 * e + 1];
+    std::vector<int32_t> order;
+    for (int64_t l = l0; l < l1; ++l) {
+      const int64_t* ln = line_nodes + l * (p + 1);
+      const int64_t* nx = line_nodes + (l + 1 < l1 ? l + 1 : l0) * (p + 1);
+      if (ln[p] != nx[0]) return bad(SBFWI_EINVAL, tag + "line elements do not form a closed loop");
+      const double xa = node_xy[2 * ln[0]], ya = node_xy[2 * ln[0] + 1];
+      const double xb = node_xy[2 * ln[p]], yb = node_xy[2 * ln[p] + 1];
+      const double len = std::hypot(xb - xa, yb - ya);
+      if (!(len > 0)) return bad(SBFWI_EINVAL, tag + "degenerate line element");
+      for (int k = 1; k < p; ++k) {
+        const double xe = xa + (xb - xa) * k / p, ye = ya + (yb - ya) * k / p;
+        if (std::hypot(node_xy[2 * ln[k]] - xe, node_xy[2 * ln[k] + 1] - ye) > 1e-9 * len)
+          return bad(SBFWI_EINVAL, tag + "line nodes must be equally spaced on a straight segment");
+      }
+      // det J_b = (x_b - x0) y_b,eta - (y_b - y0) x_b,eta; constant along a straight line
+      const double det = (xa - x0) * (yb - ya) - (ya - y0) * (xb - xa);
+      if (!(det > 1e-14 * len * len)) return bad(SBFWI_EINVAL, tag + "det J_b <= 0 (centre not strictly inside, or lines not counter-clockwise)");
+      for (int k = 0; k <= p; ++k)
+        if (std::find(order.begin(), order.end(), (int32_t)ln[k]) == order.end()) order.push_back((int32_t)ln[k]);
+    }
+    const int L = (int)(l1 - l0);
+    if ((int)order.size() != L * p) return bad(SBFWI_EINVAL, tag + "boundary nodes repeat along the loop");
+    if (nb_all < 0) { nb_all = (int)order.size(); L_all = L; }
+    if ((int)order.size() != nb_all || L != L_all)
+      return bad(SBFWI_EUNSUPPORTED, "elements with different numbers of boundary nodes are not supported by this build");
+    m->dofs.insert(m->dofs.end(), order.begin(), order.end());
+    for (int64_t l = l0; l < l1; ++l)
+      for (int k = 0; k <= p; ++k) {
+        int32_t g = (int32_t)line_nodes[l * (p + 1) + k];
+        m->line_local.push_back((int32_t)(std::find(order.begin(), order.end(), g) - order.begin()));
+      }
+  }
+  m->nb = nb_all;
+  m->L = L_all;
+  if (m->nb > 24) return bad(SBFWI_EUNSUPPORTED, "this build supports at most 24 boundary nodes per element");
+  m->n_int = m->n_elem * (int64_t)m->n * m->nb;
+  m->n_nodal = m->n_int + m->n_nodes;
+  int rc = build_tree(*m);
+  if (rc != SBFWI_OK) { delete m; return rc; }
+  *out = m;
+  return SBFWI_OK;
+}
+
+int sbfwi_mesh_info(const sbfwi_mesh* m, int64_t* info) {
+  if (!m || !info) return fail(SBFWI_EINVAL, "NULL argument");
+  info[0] = m->n_elem;
+  info[1] = m->n_nodes;
+  info[2] = m->nb;
+  info[3] = m->n_r;
+  info[4] = m->n_nodal;
+  info[5] = m->n_int;
+  info[6] = m->tree.levels;
+  info[7] = m->tree.X_total;
+  return SBFWI_OK;
+}
+
+void sbfwi_destroy_mesh(sbfwi_mesh* m) { delete m; }
+
+}  // extern "C"

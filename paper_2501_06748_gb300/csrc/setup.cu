@@ -1,0 +1,889 @@
+// Set-up of the path for one density model (per model, not per step).
+//
+//  1. density on the nodal points (bilinear map of the fine grid, or given);
+//  2. per element, one CTA: coefficient matrices E0, E1, E2, M0 at every radial
+//     point (Eq. (Es)), radial derivatives of E0 and E1 (central inside,
+//     one-sided at xi_0 and xi_n), blocks theta/phi/psi of Eq. (system), and the
+//     algorithmic condensation of Section 3.3, all in double-double; the time
+//     loop receives, rounded to FP64,
+//         P_i = G_i xi_i^2 M0_i,  Q_i = G_i theta_i,  H_i = G_i psi_i   (i = 0..n-1)
+//         R = W theta_n - theta_{n+1},  T = W xi_n^2 M0_n,  S = phi_{n+1} - W phi_n
+//     with G_i the inverse of the modified pivot block phi_i and W = psi_{n+1} psi_n^{-1};
+//  3. multifrontal factorisation of the global boundary matrix sum_e S_e along
+//     the elimination tree (FP64, one CTA per front, Gauss-Jordan with partial
+//     pivoting inside each separator block).
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "dd.cuh"
+#include "internal.h"
+
+namespace sbfwi {
+
+// ---------------------------------------------------------------------------
+// host: Gauss-Legendre rule and Lagrange tables in double-double
+// ---------------------------------------------------------------------------
+namespace {
+
+void legendre_dd(int n, dd x, dd* pn, dd* pnm1) {
+  dd p0 = dd_make(1.0), p1 = x;
+  if (n == 0) { *pn = p0; *pnm1 = dd_make(0.0); return; }
+  for (int k = 2; k <= n; ++k) {
+    // p_k = ((2k-1) x p_{k-1} - (k-1) p_{k-2}) / k
+    dd t = dd_sub(dd_mul_d(dd_mul(x, p1), 2.0 * k - 1.0), dd_mul_d(p0, k - 1.0));
+    dd pk = dd_div(t, dd_make((double)k));
+    p0 = p1;
+    p1 = pk;
+  }
+  *pn = p1;
+  *pnm1 = p0;
+}
+
+// nodes and weights of the ng-point rule, double-double, ascending
+void gauss_legendre_dd(int ng, std::vector<dd>& x, std::vector<dd>& w) {
+  x.resize(ng);
+  w.resize(ng);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < ng; ++k) {
+    // Tricomi's estimate of the (k+1)-th largest root, then Newton in double and double-double
+    double xd = std::cos(pi * (k + 0.75) / (ng + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = xd;
+      for (int j = 2; j <= ng; ++j) { double pj = ((2.0 * j - 1) * xd * p1 - (j - 1.0) * p0) / j; p0 = p1; p1 = pj; }
+      if (ng == 1) p0 = 1.0;
+      double dp = ng * (xd * p1 - p0) / (xd * xd - 1.0);
+      double dx = p1 / dp;
+      xd -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    dd xx = dd_make(xd);
+    dd pn, pm;
+    for (int it = 0; it < 3; ++it) {
+      legendre_dd(ng, xx, &pn, &pm);
+      dd dp = dd_div(dd_mul_d(dd_sub(dd_mul(xx, pn), pm), (double)ng), dd_sub(dd_mul(xx, xx), dd_make(1.0)));
+      xx = dd_sub(xx, dd_div(pn, dp));
+    }
+    legendre_dd(ng, xx, &pn, &pm);
+    dd dp = dd_div(dd_mul_d(dd_sub(dd_mul(xx, pn), pm), (double)ng), dd_sub(dd_mul(xx, xx), dd_make(1.0)));
+    dd one_m_x2 = dd_sub(dd_make(1.0), dd_mul(xx, xx));
+    w[ng - 1 - k] = dd_div(dd_make(2.0), dd_mul(one_m_x2, dd_mul(dp, dp)));
+    x[ng - 1 - k] = xx;
+  }
+}
+
+// phi_a(eta) and d phi_a / d eta for equally spaced nodes eta_b = -1 + 2b/p
+void lagrange_dd(int p, dd eta, dd* phi, dd* dphi) {
+  std::vector<dd> nodes(p + 1);
+  for (int b = 0; b <= p; ++b) nodes[b] = dd_sub(dd_div(dd_make(2.0 * b), dd_make((double)p)), dd_make(1.0));
+  for (int a = 0; a <= p; ++a) {
+    dd denom = dd_make(1.0), num = dd_make(1.0), der = dd_make(0.0);
+    for (int b = 0; b <= p; ++b) {
+      if (b == a) continue;
+      denom = dd_mul(denom, dd_sub(nodes[a], nodes[b]));
+      num = dd_mul(num, dd_sub(eta, nodes[b]));
+    }
+    for (int m = 0; m <= p; ++m) {
+      if (m == a) continue;
+      dd t = dd_make(1.0);
+      for (int b = 0; b <= p; ++b)
+        if (b != a && b != m) t = dd_mul(t, dd_sub(eta, nodes[b]));
+      der = dd_add(der, t);
+    }
+    phi[a] = dd_div(num, denom);
+    dphi[a] = dd_div(der, denom);
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_flag(int* status, int code) { atomicCAS(status, 0, code); }
+
+// ---------------------------------------------------------------------------
+// 1. density at the nodal points (double-double)
+// ---------------------------------------------------------------------------
+struct DensityArgs {
+  int64_t n_elem, n_nodes, n_int;
+  int nb, n;
+  const double* node_xy;
+  const double* centre_xy;
+  const int32_t* dofs;
+  const double* xi_hi;
+  const double* xi_lo;
+  const double* grid;        // [gy][gx] or nodal values
+  int rho_kind;
+  int64_t gx, gy;
+  double lx, ly;
+  const int32_t* cell_of_point;
+  const int8_t* clamp_of_point;
+  double* pts_hi;            // [n_nodal][2]
+  double* pts_lo;
+  double* rho_hi;            // [n_nodal]
+  double* rho_lo;
+  int* status;
+};
+
+__global__ void density_kernel(DensityArgs a) {
+  const int64_t np = a.n_int + a.n_nodes;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
+    dd px, py;
+    if (q < a.n_int) {
+      const int64_t e = q / ((int64_t)a.n * a.nb);
+      const int64_t rem = q - e * (int64_t)a.n * a.nb;
+      const int i = (int)(rem / a.nb), j = (int)(rem - (int64_t)i * a.nb);
+      const int32_t g = a.dofs[e * a.nb + j];
+      const dd xi{a.xi_hi[i], a.xi_lo[i]};
+      const double x0 = a.centre_xy[2 * e], y0 = a.centre_xy[2 * e + 1];
+      // x0 + xi (x_j - x0)
+      px = dd_add(dd_make(x0), dd_mul(xi, two_sum(a.node_xy[2 * g], -x0)));
+      py = dd_add(dd_make(y0), dd_mul(xi, two_sum(a.node_xy[2 * g + 1], -y0)));
+    } else {
+      const int64_t g = q - a.n_int;
+      px = dd_make(a.node_xy[2 * g]);
+      py = dd_make(a.node_xy[2 * g + 1]);
+    }
+    a.pts_hi[2 * q] = px.hi; a.pts_lo[2 * q] = px.lo;
+    a.pts_hi[2 * q + 1] = py.hi; a.pts_lo[2 * q + 1] = py.lo;
+    dd rho;
+    if (a.rho_kind == SBFWI_RHO_NODAL) {
+      rho = dd_make(a.grid[q]);
+    } else {
+      // bilinear interpolation of the cell-centred grid, clamped at the edges
+      const int32_t cell = a.cell_of_point[q];
+      const int8_t cl = a.clamp_of_point[q];
+      const int64_t ix = cell % a.gx, iy = cell / a.gx;
+      dd tx, ty;
+      if (cl & 1) tx = dd_make(0.0);
+      else if (cl & 2) tx = dd_make(1.0);
+      else {  // fx = x * gx / lx - 1/2 - ix
+        dd fx = dd_div(dd_mul_d(px, (double)a.gx), dd_make(a.lx));
+        tx = dd_sub(fx, dd_make(0.5 + (double)ix));
+      }
+      if (cl & 4) ty = dd_make(0.0);
+      else if (cl & 8) ty = dd_make(1.0);
+      else {
+        dd fy = dd_div(dd_mul_d(py, (double)a.gy), dd_make(a.ly));
+        ty = dd_sub(fy, dd_make(0.5 + (double)iy));
+      }
+      const double* G = a.grid;
+      const dd one = dd_make(1.0);
+      const dd wx0 = dd_sub(one, tx), wy0 = dd_sub(one, ty);
+      dd v = dd_mul(dd_mul(wx0, wy0), dd_make(G[iy * a.gx + ix]));
+      v = dd_add(v, dd_mul(dd_mul(tx, wy0), dd_make(G[iy * a.gx + ix + 1])));
+      v = dd_add(v, dd_mul(dd_mul(wx0, ty), dd_make(G[(iy + 1) * a.gx + ix])));
+      v = dd_add(v, dd_mul(dd_mul(tx, ty), dd_make(G[(iy + 1) * a.gx + ix + 1])));
+      rho = v;
+    }
+    if (!(rho.hi > 0.0)) atomic_flag(a.status, SBFWI_EINVAL);
+    a.rho_hi[q] = rho.hi;
+    a.rho_lo[q] = rho.lo;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. element set-up (double-double, one CTA per element, one thread per entry)
+// ---------------------------------------------------------------------------
+struct ElemArgs {
+  int nb, n, L, p, ng;
+  int64_t n_elem, n_int;
+  double c;
+  dd mass;                    // 1 / (beta dt^2)
+  dd h;                       // radial spacing (1 - xi0) / n
+  const double* node_xy;
+  const double* centre_xy;
+  const int64_t* line_nodes;  // [E*L][p+1] (elements own consecutive lines)
+  const int32_t* line_local;  // [E][L][p+1]
+  const int32_t* dofs;
+  const double* rho_hi;
+  const double* rho_lo;
+  const double* xi_hi;        // [n+1]
+  const double* xi_lo;
+  const double* tab;          // dd tables (hi,lo pairs): w[ng], phi[ng][p+1], dphi[ng][p+1]
+  double* mats;               // [E][n][3][nb][nb]
+  double* rt;                 // [E][2][nb][nb]
+  double* S;                  // [E][nb][nb]
+  int* status;
+};
+
+struct ElemSmem {
+  dd* K;      // [L][ng][4] geometry factors: c^2 w det (b1.b1), c^2 w det (b2.b1), c^2 w det (b2.b2), w det
+  dd* KR;     // [L][ng][4] the same times rho at the Gauss point
+  dd* Eline;  // [L][p+1][p+1][4] per-line contributions
+  dd* phi;    // [ng][p+1]
+  dd* dphi;   // [ng][p+1]
+  dd* mat;    // 16 matrices of nb*nb
+  dd* col;    // [nb] Gauss-Jordan factor column
+  int* piv;
+};
+
+__device__ __forceinline__ dd ldd(const double* hi, const double* lo, int64_t k) { return dd{hi[k], lo[k]}; }
+
+// E0, E1, E2, M0 of element e at radial point i into the four given matrices
+__device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int64_t e, int i,
+                                     dd* E0, dd* E1, dd* E2, dd* M0) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nb = a.nb, L = a.L, p = a.p, ng = a.ng, pp = p + 1;
+  // density at the Gauss points of every line, times the geometry factors
+  for (int t = tid; t < L * ng; t += nt) {
+    const int l = t / ng, g = t - l * ng;
+    dd r = dd_make(0.0);
+    for (int q = 0; q < pp; ++q) {
+      const int j = a.line_local[(e * L + l) * pp + q];
+      const int64_t idx = (i < a.n) ? e * (int64_t)a.n * nb + (int64_t)i * nb + j : a.n_int + a.dofs[e * nb + j];
+      r = dd_fma(r, sm.phi[g * pp + q], ldd(a.rho_hi, a.rho_lo, idx));
+    }
+    for (int k = 0; k < 4; ++k) sm.KR[(l * ng + g) * 4 + k] = dd_mul(sm.K[(l * ng + g) * 4 + k], r);
+  }
+  __syncthreads();
+  // per-line matrices: sum over Gauss points
+  for (int t = tid; t < L * pp * pp; t += nt) {
+    const int l = t / (pp * pp), ab = t - l * pp * pp, aa = ab / pp, bb = ab - aa * pp;
+    dd s0 = dd_make(0.0), s1 = s0, s2 = s0, sm0 = s0;
+    for (int g = 0; g < ng; ++g) {
+      const dd* kr = sm.KR + (l * ng + g) * 4;
+      const dd pa = sm.phi[g * pp + aa], pb = sm.phi[g * pp + bb];
+      const dd da = sm.dphi[g * pp + aa], db = sm.dphi[g * pp + bb];
+      const dd papb = dd_mul(pa, pb);
+      s0 = dd_fma(s0, kr[0], papb);
+      s1 = dd_fma(s1, kr[1], dd_mul(da, pb));
+      s2 = dd_fma(s2, kr[2], dd_mul(da, db));
+      sm0 = dd_fma(sm0, kr[3], papb);
+    }
+    dd* out = sm.Eline + (size_t)t * 4;
+    out[0] = s0; out[1] = s1; out[2] = s2; out[3] = sm0;
+  }
+  __syncthreads();
+  // assemble the element matrices from the lines
+  for (int t = tid; t < nb * nb; t += nt) {
+    const int A = t / nb, B = t - A * nb;
+    dd s0 = dd_make(0.0), s1 = s0, s2 = s0, s3 = s0;
+    for (int l = 0; l < L; ++l) {
+      int pa = -1, pb = -1;
+      for (int q = 0; q < pp; ++q) {
+        const int j = a.line_local[(e * L + l) * pp + q];
+        if (j == A) pa = q;
+        if (j == B) pb = q;
+      }
+      if (pa < 0 || pb < 0) continue;
+      const dd* v = sm.Eline + ((size_t)(l * pp + pa) * pp + pb) * 4;
+      s0 = dd_add(s0, v[0]); s1 = dd_add(s1, v[1]); s2 = dd_add(s2, v[2]); s3 = dd_add(s3, v[3]);
+    }
+    E0[t] = s0; E1[t] = s1; E2[t] = s2; M0[t] = s3;
+  }
+  __syncthreads();
+}
+
+// Inv = A^{-1} by Gauss-Jordan with partial pivoting; A is destroyed.
+__device__ void gj_inverse(int nb, dd* A, dd* Inv, dd* col, int* piv, int* status) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < nb * nb; t += nt) Inv[t] = dd_make((t / nb) == (t % nb) ? 1.0 : 0.0);
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      int best = k;
+      double bv = fabs(A[k * nb + k].hi);
+      for (int r = k + 1; r < nb; ++r) {
+        const double v = fabs(A[r * nb + k].hi);
+        if (v > bv) { bv = v; best = r; }
+      }
+      if (!(bv > 0.0) || !isfinite(bv)) atomic_flag(status, SBFWI_ESINGULAR);
+      *piv = best;
+    }
+    __syncthreads();
+    const int pr = *piv;
+    if (pr != k) {
+      for (int c = tid; c < nb; c += nt) {
+        dd t1 = A[k * nb + c]; A[k * nb + c] = A[pr * nb + c]; A[pr * nb + c] = t1;
+        dd t2 = Inv[k * nb + c]; Inv[k * nb + c] = Inv[pr * nb + c]; Inv[pr * nb + c] = t2;
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < nb; r += nt) col[r] = A[r * nb + k];
+    __syncthreads();
+    const dd pinv = dd_div(dd_make(1.0), col[k]);
+    for (int t = tid; t < nb * nb; t += nt) {
+      const int r = t / nb, c = t - r * nb;
+      // row k is only read here; it is normalised after the barrier below
+      const dd ak = dd_mul(A[k * nb + c], pinv), ik = dd_mul(Inv[k * nb + c], pinv);
+      if (r != k) {
+        const dd f = col[r];
+        A[t] = dd_sub(A[t], dd_mul(f, ak));
+        Inv[t] = dd_sub(Inv[t], dd_mul(f, ik));
+      }
+    }
+    __syncthreads();
+    for (int c = tid; c < nb; c += nt) {
+      A[k * nb + c] = dd_mul(A[k * nb + c], pinv);
+      Inv[k * nb + c] = dd_mul(Inv[k * nb + c], pinv);
+    }
+    __syncthreads();
+  }
+}
+
+// C = A * B (all nb x nb, distinct buffers)
+__device__ void mm(int nb, const dd* A, const dd* B, dd* C) {
+  for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+    const int r = t / nb, c = t - r * nb;
+    dd s = dd_make(0.0);
+    for (int k = 0; k < nb; ++k) s = dd_fma(s, A[r * nb + k], B[k * nb + c]);
+    C[t] = s;
+  }
+  __syncthreads();
+}
+
+__global__ void element_setup_kernel(ElemArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nb = a.nb, L = a.L, p = a.p, ng = a.ng, pp = p + 1, n = a.n;
+  const int nn = nb * nb;
+  const int64_t e = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  ElemSmem sm;
+  dd* base = reinterpret_cast<dd*>(smem_raw);
+  sm.K = base;                     base += L * ng * 4;
+  sm.KR = base;                    base += L * ng * 4;
+  sm.Eline = base;                 base += L * pp * pp * 4;
+  sm.phi = base;                   base += ng * pp;
+  sm.dphi = base;                  base += ng * pp;
+  sm.col = base;                   base += nb;
+  sm.mat = base;                   base += 16 * nn;
+  sm.piv = reinterpret_cast<int*>(base);
+  dd* E0w[3] = {sm.mat + 0 * nn, sm.mat + 1 * nn, sm.mat + 2 * nn};
+  dd* E1w[3] = {sm.mat + 3 * nn, sm.mat + 4 * nn, sm.mat + 5 * nn};
+  dd* E2w[2] = {sm.mat + 6 * nn, sm.mat + 7 * nn};
+  dd* M0w[2] = {sm.mat + 8 * nn, sm.mat + 9 * nn};
+  dd* th = sm.mat + 10 * nn;
+  dd* ph = sm.mat + 11 * nn;
+  dd* ps = sm.mat + 12 * nn;
+  dd* Hp = sm.mat + 13 * nn;
+  dd* Gm = sm.mat + 14 * nn;
+  dd* T1 = sm.mat + 15 * nn;
+
+  // Lagrange tables and line geometry (Section 3 preamble)
+  for (int t = tid; t < ng * pp; t += nt) {
+    const int g = t / pp, q = t - g * pp;
+    sm.phi[t] = dd{a.tab[2 * (ng + g * pp + q)], a.tab[2 * (ng + g * pp + q) + 1]};
+    sm.dphi[t] = dd{a.tab[2 * (ng + ng * pp + g * pp + q)], a.tab[2 * (ng + ng * pp + g * pp + q) + 1]};
+  }
+  __syncthreads();
+  const double x0 = a.centre_xy[2 * e], y0 = a.centre_xy[2 * e + 1];
+  const dd c2 = two_prod(a.c, a.c);
+  for (int t = tid; t < L * ng; t += nt) {
+    const int l = t / ng, g = t - l * ng;
+    const int64_t* ln = a.line_nodes + (e * L + l) * pp;
+    dd xb = dd_make(0.0), yb = xb, xe = xb, ye = xb;
+    for (int q = 0; q < pp; ++q) {
+      const double nx = a.node_xy[2 * ln[q]], ny = a.node_xy[2 * ln[q] + 1];
+      xb = dd_add(xb, dd_mul_d(sm.phi[g * pp + q], nx));
+      yb = dd_add(yb, dd_mul_d(sm.phi[g * pp + q], ny));
+      xe = dd_add(xe, dd_mul_d(sm.dphi[g * pp + q], nx));
+      ye = dd_add(ye, dd_mul_d(sm.dphi[g * pp + q], ny));
+    }
+    const dd rx = dd_sub(xb, dd_make(x0)), ry = dd_sub(yb, dd_make(y0));
+    const dd det = dd_sub(dd_mul(rx, ye), dd_mul(ry, xe));       // det J_b
+    // b1 = (y_b,eta, -x_b,eta)/det, b2 = (-(y_b - y0), x_b - x0)/det
+    const dd b1x = dd_div(ye, det), b1y = dd_div(dd_neg(xe), det);
+    const dd b2x = dd_div(dd_neg(ry), det), b2y = dd_div(rx, det);
+    const dd w = dd{a.tab[2 * g], a.tab[2 * g + 1]};
+    const dd wd = dd_mul(w, det);
+    const dd wdc = dd_mul(wd, c2);
+    dd* K = sm.K + (l * ng + g) * 4;
+    K[0] = dd_mul(wdc, dd_add(dd_mul(b1x, b1x), dd_mul(b1y, b1y)));
+    K[1] = dd_mul(wdc, dd_add(dd_mul(b2x, b1x), dd_mul(b2y, b1y)));
+    K[2] = dd_mul(wdc, dd_add(dd_mul(b2x, b2x), dd_mul(b2y, b2y)));
+    K[3] = wd;
+  }
+  __syncthreads();
+
+  const dd h = a.h;
+  const dd inv_h = dd_div(dd_make(1.0), h);
+  const dd inv_2h = dd_div(dd_make(0.5), h);
+  const dd inv_h2 = dd_mul(inv_h, inv_h);
+  const int64_t matstride = (int64_t)3 * nn;
+  double* mats_e = a.mats + e * (int64_t)n * matstride;
+
+  // radial window: slots of E0/E1 hold i-1, i, i+1; E2/M0 hold i, i+1
+  int s_prev = 0, s_cur = 1, s_next = 2;
+  int w_cur = 0, w_next = 1;
+  coefficient_matrices(a, sm, e, 0, E0w[s_cur], E1w[s_cur], E2w[w_cur], M0w[w_cur]);
+  coefficient_matrices(a, sm, e, 1, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
+
+  for (int i = 0; i <= n; ++i) {
+    const dd xi = dd{a.xi_hi[i], a.xi_lo[i]};
+    const dd x2 = dd_mul(xi, xi);
+    // blocks of row i (Eq. (discretized) with Eq. (FD); dE by one-sided differences at the ends)
+    for (int t = tid; t < nn; t += nt) {
+      const int r = t / nb, cc = t - r * nb, tt = cc * nb + r;
+      const dd E0 = E0w[s_cur][t], E1 = E1w[s_cur][t], E1T = E1w[s_cur][tt];
+      dd dE0, dE1T;
+      if (i == 0) {
+        dE0 = dd_mul(dd_sub(E0w[s_next][t], E0), inv_h);
+        dE1T = dd_mul(dd_sub(E1w[s_next][tt], E1T), inv_h);
+      } else if (i == n) {
+        dE0 = dd_mul(dd_sub(E0, E0w[s_prev][t]), inv_h);
+        dE1T = dd_mul(dd_sub(E1T, E1w[s_prev][tt]), inv_h);
+      } else {
+        dE0 = dd_mul(dd_sub(E0w[s_next][t], E0w[s_prev][t]), inv_2h);
+        dE1T = dd_mul(dd_sub(E1w[s_next][tt], E1w[s_prev][tt]), inv_2h);
+      }
+      const dd D = dd_add(dd_sub(dd_add(E0, E1T), E1), dd_mul(xi, dE0));
+      const dd a2 = dd_mul(dd_mul(x2, E0), inv_h2);
+      const dd a1 = dd_mul(dd_mul(xi, D), inv_2h);
+      th[t] = dd_sub(a2, a1);
+      ps[t] = dd_add(a2, a1);
+      dd f = dd_neg(dd_add(a2, a2));
+      f = dd_sub(f, E2w[w_cur][t]);
+      f = dd_add(f, dd_mul(xi, dE1T));
+      f = dd_sub(f, dd_mul(a.mass, dd_mul(x2, M0w[w_cur][t])));
+      ph[t] = f;
+    }
+    __syncthreads();
+    if (i == 0) {
+      // row -1: theta = -xi_0 E0/(2h), phi = E1^T, psi = xi_0 E0/(2h).  rho_0 = theta_0 theta_{-1}^{-1}
+      for (int t = tid; t < nn; t += nt) T1[t] = dd_mul(dd_neg(dd_mul(xi, E0w[s_cur][t])), inv_2h);
+      __syncthreads();
+      gj_inverse(nb, T1, Gm, sm.col, sm.piv, a.status);
+      mm(nb, th, Gm, Hp);                                   // Hp <- rho_0
+      // phi_0 -= rho_0 phi_{-1}; psi_0 -= rho_0 psi_{-1}
+      for (int t = tid; t < nn; t += nt) {
+        const int r = t / nb, cc = t - r * nb;
+        dd s1 = dd_make(0.0), s2 = dd_make(0.0);
+        for (int k = 0; k < nb; ++k) {
+          const dd rk = Hp[r * nb + k];
+          s1 = dd_fma(s1, rk, E1w[s_cur][cc * nb + k]);               // phi_{-1}[k][c] = E1[c][k]
+          s2 = dd_fma(s2, rk, dd_mul(dd_mul(xi, E0w[s_cur][k * nb + cc]), inv_2h));
+        }
+        T1[t] = s1;
+        Gm[t] = s2;
+      }
+      __syncthreads();
+      for (int t = tid; t < nn; t += nt) {
+        ph[t] = dd_sub(ph[t], T1[t]);
+        ps[t] = dd_sub(ps[t], Gm[t]);
+      }
+      __syncthreads();
+    } else {
+      // Thomas sweep: phi_i -= theta_i phi_{i-1}^{-1} psi_{i-1} = theta_i H_{i-1}
+      mm(nb, th, Hp, T1);
+      for (int t = tid; t < nn; t += nt) ph[t] = dd_sub(ph[t], T1[t]);
+      __syncthreads();
+    }
+    if (i < n) {
+      gj_inverse(nb, ph, Gm, sm.col, sm.piv, a.status);     // G_i, destroys ph
+      double* Pi = mats_e + (int64_t)i * matstride;
+      for (int t = tid; t < nn; t += nt) {
+        const int r = t / nb, cc = t - r * nb;
+        dd sp = dd_make(0.0), sq = dd_make(0.0), sh = dd_make(0.0);
+        for (int k = 0; k < nb; ++k) {
+          const dd gk = Gm[r * nb + k];
+          sp = dd_fma(sp, gk, M0w[w_cur][k * nb + cc]);
+          sq = dd_fma(sq, gk, th[k * nb + cc]);
+          sh = dd_fma(sh, gk, ps[k * nb + cc]);
+        }
+        sp = dd_mul(sp, x2);
+        Pi[t] = sp.hi;
+        Pi[nn + t] = (i == 0) ? 0.0 : sq.hi;
+        Pi[2 * nn + t] = sh.hi;
+        T1[t] = sh;                                         // H_i kept in double-double
+      }
+      __syncthreads();
+      for (int t = tid; t < nn; t += nt) Hp[t] = T1[t];
+      __syncthreads();
+    } else {
+      // i == n: th = theta_n, ph = modified phi_n, ps = psi_n, Hp = H_{n-1}
+      for (int t = tid; t < nn; t += nt) T1[t] = ps[t];
+      __syncthreads();
+      gj_inverse(nb, T1, Gm, sm.col, sm.piv, a.status);     // Gm = psi_n^{-1}
+      // W = psi_{n+1} psi_n^{-1}, psi_{n+1} = xi_n E0_n / (2h)
+      for (int t = tid; t < nn; t += nt) {
+        const int r = t / nb, cc = t - r * nb;
+        dd s = dd_make(0.0);
+        for (int k = 0; k < nb; ++k)
+          s = dd_fma(s, dd_mul(dd_mul(xi, E0w[s_cur][r * nb + k]), inv_2h), Gm[k * nb + cc]);
+        T1[t] = s;
+      }
+      __syncthreads();
+      // phi_{n+1} modified = E1_n^T - theta_{n+1} H_{n-1}, theta_{n+1} = -xi_n E0_n/(2h)
+      for (int t = tid; t < nn; t += nt) {
+        const int r = t / nb, cc = t - r * nb;
+        dd s = E1w[s_cur][cc * nb + r];
+        for (int k = 0; k < nb; ++k)
+          s = dd_add(s, dd_mul(dd_mul(dd_mul(xi, E0w[s_cur][r * nb + k]), inv_2h), Hp[k * nb + cc]));
+        Gm[t] = s;
+      }
+      __syncthreads();
+      double* Se = a.S + e * (int64_t)nn;
+      double* Re = a.rt + e * (int64_t)2 * nn;
+      for (int t = tid; t < nn; t += nt) {
+        const int r = t / nb, cc = t - r * nb;
+        dd s = Gm[t], rr = dd_mul(dd_mul(xi, E0w[s_cur][t]), inv_2h), tt = dd_make(0.0);  // -theta_{n+1} = xi E0/(2h)
+        for (int k = 0; k < nb; ++k) {
+          const dd wk = T1[r * nb + k];
+          s = dd_sub(s, dd_mul(wk, ph[k * nb + cc]));
+          rr = dd_fma(rr, wk, th[k * nb + cc]);
+          tt = dd_fma(tt, wk, M0w[w_cur][k * nb + cc]);
+        }
+        Se[t] = s.hi;
+        Re[t] = rr.hi;
+        Re[nn + t] = dd_mul(tt, x2).hi;
+      }
+      __syncthreads();
+    }
+    // advance the radial window
+    if (i + 1 <= n) {
+      const int old_prev = s_prev;
+      s_prev = s_cur;
+      s_cur = s_next;
+      s_next = old_prev;
+      const int ow = w_cur;
+      w_cur = w_next;
+      w_next = ow;
+      if (i + 2 <= n) coefficient_matrices(a, sm, e, i + 2, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. multifrontal factorisation of the global matrix (FP64)
+// ---------------------------------------------------------------------------
+struct FactorArgs {
+  const TreeNodeDev* nodes;
+  const int32_t* level_nodes;   // tree nodes of this level
+  const int32_t* map0;
+  const int32_t* map1;
+  const double* S;              // [E][nb][nb]
+  int nb;
+  double* F;                    // workspace fronts
+  double* U;                    // workspace update matrices
+  double* factors;
+  int* status;
+};
+
+__global__ void front_assemble_kernel(FactorArgs a) {
+  const TreeNodeDev nd = a.nodes[a.level_nodes[blockIdx.x]];
+  const int f = nd.s + nd.b;
+  double* F = a.F + nd.F_off;
+  const int32_t* m0 = a.map0 + nd.map_off;
+  const int32_t* m1 = a.map1 + nd.map_off;
+  for (int64_t t = threadIdx.x; t < (int64_t)f * f; t += blockDim.x) {
+    const int r = (int)(t / f), c = (int)(t - (int64_t)r * f);
+    double v;
+    if (nd.elem >= 0) {
+      v = a.S[(int64_t)nd.elem * a.nb * a.nb + m0[r] * a.nb + m0[c]];
+    } else {
+      v = 0.0;
+      const TreeNodeDev c0 = a.nodes[nd.child0], c1 = a.nodes[nd.child1];
+      if (m0[r] >= 0 && m0[c] >= 0) v += a.U[c0.U_off + (int64_t)m0[r] * c0.b + m0[c]];
+      if (m1[r] >= 0 && m1[c] >= 0) v += a.U[c1.U_off + (int64_t)m1[r] * c1.b + m1[c]];
+    }
+    F[t] = v;
+  }
+}
+
+// block-wide argmax of |v| over rows k..s-1 of column k (smallest index on ties)
+__device__ int block_pivot(const double* F, int f, int k, int s, double* redv, int* redi) {
+  const int tid = threadIdx.x;
+  double bv = -1.0;
+  int bi = s;
+  for (int r = k + tid; r < s; r += blockDim.x) {
+    const double v = fabs(F[(int64_t)r * f + k]);
+    if (v > bv) { bv = v; bi = r; }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+  }
+  const int w = tid >> 5, lane = tid & 31;
+  if (lane == 0) { redv[w] = bv; redi[w] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 1; j < (int)(blockDim.x >> 5); ++j)
+      if (redv[j] > redv[0] || (redv[j] == redv[0] && redi[j] < redi[0])) { redv[0] = redv[j]; redi[0] = redi[j]; }
+  }
+  __syncthreads();
+  const int r = redi[0];
+  const double v = redv[0];
+  __syncthreads();
+  return (v > 0.0 && isfinite(v)) ? r : -1;
+}
+
+__global__ void front_factor_kernel(FactorArgs a) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ double colbuf[1024];
+  const TreeNodeDev nd = a.nodes[a.level_nodes[blockIdx.x]];
+  const int s = nd.s, b = nd.b, f = s + b;
+  double* F = a.F + nd.F_off;
+  double* X = a.factors + nd.X_off;            // s x s
+  double* G = X + (int64_t)s * s;              // s x b
+  double* C = G + (int64_t)s * b;              // b x s
+  double* U = a.U + nd.U_off;                  // b x b
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (s > 0) {
+    // X = F11^{-1}: Gauss-Jordan on [F11 | I] with row pivoting inside F11
+    for (int64_t t = tid; t < (int64_t)s * s; t += nt) X[t] = ((t / s) == (t % s)) ? 1.0 : 0.0;
+    __syncthreads();
+    for (int k = 0; k < s; ++k) {
+      const int pr = block_pivot(F, f, k, s, redv, redi);
+      if (pr < 0) {
+        if (tid == 0) atomicCAS(a.status, 0, SBFWI_ESINGULAR);
+        return;
+      }
+      if (pr != k) {
+        for (int c = tid; c < s; c += nt) {
+          double t1 = F[(int64_t)k * f + c]; F[(int64_t)k * f + c] = F[(int64_t)pr * f + c]; F[(int64_t)pr * f + c] = t1;
+          double t2 = X[(int64_t)k * s + c]; X[(int64_t)k * s + c] = X[(int64_t)pr * s + c]; X[(int64_t)pr * s + c] = t2;
+        }
+        __syncthreads();
+      }
+      const double pinv = 1.0 / F[(int64_t)k * f + k];
+      // normalise row k (columns 0..s-1 of F11 and of X)
+      for (int c = tid; c < s; c += nt) {
+        F[(int64_t)k * f + c] *= pinv;
+        X[(int64_t)k * s + c] *= pinv;
+      }
+      __syncthreads();
+      // eliminate column k from the other rows, in chunks of the factor column
+      for (int r0 = 0; r0 < s; r0 += 1024) {
+        const int rn = min(1024, s - r0);
+        for (int r = tid; r < rn; r += nt) colbuf[r] = (r0 + r == k) ? 0.0 : F[(int64_t)(r0 + r) * f + k];
+        __syncthreads();
+        for (int64_t t = tid; t < (int64_t)rn * s; t += nt) {
+          const int r = (int)(t / s), c = (int)(t - (int64_t)r * s);
+          const double fr = colbuf[r];
+          if (fr != 0.0) {
+            F[(int64_t)(r0 + r) * f + c] -= fr * F[(int64_t)k * f + c];
+            X[(int64_t)(r0 + r) * s + c] -= fr * X[(int64_t)k * s + c];
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // G = X F12 (s x b), C = F21 X (b x s)
+    for (int64_t t = tid; t < (int64_t)s * b; t += nt) {
+      const int r = (int)(t / b), c = (int)(t - (int64_t)r * b);
+      double acc = 0.0;
+      for (int k = 0; k < s; ++k) acc = fma(X[(int64_t)r * s + k], F[(int64_t)k * f + s + c], acc);
+      G[t] = acc;
+    }
+    for (int64_t t = tid; t < (int64_t)b * s; t += nt) {
+      const int r = (int)(t / s), c = (int)(t - (int64_t)r * s);
+      double acc = 0.0;
+      for (int k = 0; k < s; ++k) acc = fma(F[(int64_t)(s + r) * f + k], X[(int64_t)k * s + c], acc);
+      C[t] = acc;
+    }
+    __syncthreads();
+  }
+  // update matrix U = F22 - C F12 (b x b)
+  for (int64_t t = tid; t < (int64_t)b * b; t += nt) {
+    const int r = (int)(t / b), c = (int)(t - (int64_t)r * b);
+    double acc = F[(int64_t)(s + r) * f + s + c];
+    for (int k = 0; k < s; ++k) acc = fma(-C[(int64_t)r * s + k], F[(int64_t)k * f + s + c], acc);
+    U[t] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+template <class T>
+static int upload(DevBuf& d, const std::vector<T>& h, cudaStream_t st) {
+  SBFWI_CUDA(d.alloc(sizeof(T) * h.size()));
+  if (!h.empty()) SBFWI_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+  return SBFWI_OK;
+}
+
+static int read_status(const DevBuf& st_dev, cudaStream_t st, int* code) {
+  SBFWI_CUDA(cudaMemcpyAsync(code, st_dev.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  return SBFWI_OK;
+}
+
+int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st) {
+  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
+  const int ng = (3 * p + 2) / 2;
+  const int64_t E = m.n_elem, N = m.n_nodes, np = m.n_nodal;
+  md.nb = nb; md.n = n; md.E = E; md.N = N;
+  DevBuf status;
+  SBFWI_CUDA(status.alloc(sizeof(int)));
+  SBFWI_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+
+  // radial grid xi_i = xi0 + i h (xi_n = 1), double-double
+  std::vector<double> xi_hi(n + 1), xi_lo(n + 1);
+  const dd h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
+  for (int i = 0; i <= n; ++i) {
+    dd x = (i == n) ? dd_make(1.0) : dd_add(dd_make(m.xi0), dd_mul_d(h, (double)i));
+    xi_hi[i] = x.hi; xi_lo[i] = x.lo;
+  }
+  // Gauss rule and Lagrange tables
+  std::vector<dd> gx_, gw_;
+  gauss_legendre_dd(ng, gx_, gw_);
+  std::vector<double> tab(2 * (ng + 2 * ng * pp));
+  for (int g = 0; g < ng; ++g) {
+    tab[2 * g] = gw_[g].hi; tab[2 * g + 1] = gw_[g].lo;
+    std::vector<dd> ph(pp), dph(pp);
+    lagrange_dd(p, gx_[g], ph.data(), dph.data());
+    for (int q = 0; q < pp; ++q) {
+      tab[2 * (ng + g * pp + q)] = ph[q].hi; tab[2 * (ng + g * pp + q) + 1] = ph[q].lo;
+      tab[2 * (ng + ng * pp + g * pp + q)] = dph[q].hi; tab[2 * (ng + ng * pp + g * pp + q) + 1] = dph[q].lo;
+    }
+  }
+
+  DevBuf d_xy, d_ctr, d_lines, d_lloc, d_xih, d_xil, d_tab, d_rho_in, d_rho_lo, d_cell, d_clamp;
+  int rc;
+  if ((rc = upload(d_xy, m.node_xy, st))) return rc;
+  if ((rc = upload(d_ctr, m.centre_xy, st))) return rc;
+  if ((rc = upload(d_lines, m.line_nodes, st))) return rc;
+  if ((rc = upload(d_lloc, m.line_local, st))) return rc;
+  if ((rc = upload(md.dofs, m.dofs, st))) return rc;
+  if ((rc = upload(d_xih, xi_hi, st))) return rc;
+  if ((rc = upload(d_xil, xi_lo, st))) return rc;
+  if ((rc = upload(d_tab, tab, st))) return rc;
+
+  // density input
+  const int64_t nrho = (md.rho_kind == SBFWI_RHO_NODAL) ? np : md.gx * md.gy;
+  SBFWI_CUDA(d_rho_in.alloc(sizeof(double) * nrho));
+  SBFWI_CUDA(cudaMemcpyAsync(d_rho_in.p, rho, sizeof(double) * nrho,
+                             mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+
+  // nodal point locations (host, for the grid cells of the bilinear map and its transpose)
+  std::vector<int32_t> cell(np, 0);
+  std::vector<int8_t> clamp(np, 0);
+  if (md.rho_kind == SBFWI_RHO_GRID) {
+    auto locate = [&](int64_t q, long double& x, long double& y) {
+      if (q < m.n_int) {
+        const int64_t e = q / ((int64_t)n * nb), rem = q - e * (int64_t)n * nb;
+        const int i = (int)(rem / nb), j = (int)(rem - (int64_t)i * nb);
+        const int32_t g = m.dofs[e * nb + j];
+        const long double xi = (long double)m.xi0 + (long double)i * ((1.0L - (long double)m.xi0) / n);
+        x = m.centre_xy[2 * e] + xi * ((long double)m.node_xy[2 * g] - m.centre_xy[2 * e]);
+        y = m.centre_xy[2 * e + 1] + xi * ((long double)m.node_xy[2 * g + 1] - m.centre_xy[2 * e + 1]);
+      } else {
+        x = m.node_xy[2 * (q - m.n_int)];
+        y = m.node_xy[2 * (q - m.n_int) + 1];
+      }
+    };
+    for (int64_t q = 0; q < np; ++q) {
+      long double x, y;
+      locate(q, x, y);
+      const long double fx = x * md.gx / md.lx - 0.5L, fy = y * md.gy / md.ly - 0.5L;
+      int64_t ix = (int64_t)std::floor(fx), iy = (int64_t)std::floor(fy);
+      int8_t cl = 0;
+      if (ix < 0) { ix = 0; cl |= 1; }
+      if (ix > md.gx - 2) { ix = md.gx - 2; cl |= 2; }
+      if (iy < 0) { iy = 0; cl |= 4; }
+      if (iy > md.gy - 2) { iy = md.gy - 2; cl |= 8; }
+      cell[q] = (int32_t)(iy * md.gx + ix);
+      clamp[q] = cl;
+    }
+    // CSR of grid cell -> (point, corner), sorted by point: the transpose map used
+    // by the gradient gathers in a fixed order
+    std::vector<int64_t> cnt(md.gx * md.gy + 1, 0);
+    auto corner_cell = [&](int64_t q, int k) {
+      const int64_t ix = cell[q] % md.gx, iy = cell[q] / md.gx;
+      return (iy + (k >> 1)) * md.gx + ix + (k & 1);
+    };
+    for (int64_t q = 0; q < np; ++q)
+      for (int k = 0; k < 4; ++k) cnt[corner_cell(q, k) + 1]++;
+    for (int64_t c = 0; c < md.gx * md.gy; ++c) cnt[c + 1] += cnt[c];
+    std::vector<int64_t> list(cnt.back());
+    std::vector<int64_t> fillp(cnt.begin(), cnt.end() - 1);
+    for (int64_t q = 0; q < np; ++q)
+      for (int k = 0; k < 4; ++k) list[fillp[corner_cell(q, k)]++] = q * 4 + k;
+    if ((rc = upload(md.cell_ptr, cnt, st))) return rc;
+    if ((rc = upload(md.cell_list, list, st))) return rc;
+  }
+  if ((rc = upload(md.cell_of_point, cell, st))) return rc;
+  if ((rc = upload(md.clamp_of_point, clamp, st))) return rc;
+
+  DevBuf rho_hi, rho_lo;
+  SBFWI_CUDA(rho_hi.alloc(sizeof(double) * np));
+  SBFWI_CUDA(rho_lo.alloc(sizeof(double) * np));
+  SBFWI_CUDA(md.pts_hi.alloc(sizeof(double) * 2 * np));
+  SBFWI_CUDA(md.pts_lo.alloc(sizeof(double) * 2 * np));
+  {
+    DensityArgs a;
+    a.n_elem = E; a.n_nodes = N; a.n_int = m.n_int; a.nb = nb; a.n = n;
+    a.node_xy = d_xy.as<double>(); a.centre_xy = d_ctr.as<double>(); a.dofs = md.dofs.as<int32_t>();
+    a.xi_hi = d_xih.as<double>(); a.xi_lo = d_xil.as<double>();
+    a.grid = d_rho_in.as<double>(); a.rho_kind = md.rho_kind; a.gx = md.gx; a.gy = md.gy; a.lx = md.lx; a.ly = md.ly;
+    a.cell_of_point = md.cell_of_point.as<int32_t>(); a.clamp_of_point = md.clamp_of_point.as<int8_t>();
+    a.pts_hi = md.pts_hi.as<double>(); a.pts_lo = md.pts_lo.as<double>();
+    a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>(); a.status = status.as<int>();
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((np + threads - 1) / threads, 152 * 32);
+    density_kernel<<<blocks, threads, 0, st>>>(a);
+    SBFWI_CUDA(cudaGetLastError());
+  }
+  int code = 0;
+  if ((rc = read_status(status, st, &code))) return rc;
+  if (code) return fail(SBFWI_EINVAL, "density must be positive at every nodal point");
+  SBFWI_CUDA(md.rho_nodal.alloc(sizeof(double) * np));
+  SBFWI_CUDA(cudaMemcpyAsync(md.rho_nodal.p, rho_hi.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+
+  // element set-up
+  const int64_t nn = (int64_t)nb * nb;
+  SBFWI_CUDA(md.mats.alloc(sizeof(double) * E * n * 3 * nn));
+  SBFWI_CUDA(md.rt.alloc(sizeof(double) * E * 2 * nn));
+  SBFWI_CUDA(md.S.alloc(sizeof(double) * E * nn));
+  {
+    ElemArgs a;
+    a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
+    a.c = md.c;
+    a.mass = dd_div(dd_make(1.0), dd_mul(dd_make(md.beta), two_prod(md.dt, md.dt)));
+    a.h = h;
+    a.node_xy = d_xy.as<double>(); a.centre_xy = d_ctr.as<double>();
+    a.line_nodes = d_lines.as<int64_t>(); a.line_local = d_lloc.as<int32_t>(); a.dofs = md.dofs.as<int32_t>();
+    a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>();
+    a.xi_hi = d_xih.as<double>(); a.xi_lo = d_xil.as<double>(); a.tab = d_tab.as<double>();
+    a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>(); a.S = md.S.as<double>(); a.status = status.as<int>();
+    const size_t smem = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb + 16 * nn) + 16;
+    SBFWI_CUDA(cudaFuncSetAttribute(element_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int threads = (int)((nn + 31) / 32 * 32);
+    if (threads < 64) threads = 64;
+    element_setup_kernel<<<(unsigned)E, threads, smem, st>>>(a);
+    SBFWI_CUDA(cudaGetLastError());
+  }
+  if ((rc = read_status(status, st, &code))) return rc;
+  if (code) return fail(SBFWI_ESINGULAR, "a pivot block of the radial condensation is singular");
+
+  // global factorisation along the elimination tree
+  const Tree& t = m.tree;
+  if ((rc = upload(md.tree_nodes, t.nodes, st))) return rc;
+  if ((rc = upload(md.sep_nodes, t.sep_nodes, st))) return rc;
+  if ((rc = upload(md.bnd_nodes, t.bnd_nodes, st))) return rc;
+  if ((rc = upload(md.map0, t.map0, st))) return rc;
+  if ((rc = upload(md.map1, t.map1, st))) return rc;
+  SBFWI_CUDA(md.factors.alloc(sizeof(double) * std::max<int64_t>(t.X_total, 1)));
+  {
+    DevBuf F, U, lv;
+    SBFWI_CUDA(F.alloc(sizeof(double) * std::max<int64_t>(t.F_total, 1)));
+    SBFWI_CUDA(U.alloc(sizeof(double) * std::max<int64_t>(t.U_total, 1)));
+    std::vector<int32_t> all;
+    std::vector<int64_t> start;
+    for (int l = 0; l < t.levels; ++l) {
+      start.push_back((int64_t)all.size());
+      all.insert(all.end(), t.nodes_at_level[l].begin(), t.nodes_at_level[l].end());
+    }
+    if ((rc = upload(lv, all, st))) return rc;
+    FactorArgs a;
+    a.nodes = md.tree_nodes.as<TreeNodeDev>(); a.map0 = md.map0.as<int32_t>(); a.map1 = md.map1.as<int32_t>();
+    a.S = md.S.as<double>(); a.nb = nb; a.F = F.as<double>(); a.U = U.as<double>();
+    a.factors = md.factors.as<double>(); a.status = status.as<int>();
+    for (int l = 0; l < t.levels; ++l) {
+      a.level_nodes = lv.as<int32_t>() + start[l];
+      const unsigned cnt = (unsigned)t.nodes_at_level[l].size();
+      front_assemble_kernel<<<cnt, 256, 0, st>>>(a);
+      front_factor_kernel<<<cnt, 512, 0, st>>>(a);
+      SBFWI_CUDA(cudaGetLastError());
+    }
+    if ((rc = read_status(status, st, &code))) return rc;
+    if (code) return fail(SBFWI_ESINGULAR, "the global boundary matrix has a singular separator block");
+  }
+  return SBFWI_OK;
+}
+
+}  // namespace sbfwi

@@ -1,0 +1,682 @@
+// The time loop of the path: forward and time-reversed adjoint solves, the
+// zero-lag cross-correlation kernel, the misfit, and the C-ABI entry points.
+//
+// One Newmark step (Section 3.3; Eq. (Newmark), Eq. (ODE_Newmark)) of every
+// element and shot is split into
+//   A  forward sweep:  q_i = -(P_i v_i + Q_i q_{i-1}),  i = 0..n-1,
+//                      f_hat = R q_{n-1} + T v_n,
+//      with v the Newmark predictor u/(beta dt^2) + u'/(beta dt) + (1/(2 beta) - 1) u''
+//      and q_i = phi_i^{-1} p_i the pivot-normalised right-hand side of the
+//      paper's Thomas sweep (p_i -= varrho_i p_{i-1} with varrho_i = theta_i phi_{i-1}^{-1});
+//   B  global boundary solve of sum_e S_e u_n = sum_e f_hat_e + f along the
+//      elimination tree (forward pass leaves -> root, backward pass root -> leaves),
+//      then the Newmark update of the boundary nodes, receivers and the forward
+//      store / the gradient at the boundary nodes;
+//   C  back-substitution u_i = q_i - H_i u_{i+1} (= phi_i^{-1}(p_i - psi_i u_{i+1})),
+//      i = n-1..0, Newmark update of the interior, forward store / gradient.
+// Kernel E fuses C of step k with A of step k+1 (the back-substitution runs from
+// the boundary inwards, the next forward sweep from the centre outwards), so the
+// interior state is read and written once per step.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace sbfwi {
+
+int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st);
+
+static constexpr int kMaxShots = 16;
+
+// ---------------------------------------------------------------------------
+// kernel E: back-substitution + Newmark (step k) fused with the forward sweep (step k+1)
+// ---------------------------------------------------------------------------
+struct ElemStepArgs {
+  int nb, n, B, epc;
+  int64_t E;
+  double a0, a1, a2, c1, c2, dt;
+  const double* mats;   // [E][n][3][nb][nb] P, Q, H
+  const double* rt;     // [E][2][nb][nb]    R, T
+  const int32_t* dofs;  // [E][nb]
+  double* u; double* ud; double* udd;            // interior state [E][n][nb][B]
+  const double* ub; const double* udb; const double* uddb;  // boundary state [N][B]
+  double* q;            // [E][n][nb][B]
+  double* fhat;         // [E][nb][B]
+  int do_down, do_up;
+  double* store_int;    // forward: velocities of this step, interior part [E][n][nb][B]
+  const double* fwd_int;// adjoint: paired forward velocities, interior part
+  double* grad_int;     // adjoint: accumulators [E][n][nb][B]
+};
+
+__global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
+  extern __shared__ double sh[];
+  const int nb = a.nb, n = a.n, B = a.B;
+  const int per = nb * B;
+  const int tid = threadIdx.x;
+  const int le = tid / per, rem = tid - le * per, r = rem / B, s = rem - r * B;
+  const int64_t e = (int64_t)blockIdx.x * a.epc + le;
+  const bool act = (le < a.epc) && (e < a.E);
+  double* vbuf = sh + (size_t)le * n * per;                 // [n][nb][B] predictors of the new state
+  double* xb = sh + (size_t)a.epc * n * per + (size_t)le * per;   // [nb][B] exchange
+  double* vn = sh + (size_t)a.epc * (n + 1) * per + (size_t)le * per;
+  const int64_t nn = (int64_t)nb * nb;
+  const double* Me = a.mats + (act ? e : 0) * (int64_t)n * 3 * nn;
+  const int64_t base = (act ? e : 0) * (int64_t)n * per;    // interior offset of this element
+
+  if (a.do_down) {
+    if (act) xb[r * B + s] = a.ub[(int64_t)a.dofs[e * nb + r] * B + s];
+    __syncthreads();
+    for (int i = n - 1; i >= 0; --i) {
+      double un = 0.0;
+      if (act) {
+        const int64_t o = base + (int64_t)i * per + r * B + s;
+        const double* H = Me + (int64_t)i * 3 * nn + 2 * nn + (int64_t)r * nb;
+        double acc = a.q[o];
+        for (int c = 0; c < nb; ++c) acc = fma(-H[c], xb[c * B + s], acc);
+        un = acc;
+        const double uo = a.u[o], udo = a.ud[o], uddo = a.udd[o];
+        const double vo = fma(a.a0, uo, fma(a.a1, udo, a.a2 * uddo));
+        const double uddn = fma(a.a0, un, -vo);
+        const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
+        a.u[o] = un; a.ud[o] = udn; a.udd[o] = uddn;
+        if (a.store_int) a.store_int[o] = udn;
+        if (a.grad_int) a.grad_int[o] = fma(a.dt * a.fwd_int[o], udn, a.grad_int[o]);
+        if (a.do_up) vbuf[i * per + r * B + s] = fma(a.a0, un, fma(a.a1, udn, a.a2 * uddn));
+      }
+      __syncthreads();
+      if (act) xb[r * B + s] = un;
+      __syncthreads();
+    }
+  } else if (a.do_up && act) {
+    for (int i = 0; i < n; ++i) {
+      const int64_t o = base + (int64_t)i * per + r * B + s;
+      vbuf[i * per + r * B + s] = fma(a.a0, a.u[o], fma(a.a1, a.ud[o], a.a2 * a.udd[o]));
+    }
+  }
+  if (!a.do_up) return;
+  if (act) {
+    const int64_t g = (int64_t)a.dofs[e * nb + r] * B + s;
+    vn[r * B + s] = fma(a.a0, a.ub[g], fma(a.a1, a.udb[g], a.a2 * a.uddb[g]));
+  }
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {
+    double qv = 0.0;
+    if (act) {
+      const double* P = Me + (int64_t)i * 3 * nn + (int64_t)r * nb;
+      const double* v = vbuf + i * per;
+      double acc = 0.0;
+      for (int c = 0; c < nb; ++c) acc = fma(P[c], v[c * B + s], acc);
+      if (i > 0) {
+        const double* Q = P + nn;
+        for (int c = 0; c < nb; ++c) acc = fma(Q[c], xb[c * B + s], acc);
+      }
+      qv = -acc;
+      a.q[base + (int64_t)i * per + r * B + s] = qv;
+    }
+    __syncthreads();
+    if (act) xb[r * B + s] = qv;
+    __syncthreads();
+  }
+  if (act) {
+    const double* R = a.rt + e * 2 * nn + (int64_t)r * nb;
+    const double* T = R + nn;
+    double acc = 0.0;
+    for (int c = 0; c < nb; ++c) acc = fma(R[c], xb[c * B + s], acc);
+    for (int c = 0; c < nb; ++c) acc = fma(T[c], vn[c * B + s], acc);
+    a.fhat[(e * nb + r) * B + s] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// kernel B: global boundary solve, one launch per tree level and direction
+// ---------------------------------------------------------------------------
+struct SolveArgs {
+  const TreeNodeDev* nodes;
+  const Task* tasks;
+  const int32_t* sep_nodes;
+  const int32_t* bnd_nodes;
+  const int32_t* map0;
+  const int32_t* map1;
+  const double* factors;
+  const double* fhat;    // [E][nb][B]
+  const double* ext;     // [N][B] external sources
+  double* ysep;          // [sep_rows][B]
+  double* ybnd;          // [bnd_rows][B]
+  double* x;             // [N][B] solution
+  int nb, B;
+};
+
+__device__ __forceinline__ double front_value(const SolveArgs& a, const TreeNodeDev& nd, int pos, int s) {
+  const int32_t m0 = a.map0[nd.map_off + pos];
+  if (nd.elem >= 0) return a.fhat[((int64_t)nd.elem * a.nb + m0) * a.B + s];
+  const int32_t m1 = a.map1[nd.map_off + pos];
+  double v = 0.0;
+  if (m0 >= 0) v += a.ybnd[(a.nodes[nd.child0].bnd_off + m0) * a.B + s];
+  if (m1 >= 0) v += a.ybnd[(a.nodes[nd.child1].bnd_off + m1) * a.B + s];
+  return v;
+}
+
+// forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element)
+__global__ void solve_forward_kernel(SolveArgs a) {
+  extern __shared__ double csep[];
+  const Task tk = a.tasks[blockIdx.x];
+  const TreeNodeDev nd = a.nodes[tk.node];
+  const int B = a.B, S = nd.s;
+  for (int t = threadIdx.x; t < S * B; t += blockDim.x) {
+    const int k = t / B, s = t - k * B;
+    const double v = front_value(a, nd, k, s) + a.ext[(int64_t)a.sep_nodes[nd.sep_off + k] * B + s];
+    csep[t] = v;
+    if (tk.r0 == 0) a.ysep[(nd.sep_off + k) * B + s] = v;
+  }
+  __syncthreads();
+  const double* C = a.factors + nd.X_off + (int64_t)S * S + (int64_t)S * nd.b;   // b x s
+  for (int t = threadIdx.x; t < (tk.r1 - tk.r0) * B; t += blockDim.x) {
+    const int r = tk.r0 + t / B, s = t % B;
+    double acc = front_value(a, nd, S + r, s);
+    const double* Cr = C + (int64_t)r * S;
+    for (int k = 0; k < S; ++k) acc = fma(-Cr[k], csep[k * B + s], acc);
+    a.ybnd[(nd.bnd_off + r) * B + s] = acc;
+  }
+}
+
+// backward pass: x_sep = X y_sep - G x_bnd
+__global__ void solve_backward_kernel(SolveArgs a) {
+  extern __shared__ double shb[];
+  const Task tk = a.tasks[blockIdx.x];
+  const TreeNodeDev nd = a.nodes[tk.node];
+  const int B = a.B, S = nd.s, Bn = nd.b;
+  double* ys = shb;
+  double* xbn = shb + (size_t)S * B;
+  for (int t = threadIdx.x; t < S * B; t += blockDim.x) ys[t] = a.ysep[nd.sep_off * B + t];
+  for (int t = threadIdx.x; t < Bn * B; t += blockDim.x) {
+    const int j = t / B, s = t - j * B;
+    xbn[t] = a.x[(int64_t)a.bnd_nodes[nd.bnd_off + j] * B + s];
+  }
+  __syncthreads();
+  const double* X = a.factors + nd.X_off;
+  const double* G = X + (int64_t)S * S;
+  for (int t = threadIdx.x; t < (tk.r1 - tk.r0) * B; t += blockDim.x) {
+    const int r = tk.r0 + t / B, s = t % B;
+    double acc = 0.0;
+    const double* Xr = X + (int64_t)r * S;
+    for (int k = 0; k < S; ++k) acc = fma(Xr[k], ys[k * B + s], acc);
+    const double* Gr = G + (int64_t)r * Bn;
+    for (int j = 0; j < Bn; ++j) acc = fma(-Gr[j], xbn[j * B + s], acc);
+    a.x[(int64_t)a.sep_nodes[nd.sep_off + r] * B + s] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// boundary nodes: Newmark update, receivers, store / gradient
+// ---------------------------------------------------------------------------
+struct BoundaryArgs {
+  int64_t N;
+  int B, R;
+  int64_t K, k;
+  double a0, a1, a2, c1, c2, dt;
+  const double* x;
+  double* ub; double* udb; double* uddb;
+  const int64_t* rec;
+  double* traces;         // [B][R][K]
+  double* store_b;        // forward: velocities of this step at the boundary nodes [N][B]
+  const double* fwd_b;    // adjoint: paired forward velocities [N][B]
+  double* grad_b;         // adjoint accumulators [N][B]
+};
+
+__global__ void boundary_update_kernel(BoundaryArgs a) {
+  const int64_t tot = a.N * a.B;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const double un = a.x[t];
+    const double uo = a.ub[t], udo = a.udb[t], uddo = a.uddb[t];
+    const double vo = fma(a.a0, uo, fma(a.a1, udo, a.a2 * uddo));
+    const double uddn = fma(a.a0, un, -vo);
+    const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
+    a.ub[t] = un; a.udb[t] = udn; a.uddb[t] = uddn;
+    if (a.store_b) a.store_b[t] = udn;
+    if (a.grad_b) a.grad_b[t] = fma(a.dt * a.fwd_b[t], udn, a.grad_b[t]);
+  }
+  if (a.traces) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)a.R * a.B; t += (int64_t)gridDim.x * blockDim.x) {
+      const int s = (int)(t / a.R), r = (int)(t - (int64_t)s * a.R);
+      a.traces[((int64_t)s * a.R + r) * a.K + a.k] = a.x[a.rec[r] * a.B + s];
+    }
+  }
+}
+
+// external sources of one step: forward wavelets at the source nodes, or the
+// time-reversed residuals at the receivers
+__global__ void sources_kernel(double* ext, int B, int nsrc, const int64_t* node, const double* values,
+                               int64_t stride_src, int64_t col, int per_shot) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B * nsrc) return;
+  const int s = t / nsrc, j = t - s * nsrc;
+  // per_shot: one source per shot (node[s]); otherwise nsrc receivers shared by all shots
+  const int64_t g = per_shot ? node[s] : node[j];
+  ext[g * B + s] = values[(per_shot ? (int64_t)s : ((int64_t)s * nsrc + j)) * stride_src + col];
+}
+
+// ---------------------------------------------------------------------------
+// gradient: shots summed, then optionally the transpose of the bilinear map
+// ---------------------------------------------------------------------------
+__global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double* out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < B; ++b) s += acc[q * B + b];
+    out[q] = s;
+  }
+}
+
+__global__ void grid_transpose_kernel(const double* g_nodal, const double* pts, const int32_t* cell_of_point,
+                                      const int8_t* clamp, const int64_t* cell_ptr, const int64_t* cell_list,
+                                      int64_t gx, int64_t gy, double lx, double ly, double* out) {
+  const int64_t ncell = gx * gy;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t l = cell_ptr[c]; l < cell_ptr[c + 1]; ++l) {
+      const int64_t q = cell_list[l] >> 2;
+      const int k = (int)(cell_list[l] & 3);
+      const int32_t base = cell_of_point[q];
+      const int64_t ix = base % gx, iy = base / gx;
+      const int8_t cl = clamp[q];
+      double tx = (cl & 1) ? 0.0 : (cl & 2) ? 1.0 : pts[2 * q] * gx / lx - 0.5 - (double)ix;
+      double ty = (cl & 4) ? 0.0 : (cl & 8) ? 1.0 : pts[2 * q + 1] * gy / ly - 0.5 - (double)iy;
+      const double wx = (k & 1) ? tx : 1.0 - tx;
+      const double wy = (k >> 1) ? ty : 1.0 - ty;
+      acc = fma(wx * wy, g_nodal[q], acc);
+    }
+    out[c] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// misfit (deterministic two-pass reduction)
+// ---------------------------------------------------------------------------
+__global__ void misfit_partial_kernel(const double* tr, const double* ob, int64_t n, double* res, double* partial) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double d = ob[t] - tr[t];
+    if (res) res[t] = d;
+    acc = fma(d, d, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void misfit_final_kernel(const double* partial, int nparts, double half_dt, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < nparts; t += blockDim.x) acc += partial[t];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = half_dt * red[0];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int build_level_tasks(Model& md, int rows_per_task) {
+  const Tree& t = md.mesh->tree;
+  std::vector<Task> fwd, bwd;
+  md.tasks.fwd_start.assign(t.levels + 1, 0);
+  md.tasks.bwd_start.assign(t.levels + 1, 0);
+  for (int l = 0; l < t.levels; ++l) {
+    md.tasks.fwd_start[l] = (int32_t)fwd.size();
+    md.tasks.bwd_start[l] = (int32_t)bwd.size();
+    for (int32_t nd : t.nodes_at_level[l]) {
+      const TreeNodeDev& r = t.nodes[nd];
+      if (r.b == 0) fwd.push_back(Task{nd, 0, 0, 0});
+      for (int32_t r0 = 0; r0 < r.b; r0 += rows_per_task) fwd.push_back(Task{nd, r0, std::min(r.b, r0 + rows_per_task), 0});
+      for (int32_t r0 = 0; r0 < r.s; r0 += rows_per_task) bwd.push_back(Task{nd, r0, std::min(r.s, r0 + rows_per_task), 0});
+    }
+  }
+  md.tasks.fwd_start[t.levels] = (int32_t)fwd.size();
+  md.tasks.bwd_start[t.levels] = (int32_t)bwd.size();
+  SBFWI_CUDA(md.tasks.fwd.alloc(sizeof(Task) * fwd.size()));
+  SBFWI_CUDA(md.tasks.bwd.alloc(sizeof(Task) * std::max<size_t>(bwd.size(), 1)));
+  SBFWI_CUDA(cudaMemcpy(md.tasks.fwd.p, fwd.data(), sizeof(Task) * fwd.size(), cudaMemcpyHostToDevice));
+  if (!bwd.empty()) SBFWI_CUDA(cudaMemcpy(md.tasks.bwd.p, bwd.data(), sizeof(Task) * bwd.size(), cudaMemcpyHostToDevice));
+  md.tasks.rows_per_task = rows_per_task;
+  return SBFWI_OK;
+}
+
+namespace {
+
+struct RunBuffers {
+  DevBuf u, ud, udd, ub, udb, uddb, q, fhat, ext, ysep, ybnd, x;
+  DevBuf values, nodes, grad_int;   // grad accumulators [n_nodal][B] (adjoint)
+  DevBuf traces_owned;              // staging for host traces
+  double* traces = nullptr;         // device traces [B][R][K] (owned above or the caller's)
+};
+
+enum class Mode { Forward, Adjoint };
+
+// K Newmark steps of B shots.  Forward: values = wavelets [B][K] at nodes[0..B-1],
+// receivers nodes[B..B+R-1]; writes traces and (if store) the nodal velocities of
+// every step.  Adjoint: values = residuals [B][R][K] at nodes[0..R-1], injected
+// last sample first; accumulates the correlation with the stored forward
+// velocities into grad [n_nodal][B].
+int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, double* store,
+              const double* fwd_store, cudaStream_t st) {
+  const Mesh& m = *md.mesh;
+  const Tree& t = m.tree;
+  const int nb = md.nb, n = md.n;
+  const int64_t E = md.E, N = md.N, np = m.n_nodal, nint = m.n_int;
+  const int64_t si = nint * B, sb = N * B;
+  SBFWI_CUDA(rb.u.alloc(sizeof(double) * si));
+  SBFWI_CUDA(rb.ud.alloc(sizeof(double) * si));
+  SBFWI_CUDA(rb.udd.alloc(sizeof(double) * si));
+  SBFWI_CUDA(rb.q.alloc(sizeof(double) * si));
+  SBFWI_CUDA(rb.ub.alloc(sizeof(double) * sb));
+  SBFWI_CUDA(rb.udb.alloc(sizeof(double) * sb));
+  SBFWI_CUDA(rb.uddb.alloc(sizeof(double) * sb));
+  SBFWI_CUDA(rb.ext.alloc(sizeof(double) * sb));
+  SBFWI_CUDA(rb.x.alloc(sizeof(double) * sb));
+  SBFWI_CUDA(rb.fhat.alloc(sizeof(double) * E * nb * B));
+  SBFWI_CUDA(rb.ysep.alloc(sizeof(double) * std::max<int64_t>(t.sep_rows, 1) * B));
+  SBFWI_CUDA(rb.ybnd.alloc(sizeof(double) * std::max<int64_t>(t.bnd_rows, 1) * B));
+  for (DevBuf* b : {&rb.u, &rb.ud, &rb.udd, &rb.q, &rb.ub, &rb.udb, &rb.uddb, &rb.ext, &rb.x, &rb.fhat})
+    SBFWI_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
+  if (mode == Mode::Adjoint) {
+    SBFWI_CUDA(rb.grad_int.alloc(sizeof(double) * np * B));
+    SBFWI_CUDA(cudaMemsetAsync(rb.grad_int.p, 0, rb.grad_int.bytes, st));
+  }
+  const int rpt = std::max(1, 256 / B);
+  if (md.tasks.rows_per_task != rpt) {
+    int rc = build_level_tasks(md, rpt);
+    if (rc) return rc;
+  }
+  int smax = 0, bmax = 0;
+  for (const TreeNodeDev& r : t.nodes) { smax = std::max(smax, r.s); bmax = std::max(bmax, r.b); }
+  const size_t fwd_smem = sizeof(double) * (size_t)smax * B;
+  const size_t bwd_smem = sizeof(double) * (size_t)(smax + bmax) * B;
+  if (bwd_smem > 48 * 1024)
+    SBFWI_CUDA(cudaFuncSetAttribute(solve_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem));
+  if (fwd_smem > 48 * 1024)
+    SBFWI_CUDA(cudaFuncSetAttribute(solve_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem));
+
+  ElemStepArgs ea;
+  ea.nb = nb; ea.n = n; ea.B = B; ea.E = E;
+  ea.epc = std::max(1, 128 / (nb * B));
+  ea.a0 = md.a0; ea.a1 = md.a1; ea.a2 = md.a2; ea.c1 = md.c1; ea.c2 = md.c2; ea.dt = md.dt;
+  ea.mats = md.mats.as<double>(); ea.rt = md.rt.as<double>(); ea.dofs = md.dofs.as<int32_t>();
+  ea.u = rb.u.as<double>(); ea.ud = rb.ud.as<double>(); ea.udd = rb.udd.as<double>();
+  ea.ub = rb.ub.as<double>(); ea.udb = rb.udb.as<double>(); ea.uddb = rb.uddb.as<double>();
+  ea.q = rb.q.as<double>(); ea.fhat = rb.fhat.as<double>();
+  const int e_threads = ea.epc * nb * B;
+  const unsigned e_blocks = (unsigned)((E + ea.epc - 1) / ea.epc);
+  const size_t e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
+  if (e_smem > 48 * 1024)
+    SBFWI_CUDA(cudaFuncSetAttribute(element_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem));
+
+  SolveArgs sa;
+  sa.nodes = md.tree_nodes.as<TreeNodeDev>();
+  sa.sep_nodes = md.sep_nodes.as<int32_t>(); sa.bnd_nodes = md.bnd_nodes.as<int32_t>();
+  sa.map0 = md.map0.as<int32_t>(); sa.map1 = md.map1.as<int32_t>(); sa.factors = md.factors.as<double>();
+  sa.fhat = rb.fhat.as<double>(); sa.ext = rb.ext.as<double>();
+  sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
+  sa.nb = nb; sa.B = B;
+  const Task* ftasks = md.tasks.fwd.as<Task>();
+  const Task* btasks = md.tasks.bwd.as<Task>();
+
+  BoundaryArgs ba;
+  ba.N = N; ba.B = B; ba.R = 0;
+  ba.K = K;
+  ba.a0 = md.a0; ba.a1 = md.a1; ba.a2 = md.a2; ba.c1 = md.c1; ba.c2 = md.c2; ba.dt = md.dt;
+  ba.x = rb.x.as<double>(); ba.ub = rb.ub.as<double>(); ba.udb = rb.udb.as<double>(); ba.uddb = rb.uddb.as<double>();
+  ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
+  const unsigned b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
+
+  auto element_launch = [&](int down, int up, int64_t done_step) -> int {
+    // done_step: the step whose back-substitution runs in this launch (if down)
+    ea.do_down = down; ea.do_up = up;
+    ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr;
+    if (down && mode == Mode::Forward && store) ea.store_int = store + done_step * np * B;
+    if (down && mode == Mode::Adjoint) {
+      ea.fwd_int = fwd_store + (K - 1 - done_step) * np * B;
+      ea.grad_int = rb.grad_int.as<double>();
+    }
+    element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
+    return SBFWI_OK;
+  };
+
+  for (int64_t k = 0; k < K; ++k) {
+    if (k > 0) element_launch(1, 1, k - 1);
+    // sources of step k
+    if (mode == Mode::Forward) {
+      sources_kernel<<<(B + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, 1, rb.nodes.as<int64_t>(),
+                                                      rb.values.as<double>(), K, k, 1);
+    } else if (R > 0) {
+      sources_kernel<<<(B * R + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, R, rb.nodes.as<int64_t>(),
+                                                          rb.values.as<double>(), K, K - 1 - k, 0);
+    }
+    for (int l = 0; l < t.levels; ++l) {
+      const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
+      if (cnt == 0) continue;
+      sa.tasks = ftasks + md.tasks.fwd_start[l];
+      solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
+    }
+    for (int l = t.levels - 1; l >= 0; --l) {
+      const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
+      if (cnt == 0) continue;
+      sa.tasks = btasks + md.tasks.bwd_start[l];
+      solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
+    }
+    ba.k = k;
+    if (mode == Mode::Forward) {
+      ba.R = R;
+      ba.rec = rb.nodes.as<int64_t>() + B;
+      ba.traces = R > 0 ? rb.traces : nullptr;
+      ba.store_b = store ? store + k * np * B + nint * B : nullptr;
+    } else {
+      ba.fwd_b = fwd_store + (K - 1 - k) * np * B + nint * B;
+      ba.grad_b = rb.grad_int.as<double>() + nint * B;
+    }
+    boundary_update_kernel<<<b_blocks, 256, 0, st>>>(ba);
+  }
+  element_launch(1, 0, K - 1);
+  SBFWI_CUDA(cudaGetLastError());
+  return SBFWI_OK;
+}
+
+bool have_device() {
+  int count = 0;
+  return cudaGetDeviceCount(&count) == cudaSuccess && count > 0;
+}
+
+}  // namespace
+}  // namespace sbfwi
+
+using namespace sbfwi;
+
+extern "C" {
+
+int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
+                    int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
+                    void* stream) {
+  if (!out) return fail(SBFWI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !rho) return fail(SBFWI_EINVAL, "NULL argument");
+  if (!(c > 0) || !(dt > 0) || !(beta > 0) || !(gamma >= 0)) return fail(SBFWI_EINVAL, "need c > 0, dt > 0, beta > 0, gamma >= 0");
+  if (rho_kind != SBFWI_RHO_GRID && rho_kind != SBFWI_RHO_NODAL) return fail(SBFWI_EINVAL, "unknown rho_kind");
+  if (rho_kind == SBFWI_RHO_GRID && (gx < 2 || gy < 2 || !(lx > 0) || !(ly > 0)))
+    return fail(SBFWI_EINVAL, "grid density needs gx, gy >= 2 and lx, ly > 0");
+  if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  if (!have_device()) return fail(SBFWI_ECUDA, "no CUDA device");
+  auto md = new sbfwi_model();
+  md->mesh = mesh;
+  md->c = c; md->dt = dt; md->beta = beta; md->gamma = gamma;
+  md->a0 = 1.0 / (beta * dt * dt);
+  md->a1 = 1.0 / (beta * dt);
+  md->a2 = 1.0 / (2.0 * beta) - 1.0;
+  md->c1 = dt * (1.0 - gamma);
+  md->c2 = dt * gamma;
+  md->rho_kind = rho_kind; md->gx = gx; md->gy = gy; md->lx = lx; md->ly = ly;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = setup_model(*md, *mesh, rho, mem, st);
+  if (rc == SBFWI_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "set-up kernels");
+  }
+  if (rc != SBFWI_OK) { delete md; return rc; }
+  *out = md;
+  return SBFWI_OK;
+}
+
+void sbfwi_destroy_model(sbfwi_model* m) { delete m; }
+void sbfwi_destroy_fwdstate(sbfwi_fwdstate* s) { delete s; }
+
+int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, const double* src_wavelet, int32_t n_rec,
+                  const int64_t* rec_node, int64_t K, double* traces, sbfwi_fwdstate** keep, int mem, void* stream) {
+  if (keep) *keep = nullptr;
+  if (!md) return fail(SBFWI_EINVAL, "model is NULL");
+  if (n_shots < 1 || n_shots > kMaxShots) return fail(SBFWI_EINVAL, "n_shots must be in 1..16");
+  if (K < 1) return fail(SBFWI_EINVAL, "K must be >= 1");
+  if (n_rec < 0 || (n_rec > 0 && (!rec_node || !traces))) return fail(SBFWI_EINVAL, "receivers need rec_node and traces");
+  if (!src_node || !src_wavelet) return fail(SBFWI_EINVAL, "NULL source arrays");
+  if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  const int64_t N = md->N;
+  for (int s = 0; s < n_shots; ++s)
+    if (src_node[s] < 0 || src_node[s] >= N) return fail(SBFWI_EINVAL, "source node out of range");
+  for (int r = 0; r < n_rec; ++r) {
+    if (rec_node[r] < 0 || rec_node[r] >= N) return fail(SBFWI_EINVAL, "receiver node out of range");
+    for (int r2 = 0; r2 < r; ++r2)
+      if (rec_node[r2] == rec_node[r]) return fail(SBFWI_EINVAL, "receiver nodes must be distinct");
+  }
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int B = n_shots;
+  const int64_t np = md->mesh->n_nodal;
+  RunBuffers rb;
+  SBFWI_CUDA(rb.values.alloc(sizeof(double) * B * K));
+  SBFWI_CUDA(cudaMemcpyAsync(rb.values.p, src_wavelet, sizeof(double) * B * K,
+                             mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  std::vector<int64_t> nodes(src_node, src_node + B);
+  nodes.insert(nodes.end(), rec_node, rec_node + n_rec);
+  SBFWI_CUDA(rb.nodes.alloc(sizeof(int64_t) * nodes.size()));
+  SBFWI_CUDA(cudaMemcpyAsync(rb.nodes.p, nodes.data(), sizeof(int64_t) * nodes.size(), cudaMemcpyHostToDevice, st));
+  const int64_t ntr = (int64_t)B * n_rec * K;
+  if (ntr > 0) {
+    if (mem == SBFWI_MEM_DEVICE) {
+      rb.traces = traces;             // written in place
+    } else {
+      SBFWI_CUDA(rb.traces_owned.alloc(sizeof(double) * ntr));
+      rb.traces = rb.traces_owned.as<double>();
+    }
+  }
+  sbfwi_fwdstate* fs = nullptr;
+  if (keep) {
+    fs = new sbfwi_fwdstate();
+    fs->model = md; fs->B = B; fs->R = n_rec; fs->K = K;
+    fs->rec.assign(rec_node, rec_node + n_rec);
+    cudaError_t e = fs->store.alloc(sizeof(double) * (size_t)K * np * B);
+    if (e != cudaSuccess) {
+      delete fs;
+      cudaGetLastError();
+      return fail(SBFWI_ENOMEM, "not enough device memory to keep the forward velocities (" +
+                                    std::to_string((double)K * np * B * 8 / 1e9) + " GB)");
+    }
+  }
+  int rc = run_steps(*md, Mode::Forward, B, K, n_rec, rb, fs ? fs->store.as<double>() : nullptr, nullptr, st);
+  if (rc == SBFWI_OK && ntr > 0 && mem == SBFWI_MEM_HOST) {
+    cudaError_t e = cudaMemcpyAsync(traces, rb.traces, sizeof(double) * ntr, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "copy traces");
+  }
+  if (rc == SBFWI_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "forward solve");
+  }
+  if (rc != SBFWI_OK) { delete fs; return rc; }
+  if (keep) *keep = fs;
+  return SBFWI_OK;
+}
+
+int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* residual, int mode, double* grad, int mem,
+                           void* stream) {
+  if (!md || !fs || !residual || !grad) return fail(SBFWI_EINVAL, "NULL argument");
+  if (fs->model != md) return fail(SBFWI_ESTATE, "forward state belongs to another model");
+  if (mode == SBFWI_GRAD_EXACT) return fail(SBFWI_EUNSUPPORTED, "the exact discrete adjoint is not in this build");
+  if (mode != SBFWI_GRAD_KERNEL) return fail(SBFWI_EINVAL, "unknown gradient mode");
+  if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int B = fs->B, R = fs->R;
+  const int64_t K = fs->K, np = md->mesh->n_nodal;
+  RunBuffers rb;
+  const int64_t nres = (int64_t)B * R * K;
+  SBFWI_CUDA(rb.values.alloc(sizeof(double) * std::max<int64_t>(nres, 1)));
+  if (nres > 0)
+    SBFWI_CUDA(cudaMemcpyAsync(rb.values.p, residual, sizeof(double) * nres,
+                               mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  SBFWI_CUDA(rb.nodes.alloc(sizeof(int64_t) * std::max<size_t>(fs->rec.size(), 1)));
+  if (R > 0) SBFWI_CUDA(cudaMemcpyAsync(rb.nodes.p, fs->rec.data(), sizeof(int64_t) * R, cudaMemcpyHostToDevice, st));
+  int rc = run_steps(*md, Mode::Adjoint, B, K, R, rb, nullptr, fs->store.as<double>(), st);
+  if (rc) return rc;
+  DevBuf gn, gout;
+  SBFWI_CUDA(gn.alloc(sizeof(double) * np));
+  const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
+  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, gn.as<double>());
+  const int64_t nout = (md->rho_kind == SBFWI_RHO_GRID) ? md->gx * md->gy : np;
+  double* dst = nullptr;
+  if (mem == SBFWI_MEM_DEVICE) dst = grad;
+  else { SBFWI_CUDA(gout.alloc(sizeof(double) * nout)); dst = gout.as<double>(); }
+  if (md->rho_kind == SBFWI_RHO_GRID) {
+    const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
+    grid_transpose_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->pts_hi.as<double>(), md->cell_of_point.as<int32_t>(),
+                                              md->clamp_of_point.as<int8_t>(), md->cell_ptr.as<int64_t>(),
+                                              md->cell_list.as<int64_t>(), md->gx, md->gy, md->lx, md->ly, dst);
+  } else {
+    SBFWI_CUDA(cudaMemcpyAsync(dst, gn.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+  }
+  SBFWI_CUDA(cudaGetLastError());
+  if (mem == SBFWI_MEM_HOST) SBFWI_CUDA(cudaMemcpyAsync(grad, dst, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  return SBFWI_OK;
+}
+
+int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double dt, double* E_out, double* residual_out,
+                 int mem, void* stream) {
+  if (!traces || !observed || !E_out) return fail(SBFWI_EINVAL, "NULL argument");
+  if (n < 0) return fail(SBFWI_EINVAL, "n < 0");
+  if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  if (!have_device()) return fail(SBFWI_ECUDA, "no CUDA device");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevBuf dt_, dob, dres, part, eout;
+  const double* tr = traces;
+  const double* ob = observed;
+  double* res = residual_out;
+  const int64_t nn = std::max<int64_t>(n, 1);
+  if (mem == SBFWI_MEM_HOST) {
+    SBFWI_CUDA(dt_.alloc(sizeof(double) * nn));
+    SBFWI_CUDA(dob.alloc(sizeof(double) * nn));
+    if (n > 0) {
+      SBFWI_CUDA(cudaMemcpyAsync(dt_.p, traces, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+      SBFWI_CUDA(cudaMemcpyAsync(dob.p, observed, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    }
+    tr = dt_.as<double>();
+    ob = dob.as<double>();
+    if (residual_out) { SBFWI_CUDA(dres.alloc(sizeof(double) * nn)); res = dres.as<double>(); }
+  }
+  const int parts = 256;
+  SBFWI_CUDA(part.alloc(sizeof(double) * parts));
+  SBFWI_CUDA(eout.alloc(sizeof(double)));
+  misfit_partial_kernel<<<parts, 256, 0, st>>>(tr, ob, n, res, part.as<double>());
+  misfit_final_kernel<<<1, 256, 0, st>>>(part.as<double>(), parts, 0.5 * dt, eout.as<double>());
+  SBFWI_CUDA(cudaGetLastError());
+  SBFWI_CUDA(cudaMemcpyAsync(E_out, eout.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (mem == SBFWI_MEM_HOST && residual_out && n > 0)
+    SBFWI_CUDA(cudaMemcpyAsync(residual_out, res, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  return SBFWI_OK;
+}
+
+}  // extern "C"

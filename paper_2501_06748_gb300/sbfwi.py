@@ -1,0 +1,231 @@
+"""Python binding of libsbfwi (argument marshalling only).
+
+Every call goes to the C ABI declared in ``include/sbfwi.h``; nothing here
+computes any part of the method.  Floating-point arrays may be numpy arrays (host
+memory, staged by the library) or CUDA torch tensors (device memory, used in
+place on torch's current stream).  If the compiled library is missing the import
+fails loudly: there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsbfwi.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ESINGULAR, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+MEM_HOST, MEM_DEVICE = 0, 1
+RHO_GRID, RHO_NODAL = 0, 1
+GRAD_KERNEL, GRAD_EXACT = 0, 1
+
+_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE",
+          ESINGULAR: "ESINGULAR", EUNSUPPORTED: "EUNSUPPORTED"}
+
+
+class SbfwiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing; build it with paper_2501_06748_gb300.build.build() "
+                          "(the library has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D, VP = ctypes.POINTER, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p
+    pd, pi64 = P(ctypes.c_double), P(ctypes.c_int64)
+    lib.sbfwi_last_error.restype = ctypes.c_char_p
+    lib.sbfwi_version.restype = ctypes.c_int
+    lib.sbfwi_build_mesh.argtypes = [P(VP), pd, I64, pi64, pi64, I64, pd, I64, I32, I32, D]
+    lib.sbfwi_mesh_info.argtypes = [VP, pi64]
+    lib.sbfwi_destroy_mesh.argtypes = [VP]
+    lib.sbfwi_destroy_mesh.restype = None
+    lib.sbfwi_set_model.argtypes = [P(VP), VP, D, VP, ctypes.c_int, I64, I64, D, D, D, D, D, ctypes.c_int, VP]
+    lib.sbfwi_destroy_model.argtypes = [VP]
+    lib.sbfwi_destroy_model.restype = None
+    lib.sbfwi_forward.argtypes = [VP, I32, pi64, VP, I32, pi64, I64, VP, P(VP), ctypes.c_int, VP]
+    lib.sbfwi_misfit.argtypes = [VP, VP, I64, D, pd, VP, ctypes.c_int, VP]
+    lib.sbfwi_adjoint_gradient.argtypes = [VP, VP, VP, ctypes.c_int, VP, ctypes.c_int, VP]
+    lib.sbfwi_destroy_fwdstate.argtypes = [VP]
+    lib.sbfwi_destroy_fwdstate.restype = None
+    for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
+                 "sbfwi_adjoint_gradient"):
+        getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(code):
+    if code != OK:
+        raise SbfwiError(code, _lib.sbfwi_last_error().decode(errors="replace"))
+
+
+def version() -> int:
+    return _lib.sbfwi_version()
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and bool(x.is_cuda)
+
+
+def _stream_of(x):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+
+
+def _f64_host(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i64_host(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+class _Arr:
+    """A float64 array argument: host numpy or device torch tensor."""
+
+    def __init__(self, a, writable=False):
+        if _is_torch_cuda(a):
+            import torch
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+            self.mem, self.ptr, self.obj, self.stream = MEM_DEVICE, ctypes.c_void_p(a.data_ptr()), a, _stream_of(a)
+        else:
+            if writable:
+                if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+                    raise ValueError("host output arrays must be C-contiguous float64 numpy arrays")
+                h = a
+            else:
+                h = _f64_host(a)
+            self.mem, self.ptr, self.obj, self.stream = MEM_HOST, ctypes.c_void_p(h.ctypes.data), h, ctypes.c_void_p(None)
+
+
+def _same_mem(*args):
+    mems = {a.mem for a in args if a is not None}
+    if len(mems) > 1:
+        raise ValueError("mixing host and device arrays in one call is not supported")
+    return mems.pop() if mems else MEM_HOST
+
+
+class Mesh:
+    def __init__(self, node_xy, elem_ptr, line_nodes, centre_xy, p, n_r, xi0=1e-3):
+        xy, ep, ln, ct = _f64_host(node_xy), _i64_host(elem_ptr), _i64_host(line_nodes), _f64_host(centre_xy)
+        h = ctypes.c_void_p()
+        _check(_lib.sbfwi_build_mesh(ctypes.byref(h), _dptr(xy), xy.shape[0], _iptr(ep), _iptr(ln), ln.shape[0],
+                                     _dptr(ct), ct.shape[0], int(p), int(n_r), float(xi0)))
+        self._h = h
+        info = np.zeros(8, dtype=np.int64)
+        _check(_lib.sbfwi_mesh_info(h, _iptr(info)))
+        (self.n_elem, self.n_nodes, self.n_b, self.n_r, self.n_nodal, self.n_int,
+         self.tree_levels, self.factor_entries) = (int(v) for v in info)
+
+    @classmethod
+    def from_inputs(cls, mesh, n_r, xi0=1e-3):
+        """From an ``sbfwi_inputs`` mesh object."""
+        return cls(mesh.node_xy, mesh.elem_ptr, mesh.line_nodes, mesh.centre_xy, mesh.p, n_r, xi0)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.sbfwi_destroy_mesh(h)
+            self._h = None
+
+
+class Model:
+    def __init__(self, mesh: Mesh, c, rho, dt, beta=0.25, gamma=0.5, rho_kind=RHO_GRID, lx=1.0, ly=1.0):
+        r = _Arr(rho)
+        gy, gx = (r.obj.shape if rho_kind == RHO_GRID else (0, 0))
+        h = ctypes.c_void_p()
+        _check(_lib.sbfwi_set_model(ctypes.byref(h), mesh._h, float(c), r.ptr, int(rho_kind), int(gx), int(gy),
+                                    float(lx), float(ly), float(dt), float(beta), float(gamma), r.mem, r.stream))
+        self._h = h
+        self.mesh = mesh                 # keeps the mesh alive for the model's lifetime
+        self.rho_kind, self.gx, self.gy, self.dt = rho_kind, int(gx), int(gy), float(dt)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.sbfwi_destroy_model(h)
+            self._h = None
+
+
+class FwdState:
+    def __init__(self, h, model, n_shots, n_rec, K):
+        self._h, self.model, self.n_shots, self.n_rec, self.K = h, model, n_shots, n_rec, K
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.sbfwi_destroy_fwdstate(h)
+            self._h = None
+
+
+def forward(model: Model, src_nodes, wavelets, rec_nodes, keep=True, traces_out=None):
+    """Forward solve; returns (traces [B][R][K], FwdState or None)."""
+    src = _i64_host(src_nodes)
+    rec = _i64_host(rec_nodes)
+    w = _Arr(wavelets)
+    B = int(src.shape[0])
+    K = int(w.obj.shape[-1])
+    if traces_out is None:
+        if w.mem == MEM_DEVICE:
+            import torch
+            traces_out = torch.empty((B, rec.shape[0], K), dtype=torch.float64, device=w.obj.device)
+        else:
+            traces_out = np.zeros((B, rec.shape[0], K))
+    t = _Arr(traces_out, writable=True)
+    mem = _same_mem(w, t)
+    h = ctypes.c_void_p()
+    _check(_lib.sbfwi_forward(model._h, B, _iptr(src), w.ptr, int(rec.shape[0]), _iptr(rec), K, t.ptr,
+                              ctypes.byref(h) if keep else None, mem, w.stream if mem == MEM_DEVICE else t.stream))
+    st = FwdState(h, model, B, int(rec.shape[0]), K) if keep else None
+    return traces_out, st
+
+
+def misfit(traces, observed, dt, residual_out=None, want_residual=True):
+    """E = 0.5 dt sum (observed - traces)^2 and the residual observed - traces."""
+    t, o = _Arr(traces), _Arr(observed)
+    n = int(np.prod(t.obj.shape))
+    if want_residual and residual_out is None:
+        if t.mem == MEM_DEVICE:
+            import torch
+            residual_out = torch.empty_like(t.obj)
+        else:
+            residual_out = np.zeros(t.obj.shape)
+    r = _Arr(residual_out, writable=True) if residual_out is not None else None
+    mem = _same_mem(t, o, r)
+    E = ctypes.c_double()
+    _check(_lib.sbfwi_misfit(t.ptr, o.ptr, n, float(dt), ctypes.byref(E), r.ptr if r else None, mem,
+                             t.stream if mem == MEM_DEVICE else None))
+    return E.value, residual_out
+
+
+def adjoint_gradient(model: Model, state: FwdState, residual, mode=GRAD_KERNEL, grad_out=None):
+    """Time-reversed adjoint and velocity Frechet kernel; returns the gradient on the
+    model's parameter layout ([gy][gx] grid or [n_nodal])."""
+    r = _Arr(residual)
+    if grad_out is None:
+        shape = (model.gy, model.gx) if model.rho_kind == RHO_GRID else (model.mesh.n_nodal,)
+        if r.mem == MEM_DEVICE:
+            import torch
+            grad_out = torch.zeros(shape, dtype=torch.float64, device=r.obj.device)
+        else:
+            grad_out = np.zeros(shape)
+    g = _Arr(grad_out, writable=True)
+    mem = _same_mem(r, g)
+    _check(_lib.sbfwi_adjoint_gradient(model._h, state._h, r.ptr, int(mode), g.ptr, mem,
+                                       r.stream if mem == MEM_DEVICE else None))
+    return grad_out

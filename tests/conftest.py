@@ -26,5 +26,7 @@ def lib():
     """The CUDA library through its Python binding (GPU tests only)."""
     if not gpu_available():
         pytest.skip("no CUDA device")
+    from paper_2501_06748_gb300 import build
+    build.build()
     from paper_2501_06748_gb300 import sbfwi
     return sbfwi

@@ -1,0 +1,93 @@
+"""Host-side checks of libsbfwi: it builds, loads, exports every declared entry point,
+and validates meshes and builds the elimination tree without a GPU."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from sbfwi_inputs import structured_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi
+    return sbfwi
+
+
+def test_library_exports_every_declared_symbol(binding):
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names |= set(re.findall(r"^\w[\w\s\*]*?\b(sbfwi_\w+)\s*\(", text, flags=re.M))
+    assert {"sbfwi_build_mesh", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
+            "sbfwi_adjoint_gradient"} <= names
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert binding.version() >= 100
+
+
+def test_mesh_info_and_elimination_tree(binding):
+    m = structured_mesh(4, 4, 2)
+    M = binding.Mesh.from_inputs(m, 8)
+    assert (M.n_elem, M.n_nodes, M.n_b, M.n_r) == (16, 65, 8, 8)
+    assert M.n_int == 16 * 7 * 8 and M.n_nodal == M.n_int + 65
+    assert M.tree_levels == 5                          # 16 leaves -> 8 -> 4 -> 2 -> 1
+    big = binding.Mesh.from_inputs(structured_mesh(64, 64, 4), 32)
+    assert big.n_nodes == 29185 and big.tree_levels == 13
+    # the factors of a 2-D nested dissection stay far below a dense matrix
+    assert big.factor_entries < 0.02 * big.n_nodes ** 2
+
+
+def _bad(binding, **kw):
+    m = structured_mesh(2, 2, 2)
+    args = dict(node_xy=m.node_xy.copy(), elem_ptr=m.elem_ptr.copy(), line_nodes=m.line_nodes.copy(),
+                centre_xy=m.centre_xy.copy(), p=2, n_r=5, xi0=1e-3)
+    args.update(kw)
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.Mesh(**args)
+    return ei.value
+
+
+def test_mesh_validation_errors(binding):
+    m = structured_mesh(2, 2, 2)
+    e = _bad(binding, n_r=2)
+    assert e.code == binding.EINVAL
+    lines = m.line_nodes.copy()
+    lines[0] = lines[0][::-1]                              # breaks the closed CCW loop
+    assert _bad(binding, line_nodes=lines).code == binding.EINVAL
+    cw = m.line_nodes.reshape(4, 4, 3)[:, ::-1, ::-1].reshape(-1, 3).copy()   # clockwise loops
+    err = _bad(binding, line_nodes=cw)
+    assert err.code == binding.EINVAL and "det J_b" in str(err)
+    centres = m.centre_xy.copy()
+    centres[1] = (5.0, 5.0)                                # centre outside its element
+    assert "element 1" in str(_bad(binding, centre_xy=centres))
+    xy = m.node_xy.copy()
+    xy[m.line_nodes[0][1]] += (0.0, 0.01)                  # mid-node off the straight line
+    assert _bad(binding, node_xy=xy).code == binding.EINVAL
+    ln = m.line_nodes.copy()
+    ln[3, 1] = 10_000
+    assert _bad(binding, line_nodes=ln).code == binding.EINVAL
+
+
+def test_compute_calls_fail_loudly_without_a_device(binding):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a CUDA device is present")
+    except ImportError:
+        pass
+    M = binding.Mesh.from_inputs(structured_mesh(2, 2, 1), 4)
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.Model(M, 1.0, np.ones((8, 8)), 0.1)
+    assert ei.value.code == binding.ECUDA
+    with pytest.raises(binding.SbfwiError):
+        binding.misfit(np.zeros(3), np.ones(3), 0.1)
