@@ -1,0 +1,336 @@
+"""Throughput of the SBFEM full-waveform-inversion hot path on GB300.
+
+One step = the whole path for one batch: set-up of the model (density map,
+E-matrices, condensation, global factorisation), forward solve of every shot,
+misfit, time-reversed adjoint and Frechet-kernel gradient, on the size workload
+(64x64 square S-elements, p = 4, N_r = 32, 8 Ricker shots, 32 receivers, 2000
+Newmark steps, 256x256 density grid).  The metric counts element-radial-node-steps
+of one shot taken through forward + adjoint + gradient:
+units/step = elements * N_r * time steps * shots.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) shard shots: every rank
+runs its own batch of 8 shots, no data-path collective (weak scaling).
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "S-element radial-node-steps/s fwd+adj+grad at 1e-10 rel err; p50/p99 latency"
+UNIT = "element-radial-node-steps/s"
+FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (vector and tensor), nominal; our DFMA probe measured 1.20 at 2.0 GHz
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+CPU_SAMPLE_NX = 8
+CPU_SAMPLE_K = 12
+
+_CPU_CODE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from sbfwi_inputs import size_workload
+from oracle import fwi
+w = size_workload(nx={nx}, K={K})
+t0 = time.perf_counter()
+om = fwi.build_model(w.mesh, w.n_r, w.c, w.rho_start, w.dt)
+tr, store, _ = fwi.forward(om, w.src_nodes, w.wavelets, w.rec_nodes)
+E, res = fwi.misfit(tr, np.zeros_like(tr), w.dt)
+g = fwi.gradient_to_grid(om, fwi.adjoint_gradient(om, store, res, w.rec_nodes), w.gx, w.gy)
+t1 = time.perf_counter()
+units = w.mesh.n_elem * w.n_r * w.K * w.n_shots
+print(json.dumps({{"seconds": t1 - t0, "units": units}}))
+"""
+
+
+def run_oracle_sample(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
+    """The oracle as it stands, single-threaded, in a fresh process (never forked from CUDA)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = _CPU_CODE.format(root=ROOT, nx=nx, K=K)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    sample = (f"oracle set-up + {K} Newmark steps forward, misfit, adjoint and gradient of 8 shots on a "
+              f"{nx}x{nx} sub-mesh of the same recipe (p=4, N_r=32), float64 time loop, extended-precision set-up")
+    return r["units"] / r["seconds"], r["seconds"], sample
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path, self.proc = path, None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi as lib
+    from sbfwi_inputs import size_workload
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = size_workload(K=args.time_steps, n_shots=args.shots)
+    B, K, R = w.n_shots, w.K, int(w.rec_nodes.shape[0])
+    E, N_r = w.mesh.n_elem, w.n_r
+    units_per_step = E * N_r * K * B
+    M = lib.Mesh.from_inputs(w.mesh, N_r)
+    nb, n = M.n_b, N_r - 1
+
+    rho_start = torch.tensor(w.rho_start, device=dev)
+    rho_true = torch.tensor(w.rho_true, device=dev)
+    wav = torch.tensor(w.wavelets, device=dev)
+    # observed data: the same path on the flawed model (synthetic input, made once, untimed)
+    m_true = lib.Model(M, w.c, rho_true, w.dt)
+    observed, _ = lib.forward(m_true, w.src_nodes, wav, w.rec_nodes, keep=False)
+    del m_true
+    torch.cuda.synchronize()
+
+    observed_host = observed.cpu().numpy()
+    chunk = args.shots_per_pass or B
+    chunks = [slice(s, min(B, s + chunk)) for s in range(0, B, chunk)]
+
+    def step(host=False):
+        """Set-up + forward + misfit + adjoint gradient of all shots; returns (E, grad)."""
+        if host:
+            rho_in, wav_in, obs_in = w.rho_start, w.wavelets, observed_host
+            grad = np.zeros((w.gy, w.gx))
+        else:
+            rho_in, wav_in, obs_in = rho_start, wav, observed
+            grad = torch.zeros((w.gy, w.gx), dtype=torch.float64, device=dev)
+        model = lib.Model(M, w.c, rho_in, w.dt)
+        E_tot = 0.0
+        for c in chunks:
+            tr, st = lib.forward(model, w.src_nodes[c], wav_in[c], w.rec_nodes)
+            Ec, res = lib.misfit(tr, obs_in[c], w.dt)
+            lib.adjoint_gradient(model, st, res, grad_out=grad, accumulate=True)
+            E_tot += Ec
+            del st
+        return E_tot, grad
+
+    # the forward velocity store of one pass must fit in HBM; halve the pass if it does not
+    while True:
+        try:
+            step()
+            break
+        except lib.SbfwiError as err:
+            if err.code != lib.ENOMEM or chunk == 1:
+                raise
+            chunk = (chunk + 1) // 2
+            chunks = [slice(s, min(B, s + chunk)) for s in range(0, B, chunk)]
+    for _ in range(args.warmup - 1):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/sbfwi_clocks_{rank}.csv")
+    lib.profile_read(reset=True)
+    lib.profile_enable(True)
+    stream = torch.cuda.current_stream(dev)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    evs[0].record(stream)
+    for k in range(args.steps):
+        step()
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop(dev.index or 0)
+    if dist:
+        dist.barrier()
+    lib.profile_enable(False)
+    prof = lib.profile_read(reset=True)
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = units_per_step * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if args.e2e_steps > 0:
+        step(host=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            step(host=True)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        ntr = B * R * K * 8
+        gbytes = w.gy * w.gx * 8 * len(chunks)
+        # H2D: density, wavelets, misfit inputs (traces, observed), residual, gradient (accumulated)
+        h2d = w.rho_start.nbytes + w.wavelets.nbytes + 2 * ntr + ntr + gbytes
+        # D2H: traces, residual, misfit values, gradient
+        d2h = ntr + ntr + 8 * len(chunks) + gbytes
+        e2e = {"value": units_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # roofline of the dominant kernel (fused element step), from its own CUDA events
+    el = prof["element"]
+    avg_launch_ms = el["ms"] / max(el["intervals"], 1)
+    Bc = chunks[0].stop - chunks[0].start
+    flops_launch = 2.0 * nb * nb * (3 * n + 1) * E * Bc
+    achieved_tflops = flops_launch / (avg_launch_ms / 1e3) / 1e12
+    bytes_launch = 8.0 * (3 * nb * nb * n + 2 * nb * nb) * E + 8.0 * 9 * E * n * nb * Bc
+    pk, pk_kind = peaks()
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "element_step_kernel", "flops_per_launch": flops_launch,
+                "avg_launch_ms": avg_launch_ms, "launches_timed": el["intervals"],
+                "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe); DFMA probe 1.20 TFLOP/s",
+                "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
+                             "gbs": bytes_launch / (avg_launch_ms / 1e3) / 1e9,
+                             "peak_gbs": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
+    launches = sum(v["launches"] for v in prof.values())
+
+    if rank != 0:
+        return None
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, secs, sample = run_oracle_sample()
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs}
+    lat = np.array(per_step)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"size: {w.mesh.nx}x{w.mesh.ny} square S-elements, p=4 (n_b={nb}), N_r={N_r}, "
+                               f"{B} Ricker shots, {R} receivers, {K} Newmark steps, {w.gx}x{w.gy} density grid; "
+                               "per step: set-up + forward + misfit + adjoint + gradient",
+                   "elements": E, "n_b": nb, "N_r": N_r, "shots": B, "shots_per_pass": Bc, "time_steps": K,
+                   "global_nodes": M.n_nodes, "units_per_step": units_per_step,
+                   "flaw_factor": w.info["flaws"]["factor"],
+                   "l2": "inputs larger than L2 (forward velocity store %.0f GB per pass)" % (K * M.n_nodal * Bc * 8 / 1e9),
+                   "parallelism": f"shots per GPU, {world} GPU(s)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "per_step": [float(x) for x in per_step]},
+        "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle (the only reference this path has) on the host cores, rank 0 only."""
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        run_oracle_sample()
+    rates, secs = [], []
+    sample = None
+    for _ in range(args.steps):
+        r, s, sample = run_oracle_sample()
+        rates.append(r)
+        secs.append(s)
+    value = float(np.sum([r * s for r, s in zip(rates, secs)]) / np.sum(secs))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "size recipe (p=4, N_r=32, 8 shots), bounded sample: " + sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--time-steps", type=int, default=2000, help="Newmark steps of the workload")
+    ap.add_argument("--shots", type=int, default=8)
+    ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

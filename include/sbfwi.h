@@ -56,6 +56,8 @@ enum {
 enum { SBFWI_MEM_HOST = 0, SBFWI_MEM_DEVICE = 1 };
 enum { SBFWI_RHO_GRID = 0, SBFWI_RHO_NODAL = 1 };
 enum { SBFWI_GRAD_KERNEL = 0, SBFWI_GRAD_EXACT = 1 };
+/* or-ed into the mode of sbfwi_adjoint_gradient: add into grad instead of overwriting */
+enum { SBFWI_GRAD_ACCUMULATE = 0x100 };
 
 typedef struct sbfwi_mesh sbfwi_mesh;
 typedef struct sbfwi_model sbfwi_model;
@@ -169,7 +171,9 @@ int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double
  *   fwdstate  from sbfwi_forward(..., keep) on the same model; not consumed.
  *   residual  [n_shots][n_rec][K] (d - u, as from sbfwi_misfit)
  *   mode      SBFWI_GRAD_KERNEL (the paper's kernel).  SBFWI_GRAD_EXACT returns
- *             SBFWI_EUNSUPPORTED in this build.
+ *             SBFWI_EUNSUPPORTED in this build.  With SBFWI_GRAD_ACCUMULATE or-ed
+ *             in, the result is added to grad (gradients of shot batches run one
+ *             after the other).
  *   grad      out: [gy][gx] (model set with SBFWI_RHO_GRID, the transpose of the
  *             bilinear map) or [n_nodal] (SBFWI_RHO_NODAL).
  *   mem       where residual and grad live.
@@ -177,6 +181,20 @@ int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double
 int sbfwi_adjoint_gradient(sbfwi_model* model, sbfwi_fwdstate* fwdstate, const double* residual,
                            int mode, double* grad, int mem, void* stream);
 void sbfwi_destroy_fwdstate(sbfwi_fwdstate* state);
+
+/*
+ * Tracing of the library's kernels (process-wide, not thread-safe).
+ * sbfwi_profile_enable(1) makes every later call record CUDA event pairs on its
+ * stream around each phase: 0 = set-up kernels (one interval per
+ * sbfwi_set_model), 1 = the fused element step kernel (one interval per launch),
+ * 2 = the global boundary solve (one interval per time step: all tree levels,
+ * both passes), 3 = everything else (boundary update, sources, misfit,
+ * gradient reduction).  Launch counts are kept whether or not timing is on.
+ * sbfwi_profile_read fills ms[4] (device milliseconds), intervals[4] and
+ * launches[4] (all nullable) and, if reset != 0, clears the counters.
+ */
+int sbfwi_profile_enable(int on);
+int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int reset);
 
 #ifdef __cplusplus
 }

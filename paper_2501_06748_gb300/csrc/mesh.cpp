@@ -20,6 +20,7 @@
 #include <string>
 
 #include "internal.h"
+#include "prof.h"
 
 namespace sbfwi {
 
@@ -185,7 +186,30 @@ int build_tree(Mesh& m) {
 
 using namespace sbfwi;
 
+namespace sbfwi {
+Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+}  // namespace sbfwi
+
 extern "C" {
+
+int sbfwi_profile_enable(int on) {
+  profiler().on = (on != 0);
+  return SBFWI_OK;
+}
+
+int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int reset) {
+  Profiler& p = profiler();
+  for (int k = 0; k < kPhases; ++k) {
+    if (ms) ms[k] = p.ms[k];
+    if (intervals) intervals[k] = p.intervals[k];
+    if (launches) launches[k] = p.launches[k];
+    if (reset) { p.ms[k] = 0; p.intervals[k] = 0; p.launches[k] = 0; }
+  }
+  return SBFWI_OK;
+}
 
 const char* sbfwi_last_error(void) { return g_last_error.c_str(); }
 int sbfwi_version(void) { return 100; }

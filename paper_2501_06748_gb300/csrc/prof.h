@@ -1,0 +1,61 @@
+// Tracing of the library's own kernels: launch counts per phase, and (when
+// enabled) device time per phase from CUDA event pairs recorded on the
+// launching stream around each phase.
+#pragma once
+
+#include <cstdint>
+#include <utility>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace sbfwi {
+
+enum Phase { kPhaseSetup = 0, kPhaseElement = 1, kPhaseSolve = 2, kPhaseOther = 3, kPhases = 4 };
+
+struct Profiler {
+  bool on = false;
+  int64_t launches[kPhases] = {0, 0, 0, 0};
+  double ms[kPhases] = {0, 0, 0, 0};
+  int64_t intervals[kPhases] = {0, 0, 0, 0};
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  cudaEvent_t open_start[kPhases] = {nullptr, nullptr, nullptr, nullptr};
+
+  cudaEvent_t take() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(int ph, cudaStream_t st) {
+    if (!on) return;
+    open_start[ph] = take();
+    cudaEventRecord(open_start[ph], st);
+  }
+  void end(int ph, cudaStream_t st) {
+    if (!on || !open_start[ph]) return;
+    cudaEvent_t e = take();
+    cudaEventRecord(e, st);
+    pending.push_back({ph, {open_start[ph], e}});
+    open_start[ph] = nullptr;
+  }
+  // after the stream has been synchronised
+  void resolve() {
+    for (auto& p : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, p.second.first, p.second.second) == cudaSuccess) {
+        ms[p.first] += t;
+        intervals[p.first] += 1;
+      }
+      pool.push_back(p.second.first);
+      pool.push_back(p.second.second);
+    }
+    pending.clear();
+  }
+  void count(int ph, int64_t n = 1) { launches[ph] += n; }
+};
+
+Profiler& profiler();
+
+}  // namespace sbfwi

@@ -18,6 +18,7 @@
 
 #include "dd.cuh"
 #include "internal.h"
+#include "prof.h"
 
 namespace sbfwi {
 
@@ -710,6 +711,8 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   DevBuf status;
   SBFWI_CUDA(status.alloc(sizeof(int)));
   SBFWI_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+  Profiler& prof = profiler();
+  prof.begin(kPhaseSetup, st);
 
   // radial grid xi_i = xi0 + i h (xi_n = 1), double-double
   std::vector<double> xi_hi(n + 1), xi_lo(n + 1);
@@ -816,6 +819,7 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((np + threads - 1) / threads, 152 * 32);
     density_kernel<<<blocks, threads, 0, st>>>(a);
+    prof.count(kPhaseSetup);
     SBFWI_CUDA(cudaGetLastError());
   }
   int code = 0;
@@ -845,6 +849,7 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     int threads = (int)((nn + 31) / 32 * 32);
     if (threads < 64) threads = 64;
     element_setup_kernel<<<(unsigned)E, threads, smem, st>>>(a);
+    prof.count(kPhaseSetup);
     SBFWI_CUDA(cudaGetLastError());
   }
   if ((rc = read_status(status, st, &code))) return rc;
@@ -878,8 +883,10 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
       const unsigned cnt = (unsigned)t.nodes_at_level[l].size();
       front_assemble_kernel<<<cnt, 256, 0, st>>>(a);
       front_factor_kernel<<<cnt, 512, 0, st>>>(a);
+      prof.count(kPhaseSetup, 2);
       SBFWI_CUDA(cudaGetLastError());
     }
+    prof.end(kPhaseSetup, st);
     if ((rc = read_status(status, st, &code))) return rc;
     if (code) return fail(SBFWI_ESINGULAR, "the global boundary matrix has a singular separator block");
   }

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "prof.h"
 
 namespace sbfwi {
 
@@ -260,17 +261,17 @@ __global__ void sources_kernel(double* ext, int B, int nsrc, const int64_t* node
 // ---------------------------------------------------------------------------
 // gradient: shots summed, then optionally the transpose of the bilinear map
 // ---------------------------------------------------------------------------
-__global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double* out) {
+__global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double* out, int accumulate) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < B; ++b) s += acc[q * B + b];
-    out[q] = s;
+    out[q] = accumulate ? out[q] + s : s;
   }
 }
 
 __global__ void grid_transpose_kernel(const double* g_nodal, const double* pts, const int32_t* cell_of_point,
                                       const int8_t* clamp, const int64_t* cell_ptr, const int64_t* cell_list,
-                                      int64_t gx, int64_t gy, double lx, double ly, double* out) {
+                                      int64_t gx, int64_t gy, double lx, double ly, double* out, int accumulate) {
   const int64_t ncell = gx * gy;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
     double acc = 0.0;
@@ -286,7 +287,7 @@ __global__ void grid_transpose_kernel(const double* g_nodal, const double* pts, 
       const double wy = (k >> 1) ? ty : 1.0 - ty;
       acc = fma(wx * wy, g_nodal[q], acc);
     }
-    out[c] = acc;
+    out[c] = accumulate ? out[c] + acc : acc;
   }
 }
 
@@ -438,6 +439,7 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
   const unsigned b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
 
+  Profiler& prof = profiler();
   auto element_launch = [&](int down, int up, int64_t done_step) -> int {
     // done_step: the step whose back-substitution runs in this launch (if down)
     ea.do_down = down; ea.do_up = up;
@@ -447,7 +449,10 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
       ea.fwd_int = fwd_store + (K - 1 - done_step) * np * B;
       ea.grad_int = rb.grad_int.as<double>();
     }
+    prof.begin(kPhaseElement, st);
     element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
+    prof.end(kPhaseElement, st);
+    prof.count(kPhaseElement);
     return SBFWI_OK;
   };
 
@@ -457,22 +462,28 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
     if (mode == Mode::Forward) {
       sources_kernel<<<(B + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, 1, rb.nodes.as<int64_t>(),
                                                       rb.values.as<double>(), K, k, 1);
+      prof.count(kPhaseOther);
     } else if (R > 0) {
       sources_kernel<<<(B * R + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, R, rb.nodes.as<int64_t>(),
                                                           rb.values.as<double>(), K, K - 1 - k, 0);
+      prof.count(kPhaseOther);
     }
+    prof.begin(kPhaseSolve, st);
     for (int l = 0; l < t.levels; ++l) {
       const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
       if (cnt == 0) continue;
       sa.tasks = ftasks + md.tasks.fwd_start[l];
       solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
+      prof.count(kPhaseSolve);
     }
     for (int l = t.levels - 1; l >= 0; --l) {
       const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
       if (cnt == 0) continue;
       sa.tasks = btasks + md.tasks.bwd_start[l];
       solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
+      prof.count(kPhaseSolve);
     }
+    prof.end(kPhaseSolve, st);
     ba.k = k;
     if (mode == Mode::Forward) {
       ba.R = R;
@@ -484,6 +495,7 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
       ba.grad_b = rb.grad_int.as<double>() + nint * B;
     }
     boundary_update_kernel<<<b_blocks, 256, 0, st>>>(ba);
+    prof.count(kPhaseOther);
   }
   element_launch(1, 0, K - 1);
   SBFWI_CUDA(cudaGetLastError());
@@ -529,6 +541,7 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "set-up kernels");
   }
+  profiler().resolve();
   if (rc != SBFWI_OK) { delete md; return rc; }
   *out = md;
   return SBFWI_OK;
@@ -596,6 +609,7 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "forward solve");
   }
+  profiler().resolve();
   if (rc != SBFWI_OK) { delete fs; return rc; }
   if (keep) *keep = fs;
   return SBFWI_OK;
@@ -605,6 +619,8 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
                            void* stream) {
   if (!md || !fs || !residual || !grad) return fail(SBFWI_EINVAL, "NULL argument");
   if (fs->model != md) return fail(SBFWI_ESTATE, "forward state belongs to another model");
+  const bool accumulate = (mode & SBFWI_GRAD_ACCUMULATE) != 0;
+  mode &= ~SBFWI_GRAD_ACCUMULATE;
   if (mode == SBFWI_GRAD_EXACT) return fail(SBFWI_EUNSUPPORTED, "the exact discrete adjoint is not in this build");
   if (mode != SBFWI_GRAD_KERNEL) return fail(SBFWI_EINVAL, "unknown gradient mode");
   if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
@@ -622,24 +638,33 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   int rc = run_steps(*md, Mode::Adjoint, B, K, R, rb, nullptr, fs->store.as<double>(), st);
   if (rc) return rc;
   DevBuf gn, gout;
-  SBFWI_CUDA(gn.alloc(sizeof(double) * np));
-  const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
-  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, gn.as<double>());
   const int64_t nout = (md->rho_kind == SBFWI_RHO_GRID) ? md->gx * md->gy : np;
   double* dst = nullptr;
   if (mem == SBFWI_MEM_DEVICE) dst = grad;
-  else { SBFWI_CUDA(gout.alloc(sizeof(double) * nout)); dst = gout.as<double>(); }
-  if (md->rho_kind == SBFWI_RHO_GRID) {
+  else {
+    SBFWI_CUDA(gout.alloc(sizeof(double) * nout));
+    dst = gout.as<double>();
+    if (accumulate) SBFWI_CUDA(cudaMemcpyAsync(dst, grad, sizeof(double) * nout, cudaMemcpyHostToDevice, st));
+  }
+  SBFWI_CUDA(gn.alloc(sizeof(double) * np));
+  const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
+  const bool grid = md->rho_kind == SBFWI_RHO_GRID;
+  // nodal output: shots summed straight into the output (accumulating if asked)
+  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, grid ? gn.as<double>() : dst,
+                                           (!grid && accumulate) ? 1 : 0);
+  profiler().count(kPhaseOther);
+  if (grid) {
     const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
     grid_transpose_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->pts_hi.as<double>(), md->cell_of_point.as<int32_t>(),
                                               md->clamp_of_point.as<int8_t>(), md->cell_ptr.as<int64_t>(),
-                                              md->cell_list.as<int64_t>(), md->gx, md->gy, md->lx, md->ly, dst);
-  } else {
-    SBFWI_CUDA(cudaMemcpyAsync(dst, gn.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+                                              md->cell_list.as<int64_t>(), md->gx, md->gy, md->lx, md->ly, dst,
+                                              accumulate ? 1 : 0);
+    profiler().count(kPhaseOther);
   }
   SBFWI_CUDA(cudaGetLastError());
   if (mem == SBFWI_MEM_HOST) SBFWI_CUDA(cudaMemcpyAsync(grad, dst, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
   SBFWI_CUDA(cudaStreamSynchronize(st));
+  profiler().resolve();
   return SBFWI_OK;
 }
 
@@ -671,6 +696,7 @@ int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double
   SBFWI_CUDA(eout.alloc(sizeof(double)));
   misfit_partial_kernel<<<parts, 256, 0, st>>>(tr, ob, n, res, part.as<double>());
   misfit_final_kernel<<<1, 256, 0, st>>>(part.as<double>(), parts, 0.5 * dt, eout.as<double>());
+  profiler().count(kPhaseOther, 2);
   SBFWI_CUDA(cudaGetLastError());
   SBFWI_CUDA(cudaMemcpyAsync(E_out, eout.p, sizeof(double), cudaMemcpyDeviceToHost, st));
   if (mem == SBFWI_MEM_HOST && residual_out && n > 0)

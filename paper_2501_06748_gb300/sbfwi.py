@@ -19,6 +19,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ESINGULAR, EUNSUPPORTED = 0, -1, -2
 MEM_HOST, MEM_DEVICE = 0, 1
 RHO_GRID, RHO_NODAL = 0, 1
 GRAD_KERNEL, GRAD_EXACT = 0, 1
+GRAD_ACCUMULATE = 0x100
+PHASES = ("setup", "element", "solve", "other")
 
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE",
           ESINGULAR: "ESINGULAR", EUNSUPPORTED: "EUNSUPPORTED"}
@@ -51,8 +53,10 @@ def _load():
     lib.sbfwi_adjoint_gradient.argtypes = [VP, VP, VP, ctypes.c_int, VP, ctypes.c_int, VP]
     lib.sbfwi_destroy_fwdstate.argtypes = [VP]
     lib.sbfwi_destroy_fwdstate.restype = None
+    lib.sbfwi_profile_enable.argtypes = [ctypes.c_int]
+    lib.sbfwi_profile_read.argtypes = [pd, pi64, pi64, ctypes.c_int]
     for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
-                 "sbfwi_adjoint_gradient"):
+                 "sbfwi_adjoint_gradient", "sbfwi_profile_enable", "sbfwi_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -67,6 +71,20 @@ def _check(code):
 
 def version() -> int:
     return _lib.sbfwi_version()
+
+
+def profile_enable(on: bool = True) -> None:
+    """Record CUDA-event timings of the library's kernel phases on their streams."""
+    _check(_lib.sbfwi_profile_enable(1 if on else 0))
+
+
+def profile_read(reset: bool = False) -> dict:
+    """Per phase (setup, element, solve, other): device ms, timed intervals, kernel launches."""
+    ms = np.zeros(4)
+    iv = np.zeros(4, dtype=np.int64)
+    la = np.zeros(4, dtype=np.int64)
+    _check(_lib.sbfwi_profile_read(_dptr(ms), _iptr(iv), _iptr(la), 1 if reset else 0))
+    return {ph: {"ms": float(ms[k]), "intervals": int(iv[k]), "launches": int(la[k])} for k, ph in enumerate(PHASES)}
 
 
 def _is_torch_cuda(x) -> bool:
@@ -213,9 +231,14 @@ def misfit(traces, observed, dt, residual_out=None, want_residual=True):
     return E.value, residual_out
 
 
-def adjoint_gradient(model: Model, state: FwdState, residual, mode=GRAD_KERNEL, grad_out=None):
+def adjoint_gradient(model: Model, state: FwdState, residual, mode=GRAD_KERNEL, grad_out=None, accumulate=False):
     """Time-reversed adjoint and velocity Frechet kernel; returns the gradient on the
-    model's parameter layout ([gy][gx] grid or [n_nodal])."""
+    model's parameter layout ([gy][gx] grid or [n_nodal]).  ``accumulate`` adds into
+    ``grad_out``."""
+    if accumulate:
+        if grad_out is None:
+            raise ValueError("accumulate needs grad_out")
+        mode = int(mode) | GRAD_ACCUMULATE
     r = _Arr(residual)
     if grad_out is None:
         shape = (model.gy, model.gx) if model.rho_kind == RHO_GRID else (model.mesh.n_nodal,)
