@@ -146,3 +146,27 @@ def test_errors_are_reported(lib, tiny):
     with pytest.raises(lib.SbfwiError) as ei:
         lib.adjoint_gradient(md, st, tr, mode=lib.GRAD_EXACT)
     assert ei.value.code == lib.EUNSUPPORTED
+
+
+@pytest.mark.slow
+def test_full_size_workload_few_steps(lib):
+    """The bench's workload and launch configuration (64x64 elements, p = 4, N_r = 32,
+    8 shots in one pass) for 8 Newmark steps: traces on the flawed model and the
+    gradient on the starting model, element by element against the oracle."""
+    w = size_workload(K=8)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_true, w.dt)
+    tr, _ = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes, keep=False)
+    om = fwi.build_model(w.mesh, w.n_r, w.c, w.rho_true, w.dt)
+    to, _, _ = fwi.forward(om, w.src_nodes, w.wavelets, w.rec_nodes, keep=False)
+    assert np.abs(to).max() > 0
+    assert rel(tr, to) <= TRACE_TOL
+    m0 = lib.Model(M, w.c, w.rho_start, w.dt)
+    t0, st = lib.forward(m0, w.src_nodes, w.wavelets, w.rec_nodes)
+    o0 = fwi.build_model(w.mesh, w.n_r, w.c, w.rho_start, w.dt)
+    to0, store, _ = fwi.forward(o0, w.src_nodes, w.wavelets, w.rec_nodes)
+    assert rel(t0, to0) <= TRACE_TOL
+    res = to - to0                          # residual: flawed minus starting model (oracle traces)
+    g = lib.adjoint_gradient(m0, st, res)
+    go = fwi.gradient_to_grid(o0, fwi.adjoint_gradient(o0, store, res, w.rec_nodes), w.gx, w.gy)
+    assert rel(g, go) <= GRAD_TOL
