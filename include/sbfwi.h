@@ -161,6 +161,33 @@ int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double
                  double* E_out, double* residual_out, int mem, void* stream);
 
 /*
+ * sbfwi_misfit_noalloc -- the same misfit as sbfwi_misfit, for callers that cannot
+ * let the library allocate device memory.  The paper has no counterpart; this is
+ * a service of the library.  Typical callers: a framework that has already
+ * reserved nearly all device memory in its own pool, a real-time loop that must
+ * not enter the driver's allocator (cudaMalloc/cudaFree can block and
+ * synchronise), or a process held to a fixed memory budget.
+ *
+ *   traces, observed [n], residual_out [n] (nullable), E_out [1]: all DEVICE
+ *   pointers (SBFWI_EINVAL otherwise).  n <= 268435456 (4096 blocks of 65536
+ *   samples); larger n is rejected with SBFWI_EINVAL before any work is queued.
+ *
+ * The per-block partial sums go to a fixed 32 KiB array compiled into the
+ * library (held by every device that loads it until the process exits) instead
+ * of a buffer allocated per call.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  The first call on a device looks up that array's
+ * device address (once per device, with that device current); make that first
+ * call before capturing a stream into a CUDA graph.  The work is only enqueued
+ * on `stream`: E_out and residual_out are valid once the stream reaches it.
+ * All calls share the array, so calls that may run at the same time on the GPU
+ * (different streams without ordering between them) race and can return wrong
+ * values; order them on one stream.  Every call overwrites the partial sums it
+ * uses, so nothing from an earlier call leaks into a later one.
+ */
+int sbfwi_misfit_noalloc(const double* traces, const double* observed, int64_t n, double dt,
+                         double* E_out, double* residual_out, void* stream);
+
+/*
  * sbfwi_adjoint_gradient -- time-reversed adjoint solve and zero-lag
  * cross-correlation (Section 2: adjoint equation and Frechet kernel; Section 4:
  * the c^2 grad(lambda).grad(u) term is dropped and the nodal fields are used

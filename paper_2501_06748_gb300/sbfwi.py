@@ -53,6 +53,8 @@ def _load():
     lib.sbfwi_adjoint_gradient.argtypes = [VP, VP, VP, ctypes.c_int, VP, ctypes.c_int, VP]
     lib.sbfwi_destroy_fwdstate.argtypes = [VP]
     lib.sbfwi_destroy_fwdstate.restype = None
+    lib.sbfwi_misfit_noalloc.argtypes = [VP, VP, I64, D, VP, VP, VP]
+    lib.sbfwi_misfit_noalloc.restype = ctypes.c_int
     lib.sbfwi_profile_enable.argtypes = [ctypes.c_int]
     lib.sbfwi_profile_read.argtypes = [pd, pi64, pi64, ctypes.c_int]
     for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
@@ -252,3 +254,22 @@ def adjoint_gradient(model: Model, state: FwdState, residual, mode=GRAD_KERNEL, 
     _check(_lib.sbfwi_adjoint_gradient(model._h, state._h, r.ptr, int(mode), g.ptr, mem,
                                        r.stream if mem == MEM_DEVICE else None))
     return grad_out
+
+
+def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
+    """Misfit for callers that cannot let the library allocate device memory.
+
+    All arguments are CUDA float64 tensors (E_out has one element); the call only
+    enqueues work on torch's current stream and keeps its partial sums in a fixed
+    array inside the library.  Calls that may overlap on the GPU must be ordered
+    on one stream (they share that array).
+    """
+    arrs = [_Arr(traces), _Arr(observed), _Arr(E_out, writable=True)]
+    if residual_out is not None:
+        arrs.append(_Arr(residual_out, writable=True))
+    if any(a.mem != MEM_DEVICE for a in arrs):
+        raise ValueError("misfit_noalloc takes CUDA tensors only")
+    n = int(np.prod(arrs[0].obj.shape))
+    _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
+                                     arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
+    return E_out, residual_out
