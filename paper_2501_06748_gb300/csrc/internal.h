@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -68,7 +69,7 @@ struct TreeNodeDev {
 struct Task {               // a row range of one tree node
   int32_t node;
   int32_t r0, r1;
-  int32_t pad;
+  int32_t ksplit;           // lanes that share one output's dot product (1, 2, 4 or 8)
 };
 
 struct Tree {
@@ -86,6 +87,22 @@ struct Tree {
 // ---------------------------------------------------------------------------
 // mesh
 // ---------------------------------------------------------------------------
+// Device copies of everything that depends on the mesh only (not on the density
+// model), made by the first sbfwi_set_model on a mesh and reused by later ones.
+struct MeshDevice {
+  int device = -1;
+  DevBuf xy, ctr, lines, lloc, dofs, xih, xil, tab;
+  DevBuf tree_nodes, sep_nodes, bnd_nodes, map0, map1, level_nodes;
+  std::vector<int64_t> level_start;
+  DevBuf F, U;                       // factorisation workspaces
+  // bilinear map of one fine grid: base cell and clamping of every nodal point, and
+  // the transpose as CSR grid cell -> (point*4 + corner) sorted by point
+  bool grid_ready = false;
+  int64_t gx = 0, gy = 0;
+  double lx = 0, ly = 0;
+  DevBuf cell, clamp, cell_ptr, cell_list;
+};
+
 struct Mesh {
   int64_t n_elem = 0, n_nodes = 0, n_lines = 0;
   int p = 0, n_r = 0, nb = 0, n = 0, L = 0;   // n = N_r - 1 intervals, L lines per element
@@ -96,6 +113,7 @@ struct Mesh {
   std::vector<int32_t> line_local;  // [n_elem][L][p+1] local dof of each line position
   Tree tree;
   int64_t n_int = 0, n_nodal = 0;
+  mutable std::unique_ptr<MeshDevice> dev;   // set-up cache (set_model calls on one mesh must not overlap)
 };
 
 int build_tree(Mesh& m);
@@ -106,7 +124,9 @@ int build_tree(Mesh& m);
 struct LevelTasks {
   std::vector<int32_t> fwd_start, bwd_start;   // per level: first task index (levels+1 entries)
   DevBuf fwd, bwd;                              // Task arrays
-  int rows_per_task = 0;
+  DevBuf fwd_start_dev, bwd_start_dev;          // the index arrays on the device
+  int shots = 0;                                // tasks were built for this many shots
+  int max_level_tasks = 0;
 };
 
 struct Model {
@@ -121,20 +141,15 @@ struct Model {
   // element operators, FP64: per element and radial point i = 0..n-1: P_i, Q_i, H_i; then R, T
   DevBuf mats;      // [E][n][3][nb][nb]
   DevBuf rt;        // [E][2][nb][nb]
-  DevBuf S;         // [E][nb][nb]  dynamic stiffness (kept for tests/inspection)
-  DevBuf dofs;      // [E][nb] int32
+  DevBuf S;         // [E][nb][nb]  dynamic stiffness
   DevBuf rho_nodal; // [n_nodal] FP64 (hi part of the set-up value)
-  // global elimination tree
-  DevBuf tree_nodes, sep_nodes, bnd_nodes, map0, map1, factors;
-  // fine-grid map (SBFWI_RHO_GRID)
-  DevBuf cell_of_point;  // [n_nodal] int32 base cell ix + gx*iy
-  DevBuf clamp_of_point; // [n_nodal] int8 bit0 x-low, bit1 x-high, bit2 y-low, bit3 y-high
+  DevBuf factors;   // global factors along the elimination tree
   DevBuf pts_hi, pts_lo; // [n_nodal][2] dd location of every nodal point
-  DevBuf cell_ptr, cell_list;   // CSR: grid cell -> (point*4 + corner)
-  LevelTasks tasks;        // built for tasks.rows_per_task
+  LevelTasks tasks;        // built for tasks.shots
+  const MeshDevice& dev() const { return *mesh->dev; }
 };
 
-int build_level_tasks(Model& md, int rows_per_task);
+int build_level_tasks(Model& md, int shots);
 
 struct FwdState {
   Model* model = nullptr;

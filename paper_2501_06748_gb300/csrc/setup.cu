@@ -12,7 +12,9 @@
 //  3. multifrontal factorisation of the global boundary matrix sum_e S_e along
 //     the elimination tree (FP64, one CTA per front, Gauss-Jordan with partial
 //     pivoting inside each separator block).
+#include <algorithm>
 #include <cmath>
+#include <memory>
 #include <cstdio>
 #include <vector>
 
@@ -703,17 +705,15 @@ static int read_status(const DevBuf& st_dev, cudaStream_t st, int* code) {
   return SBFWI_OK;
 }
 
-int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st) {
-  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
+// mesh-only device data (first set-up on a mesh, or after a device change)
+static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
+  int device = 0;
+  SBFWI_CUDA(cudaGetDevice(&device));
+  if (m.dev && m.dev->device == device) return SBFWI_OK;
+  auto d = std::make_unique<MeshDevice>();
+  d->device = device;
+  const int n = m.n, p = m.p, pp = p + 1;
   const int ng = (3 * p + 2) / 2;
-  const int64_t E = m.n_elem, N = m.n_nodes, np = m.n_nodal;
-  md.nb = nb; md.n = n; md.E = E; md.N = N;
-  DevBuf status;
-  SBFWI_CUDA(status.alloc(sizeof(int)));
-  SBFWI_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st));
-  Profiler& prof = profiler();
-  prof.begin(kPhaseSetup, st);
-
   // radial grid xi_i = xi0 + i h (xi_n = 1), double-double
   std::vector<double> xi_hi(n + 1), xi_lo(n + 1);
   const dd h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
@@ -734,74 +734,112 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
       tab[2 * (ng + ng * pp + g * pp + q)] = dph[q].hi; tab[2 * (ng + ng * pp + g * pp + q) + 1] = dph[q].lo;
     }
   }
-
-  DevBuf d_xy, d_ctr, d_lines, d_lloc, d_xih, d_xil, d_tab, d_rho_in, d_rho_lo, d_cell, d_clamp;
   int rc;
-  if ((rc = upload(d_xy, m.node_xy, st))) return rc;
-  if ((rc = upload(d_ctr, m.centre_xy, st))) return rc;
-  if ((rc = upload(d_lines, m.line_nodes, st))) return rc;
-  if ((rc = upload(d_lloc, m.line_local, st))) return rc;
-  if ((rc = upload(md.dofs, m.dofs, st))) return rc;
-  if ((rc = upload(d_xih, xi_hi, st))) return rc;
-  if ((rc = upload(d_xil, xi_lo, st))) return rc;
-  if ((rc = upload(d_tab, tab, st))) return rc;
+  if ((rc = upload(d->xy, m.node_xy, st))) return rc;
+  if ((rc = upload(d->ctr, m.centre_xy, st))) return rc;
+  if ((rc = upload(d->lines, m.line_nodes, st))) return rc;
+  if ((rc = upload(d->lloc, m.line_local, st))) return rc;
+  if ((rc = upload(d->dofs, m.dofs, st))) return rc;
+  if ((rc = upload(d->xih, xi_hi, st))) return rc;
+  if ((rc = upload(d->xil, xi_lo, st))) return rc;
+  if ((rc = upload(d->tab, tab, st))) return rc;
+  const Tree& t = m.tree;
+  if ((rc = upload(d->tree_nodes, t.nodes, st))) return rc;
+  if ((rc = upload(d->sep_nodes, t.sep_nodes, st))) return rc;
+  if ((rc = upload(d->bnd_nodes, t.bnd_nodes, st))) return rc;
+  if ((rc = upload(d->map0, t.map0, st))) return rc;
+  if ((rc = upload(d->map1, t.map1, st))) return rc;
+  std::vector<int32_t> all;
+  for (int l = 0; l < t.levels; ++l) {
+    d->level_start.push_back((int64_t)all.size());
+    all.insert(all.end(), t.nodes_at_level[l].begin(), t.nodes_at_level[l].end());
+  }
+  if ((rc = upload(d->level_nodes, all, st))) return rc;
+  SBFWI_CUDA(d->F.alloc(sizeof(double) * std::max<int64_t>(t.F_total, 1)));
+  SBFWI_CUDA(d->U.alloc(sizeof(double) * std::max<int64_t>(t.U_total, 1)));
+  SBFWI_CUDA(cudaStreamSynchronize(st));     // host vectors above go out of scope
+  m.dev = std::move(d);
+  return SBFWI_OK;
+}
+
+// base cell, clamping and transpose CSR of the bilinear map for one fine grid
+static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, double lx, double ly, cudaStream_t st) {
+  MeshDevice& d = *m.dev;
+  if (d.grid_ready && d.gx == gx && d.gy == gy && d.lx == lx && d.ly == ly) return SBFWI_OK;
+  d.grid_ready = false;
+  const int n = m.n, nb = m.nb;
+  const int64_t np = m.n_nodal;
+  std::vector<int32_t> cell(np, 0);
+  std::vector<int8_t> clamp(np, 0);
+  const long double h = (1.0L - (long double)m.xi0) / n;
+  for (int64_t q = 0; q < np; ++q) {
+    long double x, y;
+    if (q < m.n_int) {
+      const int64_t e = q / ((int64_t)n * nb), rem = q - e * (int64_t)n * nb;
+      const int i = (int)(rem / nb), j = (int)(rem - (int64_t)i * nb);
+      const int32_t g = m.dofs[e * nb + j];
+      const long double xi = (long double)m.xi0 + (long double)i * h;
+      x = m.centre_xy[2 * e] + xi * ((long double)m.node_xy[2 * g] - m.centre_xy[2 * e]);
+      y = m.centre_xy[2 * e + 1] + xi * ((long double)m.node_xy[2 * g + 1] - m.centre_xy[2 * e + 1]);
+    } else {
+      x = m.node_xy[2 * (q - m.n_int)];
+      y = m.node_xy[2 * (q - m.n_int) + 1];
+    }
+    const long double fx = x * gx / lx - 0.5L, fy = y * gy / ly - 0.5L;
+    int64_t ix = (int64_t)std::floor(fx), iy = (int64_t)std::floor(fy);
+    int8_t cl = 0;
+    if (ix < 0) { ix = 0; cl |= 1; }
+    if (ix > gx - 2) { ix = gx - 2; cl |= 2; }
+    if (iy < 0) { iy = 0; cl |= 4; }
+    if (iy > gy - 2) { iy = gy - 2; cl |= 8; }
+    cell[q] = (int32_t)(iy * gx + ix);
+    clamp[q] = cl;
+  }
+  // the transpose map gathers, per grid cell, the points touching it in point order
+  std::vector<int64_t> cnt(gx * gy + 1, 0);
+  auto corner_cell = [&](int64_t q, int k) {
+    const int64_t ix = cell[q] % gx, iy = cell[q] / gx;
+    return (iy + (k >> 1)) * gx + ix + (k & 1);
+  };
+  for (int64_t q = 0; q < np; ++q)
+    for (int k = 0; k < 4; ++k) cnt[corner_cell(q, k) + 1]++;
+  for (int64_t c = 0; c < gx * gy; ++c) cnt[c + 1] += cnt[c];
+  std::vector<int64_t> list(cnt.back());
+  std::vector<int64_t> fillp(cnt.begin(), cnt.end() - 1);
+  for (int64_t q = 0; q < np; ++q)
+    for (int k = 0; k < 4; ++k) list[fillp[corner_cell(q, k)]++] = q * 4 + k;
+  int rc;
+  if ((rc = upload(d.cell, cell, st))) return rc;
+  if ((rc = upload(d.clamp, clamp, st))) return rc;
+  if ((rc = upload(d.cell_ptr, cnt, st))) return rc;
+  if ((rc = upload(d.cell_list, list, st))) return rc;
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  d.gx = gx; d.gy = gy; d.lx = lx; d.ly = ly;
+  d.grid_ready = true;
+  return SBFWI_OK;
+}
+
+int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st) {
+  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
+  const int ng = (3 * p + 2) / 2;
+  const int64_t E = m.n_elem, N = m.n_nodes, np = m.n_nodal;
+  md.nb = nb; md.n = n; md.E = E; md.N = N;
+  int rc;
+  if ((rc = ensure_mesh_device(m, st))) return rc;
+  if (md.rho_kind == SBFWI_RHO_GRID && (rc = ensure_grid_map(m, md.gx, md.gy, md.lx, md.ly, st))) return rc;
+  const MeshDevice& d = *m.dev;
+  DevBuf status;
+  SBFWI_CUDA(status.alloc(sizeof(int)));
+  SBFWI_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+  Profiler& prof = profiler();
+  prof.begin(kPhaseSetup, st);
 
   // density input
+  DevBuf d_rho_in;
   const int64_t nrho = (md.rho_kind == SBFWI_RHO_NODAL) ? np : md.gx * md.gy;
   SBFWI_CUDA(d_rho_in.alloc(sizeof(double) * nrho));
   SBFWI_CUDA(cudaMemcpyAsync(d_rho_in.p, rho, sizeof(double) * nrho,
                              mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-
-  // nodal point locations (host, for the grid cells of the bilinear map and its transpose)
-  std::vector<int32_t> cell(np, 0);
-  std::vector<int8_t> clamp(np, 0);
-  if (md.rho_kind == SBFWI_RHO_GRID) {
-    auto locate = [&](int64_t q, long double& x, long double& y) {
-      if (q < m.n_int) {
-        const int64_t e = q / ((int64_t)n * nb), rem = q - e * (int64_t)n * nb;
-        const int i = (int)(rem / nb), j = (int)(rem - (int64_t)i * nb);
-        const int32_t g = m.dofs[e * nb + j];
-        const long double xi = (long double)m.xi0 + (long double)i * ((1.0L - (long double)m.xi0) / n);
-        x = m.centre_xy[2 * e] + xi * ((long double)m.node_xy[2 * g] - m.centre_xy[2 * e]);
-        y = m.centre_xy[2 * e + 1] + xi * ((long double)m.node_xy[2 * g + 1] - m.centre_xy[2 * e + 1]);
-      } else {
-        x = m.node_xy[2 * (q - m.n_int)];
-        y = m.node_xy[2 * (q - m.n_int) + 1];
-      }
-    };
-    for (int64_t q = 0; q < np; ++q) {
-      long double x, y;
-      locate(q, x, y);
-      const long double fx = x * md.gx / md.lx - 0.5L, fy = y * md.gy / md.ly - 0.5L;
-      int64_t ix = (int64_t)std::floor(fx), iy = (int64_t)std::floor(fy);
-      int8_t cl = 0;
-      if (ix < 0) { ix = 0; cl |= 1; }
-      if (ix > md.gx - 2) { ix = md.gx - 2; cl |= 2; }
-      if (iy < 0) { iy = 0; cl |= 4; }
-      if (iy > md.gy - 2) { iy = md.gy - 2; cl |= 8; }
-      cell[q] = (int32_t)(iy * md.gx + ix);
-      clamp[q] = cl;
-    }
-    // CSR of grid cell -> (point, corner), sorted by point: the transpose map used
-    // by the gradient gathers in a fixed order
-    std::vector<int64_t> cnt(md.gx * md.gy + 1, 0);
-    auto corner_cell = [&](int64_t q, int k) {
-      const int64_t ix = cell[q] % md.gx, iy = cell[q] / md.gx;
-      return (iy + (k >> 1)) * md.gx + ix + (k & 1);
-    };
-    for (int64_t q = 0; q < np; ++q)
-      for (int k = 0; k < 4; ++k) cnt[corner_cell(q, k) + 1]++;
-    for (int64_t c = 0; c < md.gx * md.gy; ++c) cnt[c + 1] += cnt[c];
-    std::vector<int64_t> list(cnt.back());
-    std::vector<int64_t> fillp(cnt.begin(), cnt.end() - 1);
-    for (int64_t q = 0; q < np; ++q)
-      for (int k = 0; k < 4; ++k) list[fillp[corner_cell(q, k)]++] = q * 4 + k;
-    if ((rc = upload(md.cell_ptr, cnt, st))) return rc;
-    if ((rc = upload(md.cell_list, list, st))) return rc;
-  }
-  if ((rc = upload(md.cell_of_point, cell, st))) return rc;
-  if ((rc = upload(md.clamp_of_point, clamp, st))) return rc;
-
   DevBuf rho_hi, rho_lo;
   SBFWI_CUDA(rho_hi.alloc(sizeof(double) * np));
   SBFWI_CUDA(rho_lo.alloc(sizeof(double) * np));
@@ -810,10 +848,11 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   {
     DensityArgs a;
     a.n_elem = E; a.n_nodes = N; a.n_int = m.n_int; a.nb = nb; a.n = n;
-    a.node_xy = d_xy.as<double>(); a.centre_xy = d_ctr.as<double>(); a.dofs = md.dofs.as<int32_t>();
-    a.xi_hi = d_xih.as<double>(); a.xi_lo = d_xil.as<double>();
+    a.node_xy = d.xy.as<double>(); a.centre_xy = d.ctr.as<double>(); a.dofs = d.dofs.as<int32_t>();
+    a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>();
     a.grid = d_rho_in.as<double>(); a.rho_kind = md.rho_kind; a.gx = md.gx; a.gy = md.gy; a.lx = md.lx; a.ly = md.ly;
-    a.cell_of_point = md.cell_of_point.as<int32_t>(); a.clamp_of_point = md.clamp_of_point.as<int8_t>();
+    a.cell_of_point = md.rho_kind == SBFWI_RHO_GRID ? d.cell.as<int32_t>() : nullptr;
+    a.clamp_of_point = md.rho_kind == SBFWI_RHO_GRID ? d.clamp.as<int8_t>() : nullptr;
     a.pts_hi = md.pts_hi.as<double>(); a.pts_lo = md.pts_lo.as<double>();
     a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>(); a.status = status.as<int>();
     const int threads = 256;
@@ -822,9 +861,6 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     prof.count(kPhaseSetup);
     SBFWI_CUDA(cudaGetLastError());
   }
-  int code = 0;
-  if ((rc = read_status(status, st, &code))) return rc;
-  if (code) return fail(SBFWI_EINVAL, "density must be positive at every nodal point");
   SBFWI_CUDA(md.rho_nodal.alloc(sizeof(double) * np));
   SBFWI_CUDA(cudaMemcpyAsync(md.rho_nodal.p, rho_hi.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
 
@@ -838,11 +874,11 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
     a.c = md.c;
     a.mass = dd_div(dd_make(1.0), dd_mul(dd_make(md.beta), two_prod(md.dt, md.dt)));
-    a.h = h;
-    a.node_xy = d_xy.as<double>(); a.centre_xy = d_ctr.as<double>();
-    a.line_nodes = d_lines.as<int64_t>(); a.line_local = d_lloc.as<int32_t>(); a.dofs = md.dofs.as<int32_t>();
+    a.h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
+    a.node_xy = d.xy.as<double>(); a.centre_xy = d.ctr.as<double>();
+    a.line_nodes = d.lines.as<int64_t>(); a.line_local = d.lloc.as<int32_t>(); a.dofs = d.dofs.as<int32_t>();
     a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>();
-    a.xi_hi = d_xih.as<double>(); a.xi_lo = d_xil.as<double>(); a.tab = d_tab.as<double>();
+    a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>(); a.tab = d.tab.as<double>();
     a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>(); a.S = md.S.as<double>(); a.status = status.as<int>();
     const size_t smem = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb + 16 * nn) + 16;
     SBFWI_CUDA(cudaFuncSetAttribute(element_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -852,44 +888,29 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     prof.count(kPhaseSetup);
     SBFWI_CUDA(cudaGetLastError());
   }
-  if ((rc = read_status(status, st, &code))) return rc;
-  if (code) return fail(SBFWI_ESINGULAR, "a pivot block of the radial condensation is singular");
 
   // global factorisation along the elimination tree
   const Tree& t = m.tree;
-  if ((rc = upload(md.tree_nodes, t.nodes, st))) return rc;
-  if ((rc = upload(md.sep_nodes, t.sep_nodes, st))) return rc;
-  if ((rc = upload(md.bnd_nodes, t.bnd_nodes, st))) return rc;
-  if ((rc = upload(md.map0, t.map0, st))) return rc;
-  if ((rc = upload(md.map1, t.map1, st))) return rc;
   SBFWI_CUDA(md.factors.alloc(sizeof(double) * std::max<int64_t>(t.X_total, 1)));
   {
-    DevBuf F, U, lv;
-    SBFWI_CUDA(F.alloc(sizeof(double) * std::max<int64_t>(t.F_total, 1)));
-    SBFWI_CUDA(U.alloc(sizeof(double) * std::max<int64_t>(t.U_total, 1)));
-    std::vector<int32_t> all;
-    std::vector<int64_t> start;
-    for (int l = 0; l < t.levels; ++l) {
-      start.push_back((int64_t)all.size());
-      all.insert(all.end(), t.nodes_at_level[l].begin(), t.nodes_at_level[l].end());
-    }
-    if ((rc = upload(lv, all, st))) return rc;
     FactorArgs a;
-    a.nodes = md.tree_nodes.as<TreeNodeDev>(); a.map0 = md.map0.as<int32_t>(); a.map1 = md.map1.as<int32_t>();
-    a.S = md.S.as<double>(); a.nb = nb; a.F = F.as<double>(); a.U = U.as<double>();
+    a.nodes = d.tree_nodes.as<TreeNodeDev>(); a.map0 = d.map0.as<int32_t>(); a.map1 = d.map1.as<int32_t>();
+    a.S = md.S.as<double>(); a.nb = nb; a.F = d.F.as<double>(); a.U = d.U.as<double>();
     a.factors = md.factors.as<double>(); a.status = status.as<int>();
     for (int l = 0; l < t.levels; ++l) {
-      a.level_nodes = lv.as<int32_t>() + start[l];
+      a.level_nodes = d.level_nodes.as<int32_t>() + d.level_start[l];
       const unsigned cnt = (unsigned)t.nodes_at_level[l].size();
       front_assemble_kernel<<<cnt, 256, 0, st>>>(a);
       front_factor_kernel<<<cnt, 512, 0, st>>>(a);
       prof.count(kPhaseSetup, 2);
       SBFWI_CUDA(cudaGetLastError());
     }
-    prof.end(kPhaseSetup, st);
-    if ((rc = read_status(status, st, &code))) return rc;
-    if (code) return fail(SBFWI_ESINGULAR, "the global boundary matrix has a singular separator block");
   }
+  prof.end(kPhaseSetup, st);
+  int code = 0;
+  if ((rc = read_status(status, st, &code))) return rc;
+  if (code == SBFWI_EINVAL) return fail(SBFWI_EINVAL, "density must be positive at every nodal point");
+  if (code) return fail(SBFWI_ESINGULAR, "a pivot block of the radial condensation or a separator block of the global matrix is singular");
   return SBFWI_OK;
 }
 

@@ -19,6 +19,7 @@
 // interior state is read and written once per step.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -154,15 +155,20 @@ __device__ __forceinline__ double front_value(const SolveArgs& a, const TreeNode
   if (nd.elem >= 0) return a.fhat[((int64_t)nd.elem * a.nb + m0) * a.B + s];
   const int32_t m1 = a.map1[nd.map_off + pos];
   double v = 0.0;
-  if (m0 >= 0) v += a.ybnd[(a.nodes[nd.child0].bnd_off + m0) * a.B + s];
-  if (m1 >= 0) v += a.ybnd[(a.nodes[nd.child1].bnd_off + m1) * a.B + s];
+  // written by other blocks earlier in the same persistent launch: read through L2
+  if (m0 >= 0) v += __ldcg(a.ybnd + (a.nodes[nd.child0].bnd_off + m0) * a.B + s);
+  if (m1 >= 0) v += __ldcg(a.ybnd + (a.nodes[nd.child1].bnd_off + m1) * a.B + s);
+  return v;
+}
+
+// sum over the ks consecutive lanes that share one output (ks in {1, 2, 4, 8})
+__device__ __forceinline__ double lane_group_sum(double v, int ks) {
+  for (int off = ks >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
 
 // forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element)
-__global__ void solve_forward_kernel(SolveArgs a) {
-  extern __shared__ double csep[];
-  const Task tk = a.tasks[blockIdx.x];
+__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* csep) {
   const TreeNodeDev nd = a.nodes[tk.node];
   const int B = a.B, S = nd.s;
   for (int t = threadIdx.x; t < S * B; t += blockDim.x) {
@@ -173,39 +179,129 @@ __global__ void solve_forward_kernel(SolveArgs a) {
   }
   __syncthreads();
   const double* C = a.factors + nd.X_off + (int64_t)S * S + (int64_t)S * nd.b;   // b x s
-  for (int t = threadIdx.x; t < (tk.r1 - tk.r0) * B; t += blockDim.x) {
-    const int r = tk.r0 + t / B, s = t % B;
-    double acc = front_value(a, nd, S + r, s);
-    const double* Cr = C + (int64_t)r * S;
-    for (int k = 0; k < S; ++k) acc = fma(-Cr[k], csep[k * B + s], acc);
-    a.ybnd[(nd.bnd_off + r) * B + s] = acc;
+  const int ks = tk.ksplit;
+  const int outputs = (tk.r1 - tk.r0) * B;
+  // every lane walks the same number of rounds so that the lane-group shuffles see full warps
+  const int rounds = (outputs * ks + blockDim.x - 1) / blockDim.x;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int t = rd * blockDim.x + threadIdx.x;
+    const int o = t / ks, kk = t - o * ks;
+    const bool live = o < outputs;
+    const int r = tk.r0 + (live ? o / B : 0), s = live ? o % B : 0;
+    double acc = 0.0;
+    if (live) {
+      const double* Cr = C + (int64_t)r * S;
+      for (int k = kk; k < S; k += ks) acc = fma(Cr[k], csep[k * B + s], acc);
+    }
+    acc = lane_group_sum(acc, ks);
+    if (live && kk == 0) a.ybnd[(nd.bnd_off + r) * B + s] = front_value(a, nd, S + r, s) - acc;
   }
+  __syncthreads();     // csep is reused by the next task of this block
 }
 
 // backward pass: x_sep = X y_sep - G x_bnd
-__global__ void solve_backward_kernel(SolveArgs a) {
-  extern __shared__ double shb[];
-  const Task tk = a.tasks[blockIdx.x];
+__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* shb) {
   const TreeNodeDev nd = a.nodes[tk.node];
   const int B = a.B, S = nd.s, Bn = nd.b;
   double* ys = shb;
   double* xbn = shb + (size_t)S * B;
-  for (int t = threadIdx.x; t < S * B; t += blockDim.x) ys[t] = a.ysep[nd.sep_off * B + t];
+  for (int t = threadIdx.x; t < S * B; t += blockDim.x) ys[t] = __ldcg(a.ysep + nd.sep_off * B + t);
   for (int t = threadIdx.x; t < Bn * B; t += blockDim.x) {
     const int j = t / B, s = t - j * B;
-    xbn[t] = a.x[(int64_t)a.bnd_nodes[nd.bnd_off + j] * B + s];
+    xbn[t] = __ldcg(a.x + (int64_t)a.bnd_nodes[nd.bnd_off + j] * B + s);
   }
   __syncthreads();
   const double* X = a.factors + nd.X_off;
   const double* G = X + (int64_t)S * S;
-  for (int t = threadIdx.x; t < (tk.r1 - tk.r0) * B; t += blockDim.x) {
-    const int r = tk.r0 + t / B, s = t % B;
+  const int ks = tk.ksplit;
+  const int outputs = (tk.r1 - tk.r0) * B;
+  const int rounds = (outputs * ks + blockDim.x - 1) / blockDim.x;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int t = rd * blockDim.x + threadIdx.x;
+    const int o = t / ks, kk = t - o * ks;
+    const bool live = o < outputs;
+    const int r = tk.r0 + (live ? o / B : 0), s = live ? o % B : 0;
     double acc = 0.0;
-    const double* Xr = X + (int64_t)r * S;
-    for (int k = 0; k < S; ++k) acc = fma(Xr[k], ys[k * B + s], acc);
-    const double* Gr = G + (int64_t)r * Bn;
-    for (int j = 0; j < Bn; ++j) acc = fma(-Gr[j], xbn[j * B + s], acc);
-    a.x[(int64_t)a.sep_nodes[nd.sep_off + r] * B + s] = acc;
+    if (live) {
+      const double* Xr = X + (int64_t)r * S;
+      for (int k = kk; k < S; k += ks) acc = fma(Xr[k], ys[k * B + s], acc);
+      const double* Gr = G + (int64_t)r * Bn;
+      for (int j = kk; j < Bn; j += ks) acc = fma(-Gr[j], xbn[j * B + s], acc);
+    }
+    acc = lane_group_sum(acc, ks);
+    if (live && kk == 0) a.x[(int64_t)a.sep_nodes[nd.sep_off + r] * B + s] = acc;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) solve_forward_kernel(SolveArgs a) {
+  extern __shared__ double sm_fwd[];
+  solve_forward_task(a, a.tasks[blockIdx.x], sm_fwd);
+}
+
+__global__ void __launch_bounds__(256) solve_backward_kernel(SolveArgs a) {
+  extern __shared__ double sm_bwd[];
+  solve_backward_task(a, a.tasks[blockIdx.x], sm_bwd);
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
+// is bounded: after `budget` clock cycles it records SBFWI_ETIMEOUT and gives up,
+// so a broken launch returns an error instead of hanging the device.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* status, long long budget) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > budget || *(volatile int*)status != 0) {
+          atomicCAS(status, 0, SBFWI_ETIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct PersistentSolveArgs {
+  SolveArgs s;
+  const Task* fwd;
+  const Task* bwd;
+  const int32_t* fwd_start;   // levels + 1
+  const int32_t* bwd_start;
+  int levels;
+  unsigned* bar;              // [2]: arrival count, generation
+  int* status;
+  long long budget;
+};
+
+// the whole boundary solve of one time step: forward pass leaves -> root, then
+// backward pass root -> leaves, one grid barrier between tree levels
+__global__ void __launch_bounds__(256) solve_persistent_kernel(PersistentSolveArgs a) {
+  extern __shared__ double sm_p[];
+  for (int l = 0; l < a.levels; ++l) {
+    for (int t = a.fwd_start[l] + blockIdx.x; t < a.fwd_start[l + 1]; t += gridDim.x)
+      solve_forward_task(a.s, a.fwd[t], sm_p);
+    if (!grid_barrier(a.bar, a.bar + 1, a.status, a.budget)) return;
+  }
+  for (int l = a.levels - 1; l >= 0; --l) {
+    for (int t = a.bwd_start[l] + blockIdx.x; t < a.bwd_start[l + 1]; t += gridDim.x)
+      solve_backward_task(a.s, a.bwd[t], sm_p);
+    if (l > 0 && !grid_barrier(a.bar, a.bar + 1, a.status, a.budget)) return;
   }
 }
 
@@ -327,7 +423,18 @@ __global__ void misfit_final_kernel(const double* partial, int nparts, double ha
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-int build_level_tasks(Model& md, int rows_per_task) {
+// Lanes per output for a dot product of length k: long products of the upper tree
+// levels are split so that few-row fronts still spread over many CTAs.
+static int ksplit_for(int k) {
+  if (k >= 128) return 8;
+  if (k >= 48) return 4;
+  if (k >= 16) return 2;
+  return 1;
+}
+
+// B shots; a block task with ksplit 1 covers 256 / B rows
+int build_level_tasks(Model& md, int B) {
+  const int rows_per_task = std::max(1, 256 / B);
   const Tree& t = md.mesh->tree;
   std::vector<Task> fwd, bwd;
   md.tasks.fwd_start.assign(t.levels + 1, 0);
@@ -337,18 +444,30 @@ int build_level_tasks(Model& md, int rows_per_task) {
     md.tasks.bwd_start[l] = (int32_t)bwd.size();
     for (int32_t nd : t.nodes_at_level[l]) {
       const TreeNodeDev& r = t.nodes[nd];
-      if (r.b == 0) fwd.push_back(Task{nd, 0, 0, 0});
-      for (int32_t r0 = 0; r0 < r.b; r0 += rows_per_task) fwd.push_back(Task{nd, r0, std::min(r.b, r0 + rows_per_task), 0});
-      for (int32_t r0 = 0; r0 < r.s; r0 += rows_per_task) bwd.push_back(Task{nd, r0, std::min(r.s, r0 + rows_per_task), 0});
+      const int kf = ksplit_for(r.s), kb = ksplit_for(r.s + r.b);
+      const int rf = std::max(1, rows_per_task / kf), rb = std::max(1, rows_per_task / kb);
+      if (r.b == 0) fwd.push_back(Task{nd, 0, 0, 1});
+      for (int32_t r0 = 0; r0 < r.b; r0 += rf) fwd.push_back(Task{nd, r0, std::min(r.b, r0 + rf), kf});
+      for (int32_t r0 = 0; r0 < r.s; r0 += rb) bwd.push_back(Task{nd, r0, std::min(r.s, r0 + rb), kb});
     }
   }
   md.tasks.fwd_start[t.levels] = (int32_t)fwd.size();
   md.tasks.bwd_start[t.levels] = (int32_t)bwd.size();
+  md.tasks.max_level_tasks = 0;
+  for (int l = 0; l < t.levels; ++l)
+    md.tasks.max_level_tasks = std::max({md.tasks.max_level_tasks, md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l],
+                                         md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l]});
+  SBFWI_CUDA(md.tasks.fwd_start_dev.alloc(sizeof(int32_t) * md.tasks.fwd_start.size()));
+  SBFWI_CUDA(md.tasks.bwd_start_dev.alloc(sizeof(int32_t) * md.tasks.bwd_start.size()));
+  SBFWI_CUDA(cudaMemcpy(md.tasks.fwd_start_dev.p, md.tasks.fwd_start.data(), sizeof(int32_t) * md.tasks.fwd_start.size(),
+                        cudaMemcpyHostToDevice));
+  SBFWI_CUDA(cudaMemcpy(md.tasks.bwd_start_dev.p, md.tasks.bwd_start.data(), sizeof(int32_t) * md.tasks.bwd_start.size(),
+                        cudaMemcpyHostToDevice));
   SBFWI_CUDA(md.tasks.fwd.alloc(sizeof(Task) * fwd.size()));
   SBFWI_CUDA(md.tasks.bwd.alloc(sizeof(Task) * std::max<size_t>(bwd.size(), 1)));
   SBFWI_CUDA(cudaMemcpy(md.tasks.fwd.p, fwd.data(), sizeof(Task) * fwd.size(), cudaMemcpyHostToDevice));
   if (!bwd.empty()) SBFWI_CUDA(cudaMemcpy(md.tasks.bwd.p, bwd.data(), sizeof(Task) * bwd.size(), cudaMemcpyHostToDevice));
-  md.tasks.rows_per_task = rows_per_task;
+  md.tasks.shots = B;
   return SBFWI_OK;
 }
 
@@ -393,9 +512,8 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
     SBFWI_CUDA(rb.grad_int.alloc(sizeof(double) * np * B));
     SBFWI_CUDA(cudaMemsetAsync(rb.grad_int.p, 0, rb.grad_int.bytes, st));
   }
-  const int rpt = std::max(1, 256 / B);
-  if (md.tasks.rows_per_task != rpt) {
-    int rc = build_level_tasks(md, rpt);
+  if (md.tasks.shots != B) {
+    int rc = build_level_tasks(md, B);
     if (rc) return rc;
   }
   int smax = 0, bmax = 0;
@@ -411,7 +529,7 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   ea.nb = nb; ea.n = n; ea.B = B; ea.E = E;
   ea.epc = std::max(1, 128 / (nb * B));
   ea.a0 = md.a0; ea.a1 = md.a1; ea.a2 = md.a2; ea.c1 = md.c1; ea.c2 = md.c2; ea.dt = md.dt;
-  ea.mats = md.mats.as<double>(); ea.rt = md.rt.as<double>(); ea.dofs = md.dofs.as<int32_t>();
+  ea.mats = md.mats.as<double>(); ea.rt = md.rt.as<double>(); ea.dofs = md.dev().dofs.as<int32_t>();
   ea.u = rb.u.as<double>(); ea.ud = rb.ud.as<double>(); ea.udd = rb.udd.as<double>();
   ea.ub = rb.ub.as<double>(); ea.udb = rb.udb.as<double>(); ea.uddb = rb.uddb.as<double>();
   ea.q = rb.q.as<double>(); ea.fhat = rb.fhat.as<double>();
@@ -422,14 +540,45 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
     SBFWI_CUDA(cudaFuncSetAttribute(element_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem));
 
   SolveArgs sa;
-  sa.nodes = md.tree_nodes.as<TreeNodeDev>();
-  sa.sep_nodes = md.sep_nodes.as<int32_t>(); sa.bnd_nodes = md.bnd_nodes.as<int32_t>();
-  sa.map0 = md.map0.as<int32_t>(); sa.map1 = md.map1.as<int32_t>(); sa.factors = md.factors.as<double>();
+  const MeshDevice& mdev = md.dev();
+  sa.nodes = mdev.tree_nodes.as<TreeNodeDev>();
+  sa.sep_nodes = mdev.sep_nodes.as<int32_t>(); sa.bnd_nodes = mdev.bnd_nodes.as<int32_t>();
+  sa.map0 = mdev.map0.as<int32_t>(); sa.map1 = mdev.map1.as<int32_t>(); sa.factors = md.factors.as<double>();
   sa.fhat = rb.fhat.as<double>(); sa.ext = rb.ext.as<double>();
   sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
   sa.nb = nb; sa.B = B;
   const Task* ftasks = md.tasks.fwd.as<Task>();
   const Task* btasks = md.tasks.bwd.as<Task>();
+
+  // one cooperative persistent launch per time step for the whole tree, unless the
+  // device cannot launch cooperatively or SBFWI_SOLVE=levels asks for one launch per level
+  int device = 0, coop = 0, sms = 0, per_sm = 0;
+  SBFWI_CUDA(cudaGetDevice(&device));
+  SBFWI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+  SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  const size_t p_smem = std::max(fwd_smem, bwd_smem);
+  if (p_smem > 48 * 1024)
+    SBFWI_CUDA(cudaFuncSetAttribute(solve_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem));
+  SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_persistent_kernel, 256, p_smem));
+  const char* solve_env = std::getenv("SBFWI_SOLVE");
+  const bool persistent = coop && per_sm > 0 && !(solve_env && std::strcmp(solve_env, "levels") == 0);
+  DevBuf bar, pstatus;
+  PersistentSolveArgs pa;
+  int p_grid = 0;
+  if (persistent) {
+    SBFWI_CUDA(bar.alloc(2 * sizeof(unsigned)));
+    SBFWI_CUDA(pstatus.alloc(sizeof(int)));
+    SBFWI_CUDA(cudaMemsetAsync(bar.p, 0, bar.bytes, st));
+    SBFWI_CUDA(cudaMemsetAsync(pstatus.p, 0, pstatus.bytes, st));
+    pa.s = sa;
+    pa.fwd = ftasks; pa.bwd = btasks;
+    pa.fwd_start = md.tasks.fwd_start_dev.as<int32_t>(); pa.bwd_start = md.tasks.bwd_start_dev.as<int32_t>();
+    pa.levels = t.levels;
+    pa.bar = bar.as<unsigned>(); pa.status = pstatus.as<int>();
+    pa.budget = 4000000000LL;            // ~2 s at 2 GHz
+    p_grid = std::min(per_sm, 4) * sms;
+    p_grid = std::max(1, std::min(p_grid, md.tasks.max_level_tasks));
+  }
 
   BoundaryArgs ba;
   ba.N = N; ba.B = B; ba.R = 0;
@@ -469,19 +618,26 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
       prof.count(kPhaseOther);
     }
     prof.begin(kPhaseSolve, st);
-    for (int l = 0; l < t.levels; ++l) {
-      const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
-      if (cnt == 0) continue;
-      sa.tasks = ftasks + md.tasks.fwd_start[l];
-      solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
+    if (persistent) {
+      void* kargs[] = {&pa};
+      SBFWI_CUDA(cudaLaunchCooperativeKernel((const void*)solve_persistent_kernel, dim3(p_grid), dim3(256), kargs,
+                                             p_smem, st));
       prof.count(kPhaseSolve);
-    }
-    for (int l = t.levels - 1; l >= 0; --l) {
-      const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
-      if (cnt == 0) continue;
-      sa.tasks = btasks + md.tasks.bwd_start[l];
-      solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
-      prof.count(kPhaseSolve);
+    } else {
+      for (int l = 0; l < t.levels; ++l) {
+        const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
+        if (cnt == 0) continue;
+        sa.tasks = ftasks + md.tasks.fwd_start[l];
+        solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
+        prof.count(kPhaseSolve);
+      }
+      for (int l = t.levels - 1; l >= 0; --l) {
+        const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
+        if (cnt == 0) continue;
+        sa.tasks = btasks + md.tasks.bwd_start[l];
+        solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
+        prof.count(kPhaseSolve);
+      }
     }
     prof.end(kPhaseSolve, st);
     ba.k = k;
@@ -499,6 +655,12 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   }
   element_launch(1, 0, K - 1);
   SBFWI_CUDA(cudaGetLastError());
+  if (persistent) {
+    int code = 0;
+    SBFWI_CUDA(cudaMemcpyAsync(&code, pstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SBFWI_CUDA(cudaStreamSynchronize(st));
+    if (code) return fail(SBFWI_ETIMEOUT, "a grid barrier of the global solve timed out");
+  }
   return SBFWI_OK;
 }
 
@@ -655,9 +817,10 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   profiler().count(kPhaseOther);
   if (grid) {
     const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
-    grid_transpose_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->pts_hi.as<double>(), md->cell_of_point.as<int32_t>(),
-                                              md->clamp_of_point.as<int8_t>(), md->cell_ptr.as<int64_t>(),
-                                              md->cell_list.as<int64_t>(), md->gx, md->gy, md->lx, md->ly, dst,
+    const MeshDevice& mdev = md->dev();
+    grid_transpose_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->pts_hi.as<double>(), mdev.cell.as<int32_t>(),
+                                              mdev.clamp.as<int8_t>(), mdev.cell_ptr.as<int64_t>(),
+                                              mdev.cell_list.as<int64_t>(), md->gx, md->gy, md->lx, md->ly, dst,
                                               accumulate ? 1 : 0);
     profiler().count(kPhaseOther);
   }

@@ -170,3 +170,15 @@ def test_full_size_workload_few_steps(lib):
     g = lib.adjoint_gradient(m0, st, res)
     go = fwi.gradient_to_grid(o0, fwi.adjoint_gradient(o0, store, res, w.rec_nodes), w.gx, w.gy)
     assert rel(g, go) <= GRAD_TOL
+
+
+def test_persistent_and_per_level_global_solves_agree(lib, tiny, monkeypatch):
+    """The cooperative one-launch solve and the one-launch-per-tree-level solve give the
+    same traces (same arithmetic, different launch structure)."""
+    mesh, rho, srcs, recs, wav, dt = _ragged_case()
+    M = lib.Mesh.from_inputs(mesh, 6)
+    md = lib.Model(M, 1.3, rho, dt, lx=1.2, ly=1.0)
+    t_persistent, _ = lib.forward(md, srcs, wav, recs, keep=False)
+    monkeypatch.setenv("SBFWI_SOLVE", "levels")
+    t_levels, _ = lib.forward(md, srcs, wav, recs, keep=False)
+    assert np.array_equal(t_persistent, t_levels)
