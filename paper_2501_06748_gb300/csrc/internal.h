@@ -145,11 +145,21 @@ struct Model {
   DevBuf rho_nodal; // [n_nodal] FP64 (hi part of the set-up value)
   DevBuf factors;   // global factors along the elimination tree
   DevBuf pts_hi, pts_lo; // [n_nodal][2] dd location of every nodal point
+  // the same operators split into FP16 digits for the tensor-core element kernel
+  DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
+  bool tc_ready = false;
   LevelTasks tasks;        // built for tasks.shots
   const MeshDevice& dev() const { return *mesh->dev; }
 };
 
 int build_level_tasks(Model& md, int shots);
+
+// tensor-core element operators (tc.cu)
+bool tc_supported(int nb, int B);
+int tc_prepare(Model& md, cudaStream_t st);
+int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
+                      const double* ub, const double* udb, const double* uddb, double* q, double* fhat,
+                      double* store_int, const double* fwd_int, double* grad_int, cudaStream_t st);
 
 struct FwdState {
   Model* model = nullptr;

@@ -889,6 +889,9 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     SBFWI_CUDA(cudaGetLastError());
   }
 
+  // the per-step operators split for the tensor cores
+  if (tc_supported(nb, 1) && (rc = tc_prepare(md, st))) return rc;
+
   // global factorisation along the elimination tree
   const Tree& t = m.tree;
   SBFWI_CUDA(md.factors.alloc(sizeof(double) * std::max<int64_t>(t.X_total, 1)));

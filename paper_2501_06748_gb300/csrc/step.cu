@@ -474,7 +474,7 @@ int build_level_tasks(Model& md, int B) {
 namespace {
 
 struct RunBuffers {
-  DevBuf u, ud, udd, ub, udb, uddb, q, fhat, ext, ysep, ybnd, x;
+  DevBuf u, ud, udd, v, ub, udb, uddb, q, fhat, ext, ysep, ybnd, x;
   DevBuf values, nodes, grad_int;   // grad accumulators [n_nodal][B] (adjoint)
   DevBuf traces_owned;              // staging for host traces
   double* traces = nullptr;         // device traces [B][R][K] (owned above or the caller's)
@@ -508,6 +508,14 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   SBFWI_CUDA(rb.ybnd.alloc(sizeof(double) * std::max<int64_t>(t.bnd_rows, 1) * B));
   for (DevBuf* b : {&rb.u, &rb.ud, &rb.udd, &rb.q, &rb.ub, &rb.udb, &rb.uddb, &rb.ext, &rb.x, &rb.fhat})
     SBFWI_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
+  // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
+  // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
+  const char* elem_env = std::getenv("SBFWI_ELEMENT");
+  const bool use_tc = md.tc_ready && tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
+  if (use_tc) {
+    SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
+    SBFWI_CUDA(cudaMemsetAsync(rb.v.p, 0, rb.v.bytes, st));
+  }
   if (mode == Mode::Adjoint) {
     SBFWI_CUDA(rb.grad_int.alloc(sizeof(double) * np * B));
     SBFWI_CUDA(cudaMemsetAsync(rb.grad_int.p, 0, rb.grad_int.bytes, st));
@@ -599,7 +607,11 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
       ea.grad_int = rb.grad_int.as<double>();
     }
     prof.begin(kPhaseElement, st);
-    element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
+    if (use_tc)
+      tc_element_launch(md, B, down, up, ea.u, ea.ud, ea.udd, rb.v.as<double>(), ea.ub, ea.udb, ea.uddb, ea.q, ea.fhat,
+                        ea.store_int, ea.fwd_int, ea.grad_int, st);
+    else
+      element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
     prof.end(kPhaseElement, st);
     prof.count(kPhaseElement);
     return SBFWI_OK;

@@ -1,0 +1,417 @@
+// FP64-accurate element operators on the FP16 tensor cores.
+//
+// GB300 executes FP64 at ~1.2 TFLOP/s but FP16 mma.sync at ~600 TFLOP/s.  The
+// per-step element work is three n_b x n_b matrix products with B shots per radial
+// point (q_i = -(P_i v_i + Q_i q_{i-1}), u_i = q_i - H_i u_{i+1}, f_hat = R q_{n-1} + T v_n),
+// so it runs here as an error-free splitting of the FP64 operands into FP16 digits
+// (the splitting idea of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication", Numer. Algorithms 59 (2012)):
+//
+//  * every row r of a matrix A is scaled by 2^(53 - e_r), |A[r][.]| < 2^e_r, and
+//    rounded to an integer of at most 53 bits; every column (shot) of a vector x the
+//    same with its own exponent f; each of the five products has its own exponents
+//    (a shared exponent for P v + Q q loses ~1e-12 relative near the scaling centre);
+//  * each integer is written in six balanced base-512 digits (|digit| <= 257, exact
+//    in FP16): A_int = sum_k a_k 2^(9(6-k)), x_int = sum_l x_l 2^(9(6-l));
+//  * the digit products of one significance level L = k + l are summed by
+//    mma.sync.m16n8k16 (FP16 in, FP32 accumulate) into one accumulator per level;
+//    every partial sum is an integer below 2^24, so the accumulation is exact;
+//  * levels L = 2..8 are kept (the dropped ones weigh < 2^-57 of the scale), turned
+//    back into integers, summed in int64 with their weights 2^(9(8-L)), the two lowest
+//    levels rounded once to the nearest unit, and converted once to FP64:
+//    A x ~ 2^(e_r + f - 52) * T'.
+//
+// The splitting of the vectors and the recombination are integer work; what stays on
+// the FP64 pipe is the conversion of each result and the Newmark arithmetic.
+// Shapes: n_b <= 16 (padded to the 16 rows/columns of one m16n8k16 tile) and B <= 8
+// shots (padded to its 8 columns); one warp per element.
+#include <cstdint>
+#include <cuda_fp16.h>
+
+#include "internal.h"
+#include "prof.h"
+
+namespace sbfwi {
+
+namespace tc {
+
+constexpr int kSlices = 6;      // base-512 digits per operand
+constexpr int kLevels = 7;      // significance levels kept: k + l = 2..8
+constexpr int kTile = 16;       // rows / inner dimension of one mma tile
+constexpr int kCols = 8;        // shots of one mma tile
+
+// round(a * 2^(53 - e)) for |a| < 2^e, from the binary64 fields (integer work only)
+__device__ __forceinline__ long long to_fixed(double a, int e) {
+  const long long bits = __double_as_longlong(a);
+  if ((bits & 0x7FFFFFFFFFFFFFFFLL) == 0) return 0;
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long mant = bits & 0x000FFFFFFFFFFFFFLL;
+  int ex_eff = ex;
+  if (ex == 0) ex_eff = 1;              // subnormal
+  else mant |= 0x0010000000000000LL;
+  // right shift of the 53-bit significand; |a| < 2^e makes it >= 0
+  const int sh = e + 1022 - ex_eff;
+  long long v;
+  if (sh <= 0) v = mant;
+  else if (sh >= 60) v = 0;
+  else v = (mant + (1LL << (sh - 1))) >> sh;
+  return bits < 0 ? -v : v;
+}
+
+// exponent e with |a| < 2^e (for a != 0); very small for a == 0
+__device__ __forceinline__ int exp_bound(double a) {
+  const long long bits = __double_as_longlong(a);
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return a == 0.0 ? -1100 : -1021;
+  return ex - 1022;
+}
+
+// six balanced base-512 digits, most significant first, as FP16 bit patterns of 1536 + d
+__device__ __forceinline__ void digits(long long v, unsigned short (&h)[kSlices]) {
+#pragma unroll
+  for (int k = kSlices - 1; k >= 1; --k) {
+    const int d = (int)(((v + 256) & 511) - 256);
+    v = (v - d) >> 9;
+    h[k] = (unsigned short)(0x6600 + d);
+  }
+  h[0] = (unsigned short)(0x6600 + (int)v);
+}
+
+// two FP16 patterns of 1536 + d packed in a register -> the pair (d0, d1) as half2
+__device__ __forceinline__ unsigned pack_digits(unsigned short lo, unsigned short hi) {
+  const unsigned u = (unsigned)lo | ((unsigned)hi << 16);
+  __half2 h = *reinterpret_cast<const __half2*>(&u);
+  h = __hsub2(h, __halves2half2(__ushort_as_half(0x6600), __ushort_as_half(0x6600)));
+  return *reinterpret_cast<const unsigned*>(&h);
+}
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint4& a, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// Sum of the levels as an int64 with weight 2^-52 relative to 2^(e_r + f).  Levels
+// 2..6 are added exactly; levels 7 and 8 are summed exactly apart and rounded once to
+// the nearest unit (flooring them with shifts biases every product by about -1 unit,
+// which the energy-conserving time loop then accumulates).
+__device__ __forceinline__ double recombine(const float (&acc)[kLevels][4], int j, int e) {
+  long long t = 0;
+  t += (long long)__float2int_rn(acc[0][j]) << 36;
+  t += (long long)__float2int_rn(acc[1][j]) << 27;
+  t += (long long)__float2int_rn(acc[2][j]) << 18;
+  t += (long long)__float2int_rn(acc[3][j]) << 9;
+  t += (long long)__float2int_rn(acc[4][j]);
+  const long long low = ((long long)__float2int_rn(acc[5][j]) << 9) + (long long)__float2int_rn(acc[6][j]);
+  t += (low + (1LL << 17)) >> 18;
+  const int E = e - 52;
+  if (E > -1000 && E < 1000) return (double)t * __longlong_as_double((long long)(1023 + E) << 52);
+  return ldexp((double)t, E);
+}
+
+// Digits of an operand held in the B-fragment layout of m16n8k16: lane (g, t) holds
+// rows 2t, 2t+1, 2t+8, 2t+9 of column g.  f is that column's exponent.
+struct BDigits {
+  unsigned r[kSlices][2];
+};
+
+__device__ __forceinline__ void split_b(const double (&x)[4], int f, BDigits& d) {
+  unsigned short h[4][kSlices];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) digits(to_fixed(x[j], f), h[j]);
+#pragma unroll
+  for (int k = 0; k < kSlices; ++k) {
+    d.r[k][0] = pack_digits(h[0][k], h[1][k]);
+    d.r[k][1] = pack_digits(h[2][k], h[3][k]);
+  }
+}
+
+// column exponent: max over the four lanes of a column group (lanes 4g..4g+3)
+__device__ __forceinline__ int column_exponent(int e) {
+  e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
+  e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
+  return e;
+}
+
+// acc[L] += sum_{k + l = L} A_k x_l over the kept levels; A slices in fragment layout
+__device__ __forceinline__ void product(float (&acc)[kLevels][4], const uint4* Aslices, const BDigits& x) {
+#pragma unroll
+  for (int k = 0; k < kSlices; ++k) {
+    const uint4 a = Aslices[k * 32];
+#pragma unroll
+    for (int l = 0; l < kSlices; ++l)
+      if (k + l < kLevels) mma16816(acc[k + l], a, x.r[l][0], x.r[l][1]);
+  }
+}
+
+__device__ __forceinline__ void zero(float (&acc)[kLevels][4]) {
+#pragma unroll
+  for (int L = 0; L < kLevels; ++L)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[L][j] = 0.f;
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// set-up: slices of the per-step operators in mma fragment layout
+// ---------------------------------------------------------------------------
+// Operators per element and radial point i: P_i, Q_i, H_i (16 x 16 each after
+// padding); per element R and T.  Each is stored as kSlices fragments of 32 lanes x
+// uint4 with its own 16 row exponents.  Every product is scaled on its own: a pair
+// such as P_i v_i + Q_i q_{i-1} is formed as two products recombined separately,
+// because P and Q (and v and q) differ by orders of magnitude near the scaling
+// centre and a shared exponent would cost them significant bits.
+struct SliceArgs {
+  int nb, n;
+  int64_t E;
+  const double* mats;     // [E][n][3][nb][nb]
+  const double* rt;       // [E][2][nb][nb]
+  uint4* frag;            // [E][n][3: P, Q, H][kSlices][32]
+  uint4* frag_rt;         // [E][2: R, T][kSlices][32]
+  int* exps;              // [E][n][3][16]
+  int* exps_rt;           // [E][2][16]
+};
+
+__global__ void slice_operators_kernel(SliceArgs a) {
+  using namespace tc;
+  // one warp per operator: warps 0..E*n*3-1 are (e, i, P|Q|H), then E*2 warps of (e, R|T)
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int nb = a.nb, n = a.n;
+  const int64_t nn = (int64_t)nb * nb;
+  const int64_t nmat = a.E * n * 3;
+  if (w >= nmat + a.E * 2) return;
+  const double* h;
+  uint4* out;
+  int* eout;
+  if (w < nmat) {
+    h = a.mats + w * nn;
+    out = a.frag + w * kSlices * 32;
+    eout = a.exps + w * 16;
+  } else {
+    const int64_t k = w - nmat;
+    h = a.rt + k * nn;
+    out = a.frag_rt + k * kSlices * 32;
+    eout = a.exps_rt + k * 16;
+  }
+  auto val = [&](int r, int c) { return (r < nb && c < nb) ? h[(int64_t)r * nb + c] : 0.0; };
+  int er = -1100;           // lanes 0..15 own one row each
+  if (lane < 16) {
+    for (int c = 0; c < nb; ++c) er = max(er, exp_bound(val(lane, c)));
+    eout[lane] = er;
+  }
+  const int e_lo = __shfl_sync(0xffffffffu, er, g), e_hi = __shfl_sync(0xffffffffu, er, g + 8);
+  // fragment entries: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1), then columns + 8
+  unsigned short dg[8][kSlices];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int r = g + ((j >> 1) & 1) * 8, c = 2 * t + (j & 1) + (j >> 2) * 8;
+    digits(to_fixed(val(r, c), r < 8 ? e_lo : e_hi), dg[j]);
+  }
+#pragma unroll
+  for (int k = 0; k < kSlices; ++k) {
+    uint4 v;
+    v.x = pack_digits(dg[0][k], dg[1][k]);
+    v.y = pack_digits(dg[2][k], dg[3][k]);
+    v.z = pack_digits(dg[4][k], dg[5][k]);
+    v.w = pack_digits(dg[6][k], dg[7][k]);
+    out[k * 32 + lane] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// element step on the tensor cores (one warp per element)
+// ---------------------------------------------------------------------------
+struct ElemTcArgs {
+  int nb, n, B;
+  int64_t E;
+  double a0, a1, a2, c1, c2, dt;
+  const uint4* frag;
+  const uint4* frag_rt;
+  const int* exps;
+  const int* exps_rt;
+  const int32_t* dofs;
+  double* u; double* ud; double* udd; double* v;          // interior state [E][n][nb][B]
+  const double* ub; const double* udb; const double* uddb;
+  double* q;
+  double* fhat;
+  int do_down, do_up;
+  double* store_int;
+  const double* fwd_int;
+  double* grad_int;
+};
+
+__global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
+  using namespace tc;
+  __shared__ double xch[4][kTile * kCols];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t e = (int64_t)blockIdx.x * 4 + warp;
+  if (e >= a.E) return;                       // whole warp leaves together
+  const int nb = a.nb, n = a.n, B = a.B;
+  const int per = nb * B;
+  double* X = xch[warp];
+  const int64_t base = e * (int64_t)n * per;
+  // C-fragment positions of this lane: (row, col) = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)
+  const int cr[4] = {g, g, g + 8, g + 8};
+  const int cc[4] = {2 * t, 2 * t + 1, 2 * t, 2 * t + 1};
+  bool cok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) cok[j] = cr[j] < nb && cc[j] < B;
+  // B-fragment positions: (row, col) = (2t, g), (2t+1, g), (2t+8, g), (2t+9, g)
+  const int br[4] = {2 * t, 2 * t + 1, 2 * t + 8, 2 * t + 9};
+  bool bok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) bok[j] = br[j] < nb && g < B;
+
+  // C layout -> B layout through the warp's shared tile
+  auto c_to_b = [&](const double (&c)[4], double (&b)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) X[cr[j] * kCols + cc[j]] = c[j];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[j] = X[br[j] * kCols + g];
+    __syncwarp();
+  };
+  auto col_exp_b = [&](const double (&b)[4]) {
+    int f = -1100;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) f = max(f, exp_bound(b[j]));
+    return column_exponent(f);
+  };
+
+  double xb[4];       // the operand of the next product, B layout
+  if (a.do_down) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xb[j] = bok[j] ? a.ub[(int64_t)a.dofs[e * nb + br[j]] * B + g] : 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+      BDigits d;
+      const int f = col_exp_b(xb);
+      split_b(xb, f, d);
+      float acc[kLevels][4];
+      zero(acc);
+      const uint4* Hs = a.frag + ((e * n + i) * 3 + 2) * kSlices * 32 + lane;
+      product(acc, Hs, d);
+      const int* ex = a.exps + ((e * n + i) * 3 + 2) * 16;
+      const int er0 = ex[g], er1 = ex[g + 8];
+      const int fc0 = __shfl_sync(0xffffffffu, f, 4 * cc[0]), fc1 = __shfl_sync(0xffffffffu, f, 4 * cc[1]);
+      double un[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const double hu = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
+        un[j] = 0.0;
+        if (cok[j]) {
+          const int64_t o = base + (int64_t)i * per + cr[j] * B + cc[j];
+          const double udo = a.ud[o], uddo = a.udd[o], vo = a.v[o];
+          const double u_new = a.q[o] - hu;
+          const double uddn = fma(a.a0, u_new, -vo);
+          const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
+          a.u[o] = u_new; a.ud[o] = udn; a.udd[o] = uddn;
+          a.v[o] = fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+          if (a.store_int) a.store_int[o] = udn;
+          if (a.grad_int) a.grad_int[o] = fma(a.dt * a.fwd_int[o], udn, a.grad_int[o]);
+          un[j] = u_new;
+        }
+      }
+      c_to_b(un, xb);
+    }
+  }
+  if (!a.do_up) return;
+  __syncwarp();
+  // one product y = A x with its own row exponents (rows g, g+8) and column exponent,
+  // returned in C layout
+  auto apply = [&](const uint4* A, const int* rexp, const double (&xbv)[4], double (&y)[4]) {
+    const int f = col_exp_b(xbv);
+    BDigits d;
+    split_b(xbv, f, d);
+    float acc[kLevels][4];
+    zero(acc);
+    product(acc, A + lane, d);
+    const int er0 = rexp[g], er1 = rexp[g + 8];
+    const int fc0 = __shfl_sync(0xffffffffu, f, 4 * cc[0]), fc1 = __shfl_sync(0xffffffffu, f, 4 * cc[1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[j] = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
+  };
+  // forward sweep: q_i = -(P_i v_i + Q_i q_{i-1})
+  double qb[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < n; ++i) {
+    double vb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) vb[j] = bok[j] ? a.v[base + (int64_t)i * per + br[j] * B + g] : 0.0;
+    const uint4* Fi = a.frag + (e * n + i) * 3 * kSlices * 32;
+    const int* ex = a.exps + (e * n + i) * 3 * 16;
+    double pv[4], qq[4] = {0.0, 0.0, 0.0, 0.0};
+    apply(Fi, ex, vb, pv);
+    if (i > 0) apply(Fi + kSlices * 32, ex + 16, qb, qq);
+    double qc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      qc[j] = -(pv[j] + qq[j]);
+      if (cok[j]) a.q[base + (int64_t)i * per + cr[j] * B + cc[j]] = qc[j];
+      else qc[j] = 0.0;
+    }
+    c_to_b(qc, qb);
+  }
+  // effective source: f_hat = R q_{n-1} + T v_n, v_n the predictor of the boundary state
+  double vb[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    vb[j] = 0.0;
+    if (bok[j]) {
+      const int64_t gi = (int64_t)a.dofs[e * nb + br[j]] * B + g;
+      vb[j] = fma(a.a0, a.ub[gi], fma(a.a1, a.udb[gi], a.a2 * a.uddb[gi]));
+    }
+  }
+  double rq[4], tv[4];
+  const uint4* RT = a.frag_rt + e * 2 * kSlices * 32;
+  apply(RT, a.exps_rt + e * 32, qb, rq);
+  apply(RT + kSlices * 32, a.exps_rt + e * 32 + 16, vb, tv);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (cok[j]) a.fhat[(e * nb + cr[j]) * B + cc[j]] = rq[j] + tv[j];
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+bool tc_supported(int nb, int B) { return nb <= tc::kTile && B <= tc::kCols; }
+
+int tc_prepare(Model& md, cudaStream_t st) {
+  using namespace tc;
+  const int nb = md.nb, n = md.n;
+  const int64_t E = md.E;
+  SBFWI_CUDA(md.tc_frag.alloc(sizeof(uint4) * (size_t)E * n * 3 * kSlices * 32));
+  SBFWI_CUDA(md.tc_frag_rt.alloc(sizeof(uint4) * (size_t)E * 2 * kSlices * 32));
+  SBFWI_CUDA(md.tc_exps.alloc(sizeof(int) * (size_t)E * n * 3 * 16));
+  SBFWI_CUDA(md.tc_exps_rt.alloc(sizeof(int) * (size_t)E * 2 * 16));
+  SliceArgs a;
+  a.nb = nb; a.n = n; a.E = E;
+  a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>();
+  a.frag = md.tc_frag.as<uint4>(); a.frag_rt = md.tc_frag_rt.as<uint4>();
+  a.exps = md.tc_exps.as<int>(); a.exps_rt = md.tc_exps_rt.as<int>();
+  const int64_t warps = E * n * 3 + E * 2;
+  slice_operators_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(a);
+  profiler().count(kPhaseSetup);
+  SBFWI_CUDA(cudaGetLastError());
+  md.tc_ready = true;
+  return SBFWI_OK;
+}
+
+int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
+                      const double* ub, const double* udb, const double* uddb, double* q, double* fhat,
+                      double* store_int, const double* fwd_int, double* grad_int, cudaStream_t st) {
+  ElemTcArgs a;
+  a.nb = md.nb; a.n = md.n; a.B = B; a.E = md.E;
+  a.a0 = md.a0; a.a1 = md.a1; a.a2 = md.a2; a.c1 = md.c1; a.c2 = md.c2; a.dt = md.dt;
+  a.frag = md.tc_frag.as<uint4>(); a.frag_rt = md.tc_frag_rt.as<uint4>();
+  a.exps = md.tc_exps.as<int>(); a.exps_rt = md.tc_exps_rt.as<int>();
+  a.dofs = md.dev().dofs.as<int32_t>();
+  a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
+  a.do_down = down; a.do_up = up;
+  a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
+  element_step_tc_kernel<<<(unsigned)((md.E + 3) / 4), 128, 0, st>>>(a);
+  return SBFWI_OK;
+}
+
+}  // namespace sbfwi

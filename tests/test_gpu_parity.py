@@ -182,3 +182,25 @@ def test_persistent_and_per_level_global_solves_agree(lib, tiny, monkeypatch):
     monkeypatch.setenv("SBFWI_SOLVE", "levels")
     t_levels, _ = lib.forward(md, srcs, wav, recs, keep=False)
     assert np.array_equal(t_persistent, t_levels)
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged"])
+def test_tensor_core_and_fp64_element_kernels_agree(lib, tiny, monkeypatch, case):
+    """The element step on the FP16 tensor cores (error-free digit splitting) and the
+    FP64 element step give the same traces and gradient to FP64 rounding."""
+    if case == "tiny":
+        w = tiny
+        mesh, rho, srcs, recs, wav, dt, c, lx, ly, n_r = (w.mesh, w.rho_true, w.src_nodes, w.rec_nodes,
+                                                          w.wavelets, w.dt, w.c, 1.0, 1.0, w.n_r)
+    else:
+        mesh, rho, srcs, recs, wav, dt = _ragged_case()
+        c, lx, ly, n_r = 1.3, 1.2, 1.0, 6
+    M = lib.Mesh.from_inputs(mesh, n_r)
+    md = lib.Model(M, c, rho, dt, lx=lx, ly=ly)
+    t_tc, s_tc = lib.forward(md, srcs, wav, recs)
+    g_tc = lib.adjoint_gradient(md, s_tc, t_tc)
+    monkeypatch.setenv("SBFWI_ELEMENT", "fp64")
+    t_64, s_64 = lib.forward(md, srcs, wav, recs)
+    g_64 = lib.adjoint_gradient(md, s_64, t_64)
+    assert rel(t_tc, t_64) <= 1e-12
+    assert rel(g_tc, g_64) <= 1e-11
