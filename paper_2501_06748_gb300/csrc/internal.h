@@ -66,10 +66,14 @@ struct TreeNodeDev {
   int64_t U_off;           // set-up workspace: update matrix (b*b)
 };
 
-struct Task {               // a row range of one tree node
+struct Task {               // a row range of one tree node, with the node's fields inline
   int32_t node;
   int32_t r0, r1;
   int32_t ksplit;           // lanes that share one output's dot product (1, 2, 4 or 8)
+  int32_t s, b;             // separator and boundary sizes of the node
+  int32_t leaf;             // 1 if the node is an element (front values come from f_hat)
+  int32_t pad;
+  int64_t sep_off, bnd_off, map_off, X_off;
 };
 
 struct Tree {
@@ -79,6 +83,8 @@ struct Tree {
   std::vector<int32_t> sep_nodes, bnd_nodes;
   std::vector<int32_t> map0, map1;     // per front position: child0 / child1 bnd index, -1 if absent;
                                        // leaves: map0 = local dof of the element
+  std::vector<int32_t> src0, src1;     // the same as absolute rows: of ybnd (children), of f_hat
+                                       // (leaves: element * n_b + local dof), -1 if absent
   std::vector<std::vector<int32_t>> nodes_at_level;
   int64_t X_total = 0, F_total = 0, U_total = 0, sep_rows = 0, bnd_rows = 0;
   std::vector<int32_t> sep_owner;      // per global node: tree node that eliminates it
@@ -92,7 +98,7 @@ struct Tree {
 struct MeshDevice {
   int device = -1;
   DevBuf xy, ctr, lines, lloc, dofs, xih, xil, tab;
-  DevBuf tree_nodes, sep_nodes, bnd_nodes, map0, map1, level_nodes;
+  DevBuf tree_nodes, sep_nodes, bnd_nodes, map0, map1, src0, src1, level_nodes;
   std::vector<int64_t> level_start;
   DevBuf F, U;                       // factorisation workspaces
   // bilinear map of one fine grid: base cell and clamping of every nodal point, and

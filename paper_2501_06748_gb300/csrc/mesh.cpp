@@ -157,15 +157,24 @@ int build_tree(Mesh& m) {
     if (r.elem >= 0) {
       std::map<int32_t, int32_t> local;
       for (int j = 0; j < m.nb; ++j) local[m.dofs[(int64_t)r.elem * m.nb + j]] = j;
-      for (int32_t g : front) { t.map0.push_back(local.at(g)); t.map1.push_back(-1); }
+      for (int32_t g : front) {
+        const int32_t j = local.at(g);
+        t.map0.push_back(j);
+        t.map1.push_back(-1);
+        t.src0.push_back((int32_t)(r.elem * m.nb + j));
+        t.src1.push_back(-1);
+      }
     } else {
       std::map<int32_t, int32_t> in0, in1;
       for (size_t k = 0; k < bnd[r.child0].size(); ++k) in0[bnd[r.child0][k]] = (int32_t)k;
       for (size_t k = 0; k < bnd[r.child1].size(); ++k) in1[bnd[r.child1][k]] = (int32_t)k;
+      const int64_t off0 = t.nodes[r.child0].bnd_off, off1 = t.nodes[r.child1].bnd_off;
       for (int32_t g : front) {
         auto a = in0.find(g), b2 = in1.find(g);
         t.map0.push_back(a == in0.end() ? -1 : a->second);
         t.map1.push_back(b2 == in1.end() ? -1 : b2->second);
+        t.src0.push_back(a == in0.end() ? -1 : (int32_t)(off0 + a->second));
+        t.src1.push_back(b2 == in1.end() ? -1 : (int32_t)(off1 + b2->second));
       }
       t.level_of[nd] = 1 + std::max(t.level_of[r.child0], t.level_of[r.child1]);
     }

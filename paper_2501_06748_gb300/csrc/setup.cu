@@ -749,6 +749,8 @@ static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
   if ((rc = upload(d->bnd_nodes, t.bnd_nodes, st))) return rc;
   if ((rc = upload(d->map0, t.map0, st))) return rc;
   if ((rc = upload(d->map1, t.map1, st))) return rc;
+  if ((rc = upload(d->src0, t.src0, st))) return rc;
+  if ((rc = upload(d->src1, t.src1, st))) return rc;
   std::vector<int32_t> all;
   for (int l = 0; l < t.levels; ++l) {
     d->level_start.push_back((int64_t)all.size());

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
         const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
         a.u[o] = un; a.ud[o] = udn; a.udd[o] = uddn;
         if (a.store_int) a.store_int[o] = udn;
-        if (a.grad_int) a.grad_int[o] = fma(a.dt * a.fwd_int[o], udn, a.grad_int[o]);
+        if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);   // dt applied at the end
         if (a.do_up) vbuf[i * per + r * B + s] = fma(a.a0, un, fma(a.a1, udn, a.a2 * uddn));
       }
       __syncthreads();
@@ -135,12 +135,11 @@ __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
 // kernel B: global boundary solve, one launch per tree level and direction
 // ---------------------------------------------------------------------------
 struct SolveArgs {
-  const TreeNodeDev* nodes;
   const Task* tasks;
   const int32_t* sep_nodes;
   const int32_t* bnd_nodes;
-  const int32_t* map0;
-  const int32_t* map1;
+  const int32_t* src0;   // per front position: absolute row of f_hat (leaves) or ybnd, -1 if absent
+  const int32_t* src1;
   const double* factors;
   const double* fhat;    // [E][nb][B]
   const double* ext;     // [N][B] external sources
@@ -150,14 +149,14 @@ struct SolveArgs {
   int nb, B;
 };
 
-__device__ __forceinline__ double front_value(const SolveArgs& a, const TreeNodeDev& nd, int pos, int s) {
-  const int32_t m0 = a.map0[nd.map_off + pos];
-  if (nd.elem >= 0) return a.fhat[((int64_t)nd.elem * a.nb + m0) * a.B + s];
-  const int32_t m1 = a.map1[nd.map_off + pos];
+__device__ __forceinline__ double front_value(const SolveArgs& a, const Task& tk, int pos, int s) {
+  const int32_t r0 = a.src0[tk.map_off + pos];
+  if (tk.leaf) return a.fhat[(int64_t)r0 * a.B + s];
+  const int32_t r1 = a.src1[tk.map_off + pos];
   double v = 0.0;
   // written by other blocks earlier in the same persistent launch: read through L2
-  if (m0 >= 0) v += __ldcg(a.ybnd + (a.nodes[nd.child0].bnd_off + m0) * a.B + s);
-  if (m1 >= 0) v += __ldcg(a.ybnd + (a.nodes[nd.child1].bnd_off + m1) * a.B + s);
+  if (r0 >= 0) v += __ldcg(a.ybnd + (int64_t)r0 * a.B + s);
+  if (r1 >= 0) v += __ldcg(a.ybnd + (int64_t)r1 * a.B + s);
   return v;
 }
 
@@ -169,16 +168,16 @@ __device__ __forceinline__ double lane_group_sum(double v, int ks) {
 
 // forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element)
 __device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* csep) {
-  const TreeNodeDev nd = a.nodes[tk.node];
-  const int B = a.B, S = nd.s;
+  const int B = a.B, S = tk.s;
+#pragma unroll 4
   for (int t = threadIdx.x; t < S * B; t += blockDim.x) {
     const int k = t / B, s = t - k * B;
-    const double v = front_value(a, nd, k, s) + a.ext[(int64_t)a.sep_nodes[nd.sep_off + k] * B + s];
+    const double v = front_value(a, tk, k, s) + a.ext[(int64_t)a.sep_nodes[tk.sep_off + k] * B + s];
     csep[t] = v;
-    if (tk.r0 == 0) a.ysep[(nd.sep_off + k) * B + s] = v;
+    if (tk.r0 == 0) a.ysep[(tk.sep_off + k) * B + s] = v;
   }
   __syncthreads();
-  const double* C = a.factors + nd.X_off + (int64_t)S * S + (int64_t)S * nd.b;   // b x s
+  const double* C = a.factors + tk.X_off + (int64_t)S * S + (int64_t)S * tk.b;   // b x s
   const int ks = tk.ksplit;
   const int outputs = (tk.r1 - tk.r0) * B;
   // every lane walks the same number of rounds so that the lane-group shuffles see full warps
@@ -191,27 +190,29 @@ __device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* cs
     double acc = 0.0;
     if (live) {
       const double* Cr = C + (int64_t)r * S;
+#pragma unroll 4
       for (int k = kk; k < S; k += ks) acc = fma(Cr[k], csep[k * B + s], acc);
     }
     acc = lane_group_sum(acc, ks);
-    if (live && kk == 0) a.ybnd[(nd.bnd_off + r) * B + s] = front_value(a, nd, S + r, s) - acc;
+    if (live && kk == 0) a.ybnd[(tk.bnd_off + r) * B + s] = front_value(a, tk, S + r, s) - acc;
   }
   __syncthreads();     // csep is reused by the next task of this block
 }
 
 // backward pass: x_sep = X y_sep - G x_bnd
 __device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* shb) {
-  const TreeNodeDev nd = a.nodes[tk.node];
-  const int B = a.B, S = nd.s, Bn = nd.b;
+  const int B = a.B, S = tk.s, Bn = tk.b;
   double* ys = shb;
   double* xbn = shb + (size_t)S * B;
-  for (int t = threadIdx.x; t < S * B; t += blockDim.x) ys[t] = __ldcg(a.ysep + nd.sep_off * B + t);
+#pragma unroll 4
+  for (int t = threadIdx.x; t < S * B; t += blockDim.x) ys[t] = __ldcg(a.ysep + tk.sep_off * B + t);
+#pragma unroll 4
   for (int t = threadIdx.x; t < Bn * B; t += blockDim.x) {
     const int j = t / B, s = t - j * B;
-    xbn[t] = __ldcg(a.x + (int64_t)a.bnd_nodes[nd.bnd_off + j] * B + s);
+    xbn[t] = __ldcg(a.x + (int64_t)a.bnd_nodes[tk.bnd_off + j] * B + s);
   }
   __syncthreads();
-  const double* X = a.factors + nd.X_off;
+  const double* X = a.factors + tk.X_off;
   const double* G = X + (int64_t)S * S;
   const int ks = tk.ksplit;
   const int outputs = (tk.r1 - tk.r0) * B;
@@ -224,24 +225,28 @@ __device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* s
     double acc = 0.0;
     if (live) {
       const double* Xr = X + (int64_t)r * S;
+#pragma unroll 4
       for (int k = kk; k < S; k += ks) acc = fma(Xr[k], ys[k * B + s], acc);
       const double* Gr = G + (int64_t)r * Bn;
+#pragma unroll 4
       for (int j = kk; j < Bn; j += ks) acc = fma(-Gr[j], xbn[j * B + s], acc);
     }
     acc = lane_group_sum(acc, ks);
-    if (live && kk == 0) a.x[(int64_t)a.sep_nodes[nd.sep_off + r] * B + s] = acc;
+    if (live && kk == 0) a.x[(int64_t)a.sep_nodes[tk.sep_off + r] * B + s] = acc;
   }
   __syncthreads();
 }
 
 __global__ void __launch_bounds__(256) solve_forward_kernel(SolveArgs a) {
   extern __shared__ double sm_fwd[];
-  solve_forward_task(a, a.tasks[blockIdx.x], sm_fwd);
+  const Task tk = a.tasks[blockIdx.x];
+  solve_forward_task(a, tk, sm_fwd);
 }
 
 __global__ void __launch_bounds__(256) solve_backward_kernel(SolveArgs a) {
   extern __shared__ double sm_bwd[];
-  solve_backward_task(a, a.tasks[blockIdx.x], sm_bwd);
+  const Task tk = a.tasks[blockIdx.x];
+  solve_backward_task(a, tk, sm_bwd);
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
@@ -332,7 +337,7 @@ __global__ void boundary_update_kernel(BoundaryArgs a) {
     const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
     a.ub[t] = un; a.udb[t] = udn; a.uddb[t] = uddn;
     if (a.store_b) a.store_b[t] = udn;
-    if (a.grad_b) a.grad_b[t] = fma(a.dt * a.fwd_b[t], udn, a.grad_b[t]);
+    if (a.grad_b) a.grad_b[t] = fma(a.fwd_b[t], udn, a.grad_b[t]);          // dt applied at the end
   }
   if (a.traces) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)a.R * a.B; t += (int64_t)gridDim.x * blockDim.x) {
@@ -357,10 +362,12 @@ __global__ void sources_kernel(double* ext, int B, int nsrc, const int64_t* node
 // ---------------------------------------------------------------------------
 // gradient: shots summed, then optionally the transpose of the bilinear map
 // ---------------------------------------------------------------------------
-__global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double* out, int accumulate) {
+// g(node) = dt * sum over shots of the accumulated sum_m udot_fwd * lambdadot
+__global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double dt, double* out, int accumulate) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < B; ++b) s += acc[q * B + b];
+    s *= dt;
     out[q] = accumulate ? out[q] + s : s;
   }
 }
@@ -446,9 +453,16 @@ int build_level_tasks(Model& md, int B) {
       const TreeNodeDev& r = t.nodes[nd];
       const int kf = ksplit_for(r.s), kb = ksplit_for(r.s + r.b);
       const int rf = std::max(1, rows_per_task / kf), rb = std::max(1, rows_per_task / kb);
-      if (r.b == 0) fwd.push_back(Task{nd, 0, 0, 1});
-      for (int32_t r0 = 0; r0 < r.b; r0 += rf) fwd.push_back(Task{nd, r0, std::min(r.b, r0 + rf), kf});
-      for (int32_t r0 = 0; r0 < r.s; r0 += rb) bwd.push_back(Task{nd, r0, std::min(r.s, r0 + rb), kb});
+      auto task = [&](int32_t r0, int32_t r1, int ks) {
+        Task tk;
+        tk.node = nd; tk.r0 = r0; tk.r1 = r1; tk.ksplit = ks;
+        tk.s = r.s; tk.b = r.b; tk.leaf = r.elem >= 0 ? 1 : 0; tk.pad = 0;
+        tk.sep_off = r.sep_off; tk.bnd_off = r.bnd_off; tk.map_off = r.map_off; tk.X_off = r.X_off;
+        return tk;
+      };
+      if (r.b == 0) fwd.push_back(task(0, 0, 1));
+      for (int32_t r0 = 0; r0 < r.b; r0 += rf) fwd.push_back(task(r0, std::min(r.b, r0 + rf), kf));
+      for (int32_t r0 = 0; r0 < r.s; r0 += rb) bwd.push_back(task(r0, std::min(r.s, r0 + rb), kb));
     }
   }
   md.tasks.fwd_start[t.levels] = (int32_t)fwd.size();
@@ -549,9 +563,8 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
 
   SolveArgs sa;
   const MeshDevice& mdev = md.dev();
-  sa.nodes = mdev.tree_nodes.as<TreeNodeDev>();
   sa.sep_nodes = mdev.sep_nodes.as<int32_t>(); sa.bnd_nodes = mdev.bnd_nodes.as<int32_t>();
-  sa.map0 = mdev.map0.as<int32_t>(); sa.map1 = mdev.map1.as<int32_t>(); sa.factors = md.factors.as<double>();
+  sa.src0 = mdev.src0.as<int32_t>(); sa.src1 = mdev.src1.as<int32_t>(); sa.factors = md.factors.as<double>();
   sa.fhat = rb.fhat.as<double>(); sa.ext = rb.ext.as<double>();
   sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
   sa.nb = nb; sa.B = B;
@@ -824,7 +837,7 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
   const bool grid = md->rho_kind == SBFWI_RHO_GRID;
   // nodal output: shots summed straight into the output (accumulating if asked)
-  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, grid ? gn.as<double>() : dst,
+  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, md->dt, grid ? gn.as<double>() : dst,
                                            (!grid && accumulate) ? 1 : 0);
   profiler().count(kPhaseOther);
   if (grid) {

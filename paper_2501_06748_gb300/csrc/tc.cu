@@ -58,12 +58,30 @@ __device__ __forceinline__ long long to_fixed(double a, int e) {
   return bits < 0 ? -v : v;
 }
 
-// exponent e with |a| < 2^e (for a != 0); very small for a == 0
+// exponent e with |a| < 2^e (for a != 0); very small for a == 0 (integer work only)
 __device__ __forceinline__ int exp_bound(double a) {
   const long long bits = __double_as_longlong(a);
   const int ex = (int)((bits >> 52) & 0x7FF);
-  if (ex == 0) return a == 0.0 ? -1100 : -1021;
+  if (ex == 0) return (bits & 0x7FFFFFFFFFFFFFFFLL) == 0 ? -1100 : -1021;
   return ex - 1022;
+}
+
+// t * 2^E as a binary64, rounded to nearest-even like a conversion of t, built with
+// integer operations (the scaling by 2^E is exact unless the result is subnormal)
+__device__ __forceinline__ double int_to_double_scaled(long long t, int E) {
+  if (t == 0) return 0.0;
+  const unsigned long long sign = t < 0 ? 0x8000000000000000ULL : 0ULL;
+  unsigned long long m = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
+  const int lz = __clzll((long long)m);
+  m <<= lz;                                   // top bit at position 63
+  unsigned long long hi = m >> 11;            // 53 bits
+  const unsigned long long rem = m & 0x7FFULL;
+  if (rem > 0x400ULL || (rem == 0x400ULL && (hi & 1ULL))) ++hi;
+  int bexp = E - lz + 11 + 52 + 1023;
+  if (hi == (1ULL << 53)) { hi >>= 1; ++bexp; }
+  if (bexp >= 1 && bexp <= 2046)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)bexp << 52) | (hi & 0x000FFFFFFFFFFFFFULL)));
+  return ldexp((double)t, E);
 }
 
 // six balanced base-512 digits, most significant first, as FP16 bit patterns of 1536 + d
@@ -105,9 +123,7 @@ __device__ __forceinline__ double recombine(const float (&acc)[kLevels][4], int 
   t += (long long)__float2int_rn(acc[4][j]);
   const long long low = ((long long)__float2int_rn(acc[5][j]) << 9) + (long long)__float2int_rn(acc[6][j]);
   t += (low + (1LL << 17)) >> 18;
-  const int E = e - 52;
-  if (E > -1000 && E < 1000) return (double)t * __longlong_as_double((long long)(1023 + E) << 52);
-  return ldexp((double)t, E);
+  return int_to_double_scaled(t, e - 52);
 }
 
 // Digits of an operand held in the B-fragment layout of m16n8k16: lane (g, t) holds
@@ -241,6 +257,7 @@ struct ElemTcArgs {
   double* store_int;
   const double* fwd_int;
   double* grad_int;
+  int a2_is_one;        // beta = 1/4: the predictor needs no multiply by a2
 };
 
 __global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
@@ -307,10 +324,11 @@ __global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
           const double u_new = a.q[o] - hu;
           const double uddn = fma(a.a0, u_new, -vo);
           const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
-          a.u[o] = u_new; a.ud[o] = udn; a.udd[o] = uddn;
-          a.v[o] = fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+          // the interior displacement is not kept: the predictor v carries it
+          a.ud[o] = udn; a.udd[o] = uddn;
+          a.v[o] = a.a2_is_one ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
           if (a.store_int) a.store_int[o] = udn;
-          if (a.grad_int) a.grad_int[o] = fma(a.dt * a.fwd_int[o], udn, a.grad_int[o]);
+          if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);    // dt applied at the end
           un[j] = u_new;
         }
       }
@@ -410,6 +428,7 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
   a.do_down = down; a.do_up = up;
   a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
+  a.a2_is_one = md.a2 == 1.0;
   element_step_tc_kernel<<<(unsigned)((md.E + 3) / 4), 128, 0, st>>>(a);
   return SBFWI_OK;
 }
