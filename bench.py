@@ -10,13 +10,15 @@ units/step = elements * N_r * time steps * shots.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) shard shots: every rank
-runs its own batch of 8 shots, no data-path collective (weak scaling).
+Prints one JSON line (rank 0).  Multi-GPU runs (torchrun) shard shots: the job has
+8 shots per rank, every rank runs its own 8 on its own GPU, and the ranks exchange
+only the misfit and gradient sum (one all-reduce per step; weak scaling).
 """
 
 import argparse
 import json
 import os
+import re
 import subprocess
 import sys
 import time
@@ -38,6 +40,37 @@ def peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def algorithmic_bytes_per_unit_launch(nb, B):
+    """HBM bytes one element-radial-node-step of one shot needs in one pass (forward or
+    adjoint): the four n_b x n_b FP64 operators of the radial point shared by the B shots of
+    the pass, read+write of u, u-dot, u-ddot, one spill of the condensed load, and the
+    forward velocity written to (forward) or read from (adjoint) the store."""
+    return 4 * nb * nb * 8 / B + 6 * nb * 8 + 2 * nb * 8 + nb * 8
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the kernel's
+    source has not changed since the counters were taken; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_size_workload.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no ncu summary"
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_h = re.search(r"source_sha256:\s*(\S+)\s+(\S+)", text)
+    if not m_b or not m_h:
+        return None, "ncu summary without traffic"
+    src = os.path.join(ROOT, m_h.group(1))
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None, "kernel source missing"
+    if digest != m_h.group(2):
+        return None, "kernel changed since the ncu capture"
+    return float(m_b.group(1)), os.path.relpath(path, ROOT)
 
 
 # ---------------------------------------------------------------------------
@@ -133,6 +166,7 @@ def run_ours(args, rank, world):
     from paper_2501_06748_gb300 import build
     build.build()
     from paper_2501_06748_gb300 import sbfwi as lib
+    from paper_2501_06748_gb300.shots import shard, allreduce_misfit_gradient
     from sbfwi_inputs import size_workload
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -142,8 +176,12 @@ def run_ours(args, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w = size_workload(K=args.time_steps, n_shots=args.shots)
-    B, K, R = w.n_shots, w.K, int(w.rec_nodes.shape[0])
+    # weak scaling: the job has shots x ranks sources; each rank takes its shard
+    w = size_workload(K=args.time_steps, n_shots=args.shots * world)
+    mine = shard(w.n_shots, rank, world)
+    src_nodes = w.src_nodes[mine.start:mine.stop]
+    wav_host = np.ascontiguousarray(w.wavelets[mine.start:mine.stop])
+    B, K, R = len(mine), w.K, int(w.rec_nodes.shape[0])
     E, N_r = w.mesh.n_elem, w.n_r
     units_per_step = E * N_r * K * B
     M = lib.Mesh.from_inputs(w.mesh, N_r)
@@ -151,10 +189,10 @@ def run_ours(args, rank, world):
 
     rho_start = torch.tensor(w.rho_start, device=dev)
     rho_true = torch.tensor(w.rho_true, device=dev)
-    wav = torch.tensor(w.wavelets, device=dev)
+    wav = torch.tensor(wav_host, device=dev)
     # observed data: the same path on the flawed model (synthetic input, made once, untimed)
     m_true = lib.Model(M, w.c, rho_true, w.dt)
-    observed, _ = lib.forward(m_true, w.src_nodes, wav, w.rec_nodes, keep=False)
+    observed, _ = lib.forward(m_true, src_nodes, wav, w.rec_nodes, keep=False)
     del m_true
     torch.cuda.synchronize()
 
@@ -165,7 +203,7 @@ def run_ours(args, rank, world):
     def step(host=False):
         """Set-up + forward + misfit + adjoint gradient of all shots; returns (E, grad)."""
         if host:
-            rho_in, wav_in, obs_in = w.rho_start, w.wavelets, observed_host
+            rho_in, wav_in, obs_in = w.rho_start, wav_host, observed_host
             grad = np.zeros((w.gy, w.gx))
         else:
             rho_in, wav_in, obs_in = rho_start, wav, observed
@@ -173,11 +211,19 @@ def run_ours(args, rank, world):
         model = lib.Model(M, w.c, rho_in, w.dt)
         E_tot = 0.0
         for c in chunks:
-            tr, st = lib.forward(model, w.src_nodes[c], wav_in[c], w.rec_nodes)
+            tr, st = lib.forward(model, src_nodes[c], wav_in[c], w.rec_nodes)
             Ec, res = lib.misfit(tr, obs_in[c], w.dt)
             lib.adjoint_gradient(model, st, res, grad_out=grad, accumulate=True)
             E_tot += Ec
             del st
+        if dist:
+            # the one exchange of the path: sum of misfit and gradient over the ranks' shots
+            if host:
+                g_dev = torch.from_numpy(grad).to(dev)
+                E_tot, g_dev = allreduce_misfit_gradient(E_tot, g_dev)
+                grad = g_dev.cpu().numpy()
+            else:
+                E_tot, grad = allreduce_misfit_gradient(E_tot, grad)
         return E_tot, grad
 
     # the forward velocity store of one pass must fit in HBM; halve the pass if it does not
@@ -235,28 +281,61 @@ def run_ours(args, rank, world):
         ntr = B * R * K * 8
         gbytes = w.gy * w.gx * 8 * len(chunks)
         # H2D: density, wavelets, misfit inputs (traces, observed), residual, gradient (accumulated)
-        h2d = w.rho_start.nbytes + w.wavelets.nbytes + 2 * ntr + ntr + gbytes
+        h2d = w.rho_start.nbytes + wav_host.nbytes + 2 * ntr + ntr + gbytes
         # D2H: traces, residual, misfit values, gradient
         d2h = ntr + ntr + 8 * len(chunks) + gbytes
+        if dist:
+            h2d += w.gy * w.gx * 8            # the gradient goes through the device for the all-reduce
+            d2h += w.gy * w.gx * 8
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
         e2e = {"value": units_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    # roofline of the dominant kernel (fused element step), from its own CUDA events
+    # the same path one shot at a time (B = 1 per pass), for comparison with the batched pass
+    one_shot = None
+    if args.one_shot:
+        def step_one():
+            model = lib.Model(M, w.c, rho_start, w.dt)
+            tr, st = lib.forward(model, src_nodes[:1], wav[:1], w.rec_nodes)
+            _, res = lib.misfit(tr, observed[:1], w.dt)
+            return lib.adjoint_gradient(model, st, res)
+        step_one()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step_one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        one_shot = {"value": E * N_r * K / (ms1 / 1e3), "unit": UNIT, "ms_per_shot": ms1,
+                    "note": "set-up + forward + misfit + adjoint + gradient of shot 0 alone (one pass, B = 1)"}
+
+    # roofline of the dominant kernel (the element step), from its own CUDA events
     el = prof["element"]
     avg_launch_ms = el["ms"] / max(el["intervals"], 1)
     Bc = chunks[0].stop - chunks[0].start
-    flops_launch = 2.0 * nb * nb * (3 * n + 1) * E * Bc
-    achieved_tflops = flops_launch / (avg_launch_ms / 1e3) / 1e12
-    bytes_launch = 8.0 * (3 * nb * nb * n + 2 * nb * nb) * E + 8.0 * 9 * E * n * nb * Bc
+    use_tc = os.environ.get("SBFWI_ELEMENT", "") != "fp64" and nb <= 16 and Bc <= 8
+    kernel = "element_step_tc_kernel" if use_tc else "element_step_kernel"
+    units_launch = E * N_r * Bc                      # one pass (forward or adjoint) of one time step
+    bpu = algorithmic_bytes_per_unit_launch(nb, Bc)
+    bytes_launch = bpu * units_launch
     pk, pk_kind = peaks()
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "element_step_kernel", "flops_per_launch": flops_launch,
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    achieved_gbs = bytes_launch / (avg_launch_ms / 1e3) / 1e9
+    flops_launch = 8.0 * nb * nb * units_launch      # four n_b x n_b mat-vecs per radial point and shot
+    traffic, traffic_src = profiled_traffic(kernel)
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                "kernel": kernel, "algorithmic_bytes_per_launch": bytes_launch,
+                "bytes_per_unit": bpu, "units_per_launch": units_launch,
                 "avg_launch_ms": avg_launch_ms, "launches_timed": el["intervals"],
-                "peak_note": "FP64 nominal 1.25 TFLOP/s (recipe); DFMA probe 1.20 TFLOP/s",
-                "hbm_view": {"algorithmic_bytes_per_launch": bytes_launch,
-                             "gbs": bytes_launch / (avg_launch_ms / 1e3) / 1e9,
-                             "peak_gbs": pk.get("hbm_gbs"), "peak_kind": pk_kind}}
+                "peak_note": f"HBM copy bandwidth, {pk_kind} (burst)", "traffic_source": traffic_src,
+                "fp64_view": {"fp64_equiv_tflops": flops_launch / (avg_launch_ms / 1e3) / 1e12,
+                              "fp64_nominal_tflops": FP64_PEAK_TFLOPS,
+                              "note": "mat-vec flops at FP64 accuracy; the tensor-core kernel computes them "
+                                      "as exact FP16 digit products, so this may exceed the FP64 pipe"}}
     launches = sum(v["launches"] for v in prof.values())
 
     if rank != 0:
@@ -281,7 +360,7 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "per_step": [float(x) for x in per_step]},
         "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "one_shot_path": one_shot, "gpu_launches": int(launches),
         "clocks": clk,
     }
     if dist:
@@ -321,6 +400,8 @@ def main():
     ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-one-shot", dest="one_shot", action="store_false",
+                    help="skip the one-shot-per-pass comparison")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -58,6 +58,8 @@ enum { SBFWI_RHO_GRID = 0, SBFWI_RHO_NODAL = 1 };
 enum { SBFWI_GRAD_KERNEL = 0, SBFWI_GRAD_EXACT = 1 };
 /* or-ed into the mode of sbfwi_adjoint_gradient: add into grad instead of overwriting */
 enum { SBFWI_GRAD_ACCUMULATE = 0x100 };
+/* sbfwi_forward's ckpt_every: choose the checkpoint interval automatically */
+enum { SBFWI_CKPT_AUTO = -1 };
 
 typedef struct sbfwi_mesh sbfwi_mesh;
 typedef struct sbfwi_model sbfwi_model;
@@ -141,15 +143,24 @@ void sbfwi_destroy_model(sbfwi_model* model);
  *                                  the state at t_{k+1} = (k+1) dt
  *   rec_node    [n_rec]            host; receiver nodes shared by all shots (distinct)
  *   traces      [n_shots][n_rec][K] out: u at the receivers at t_{k+1}
- *   keep        if not NULL, receives a forward state holding the nodal velocities
- *               of every step (Section 4 stores the forward field for the adjoint);
- *               it needs K * n_nodal * n_shots * 8 bytes of device memory
- *               (SBFWI_ENOMEM if that is not available).
+ *   keep        if not NULL, receives a forward state for sbfwi_adjoint_gradient.
+ *   ckpt_every  what that state holds (ignored without keep):
+ *               0   the nodal velocities of every step, as Section 4 stores the
+ *                   forward field for the adjoint: K * n_nodal * n_shots * 8 bytes
+ *                   of device memory;
+ *               c>0 the complete Newmark state before steps c, 2c, ... only
+ *                   (checkpoints); the adjoint recomputes the forward field one
+ *                   window of c steps at a time from them (one more forward solve
+ *                   in time, memory (ceil(K/c) - 1) checkpoints here plus
+ *                   c * n_nodal * n_shots * 8 bytes during the adjoint);
+ *               SBFWI_CKPT_AUTO (-1) picks the c that minimises that memory.
+ *               The traces, and the gradient of the adjoint, are bit for bit the
+ *               same for every ckpt_every.  SBFWI_ENOMEM if the state does not fit.
  *   mem         where src_wavelet and traces live.
  */
 int sbfwi_forward(sbfwi_model* model, int32_t n_shots, const int64_t* src_node,
                   const double* src_wavelet, int32_t n_rec, const int64_t* rec_node, int64_t K,
-                  double* traces, sbfwi_fwdstate** keep, int mem, void* stream);
+                  double* traces, sbfwi_fwdstate** keep, int64_t ckpt_every, int mem, void* stream);
 
 /*
  * sbfwi_misfit -- E = 1/2 sum_{shot,rec} int (d - u)^2 dt (Eq. (misfit)) with the
@@ -195,7 +206,10 @@ int sbfwi_misfit_noalloc(const double* traces, const double* observed, int64_t n
  * rec_node[r] (same sign slot as the forward source) and accumulates
  *     g(node) += dt * sum_s udot_fwd[K-1-m](node, s) * lambdadot^{m+1}(node, s).
  *
- *   fwdstate  from sbfwi_forward(..., keep) on the same model; not consumed.
+ *   fwdstate  from sbfwi_forward(..., keep, ...) on the same model; not consumed.
+ *             If it holds checkpoints, the forward field is recomputed window by
+ *             window (last window first) with the element kernel that wrote them
+ *             (SBFWI_ESTATE if SBFWI_ELEMENT now selects the other one).
  *   residual  [n_shots][n_rec][K] (d - u, as from sbfwi_misfit)
  *   mode      SBFWI_GRAD_KERNEL (the paper's kernel).  SBFWI_GRAD_EXACT returns
  *             SBFWI_EUNSUPPORTED in this build.  With SBFWI_GRAD_ACCUMULATE or-ed
@@ -222,6 +236,37 @@ void sbfwi_destroy_fwdstate(sbfwi_fwdstate* state);
  */
 int sbfwi_profile_enable(int on);
 int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int reset);
+
+/*
+ * Per-level tracing of the one-launch global solve (a diagnostic of this
+ * implementation; the paper does not specify the solver).  While profiling is on,
+ * block 0 of every persistent solve launch reads the global timer after each grid
+ * barrier; slot j accumulates the time between barrier j-1 and barrier j: slots
+ * 0..L-1 are the forward (leaves -> root) levels, L..2L-1 the backward levels
+ * (root -> leaves; the last slot ends when block 0 finishes).  Fills us[min(cap,
+ * 2L)] with the mean microseconds per solve, *n_slots = 2L (0 if nothing was
+ * recorded), *steps = solves recorded; reset != 0 clears the accumulators.
+ * Synchronises the current device.  SBFWI_ESTATE if the trace lives on another
+ * device.
+ */
+int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_t* steps, int reset);
+
+/*
+ * Failure-detection self-test (no counterpart in the paper; a guard of this
+ * implementation).  Every device-side wait of the library is bounded: the grid
+ * barrier between the tree levels of the global solve gives up after a budget of
+ * clock cycles, records SBFWI_ETIMEOUT in a device status word and returns, so a
+ * block that never arrives turns into an error code, not a hung device.  This
+ * call runs that same barrier `rounds` times in a cooperative launch of n_blocks
+ * blocks (64 threads each) of which the last n_absent return without arriving.
+ *   n_absent = 0   every barrier completes; returns SBFWI_OK.
+ *   n_absent > 0   the first barrier times out after about budget_cycles SM
+ *                  cycles; returns SBFWI_ETIMEOUT and the device stays usable.
+ * Synchronous on `stream`.  SBFWI_EINVAL if n_blocks exceeds what can be
+ * co-resident, n_absent is not in [0, n_blocks), budget_cycles is not in
+ * [1e3, 4e9] or rounds is not in [1, 1000].
+ */
+int sbfwi_selftest_barrier(int32_t n_blocks, int32_t n_absent, int64_t budget_cycles, int32_t rounds, void* stream);
 
 #ifdef __cplusplus
 }

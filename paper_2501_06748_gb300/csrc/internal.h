@@ -32,6 +32,15 @@ struct DevBuf {
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
   ~DevBuf() { release(); }
   void release() {
     if (p) cudaFree(p);
@@ -172,7 +181,13 @@ struct FwdState {
   int32_t B = 0, R = 0;
   int64_t K = 0;
   std::vector<int64_t> rec;
-  DevBuf store;      // [K][n_nodal][B] nodal velocities after every step
+  int64_t ckpt_every = 0;       // 0: store holds the velocities of every step
+  int64_t state_doubles = 0;    // size of one checkpoint
+  bool tensor_core_path = false;
+  // ckpt_every == 0: [K][n_nodal][B] nodal velocities after every step;
+  // ckpt_every == c > 0: [ceil(K/c) - 1][state_doubles] Newmark states before steps c, 2c, ...
+  DevBuf store;
+  DevBuf values, nodes;         // wavelets and source nodes, for the recompute (c > 0)
 };
 
 }  // namespace sbfwi

@@ -220,6 +220,31 @@ int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int re
   return SBFWI_OK;
 }
 
+int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_t* steps, int reset) {
+  Profiler& p = profiler();
+  if (n_slots) *n_slots = p.level_acc ? p.level_slots : 0;
+  if (steps) *steps = p.level_steps;
+  if (!p.level_acc) return SBFWI_OK;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != p.level_device) return fail(SBFWI_ESTATE, "the solve trace was recorded on another device");
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  std::vector<unsigned long long> acc(p.level_slots);
+  e = cudaMemcpy(acc.data(), p.level_acc, sizeof(unsigned long long) * p.level_slots, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read solve trace");
+  if (us)
+    for (int k = 0; k < std::min<int>(cap, p.level_slots); ++k)
+      us[k] = p.level_steps ? (double)acc[k] / 1e3 / (double)p.level_steps : 0.0;
+  if (reset) {
+    e = cudaMemset(p.level_acc, 0, sizeof(unsigned long long) * p.level_slots);
+    if (e != cudaSuccess) return cuda_fail(e, "reset solve trace");
+    p.level_steps = 0;
+  }
+  return SBFWI_OK;
+}
+
 const char* sbfwi_last_error(void) { return g_last_error.c_str(); }
 int sbfwi_version(void) { return 100; }
 

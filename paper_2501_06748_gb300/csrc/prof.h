@@ -54,6 +54,36 @@ struct Profiler {
     pending.clear();
   }
   void count(int ph, int64_t n = 1) { launches[ph] += n; }
+
+  // Per-level wall time of the persistent global solve: block 0 stamps the global
+  // timer after every grid barrier and adds the differences (ns) to level_acc
+  // (device, [slots]); one slot per barrier-separated phase, forward levels first.
+  unsigned long long* level_acc = nullptr;
+  int level_slots = 0;
+  int level_device = -1;
+  int64_t level_steps = 0;
+  // a zeroed accumulator of `slots` entries on the current device, or nullptr
+  unsigned long long* level_trace(int slots, cudaStream_t st) {
+    if (!on) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (level_acc && (level_device != dev || level_slots != slots)) {
+      cudaFree(level_acc);
+      level_acc = nullptr;
+    }
+    if (!level_acc) {
+      if (cudaMalloc(&level_acc, sizeof(unsigned long long) * slots) != cudaSuccess) {
+        cudaGetLastError();
+        level_acc = nullptr;
+        return nullptr;
+      }
+      cudaMemsetAsync(level_acc, 0, sizeof(unsigned long long) * slots, st);
+      level_slots = slots;
+      level_device = dev;
+      level_steps = 0;
+    }
+    return level_acc;
+  }
 };
 
 Profiler& profiler();

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "internal.h"
@@ -292,22 +293,51 @@ struct PersistentSolveArgs {
   unsigned* bar;              // [2]: arrival count, generation
   int* status;
   long long budget;
+  unsigned long long* trace;   // nullable: per-level wall time accumulators (block 0)
 };
 
 // the whole boundary solve of one time step: forward pass leaves -> root, then
 // backward pass root -> leaves, one grid barrier between tree levels
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __global__ void __launch_bounds__(256) solve_persistent_kernel(PersistentSolveArgs a) {
   extern __shared__ double sm_p[];
+  const bool stamp = a.trace && blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long t_prev = stamp ? global_ns() : 0ULL;
+  int slot = 0;
+  auto mark = [&]() {
+    if (stamp) {
+      const unsigned long long t = global_ns();
+      a.trace[slot] += t - t_prev;
+      t_prev = t;
+    }
+    ++slot;
+  };
   for (int l = 0; l < a.levels; ++l) {
     for (int t = a.fwd_start[l] + blockIdx.x; t < a.fwd_start[l + 1]; t += gridDim.x)
       solve_forward_task(a.s, a.fwd[t], sm_p);
     if (!grid_barrier(a.bar, a.bar + 1, a.status, a.budget)) return;
+    mark();
   }
   for (int l = a.levels - 1; l >= 0; --l) {
     for (int t = a.bwd_start[l] + blockIdx.x; t < a.bwd_start[l + 1]; t += gridDim.x)
       solve_backward_task(a.s, a.bwd[t], sm_p);
     if (l > 0 && !grid_barrier(a.bar, a.bar + 1, a.status, a.budget)) return;
+    mark();              // the last one: block 0's own finish
   }
+}
+
+// Self-test of the bounded grid barrier: blocks with index >= gridDim.x - absent
+// return at once and never arrive, so with absent > 0 every other block gives up
+// after `budget` cycles and the status reads SBFWI_ETIMEOUT.
+__global__ void barrier_selftest_kernel(unsigned* bar, int* status, long long budget, int absent, int rounds) {
+  if ((int)blockIdx.x >= (int)gridDim.x - absent) return;
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_barrier(bar, bar + 1, status, budget)) return;
 }
 
 // ---------------------------------------------------------------------------
@@ -489,29 +519,93 @@ namespace {
 
 struct RunBuffers {
   DevBuf u, ud, udd, v, ub, udb, uddb, q, fhat, ext, ysep, ybnd, x;
-  DevBuf values, nodes, grad_int;   // grad accumulators [n_nodal][B] (adjoint)
-  DevBuf traces_owned;              // staging for host traces
-  double* traces = nullptr;         // device traces [B][R][K] (owned above or the caller's)
+  DevBuf grad_int;                  // grad accumulators [n_nodal][B] (adjoint)
 };
 
 enum class Mode { Forward, Adjoint };
 
-// K Newmark steps of B shots.  Forward: values = wavelets [B][K] at nodes[0..B-1],
-// receivers nodes[B..B+R-1]; writes traces and (if store) the nodal velocities of
-// every step.  Adjoint: values = residuals [B][R][K] at nodes[0..R-1], injected
-// last sample first; accumulates the correlation with the stored forward
-// velocities into grad [n_nodal][B].
-int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, double* store,
-              const double* fwd_store, cudaStream_t st) {
+// The time loop of B shots over K Newmark steps, resumable over windows of steps.
+// Forward: values = wavelets [B][K] at nodes[0..B-1], receivers nodes[B..B+R-1];
+// writes traces and (if `store`) the nodal velocities of every step it runs.
+// Adjoint: values = residuals [B][R][K] at nodes[0..R-1], injected last sample
+// first; accumulates the correlation with the forward velocities in `fwd` into
+// grad_int [n_nodal][B].
+//
+// run(k0, k1) takes steps k0..k1-1 and ends with the back-substitution of step
+// k1-1, so between two windows the state is the complete Newmark state after
+// step k0-1: {u or v, u', u''} of the interior and {u, u', u''} of the boundary
+// nodes.  A window that starts at k0 > 0 first runs the forward sweep of step k0
+// from that state.  Splitting the fused element launch at a window edge gives the
+// same values bit for bit (the two halves compute exactly what the fused launch
+// does), so a run cut into windows, or resumed from a saved state, reproduces the
+// uncut run.
+struct Stepper {
+  Model& md;
+  const Mode mode;
+  const int B, R;
+  const int64_t K;
+  RunBuffers& rb;
+  const cudaStream_t st;
+  // forward: velocities of step k go to store + (k - store_k0) * n_nodal * B
+  double* store = nullptr;
+  int64_t store_k0 = 0;
+  // adjoint: forward velocities of step j are read at fwd + (j - fwd_k0) * n_nodal * B
+  const double* fwd = nullptr;
+  int64_t fwd_k0 = 0;
+  // source values and nodes (forward: wavelets [B][K], nodes = B sources then R
+  // receivers; adjoint: residuals [B][R][K], nodes = R receivers) and the device
+  // traces [B][R][K] (forward with R > 0)
+  const double* values = nullptr;
+  const int64_t* nodes = nullptr;
+  double* traces = nullptr;
+
+  Stepper(Model& m, Mode mo, int b, int64_t k, int r, RunBuffers& buffers, cudaStream_t s)
+      : md(m), mode(mo), B(b), R(r), K(k), rb(buffers), st(s) {}
+
+  int init();
+  int zero_state();
+  int run(int64_t k0, int64_t k1);
+  int check_status();
+  bool tensor_core_path() const { return use_tc; }
+  // the Newmark state between windows, as one flat array of state_doubles() values
+  int64_t state_doubles() const;
+  int save_state(double* dst);
+  int restore_state(const double* src);
+
+ private:
+  int nb = 0, n = 0;
+  int64_t E = 0, N = 0, np = 0, nint = 0;
+  bool use_tc = false, persistent = false;
+  ElemStepArgs ea;
+  SolveArgs sa;
+  PersistentSolveArgs pa;
+  BoundaryArgs ba;
+  const Task* ftasks = nullptr;
+  const Task* btasks = nullptr;
+  size_t fwd_smem = 0, bwd_smem = 0, p_smem = 0, e_smem = 0;
+  int e_threads = 0, p_grid = 0;
+  unsigned e_blocks = 0, b_blocks = 0;
+  DevBuf bar, pstatus;
+  std::vector<DevBuf*> state_bufs() const;
+  int element_launch(int down, int up, int64_t done_step);
+  int solve();
+};
+
+int Stepper::init() {
   const Mesh& m = *md.mesh;
   const Tree& t = m.tree;
-  const int nb = md.nb, n = md.n;
-  const int64_t E = md.E, N = md.N, np = m.n_nodal, nint = m.n_int;
+  nb = md.nb; n = md.n;
+  E = md.E; N = md.N; np = m.n_nodal; nint = m.n_int;
   const int64_t si = nint * B, sb = N * B;
-  SBFWI_CUDA(rb.u.alloc(sizeof(double) * si));
+  // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
+  // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
+  const char* elem_env = std::getenv("SBFWI_ELEMENT");
+  use_tc = md.tc_ready && tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
+  SBFWI_CUDA(rb.u.alloc(sizeof(double) * (use_tc ? 1 : si)));     // the tensor-core path carries v, not u
   SBFWI_CUDA(rb.ud.alloc(sizeof(double) * si));
   SBFWI_CUDA(rb.udd.alloc(sizeof(double) * si));
   SBFWI_CUDA(rb.q.alloc(sizeof(double) * si));
+  if (use_tc) SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
   SBFWI_CUDA(rb.ub.alloc(sizeof(double) * sb));
   SBFWI_CUDA(rb.udb.alloc(sizeof(double) * sb));
   SBFWI_CUDA(rb.uddb.alloc(sizeof(double) * sb));
@@ -520,34 +614,25 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   SBFWI_CUDA(rb.fhat.alloc(sizeof(double) * E * nb * B));
   SBFWI_CUDA(rb.ysep.alloc(sizeof(double) * std::max<int64_t>(t.sep_rows, 1) * B));
   SBFWI_CUDA(rb.ybnd.alloc(sizeof(double) * std::max<int64_t>(t.bnd_rows, 1) * B));
-  for (DevBuf* b : {&rb.u, &rb.ud, &rb.udd, &rb.q, &rb.ub, &rb.udb, &rb.uddb, &rb.ext, &rb.x, &rb.fhat})
-    SBFWI_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
-  // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
-  // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
-  const char* elem_env = std::getenv("SBFWI_ELEMENT");
-  const bool use_tc = md.tc_ready && tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
-  if (use_tc) {
-    SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
-    SBFWI_CUDA(cudaMemsetAsync(rb.v.p, 0, rb.v.bytes, st));
-  }
   if (mode == Mode::Adjoint) {
     SBFWI_CUDA(rb.grad_int.alloc(sizeof(double) * np * B));
     SBFWI_CUDA(cudaMemsetAsync(rb.grad_int.p, 0, rb.grad_int.bytes, st));
   }
+  int rc = zero_state();
+  if (rc) return rc;
   if (md.tasks.shots != B) {
-    int rc = build_level_tasks(md, B);
+    rc = build_level_tasks(md, B);
     if (rc) return rc;
   }
   int smax = 0, bmax = 0;
   for (const TreeNodeDev& r : t.nodes) { smax = std::max(smax, r.s); bmax = std::max(bmax, r.b); }
-  const size_t fwd_smem = sizeof(double) * (size_t)smax * B;
-  const size_t bwd_smem = sizeof(double) * (size_t)(smax + bmax) * B;
+  fwd_smem = sizeof(double) * (size_t)smax * B;
+  bwd_smem = sizeof(double) * (size_t)(smax + bmax) * B;
   if (bwd_smem > 48 * 1024)
     SBFWI_CUDA(cudaFuncSetAttribute(solve_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem));
   if (fwd_smem > 48 * 1024)
     SBFWI_CUDA(cudaFuncSetAttribute(solve_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem));
 
-  ElemStepArgs ea;
   ea.nb = nb; ea.n = n; ea.B = B; ea.E = E;
   ea.epc = std::max(1, 128 / (nb * B));
   ea.a0 = md.a0; ea.a1 = md.a1; ea.a2 = md.a2; ea.c1 = md.c1; ea.c2 = md.c2; ea.dt = md.dt;
@@ -555,21 +640,20 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   ea.u = rb.u.as<double>(); ea.ud = rb.ud.as<double>(); ea.udd = rb.udd.as<double>();
   ea.ub = rb.ub.as<double>(); ea.udb = rb.udb.as<double>(); ea.uddb = rb.uddb.as<double>();
   ea.q = rb.q.as<double>(); ea.fhat = rb.fhat.as<double>();
-  const int e_threads = ea.epc * nb * B;
-  const unsigned e_blocks = (unsigned)((E + ea.epc - 1) / ea.epc);
-  const size_t e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
+  e_threads = ea.epc * nb * B;
+  e_blocks = (unsigned)((E + ea.epc - 1) / ea.epc);
+  e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
   if (e_smem > 48 * 1024)
     SBFWI_CUDA(cudaFuncSetAttribute(element_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem));
 
-  SolveArgs sa;
   const MeshDevice& mdev = md.dev();
   sa.sep_nodes = mdev.sep_nodes.as<int32_t>(); sa.bnd_nodes = mdev.bnd_nodes.as<int32_t>();
   sa.src0 = mdev.src0.as<int32_t>(); sa.src1 = mdev.src1.as<int32_t>(); sa.factors = md.factors.as<double>();
   sa.fhat = rb.fhat.as<double>(); sa.ext = rb.ext.as<double>();
   sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
   sa.nb = nb; sa.B = B;
-  const Task* ftasks = md.tasks.fwd.as<Task>();
-  const Task* btasks = md.tasks.bwd.as<Task>();
+  ftasks = md.tasks.fwd.as<Task>();
+  btasks = md.tasks.bwd.as<Task>();
 
   // one cooperative persistent launch per time step for the whole tree, unless the
   // device cannot launch cooperatively or SBFWI_SOLVE=levels asks for one launch per level
@@ -577,15 +661,12 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
   SBFWI_CUDA(cudaGetDevice(&device));
   SBFWI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
   SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-  const size_t p_smem = std::max(fwd_smem, bwd_smem);
+  p_smem = std::max(fwd_smem, bwd_smem);
   if (p_smem > 48 * 1024)
     SBFWI_CUDA(cudaFuncSetAttribute(solve_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem));
   SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_persistent_kernel, 256, p_smem));
   const char* solve_env = std::getenv("SBFWI_SOLVE");
-  const bool persistent = coop && per_sm > 0 && !(solve_env && std::strcmp(solve_env, "levels") == 0);
-  DevBuf bar, pstatus;
-  PersistentSolveArgs pa;
-  int p_grid = 0;
+  persistent = coop && per_sm > 0 && !(solve_env && std::strcmp(solve_env, "levels") == 0);
   if (persistent) {
     SBFWI_CUDA(bar.alloc(2 * sizeof(unsigned)));
     SBFWI_CUDA(pstatus.alloc(sizeof(int)));
@@ -597,95 +678,147 @@ int run_steps(Model& md, Mode mode, int B, int64_t K, int R, RunBuffers& rb, dou
     pa.levels = t.levels;
     pa.bar = bar.as<unsigned>(); pa.status = pstatus.as<int>();
     pa.budget = 4000000000LL;            // ~2 s at 2 GHz
+    pa.trace = nullptr;
     p_grid = std::min(per_sm, 4) * sms;
     p_grid = std::max(1, std::min(p_grid, md.tasks.max_level_tasks));
   }
 
-  BoundaryArgs ba;
   ba.N = N; ba.B = B; ba.R = 0;
   ba.K = K;
   ba.a0 = md.a0; ba.a1 = md.a1; ba.a2 = md.a2; ba.c1 = md.c1; ba.c2 = md.c2; ba.dt = md.dt;
   ba.x = rb.x.as<double>(); ba.ub = rb.ub.as<double>(); ba.udb = rb.udb.as<double>(); ba.uddb = rb.uddb.as<double>();
   ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
-  const unsigned b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
+  b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
+  return SBFWI_OK;
+}
 
+int Stepper::zero_state() {
+  for (DevBuf* b : {&rb.u, &rb.ud, &rb.udd, &rb.v, &rb.q, &rb.ub, &rb.udb, &rb.uddb, &rb.ext, &rb.x, &rb.fhat})
+    if (b->p) SBFWI_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
+  return SBFWI_OK;
+}
+
+std::vector<DevBuf*> Stepper::state_bufs() const {
+  if (use_tc) return {&rb.v, &rb.ud, &rb.udd, &rb.ub, &rb.udb, &rb.uddb};
+  return {&rb.u, &rb.ud, &rb.udd, &rb.ub, &rb.udb, &rb.uddb};
+}
+
+int64_t Stepper::state_doubles() const {
+  int64_t tot = 0;
+  for (DevBuf* b : state_bufs()) tot += (int64_t)(b->bytes / sizeof(double));
+  return tot;
+}
+
+int Stepper::save_state(double* dst) {
+  for (DevBuf* b : state_bufs()) {
+    SBFWI_CUDA(cudaMemcpyAsync(dst, b->p, b->bytes, cudaMemcpyDeviceToDevice, st));
+    dst += b->bytes / sizeof(double);
+  }
+  return SBFWI_OK;
+}
+
+int Stepper::restore_state(const double* src) {
+  int rc = zero_state();
+  if (rc) return rc;
+  for (DevBuf* b : state_bufs()) {
+    SBFWI_CUDA(cudaMemcpyAsync(b->p, src, b->bytes, cudaMemcpyDeviceToDevice, st));
+    src += b->bytes / sizeof(double);
+  }
+  return SBFWI_OK;
+}
+
+int Stepper::element_launch(int down, int up, int64_t done_step) {
+  // done_step: the step whose back-substitution runs in this launch (if down)
   Profiler& prof = profiler();
-  auto element_launch = [&](int down, int up, int64_t done_step) -> int {
-    // done_step: the step whose back-substitution runs in this launch (if down)
-    ea.do_down = down; ea.do_up = up;
-    ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr;
-    if (down && mode == Mode::Forward && store) ea.store_int = store + done_step * np * B;
-    if (down && mode == Mode::Adjoint) {
-      ea.fwd_int = fwd_store + (K - 1 - done_step) * np * B;
-      ea.grad_int = rb.grad_int.as<double>();
-    }
-    prof.begin(kPhaseElement, st);
-    if (use_tc)
-      tc_element_launch(md, B, down, up, ea.u, ea.ud, ea.udd, rb.v.as<double>(), ea.ub, ea.udb, ea.uddb, ea.q, ea.fhat,
-                        ea.store_int, ea.fwd_int, ea.grad_int, st);
-    else
-      element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
-    prof.end(kPhaseElement, st);
-    prof.count(kPhaseElement);
-    return SBFWI_OK;
-  };
+  ea.do_down = down; ea.do_up = up;
+  ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr;
+  if (down && mode == Mode::Forward && store) ea.store_int = store + (done_step - store_k0) * np * B;
+  if (down && mode == Mode::Adjoint) {
+    ea.fwd_int = fwd + (K - 1 - done_step - fwd_k0) * np * B;
+    ea.grad_int = rb.grad_int.as<double>();
+  }
+  prof.begin(kPhaseElement, st);
+  if (use_tc)
+    tc_element_launch(md, B, down, up, ea.u, ea.ud, ea.udd, rb.v.as<double>(), ea.ub, ea.udb, ea.uddb, ea.q, ea.fhat,
+                      ea.store_int, ea.fwd_int, ea.grad_int, st);
+  else
+    element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
+  prof.end(kPhaseElement, st);
+  prof.count(kPhaseElement);
+  return SBFWI_OK;
+}
 
-  for (int64_t k = 0; k < K; ++k) {
-    if (k > 0) element_launch(1, 1, k - 1);
+int Stepper::solve() {
+  Profiler& prof = profiler();
+  const Tree& t = md.mesh->tree;
+  prof.begin(kPhaseSolve, st);
+  if (persistent) {
+    pa.trace = prof.level_trace(2 * t.levels, st);
+    if (pa.trace) ++prof.level_steps;
+    void* kargs[] = {&pa};
+    SBFWI_CUDA(cudaLaunchCooperativeKernel((const void*)solve_persistent_kernel, dim3(p_grid), dim3(256), kargs,
+                                           p_smem, st));
+    prof.count(kPhaseSolve);
+  } else {
+    for (int l = 0; l < t.levels; ++l) {
+      const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
+      if (cnt == 0) continue;
+      sa.tasks = ftasks + md.tasks.fwd_start[l];
+      solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
+      prof.count(kPhaseSolve);
+    }
+    for (int l = t.levels - 1; l >= 0; --l) {
+      const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
+      if (cnt == 0) continue;
+      sa.tasks = btasks + md.tasks.bwd_start[l];
+      solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
+      prof.count(kPhaseSolve);
+    }
+  }
+  prof.end(kPhaseSolve, st);
+  return SBFWI_OK;
+}
+
+int Stepper::run(int64_t k0, int64_t k1) {
+  Profiler& prof = profiler();
+  if (k0 < 0 || k1 > K || k0 >= k1) return fail(SBFWI_EINVAL, "bad step window");
+  // the forward sweep of step k0 (at k0 = 0 the zero state gives f_hat = 0)
+  if (k0 > 0) element_launch(0, 1, k0 - 1);
+  for (int64_t k = k0; k < k1; ++k) {
+    if (k > k0) element_launch(1, 1, k - 1);
     // sources of step k
     if (mode == Mode::Forward) {
-      sources_kernel<<<(B + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, 1, rb.nodes.as<int64_t>(),
-                                                      rb.values.as<double>(), K, k, 1);
+      sources_kernel<<<(B + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, 1, nodes, values, K, k, 1);
       prof.count(kPhaseOther);
     } else if (R > 0) {
-      sources_kernel<<<(B * R + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, R, rb.nodes.as<int64_t>(),
-                                                          rb.values.as<double>(), K, K - 1 - k, 0);
+      sources_kernel<<<(B * R + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, R, nodes, values, K, K - 1 - k, 0);
       prof.count(kPhaseOther);
     }
-    prof.begin(kPhaseSolve, st);
-    if (persistent) {
-      void* kargs[] = {&pa};
-      SBFWI_CUDA(cudaLaunchCooperativeKernel((const void*)solve_persistent_kernel, dim3(p_grid), dim3(256), kargs,
-                                             p_smem, st));
-      prof.count(kPhaseSolve);
-    } else {
-      for (int l = 0; l < t.levels; ++l) {
-        const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
-        if (cnt == 0) continue;
-        sa.tasks = ftasks + md.tasks.fwd_start[l];
-        solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
-        prof.count(kPhaseSolve);
-      }
-      for (int l = t.levels - 1; l >= 0; --l) {
-        const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
-        if (cnt == 0) continue;
-        sa.tasks = btasks + md.tasks.bwd_start[l];
-        solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
-        prof.count(kPhaseSolve);
-      }
-    }
-    prof.end(kPhaseSolve, st);
+    solve();
     ba.k = k;
     if (mode == Mode::Forward) {
       ba.R = R;
-      ba.rec = rb.nodes.as<int64_t>() + B;
-      ba.traces = R > 0 ? rb.traces : nullptr;
-      ba.store_b = store ? store + k * np * B + nint * B : nullptr;
+      ba.rec = nodes + B;
+      ba.traces = R > 0 ? traces : nullptr;
+      ba.store_b = store ? store + (k - store_k0) * np * B + nint * B : nullptr;
     } else {
-      ba.fwd_b = fwd_store + (K - 1 - k) * np * B + nint * B;
+      ba.fwd_b = fwd + (K - 1 - k - fwd_k0) * np * B + nint * B;
       ba.grad_b = rb.grad_int.as<double>() + nint * B;
     }
     boundary_update_kernel<<<b_blocks, 256, 0, st>>>(ba);
     prof.count(kPhaseOther);
   }
-  element_launch(1, 0, K - 1);
+  element_launch(1, 0, k1 - 1);
   SBFWI_CUDA(cudaGetLastError());
-  if (persistent) {
-    int code = 0;
-    SBFWI_CUDA(cudaMemcpyAsync(&code, pstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SBFWI_CUDA(cudaStreamSynchronize(st));
-    if (code) return fail(SBFWI_ETIMEOUT, "a grid barrier of the global solve timed out");
-  }
+  return SBFWI_OK;
+}
+
+int Stepper::check_status() {
+  if (!persistent) return SBFWI_OK;
+  int code = 0;
+  SBFWI_CUDA(cudaMemcpyAsync(&code, pstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  if (code) return fail(SBFWI_ETIMEOUT, "a grid barrier of the global solve timed out");
   return SBFWI_OK;
 }
 
@@ -738,7 +871,8 @@ void sbfwi_destroy_model(sbfwi_model* m) { delete m; }
 void sbfwi_destroy_fwdstate(sbfwi_fwdstate* s) { delete s; }
 
 int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, const double* src_wavelet, int32_t n_rec,
-                  const int64_t* rec_node, int64_t K, double* traces, sbfwi_fwdstate** keep, int mem, void* stream) {
+                  const int64_t* rec_node, int64_t K, double* traces, sbfwi_fwdstate** keep, int64_t ckpt_every,
+                  int mem, void* stream) {
   if (keep) *keep = nullptr;
   if (!md) return fail(SBFWI_EINVAL, "model is NULL");
   if (n_shots < 1 || n_shots > kMaxShots) return fail(SBFWI_EINVAL, "n_shots must be in 1..16");
@@ -746,6 +880,7 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
   if (n_rec < 0 || (n_rec > 0 && (!rec_node || !traces))) return fail(SBFWI_EINVAL, "receivers need rec_node and traces");
   if (!src_node || !src_wavelet) return fail(SBFWI_EINVAL, "NULL source arrays");
   if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  if (ckpt_every < SBFWI_CKPT_AUTO) return fail(SBFWI_EINVAL, "ckpt_every must be >= -1");
   const int64_t N = md->N;
   for (int s = 0; s < n_shots; ++s)
     if (src_node[s] < 0 || src_node[s] >= N) return fail(SBFWI_EINVAL, "source node out of range");
@@ -757,39 +892,76 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int B = n_shots;
   const int64_t np = md->mesh->n_nodal;
-  RunBuffers rb;
-  SBFWI_CUDA(rb.values.alloc(sizeof(double) * B * K));
-  SBFWI_CUDA(cudaMemcpyAsync(rb.values.p, src_wavelet, sizeof(double) * B * K,
+  DevBuf values, nodes, traces_owned;
+  SBFWI_CUDA(values.alloc(sizeof(double) * B * K));
+  SBFWI_CUDA(cudaMemcpyAsync(values.p, src_wavelet, sizeof(double) * B * K,
                              mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  std::vector<int64_t> nodes(src_node, src_node + B);
-  nodes.insert(nodes.end(), rec_node, rec_node + n_rec);
-  SBFWI_CUDA(rb.nodes.alloc(sizeof(int64_t) * nodes.size()));
-  SBFWI_CUDA(cudaMemcpyAsync(rb.nodes.p, nodes.data(), sizeof(int64_t) * nodes.size(), cudaMemcpyHostToDevice, st));
+  std::vector<int64_t> nv(src_node, src_node + B);
+  nv.insert(nv.end(), rec_node, rec_node + n_rec);
+  SBFWI_CUDA(nodes.alloc(sizeof(int64_t) * nv.size()));
+  SBFWI_CUDA(cudaMemcpyAsync(nodes.p, nv.data(), sizeof(int64_t) * nv.size(), cudaMemcpyHostToDevice, st));
   const int64_t ntr = (int64_t)B * n_rec * K;
+  double* dtraces = nullptr;
   if (ntr > 0) {
     if (mem == SBFWI_MEM_DEVICE) {
-      rb.traces = traces;             // written in place
+      dtraces = traces;               // written in place
     } else {
-      SBFWI_CUDA(rb.traces_owned.alloc(sizeof(double) * ntr));
-      rb.traces = rb.traces_owned.as<double>();
+      SBFWI_CUDA(traces_owned.alloc(sizeof(double) * ntr));
+      dtraces = traces_owned.as<double>();
     }
   }
-  sbfwi_fwdstate* fs = nullptr;
+  RunBuffers rb;
+  Stepper f(*md, Mode::Forward, B, K, n_rec, rb, st);
+  f.values = values.as<double>(); f.nodes = nodes.as<int64_t>(); f.traces = dtraces;
+  int rc = f.init();
+  if (rc) return rc;
+  std::unique_ptr<sbfwi_fwdstate> fs;
+  int64_t c = 0;
   if (keep) {
-    fs = new sbfwi_fwdstate();
+    fs.reset(new sbfwi_fwdstate());
     fs->model = md; fs->B = B; fs->R = n_rec; fs->K = K;
     fs->rec.assign(rec_node, rec_node + n_rec);
-    cudaError_t e = fs->store.alloc(sizeof(double) * (size_t)K * np * B);
+    const int64_t sd = f.state_doubles();
+    c = ckpt_every;
+    if (c == SBFWI_CKPT_AUTO) {
+      // memory (K/c) * sd + c * np * B is least at c = sqrt(K sd / (np B))
+      c = (int64_t)std::ceil(std::sqrt((double)K * (double)sd / ((double)np * B)));
+    }
+    c = std::min<int64_t>(c, K);
+    fs->ckpt_every = c;
+    fs->state_doubles = sd;
+    fs->tensor_core_path = f.tensor_core_path();
+    cudaError_t e = cudaSuccess;
+    double gb = 0;
+    if (c == 0) {
+      gb = (double)K * np * B * 8 / 1e9;
+      e = fs->store.alloc(sizeof(double) * (size_t)K * np * B);
+    } else {
+      const int64_t nseg = (K + c - 1) / c;
+      gb = (double)(nseg - 1) * sd * 8 / 1e9;
+      if (nseg > 1) e = fs->store.alloc(sizeof(double) * (size_t)(nseg - 1) * sd);
+    }
     if (e != cudaSuccess) {
-      delete fs;
       cudaGetLastError();
-      return fail(SBFWI_ENOMEM, "not enough device memory to keep the forward velocities (" +
-                                    std::to_string((double)K * np * B * 8 / 1e9) + " GB)");
+      return fail(SBFWI_ENOMEM, "not enough device memory to keep the forward state (" + std::to_string(gb) + " GB)");
     }
   }
-  int rc = run_steps(*md, Mode::Forward, B, K, n_rec, rb, fs ? fs->store.as<double>() : nullptr, nullptr, st);
+  if (!keep || c == 0) {
+    f.store = fs ? fs->store.as<double>() : nullptr;
+    rc = f.run(0, K);
+  } else {
+    // checkpoints: the Newmark state before steps c, 2c, ... (before step 0 it is zero)
+    const int64_t sd = fs->state_doubles;
+    for (int64_t a = 0; a < K && rc == SBFWI_OK; a += c) {
+      if (a > 0) rc = f.save_state(fs->store.as<double>() + (a / c - 1) * sd);
+      if (rc == SBFWI_OK) rc = f.run(a, std::min(K, a + c));
+    }
+    fs->values = std::move(values);
+    fs->nodes = std::move(nodes);
+  }
+  if (rc == SBFWI_OK) rc = f.check_status();
   if (rc == SBFWI_OK && ntr > 0 && mem == SBFWI_MEM_HOST) {
-    cudaError_t e = cudaMemcpyAsync(traces, rb.traces, sizeof(double) * ntr, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(traces, dtraces, sizeof(double) * ntr, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "copy traces");
   }
   if (rc == SBFWI_OK) {
@@ -797,8 +969,8 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     if (e != cudaSuccess) rc = cuda_fail(e, "forward solve");
   }
   profiler().resolve();
-  if (rc != SBFWI_OK) { delete fs; return rc; }
-  if (keep) *keep = fs;
+  if (rc != SBFWI_OK) return rc;
+  if (keep) *keep = fs.release();
   return SBFWI_OK;
 }
 
@@ -814,15 +986,52 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int B = fs->B, R = fs->R;
   const int64_t K = fs->K, np = md->mesh->n_nodal;
-  RunBuffers rb;
+  DevBuf values, nodes;
   const int64_t nres = (int64_t)B * R * K;
-  SBFWI_CUDA(rb.values.alloc(sizeof(double) * std::max<int64_t>(nres, 1)));
+  SBFWI_CUDA(values.alloc(sizeof(double) * std::max<int64_t>(nres, 1)));
   if (nres > 0)
-    SBFWI_CUDA(cudaMemcpyAsync(rb.values.p, residual, sizeof(double) * nres,
+    SBFWI_CUDA(cudaMemcpyAsync(values.p, residual, sizeof(double) * nres,
                                mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-  SBFWI_CUDA(rb.nodes.alloc(sizeof(int64_t) * std::max<size_t>(fs->rec.size(), 1)));
-  if (R > 0) SBFWI_CUDA(cudaMemcpyAsync(rb.nodes.p, fs->rec.data(), sizeof(int64_t) * R, cudaMemcpyHostToDevice, st));
-  int rc = run_steps(*md, Mode::Adjoint, B, K, R, rb, nullptr, fs->store.as<double>(), st);
+  SBFWI_CUDA(nodes.alloc(sizeof(int64_t) * std::max<size_t>(fs->rec.size(), 1)));
+  if (R > 0) SBFWI_CUDA(cudaMemcpyAsync(nodes.p, fs->rec.data(), sizeof(int64_t) * R, cudaMemcpyHostToDevice, st));
+  RunBuffers rb;
+  Stepper adj(*md, Mode::Adjoint, B, K, R, rb, st);
+  adj.values = values.as<double>(); adj.nodes = nodes.as<int64_t>();
+  int rc = adj.init();
+  if (rc) return rc;
+  const int64_t c = fs->ckpt_every;
+  if (c == 0) {
+    adj.fwd = fs->store.as<double>();
+    rc = adj.run(0, K);
+  } else {
+    // recompute the forward velocities one window of c steps at a time from the
+    // checkpoints, last window first, and run the adjoint steps that pair with them
+    RunBuffers rf;
+    Stepper fwd(*md, Mode::Forward, B, K, 0, rf, st);
+    fwd.values = fs->values.as<double>(); fwd.nodes = fs->nodes.as<int64_t>();
+    rc = fwd.init();
+    if (rc) return rc;
+    if (fwd.tensor_core_path() != fs->tensor_core_path || fwd.state_doubles() != fs->state_doubles)
+      return fail(SBFWI_ESTATE, "the element kernel differs from the one that wrote the checkpoints");
+    DevBuf window;
+    cudaError_t e = window.alloc(sizeof(double) * (size_t)c * np * B);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SBFWI_ENOMEM, "not enough device memory for one recompute window (" +
+                                    std::to_string((double)c * np * B * 8 / 1e9) + " GB)");
+    }
+    const int64_t nseg = (K + c - 1) / c;
+    for (int64_t seg = nseg - 1; seg >= 0 && rc == SBFWI_OK; --seg) {
+      const int64_t a = seg * c, b = std::min(K, a + c);
+      rc = seg == 0 ? fwd.zero_state() : fwd.restore_state(fs->store.as<double>() + (seg - 1) * fs->state_doubles);
+      fwd.store = window.as<double>(); fwd.store_k0 = a;
+      if (rc == SBFWI_OK) rc = fwd.run(a, b);
+      adj.fwd = window.as<double>(); adj.fwd_k0 = a;
+      if (rc == SBFWI_OK) rc = adj.run(K - b, K - a);
+    }
+    if (rc == SBFWI_OK) rc = fwd.check_status();
+  }
+  if (rc == SBFWI_OK) rc = adj.check_status();
   if (rc) return rc;
   DevBuf gn, gout;
   const int64_t nout = (md->rho_kind == SBFWI_RHO_GRID) ? md->gx * md->gy : np;
@@ -890,6 +1099,37 @@ int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double
   if (mem == SBFWI_MEM_HOST && residual_out && n > 0)
     SBFWI_CUDA(cudaMemcpyAsync(residual_out, res, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
   SBFWI_CUDA(cudaStreamSynchronize(st));
+  return SBFWI_OK;
+}
+
+int sbfwi_selftest_barrier(int32_t n_blocks, int32_t n_absent, int64_t budget_cycles, int32_t rounds, void* stream) {
+  if (n_blocks < 1 || n_absent < 0 || n_absent >= n_blocks) return fail(SBFWI_EINVAL, "need 0 <= n_absent < n_blocks");
+  if (budget_cycles < 1000 || budget_cycles > 4000000000LL) return fail(SBFWI_EINVAL, "budget_cycles must be in [1e3, 4e9]");
+  if (rounds < 1 || rounds > 1000) return fail(SBFWI_EINVAL, "rounds must be in 1..1000");
+  if (!have_device()) return fail(SBFWI_ECUDA, "no CUDA device");
+  int device = 0, coop = 0, sms = 0, per_sm = 0;
+  SBFWI_CUDA(cudaGetDevice(&device));
+  SBFWI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+  SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_selftest_kernel, 64, 0));
+  if (!coop) return fail(SBFWI_EUNSUPPORTED, "device cannot launch cooperatively");
+  if ((int64_t)n_blocks > (int64_t)per_sm * sms) return fail(SBFWI_EINVAL, "n_blocks exceeds the co-resident limit");
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevBuf bar, status;
+  SBFWI_CUDA(bar.alloc(2 * sizeof(unsigned)));
+  SBFWI_CUDA(status.alloc(sizeof(int)));
+  SBFWI_CUDA(cudaMemsetAsync(bar.p, 0, bar.bytes, st));
+  SBFWI_CUDA(cudaMemsetAsync(status.p, 0, status.bytes, st));
+  unsigned* barp = bar.as<unsigned>();
+  int* statusp = status.as<int>();
+  long long budget = budget_cycles;
+  int absent = n_absent, r = rounds;
+  void* kargs[] = {&barp, &statusp, &budget, &absent, &r};
+  SBFWI_CUDA(cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(n_blocks), dim3(64), kargs, 0, st));
+  int code = 0;
+  SBFWI_CUDA(cudaMemcpyAsync(&code, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  if (code) return fail(SBFWI_ETIMEOUT, "grid barrier self-test: a block did not arrive within the budget");
   return SBFWI_OK;
 }
 

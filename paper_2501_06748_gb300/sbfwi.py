@@ -20,6 +20,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 RHO_GRID, RHO_NODAL = 0, 1
 GRAD_KERNEL, GRAD_EXACT = 0, 1
 GRAD_ACCUMULATE = 0x100
+CKPT_AUTO = -1
 PHASES = ("setup", "element", "solve", "other")
 
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE",
@@ -48,7 +49,7 @@ def _load():
     lib.sbfwi_set_model.argtypes = [P(VP), VP, D, VP, ctypes.c_int, I64, I64, D, D, D, D, D, ctypes.c_int, VP]
     lib.sbfwi_destroy_model.argtypes = [VP]
     lib.sbfwi_destroy_model.restype = None
-    lib.sbfwi_forward.argtypes = [VP, I32, pi64, VP, I32, pi64, I64, VP, P(VP), ctypes.c_int, VP]
+    lib.sbfwi_forward.argtypes = [VP, I32, pi64, VP, I32, pi64, I64, VP, P(VP), I64, ctypes.c_int, VP]
     lib.sbfwi_misfit.argtypes = [VP, VP, I64, D, pd, VP, ctypes.c_int, VP]
     lib.sbfwi_adjoint_gradient.argtypes = [VP, VP, VP, ctypes.c_int, VP, ctypes.c_int, VP]
     lib.sbfwi_destroy_fwdstate.argtypes = [VP]
@@ -57,6 +58,10 @@ def _load():
     lib.sbfwi_misfit_noalloc.restype = ctypes.c_int
     lib.sbfwi_profile_enable.argtypes = [ctypes.c_int]
     lib.sbfwi_profile_read.argtypes = [pd, pi64, pi64, ctypes.c_int]
+    lib.sbfwi_profile_solve_levels.argtypes = [pd, I32, P(I32), pi64, ctypes.c_int]
+    lib.sbfwi_profile_solve_levels.restype = ctypes.c_int
+    lib.sbfwi_selftest_barrier.argtypes = [I32, I32, I64, I32, VP]
+    lib.sbfwi_selftest_barrier.restype = ctypes.c_int
     for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
                  "sbfwi_adjoint_gradient", "sbfwi_profile_enable", "sbfwi_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
@@ -87,6 +92,18 @@ def profile_read(reset: bool = False) -> dict:
     la = np.zeros(4, dtype=np.int64)
     _check(_lib.sbfwi_profile_read(_dptr(ms), _iptr(iv), _iptr(la), 1 if reset else 0))
     return {ph: {"ms": float(ms[k]), "intervals": int(iv[k]), "launches": int(la[k])} for k, ph in enumerate(PHASES)}
+
+
+def profile_solve_levels(reset: bool = False):
+    """Mean wall time (us) of every barrier-separated phase of the one-launch global
+    solve while profiling was on: forward levels (leaves -> root), then backward
+    levels (root -> leaves).  Returns (array of 2L values, solves recorded)."""
+    cap = 256
+    us = np.zeros(cap)
+    n = ctypes.c_int32(0)
+    steps = ctypes.c_int64(0)
+    _check(_lib.sbfwi_profile_solve_levels(_dptr(us), cap, ctypes.byref(n), ctypes.byref(steps), 1 if reset else 0))
+    return us[:n.value].copy(), int(steps.value)
 
 
 def _is_torch_cuda(x) -> bool:
@@ -193,8 +210,10 @@ class FwdState:
             self._h = None
 
 
-def forward(model: Model, src_nodes, wavelets, rec_nodes, keep=True, traces_out=None):
-    """Forward solve; returns (traces [B][R][K], FwdState or None)."""
+def forward(model: Model, src_nodes, wavelets, rec_nodes, keep=True, traces_out=None, ckpt_every=0):
+    """Forward solve; returns (traces [B][R][K], FwdState or None).  With ``keep``,
+    ``ckpt_every`` = 0 stores the velocities of every step for the adjoint, c > 0 keeps
+    checkpoints every c steps (recomputed in the adjoint), CKPT_AUTO picks c."""
     src = _i64_host(src_nodes)
     rec = _i64_host(rec_nodes)
     w = _Arr(wavelets)
@@ -210,7 +229,8 @@ def forward(model: Model, src_nodes, wavelets, rec_nodes, keep=True, traces_out=
     mem = _same_mem(w, t)
     h = ctypes.c_void_p()
     _check(_lib.sbfwi_forward(model._h, B, _iptr(src), w.ptr, int(rec.shape[0]), _iptr(rec), K, t.ptr,
-                              ctypes.byref(h) if keep else None, mem, w.stream if mem == MEM_DEVICE else t.stream))
+                              ctypes.byref(h) if keep else None, int(ckpt_every), mem,
+                              w.stream if mem == MEM_DEVICE else t.stream))
     st = FwdState(h, model, B, int(rec.shape[0]), K) if keep else None
     return traces_out, st
 
@@ -273,3 +293,14 @@ def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
     _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
                                      arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
     return E_out, residual_out
+
+
+def selftest_barrier(n_blocks, n_absent=0, budget_cycles=2_000_000, rounds=8, stream=None) -> int:
+    """Run the library's bounded grid barrier with `n_absent` blocks that never arrive.
+    Returns the status code (OK, or ETIMEOUT when the wait gave up) instead of raising
+    on ETIMEOUT; other errors raise SbfwiError."""
+    code = _lib.sbfwi_selftest_barrier(int(n_blocks), int(n_absent), int(budget_cycles), int(rounds),
+                                       ctypes.c_void_p(stream))
+    if code not in (OK, ETIMEOUT):
+        _check(code)
+    return code

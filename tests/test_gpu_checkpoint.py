@@ -1,0 +1,69 @@
+"""Checkpoint-and-recompute memory strategy for the adjoint (the alternative to
+storing the forward field, Section 4): traces and gradient must be bit for bit
+those of the stored-field run, for every checkpoint interval and both element
+kernels; the oracle pins the stored-field run."""
+
+import numpy as np
+import pytest
+
+from oracle import fwi
+from test_gpu_parity import _ragged_case, rel, GRAD_TOL, TRACE_TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ragged(lib):
+    mesh, rho, srcs, recs, wav, dt = _ragged_case()
+    M = lib.Mesh.from_inputs(mesh, 6)
+    md = lib.Model(M, 1.3, rho, dt, lx=1.2, ly=1.0)
+    rng = np.random.default_rng(5)
+    res = rng.standard_normal((len(srcs), len(recs), wav.shape[1]))
+    return md, srcs, recs, wav, res
+
+
+@pytest.mark.parametrize("element", ["tc", "fp64"])
+def test_checkpointed_gradient_is_bitwise_the_stored_field_gradient(lib, ragged, monkeypatch, element):
+    md, srcs, recs, wav, res = ragged
+    if element == "fp64":
+        monkeypatch.setenv("SBFWI_ELEMENT", "fp64")
+    t0, s0 = lib.forward(md, srcs, wav, recs, ckpt_every=0)
+    g0 = lib.adjoint_gradient(md, s0, res)
+    K = wav.shape[1]
+    for c in (1, 7, 13, K - 1, K, K + 5, lib.CKPT_AUTO):
+        t, s = lib.forward(md, srcs, wav, recs, ckpt_every=c)
+        assert np.array_equal(t, t0), c
+        g = lib.adjoint_gradient(md, s, res)
+        assert np.array_equal(g, g0), c
+        # the state can be used again
+        assert np.array_equal(lib.adjoint_gradient(md, s, res), g0), c
+
+
+def test_checkpointed_gradient_matches_the_oracle(lib):
+    mesh, rho, srcs, recs, wav, dt = _ragged_case()
+    M = lib.Mesh.from_inputs(mesh, 6)
+    md = lib.Model(M, 1.3, rho, dt, lx=1.2, ly=1.0)
+    tr, st = lib.forward(md, srcs, wav, recs, ckpt_every=9)
+    om = fwi.build_model(mesh, 6, 1.3, rho, dt, lx=1.2, ly=1.0)
+    to, store, _ = fwi.forward(om, srcs, wav, recs)
+    assert rel(tr, to) <= TRACE_TOL
+    res = -to
+    g = lib.adjoint_gradient(md, st, res)
+    go = fwi.gradient_to_grid(om, fwi.adjoint_gradient(om, store, res, recs), rho.shape[1], rho.shape[0], 1.2, 1.0)
+    assert rel(g, go) <= GRAD_TOL
+
+
+def test_checkpoints_from_the_other_element_kernel_are_refused(lib, ragged, monkeypatch):
+    md, srcs, recs, wav, res = ragged
+    _, s = lib.forward(md, srcs, wav, recs, ckpt_every=10)
+    monkeypatch.setenv("SBFWI_ELEMENT", "fp64")
+    with pytest.raises(lib.SbfwiError) as ei:
+        lib.adjoint_gradient(md, s, res)
+    assert ei.value.code == lib.ESTATE
+
+
+def test_negative_interval_is_rejected(lib, ragged):
+    md, srcs, recs, wav, res = ragged
+    with pytest.raises(lib.SbfwiError) as ei:
+        lib.forward(md, srcs, wav, recs, ckpt_every=-2)
+    assert ei.value.code == lib.EINVAL

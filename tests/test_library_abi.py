@@ -91,3 +91,6 @@ def test_compute_calls_fail_loudly_without_a_device(binding):
     assert ei.value.code == binding.ECUDA
     with pytest.raises(binding.SbfwiError):
         binding.misfit(np.zeros(3), np.ones(3), 0.1)
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.selftest_barrier(4, 1)
+    assert ei.value.code == binding.ECUDA
