@@ -77,7 +77,7 @@ def profiled_traffic(kernel):
 # the oracle on the host cores (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 CPU_SAMPLE_NX = 8
-CPU_SAMPLE_K = 12
+CPU_SAMPLE_K = 200
 
 _CPU_CODE = r"""
 import json, os, sys, time

@@ -260,15 +260,52 @@ struct ElemTcArgs {
   int a2_is_one;        // beta = 1/4: the predictor needs no multiply by a2
 };
 
-__global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
+namespace tc {
+
+// asynchronous global -> shared copies (Ampere-style cp.async; completion per thread)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// One pipeline stage: the digit fragments of one or two operators and their row
+// exponents.  Each lane copies its own fragments; lanes 0..16*nops-1 the exponents.
+constexpr int kStageFrags = 2 * kSlices * 32;     // uint4
+struct WarpSmem {
+  uint4 frag[2][kStageFrags];
+  int exps[2][32];
+  double xch[kTile * kCols];
+};
+constexpr int kWarpsPerBlock = 4;
+
+__device__ __forceinline__ void stage_ops(uint4* dst, int* dexp, const uint4* src, const int* sexp, int nops, int lane) {
+  for (int k = 0; k < nops * kSlices; ++k) cp_async16(dst + k * 32 + lane, src + k * 32 + lane);
+  if (lane < 16 * nops) cp_async4(dexp + lane, sexp + lane);
+}
+
+}  // namespace tc
+
+// One warp per element.  The operator digits of the next radial point are copied to
+// shared memory (cp.async, two stages) while the current point computes, and each
+// point's state is loaded before its products, so the memory latency overlaps the
+// tensor-core and integer work instead of stalling every radial point.
+__global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
   using namespace tc;
-  __shared__ double xch[4][kTile * kCols];
+  extern __shared__ __align__(16) unsigned char tc_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int64_t e = (int64_t)blockIdx.x * 4 + warp;
+  WarpSmem& W = reinterpret_cast<WarpSmem*>(tc_smem)[warp];
+  const int64_t e = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
   if (e >= a.E) return;                       // whole warp leaves together
   const int nb = a.nb, n = a.n, B = a.B;
   const int per = nb * B;
-  double* X = xch[warp];
+  double* X = W.xch;
   const int64_t base = e * (int64_t)n * per;
   // C-fragment positions of this lane: (row, col) = (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1)
   const int cr[4] = {g, g, g + 8, g + 8};
@@ -297,48 +334,8 @@ __global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
     for (int j = 0; j < 4; ++j) f = max(f, exp_bound(b[j]));
     return column_exponent(f);
   };
-
-  double xb[4];       // the operand of the next product, B layout
-  if (a.do_down) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) xb[j] = bok[j] ? a.ub[(int64_t)a.dofs[e * nb + br[j]] * B + g] : 0.0;
-    for (int i = n - 1; i >= 0; --i) {
-      BDigits d;
-      const int f = col_exp_b(xb);
-      split_b(xb, f, d);
-      float acc[kLevels][4];
-      zero(acc);
-      const uint4* Hs = a.frag + ((e * n + i) * 3 + 2) * kSlices * 32 + lane;
-      product(acc, Hs, d);
-      const int* ex = a.exps + ((e * n + i) * 3 + 2) * 16;
-      const int er0 = ex[g], er1 = ex[g + 8];
-      const int fc0 = __shfl_sync(0xffffffffu, f, 4 * cc[0]), fc1 = __shfl_sync(0xffffffffu, f, 4 * cc[1]);
-      double un[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const double hu = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
-        un[j] = 0.0;
-        if (cok[j]) {
-          const int64_t o = base + (int64_t)i * per + cr[j] * B + cc[j];
-          const double udo = a.ud[o], uddo = a.udd[o], vo = a.v[o];
-          const double u_new = a.q[o] - hu;
-          const double uddn = fma(a.a0, u_new, -vo);
-          const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
-          // the interior displacement is not kept: the predictor v carries it
-          a.ud[o] = udn; a.udd[o] = uddn;
-          a.v[o] = a.a2_is_one ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
-          if (a.store_int) a.store_int[o] = udn;
-          if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);    // dt applied at the end
-          un[j] = u_new;
-        }
-      }
-      c_to_b(un, xb);
-    }
-  }
-  if (!a.do_up) return;
-  __syncwarp();
-  // one product y = A x with its own row exponents (rows g, g+8) and column exponent,
-  // returned in C layout
+  // one product y = A x with A's row exponents (rows g, g+8) and x's column exponent,
+  // A's digits in shared memory; returned in C layout
   auto apply = [&](const uint4* A, const int* rexp, const double (&xbv)[4], double (&y)[4]) {
     const int f = col_exp_b(xbv);
     BDigits d;
@@ -351,17 +348,87 @@ __global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) y[j] = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
   };
-  // forward sweep: q_i = -(P_i v_i + Q_i q_{i-1})
+
+  double xb[4];       // the operand of the next product, B layout
+  if (a.do_down) {
+    const int64_t hop = (int64_t)3 * kSlices * 32;       // uint4 between radial points
+    const uint4* Hsrc = a.frag + ((e * n + (n - 1)) * 3 + 2) * kSlices * 32;
+    const int* Hexp = a.exps + ((e * n + (n - 1)) * 3 + 2) * 16;
+    stage_ops(W.frag[(n - 1) & 1], W.exps[(n - 1) & 1], Hsrc, Hexp, 1, lane);
+    cp_async_commit();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xb[j] = bok[j] ? a.ub[(int64_t)a.dofs[e * nb + br[j]] * B + g] : 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+      const int buf = i & 1;
+      if (i > 0) stage_ops(W.frag[buf ^ 1], W.exps[buf ^ 1], Hsrc - (int64_t)(n - i) * hop,
+                           Hexp - (int64_t)(n - i) * 48, 1, lane);
+      cp_async_commit();
+      // the state of this radial point, loaded ahead of the product
+      double udo[4], uddo[4], vo[4], qo[4], fw[4], gr[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t o = base + (int64_t)i * per + cr[j] * B + cc[j];
+        udo[j] = cok[j] ? a.ud[o] : 0.0;
+        uddo[j] = cok[j] ? a.udd[o] : 0.0;
+        vo[j] = cok[j] ? a.v[o] : 0.0;
+        qo[j] = cok[j] ? a.q[o] : 0.0;
+        fw[j] = (cok[j] && a.grad_int) ? a.fwd_int[o] : 0.0;
+        gr[j] = (cok[j] && a.grad_int) ? a.grad_int[o] : 0.0;
+      }
+      cp_async_wait<1>();
+      __syncwarp();
+      double hu[4];
+      apply(W.frag[buf], W.exps[buf], xb, hu);
+      double un[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        un[j] = 0.0;
+        if (cok[j]) {
+          const int64_t o = base + (int64_t)i * per + cr[j] * B + cc[j];
+          const double u_new = qo[j] - hu[j];
+          const double uddn = fma(a.a0, u_new, -vo[j]);
+          const double udn = fma(a.c2, uddn, fma(a.c1, uddo[j], udo[j]));
+          // the interior displacement is not kept: the predictor v carries it
+          a.ud[o] = udn; a.udd[o] = uddn;
+          a.v[o] = a.a2_is_one ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+          if (a.store_int) a.store_int[o] = udn;
+          if (a.grad_int) a.grad_int[o] = fma(fw[j], udn, gr[j]);    // dt applied at the end
+          un[j] = u_new;
+        }
+      }
+      c_to_b(un, xb);     // ends with __syncwarp: the stage just read may be refilled
+    }
+    cp_async_wait<0>();
+  }
+  if (!a.do_up) return;
+  __syncwarp();
+  // forward sweep: q_i = -(P_i v_i + Q_i q_{i-1}); stage i holds P_i and Q_i, stage n R and T
+  auto stage_up = [&](int i, int buf) {
+    if (i < n) stage_ops(W.frag[buf], W.exps[buf], a.frag + (e * n + i) * 3 * kSlices * 32, a.exps + (e * n + i) * 3 * 16,
+                         2, lane);
+    else stage_ops(W.frag[buf], W.exps[buf], a.frag_rt + e * 2 * kSlices * 32, a.exps_rt + e * 32, 2, lane);
+  };
+  stage_up(0, 0);
+  cp_async_commit();
+  double vnext[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) vnext[j] = bok[j] ? a.v[base + br[j] * B + g] : 0.0;
   double qb[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = 0; i < n; ++i) {
+    const int buf = i & 1;
+    stage_up(i + 1, buf ^ 1);
+    cp_async_commit();
     double vb[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) vb[j] = bok[j] ? a.v[base + (int64_t)i * per + br[j] * B + g] : 0.0;
-    const uint4* Fi = a.frag + (e * n + i) * 3 * kSlices * 32;
-    const int* ex = a.exps + (e * n + i) * 3 * 16;
+    for (int j = 0; j < 4; ++j) {
+      vb[j] = vnext[j];
+      vnext[j] = (i + 1 < n && bok[j]) ? a.v[base + (int64_t)(i + 1) * per + br[j] * B + g] : 0.0;
+    }
+    cp_async_wait<1>();
+    __syncwarp();
     double pv[4], qq[4] = {0.0, 0.0, 0.0, 0.0};
-    apply(Fi, ex, vb, pv);
-    if (i > 0) apply(Fi + kSlices * 32, ex + 16, qb, qq);
+    apply(W.frag[buf], W.exps[buf], vb, pv);
+    if (i > 0) apply(W.frag[buf] + kSlices * 32, W.exps[buf] + 16, qb, qq);
     double qc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -381,10 +448,12 @@ __global__ void __launch_bounds__(128) element_step_tc_kernel(ElemTcArgs a) {
       vb[j] = fma(a.a0, a.ub[gi], fma(a.a1, a.udb[gi], a.a2 * a.uddb[gi]));
     }
   }
+  cp_async_wait<0>();
+  __syncwarp();
   double rq[4], tv[4];
-  const uint4* RT = a.frag_rt + e * 2 * kSlices * 32;
-  apply(RT, a.exps_rt + e * 32, qb, rq);
-  apply(RT + kSlices * 32, a.exps_rt + e * 32 + 16, vb, tv);
+  const int bn = n & 1;
+  apply(W.frag[bn], W.exps[bn], qb, rq);
+  apply(W.frag[bn] + kSlices * 32, W.exps[bn] + 16, vb, tv);
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     if (cok[j]) a.fhat[(e * nb + cr[j]) * B + cc[j]] = rq[j] + tv[j];
@@ -412,6 +481,9 @@ int tc_prepare(Model& md, cudaStream_t st) {
   slice_operators_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(a);
   profiler().count(kPhaseSetup);
   SBFWI_CUDA(cudaGetLastError());
+  // the element kernel's two-stage operator pipeline needs more than the default 48 KiB
+  SBFWI_CUDA(cudaFuncSetAttribute(element_step_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(WarpSmem) * kWarpsPerBlock)));
   md.tc_ready = true;
   return SBFWI_OK;
 }
@@ -429,7 +501,9 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.do_down = down; a.do_up = up;
   a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
   a.a2_is_one = md.a2 == 1.0;
-  element_step_tc_kernel<<<(unsigned)((md.E + 3) / 4), 128, 0, st>>>(a);
+  const int smem = (int)(sizeof(tc::WarpSmem) * tc::kWarpsPerBlock);   // attribute set by tc_prepare
+  element_step_tc_kernel<<<(unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock), 32 * tc::kWarpsPerBlock,
+                           smem, st>>>(a);
   return SBFWI_OK;
 }
 
