@@ -240,12 +240,16 @@ int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int re
 /*
  * Per-level tracing of the one-launch global solve (a diagnostic of this
  * implementation; the paper does not specify the solver).  While profiling is on,
- * block 0 of every persistent solve launch reads the global timer after each grid
- * barrier; slot j accumulates the time between barrier j-1 and barrier j: slots
- * 0..L-1 are the forward (leaves -> root) levels, L..2L-1 the backward levels
- * (root -> leaves; the last slot ends when block 0 finishes).  Fills us[min(cap,
- * 2L)] with the mean microseconds per solve, *n_slots = 2L (0 if nothing was
- * recorded), *steps = solves recorded; reset != 0 clears the accumulators.
+ * every persistent solve launch reads the global timer around each phase (a tree
+ * level of one pass, between two grid barriers).  Phases 0..L-1 are the forward
+ * (leaves -> root) levels, L..2L-1 the backward levels (root -> leaves).  Slots
+ * [0, 2L): wall time of the phase seen by block 0 (the last phase ends when block
+ * 0 finishes); [2L, 4L): the longest time one block spent in its tasks of the
+ * phase (maximum over blocks and solves, not a mean); [4L, 6L): the time blocks
+ * spent in their tasks of the phase, summed over blocks.  Fills us[min(cap, 6L)]
+ * with microseconds per solve (per solve and block for the maxima as recorded),
+ * *n_slots = 6L (0 if nothing was recorded), *steps = solves recorded; reset != 0
+ * clears the accumulators.
  * Synchronises the current device.  SBFWI_ESTATE if the trace lives on another
  * device.
  */

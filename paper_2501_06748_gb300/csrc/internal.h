@@ -92,8 +92,10 @@ struct Tree {
   std::vector<int32_t> sep_nodes, bnd_nodes;
   std::vector<int32_t> map0, map1;     // per front position: child0 / child1 bnd index, -1 if absent;
                                        // leaves: map0 = local dof of the element
-  std::vector<int32_t> src0, src1;     // the same as absolute rows: of ybnd (children), of f_hat
-                                       // (leaves: element * n_b + local dof), -1 if absent
+  std::vector<int32_t> src0, src1;     // the same for the solve: >= 0 a row of ybnd (a child's
+                                       // boundary); <= -2 the f_hat row -2 - src (element * n_b +
+                                       // local dof) of the leaf's own element or of a child leaf
+                                       // that eliminates nothing (no solve task); -1 absent
   std::vector<std::vector<int32_t>> nodes_at_level;
   int64_t X_total = 0, F_total = 0, U_total = 0, sep_rows = 0, bnd_rows = 0;
   std::vector<int32_t> sep_owner;      // per global node: tree node that eliminates it
@@ -136,12 +138,25 @@ int build_tree(Mesh& m);
 // ---------------------------------------------------------------------------
 // model (device resident)
 // ---------------------------------------------------------------------------
+// Per level and direction the tasks are [block tasks | warp tasks]: a block task is a
+// row range of a large front done by the whole block; a warp task is a whole small
+// front done by one warp, and `group` warp tasks form one block item.
 struct LevelTasks {
   std::vector<int32_t> fwd_start, bwd_start;   // per level: first task index (levels+1 entries)
+  std::vector<int32_t> fwd_wstart, bwd_wstart; // per level: first warp task
+  std::vector<int32_t> fwd_group, bwd_group;   // per level: warp tasks per block item
   DevBuf fwd, bwd;                              // Task arrays
-  DevBuf fwd_start_dev, bwd_start_dev;          // the index arrays on the device
+  DevBuf fwd_meta, bwd_meta;                    // device: start[L+1] | wstart[L] | group[L]
   int shots = 0;                                // tasks were built for this many shots
-  int max_level_tasks = 0;
+  int grid = 0;                                 // and this many blocks
+  int max_level_items = 0;
+  size_t block_doubles = 0;                     // largest staging area of a block task
+  int items(bool fwd, int l) const {
+    const auto& st = fwd ? fwd_start : bwd_start;
+    const auto& ws = fwd ? fwd_wstart : bwd_wstart;
+    const auto& gr = fwd ? fwd_group : bwd_group;
+    return (ws[l] - st[l]) + (st[l + 1] - ws[l] + gr[l] - 1) / gr[l];
+  }
 };
 
 struct Model {
@@ -158,7 +173,15 @@ struct Model {
   DevBuf rt;        // [E][2][nb][nb]
   DevBuf S;         // [E][nb][nb]  dynamic stiffness
   DevBuf rho_nodal; // [n_nodal] FP64 (hi part of the set-up value)
-  DevBuf factors;   // global factors along the elimination tree
+  // global factors along the elimination tree, followed by copies of the solve's index
+  // arrays (src0, src1, sep_nodes, bnd_nodes): one range that the per-step solve
+  // keeps resident in L2
+  DevBuf factors;
+  const int32_t* solve_src0 = nullptr;
+  const int32_t* solve_src1 = nullptr;
+  const int32_t* solve_sep = nullptr;
+  const int32_t* solve_bnd = nullptr;
+  size_t solve_bytes = 0;
   DevBuf pts_hi, pts_lo; // [n_nodal][2] dd location of every nodal point
   // the same operators split into FP16 digits for the tensor-core element kernel
   DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
@@ -167,7 +190,7 @@ struct Model {
   const MeshDevice& dev() const { return *mesh->dev; }
 };
 
-int build_level_tasks(Model& md, int shots);
+int build_level_tasks(Model& md, int shots, int grid);
 
 // tensor-core element operators (tc.cu)
 bool tc_supported(int nb, int B);

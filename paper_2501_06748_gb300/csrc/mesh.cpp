@@ -161,7 +161,7 @@ int build_tree(Mesh& m) {
         const int32_t j = local.at(g);
         t.map0.push_back(j);
         t.map1.push_back(-1);
-        t.src0.push_back((int32_t)(r.elem * m.nb + j));
+        t.src0.push_back(-2 - (int32_t)(r.elem * m.nb + j));     // the element's own f_hat row
         t.src1.push_back(-1);
       }
     } else {
@@ -169,12 +169,23 @@ int build_tree(Mesh& m) {
       for (size_t k = 0; k < bnd[r.child0].size(); ++k) in0[bnd[r.child0][k]] = (int32_t)k;
       for (size_t k = 0; k < bnd[r.child1].size(); ++k) in1[bnd[r.child1][k]] = (int32_t)k;
       const int64_t off0 = t.nodes[r.child0].bnd_off, off1 = t.nodes[r.child1].bnd_off;
+      // a child leaf that eliminates nothing passes its f_hat through unchanged: the
+      // solve reads f_hat directly (encoded -2 - row) and runs no task for it
+      auto src_of = [&](int32_t child, int64_t off, int32_t k, int32_t g) -> int32_t {
+        const TreeNodeDev& c = t.nodes[child];
+        if (c.elem >= 0 && c.s == 0) {
+          int32_t j = 0;
+          while (m.dofs[(int64_t)c.elem * m.nb + j] != g) ++j;
+          return -2 - (int32_t)(c.elem * m.nb + j);
+        }
+        return (int32_t)(off + k);
+      };
       for (int32_t g : front) {
         auto a = in0.find(g), b2 = in1.find(g);
         t.map0.push_back(a == in0.end() ? -1 : a->second);
         t.map1.push_back(b2 == in1.end() ? -1 : b2->second);
-        t.src0.push_back(a == in0.end() ? -1 : (int32_t)(off0 + a->second));
-        t.src1.push_back(b2 == in1.end() ? -1 : (int32_t)(off1 + b2->second));
+        t.src0.push_back(a == in0.end() ? -1 : src_of(r.child0, off0, a->second, g));
+        t.src1.push_back(b2 == in1.end() ? -1 : src_of(r.child1, off1, b2->second, g));
       }
       t.level_of[nd] = 1 + std::max(t.level_of[r.child0], t.level_of[r.child1]);
     }
@@ -234,9 +245,13 @@ int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_
   std::vector<unsigned long long> acc(p.level_slots);
   e = cudaMemcpy(acc.data(), p.level_acc, sizeof(unsigned long long) * p.level_slots, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "read solve trace");
+  // slots [2L, 4L) hold maxima (not divided by the number of solves)
+  const int L2 = p.level_slots / 3;
   if (us)
-    for (int k = 0; k < std::min<int>(cap, p.level_slots); ++k)
-      us[k] = p.level_steps ? (double)acc[k] / 1e3 / (double)p.level_steps : 0.0;
+    for (int k = 0; k < std::min<int>(cap, p.level_slots); ++k) {
+      const bool is_max = k >= L2 && k < 2 * L2;
+      us[k] = (is_max || !p.level_steps) ? (double)acc[k] / 1e3 : (double)acc[k] / 1e3 / (double)p.level_steps;
+    }
   if (reset) {
     e = cudaMemset(p.level_acc, 0, sizeof(unsigned long long) * p.level_slots);
     if (e != cudaSuccess) return cuda_fail(e, "reset solve trace");

@@ -896,7 +896,25 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
 
   // global factorisation along the elimination tree
   const Tree& t = m.tree;
-  SBFWI_CUDA(md.factors.alloc(sizeof(double) * std::max<int64_t>(t.X_total, 1)));
+  {
+    const size_t fb = sizeof(double) * (size_t)std::max<int64_t>(t.X_total, 1);
+    const size_t nmap = t.src0.size(), nsep = t.sep_nodes.size(), nbnd = t.bnd_nodes.size();
+    const size_t ib = sizeof(int32_t) * (2 * nmap + nsep + nbnd);
+    SBFWI_CUDA(md.factors.alloc(fb + ib));
+    int32_t* tail = reinterpret_cast<int32_t*>(md.factors.as<char>() + fb);
+    md.solve_src0 = tail;
+    md.solve_src1 = tail + nmap;
+    md.solve_sep = tail + 2 * nmap;
+    md.solve_bnd = tail + 2 * nmap + nsep;
+    md.solve_bytes = fb + ib;
+    if (nmap) {
+      SBFWI_CUDA(cudaMemcpyAsync(tail, d.src0.p, sizeof(int32_t) * nmap, cudaMemcpyDeviceToDevice, st));
+      SBFWI_CUDA(cudaMemcpyAsync(tail + nmap, d.src1.p, sizeof(int32_t) * nmap, cudaMemcpyDeviceToDevice, st));
+    }
+    if (nsep) SBFWI_CUDA(cudaMemcpyAsync(tail + 2 * nmap, d.sep_nodes.p, sizeof(int32_t) * nsep, cudaMemcpyDeviceToDevice, st));
+    if (nbnd)
+      SBFWI_CUDA(cudaMemcpyAsync(tail + 2 * nmap + nsep, d.bnd_nodes.p, sizeof(int32_t) * nbnd, cudaMemcpyDeviceToDevice, st));
+  }
   {
     FactorArgs a;
     a.nodes = d.tree_nodes.as<TreeNodeDev>(); a.map0 = d.map0.as<int32_t>(); a.map1 = d.map1.as<int32_t>();

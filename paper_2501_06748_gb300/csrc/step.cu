@@ -136,10 +136,10 @@ __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
 // kernel B: global boundary solve, one launch per tree level and direction
 // ---------------------------------------------------------------------------
 struct SolveArgs {
-  const Task* tasks;
   const int32_t* sep_nodes;
   const int32_t* bnd_nodes;
-  const int32_t* src0;   // per front position: absolute row of f_hat (leaves) or ybnd, -1 if absent
+  const int32_t* src0;   // per front position: row of ybnd (or f_hat in a leaf); <= -2: f_hat row -2 - v
+                         // of a pass-through child leaf; -1 absent
   const int32_t* src1;
   const double* factors;
   const double* fhat;    // [E][nb][B]
@@ -148,37 +148,107 @@ struct SolveArgs {
   double* ybnd;          // [bnd_rows][B]
   double* x;             // [N][B] solution
   int nb, B;
+  int warp_doubles;      // shared memory of one warp task (doubles)
 };
 
+// One source term of a front position: a row of ybnd (r >= 0, a child's boundary),
+// an f_hat row (r <= -2: the leaf's own element or a pass-through child leaf) or
+// nothing (r = -1).  Branch-free (the absent case reads f_hat row 0 and drops it).
+// ybnd is written by other blocks earlier in the same persistent launch: read through L2.
+__device__ __forceinline__ double src_value(const SolveArgs& a, int32_t r, int s) {
+  const bool in_y = r >= 0;
+  const int64_t row = in_y ? (int64_t)r : (r <= -2 ? (int64_t)(-2 - r) : 0);
+  const double v = __ldcg((in_y ? a.ybnd : a.fhat) + row * a.B + s);
+  return r == -1 ? 0.0 : v;
+}
+
 __device__ __forceinline__ double front_value(const SolveArgs& a, const Task& tk, int pos, int s) {
-  const int32_t r0 = a.src0[tk.map_off + pos];
-  if (tk.leaf) return a.fhat[(int64_t)r0 * a.B + s];
-  const int32_t r1 = a.src1[tk.map_off + pos];
+  const int32_t r0 = a.src0[tk.map_off + pos], r1 = a.src1[tk.map_off + pos];
   double v = 0.0;
-  // written by other blocks earlier in the same persistent launch: read through L2
-  if (r0 >= 0) v += __ldcg(a.ybnd + (int64_t)r0 * a.B + s);
-  if (r1 >= 0) v += __ldcg(a.ybnd + (int64_t)r1 * a.B + s);
+  v += src_value(a, r0, s);
+  v += src_value(a, r1, s);
   return v;
 }
 
-// sum over the ks consecutive lanes that share one output (ks in {1, 2, 4, 8})
+// sum over the ks consecutive lanes that share one output (ks in {1, 2, ..., 32})
 __device__ __forceinline__ double lane_group_sum(double v, int ks) {
   for (int off = ks >> 1; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   return v;
 }
 
-// forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element)
-__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* csep) {
-  const int B = a.B, S = tk.s;
-#pragma unroll 4
-  for (int t = threadIdx.x; t < S * B; t += blockDim.x) {
-    const int k = t / B, s = t - k * B;
-    const double v = front_value(a, tk, k, s) + a.ext[(int64_t)a.sep_nodes[tk.sep_off + k] * B + s];
-    csep[t] = v;
-    if (tk.r0 == 0) a.ysep[(tk.sep_off + k) * B + s] = v;
+// Shared-memory staging of a task, U values per thread at a time: all loads of a
+// batch are issued before any of its stores, so the loads of different positions
+// overlap instead of running one after another.
+//
+// Forward: [c_sep (s B values, + external sources at the separator nodes) | the
+// task's rows of C (rows x s)]; c_sep also goes to ysep if asked.
+template <int U>
+__device__ __forceinline__ void stage_forward(const SolveArgs& a, const Task& tk, double* sm, bool write_ysep, int tid,
+                                              int nthr) {
+  const int B = a.B, S = tk.s, n1 = S * B, n2 = (tk.r1 - tk.r0) * S;
+  const double* C = a.factors + tk.X_off + (int64_t)S * S + (int64_t)S * tk.b + (int64_t)tk.r0 * S;
+  for (int base = 0; base < n1 + n2; base += U * nthr) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      v[u] = 0.0;
+      if (t < n1) {
+        const int k = t / B, s = t - k * B;
+        v[u] = front_value(a, tk, k, s) + a.ext[(int64_t)a.sep_nodes[tk.sep_off + k] * B + s];
+      } else if (t < n1 + n2) {
+        v[u] = C[t - n1];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < n1 + n2) sm[t] = v[u];
+      if (write_ysep && t < n1) a.ysep[tk.sep_off * B + t] = v[u];
+    }
   }
+}
+
+// Backward: [y_sep (s B) | x at the front's boundary nodes (b B) | the task's rows of
+// X (rows x s) | the task's rows of G (rows x b)]
+template <int U>
+__device__ __forceinline__ void stage_backward(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+  const int B = a.B, S = tk.s, Bn = tk.b, rows = tk.r1 - tk.r0;
+  const int n1 = S * B, n2 = n1 + Bn * B, n3 = n2 + rows * S, n4 = n3 + rows * Bn;
+  const double* X = a.factors + tk.X_off + (int64_t)tk.r0 * S;
+  const double* G = a.factors + tk.X_off + (int64_t)S * S + (int64_t)tk.r0 * Bn;
+  for (int base = 0; base < n4; base += U * nthr) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      v[u] = 0.0;
+      if (t < n1) {
+        v[u] = __ldcg(a.ysep + tk.sep_off * B + t);
+      } else if (t < n2) {
+        const int q = t - n1, j = q / B, s = q - j * B;
+        v[u] = __ldcg(a.x + (int64_t)a.bnd_nodes[tk.bnd_off + j] * B + s);
+      } else if (t < n3) {
+        v[u] = X[t - n2];
+      } else if (t < n4) {
+        v[u] = G[t - n3];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < n4) sm[t] = v[u];
+    }
+  }
+}
+
+// forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element)
+__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* sm) {
+  const int B = a.B, S = tk.s;
+  stage_forward<8>(a, tk, sm, tk.r0 == 0, threadIdx.x, blockDim.x);
   __syncthreads();
-  const double* C = a.factors + tk.X_off + (int64_t)S * S + (int64_t)S * tk.b;   // b x s
+  const double* csep = sm;
+  const double* Cs = sm + S * B;          // rows r0.. of C, s each
   const int ks = tk.ksplit;
   const int outputs = (tk.r1 - tk.r0) * B;
   // every lane walks the same number of rounds so that the lane-group shuffles see full warps
@@ -187,67 +257,140 @@ __device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* cs
     const int t = rd * blockDim.x + threadIdx.x;
     const int o = t / ks, kk = t - o * ks;
     const bool live = o < outputs;
-    const int r = tk.r0 + (live ? o / B : 0), s = live ? o % B : 0;
-    double acc = 0.0;
+    const int ro = live ? o / B : 0, s = live ? o % B : 0;
+    double acc = 0.0, cb = 0.0;
     if (live) {
-      const double* Cr = C + (int64_t)r * S;
+      if (kk == 0) cb = front_value(a, tk, S + tk.r0 + ro, s);
+      const double* Cr = Cs + ro * S;
 #pragma unroll 4
       for (int k = kk; k < S; k += ks) acc = fma(Cr[k], csep[k * B + s], acc);
     }
     acc = lane_group_sum(acc, ks);
-    if (live && kk == 0) a.ybnd[(tk.bnd_off + r) * B + s] = front_value(a, tk, S + r, s) - acc;
+    if (live && kk == 0) a.ybnd[(tk.bnd_off + tk.r0 + ro) * B + s] = cb - acc;
   }
-  __syncthreads();     // csep is reused by the next task of this block
+  __syncthreads();     // the staging area is reused by the next task of this block
 }
 
 // backward pass: x_sep = X y_sep - G x_bnd
-__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* shb) {
-  const int B = a.B, S = tk.s, Bn = tk.b;
-  double* ys = shb;
-  double* xbn = shb + (size_t)S * B;
-#pragma unroll 4
-  for (int t = threadIdx.x; t < S * B; t += blockDim.x) ys[t] = __ldcg(a.ysep + tk.sep_off * B + t);
-#pragma unroll 4
-  for (int t = threadIdx.x; t < Bn * B; t += blockDim.x) {
-    const int j = t / B, s = t - j * B;
-    xbn[t] = __ldcg(a.x + (int64_t)a.bnd_nodes[tk.bnd_off + j] * B + s);
-  }
+__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* sm) {
+  const int B = a.B, S = tk.s, Bn = tk.b, rows = tk.r1 - tk.r0;
+  stage_backward<8>(a, tk, sm, threadIdx.x, blockDim.x);
   __syncthreads();
-  const double* X = a.factors + tk.X_off;
-  const double* G = X + (int64_t)S * S;
+  const double* ys = sm;
+  const double* xbn = ys + S * B;
+  const double* Xs = xbn + Bn * B;
+  const double* Gs = Xs + rows * S;
   const int ks = tk.ksplit;
-  const int outputs = (tk.r1 - tk.r0) * B;
+  const int outputs = rows * B;
   const int rounds = (outputs * ks + blockDim.x - 1) / blockDim.x;
   for (int rd = 0; rd < rounds; ++rd) {
     const int t = rd * blockDim.x + threadIdx.x;
     const int o = t / ks, kk = t - o * ks;
     const bool live = o < outputs;
-    const int r = tk.r0 + (live ? o / B : 0), s = live ? o % B : 0;
+    const int ro = live ? o / B : 0, s = live ? o % B : 0;
     double acc = 0.0;
     if (live) {
-      const double* Xr = X + (int64_t)r * S;
+      const double* Xr = Xs + ro * S;
 #pragma unroll 4
       for (int k = kk; k < S; k += ks) acc = fma(Xr[k], ys[k * B + s], acc);
-      const double* Gr = G + (int64_t)r * Bn;
+      const double* Gr = Gs + ro * Bn;
 #pragma unroll 4
       for (int j = kk; j < Bn; j += ks) acc = fma(-Gr[j], xbn[j * B + s], acc);
     }
     acc = lane_group_sum(acc, ks);
-    if (live && kk == 0) a.x[(int64_t)a.sep_nodes[tk.sep_off + r] * B + s] = acc;
+    if (live && kk == 0) a.x[(int64_t)a.sep_nodes[tk.sep_off + tk.r0 + ro] * B + s] = acc;
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) solve_forward_kernel(SolveArgs a) {
-  extern __shared__ double sm_fwd[];
-  const Task tk = a.tasks[blockIdx.x];
-  solve_forward_task(a, tk, sm_fwd);
+// the same for a small front done by one warp (all rows; no block synchronisation)
+__device__ void solve_forward_warp(const SolveArgs& a, const Task tk, double* sm, int lane) {
+  const int B = a.B, S = tk.s, Bn = tk.b;
+  stage_forward<8>(a, tk, sm, true, lane, 32);
+  __syncwarp();
+  const double* csep = sm;
+  const double* Cs = sm + S * B;           // all b rows of C, s each
+  constexpr int U = 8;
+  for (int base = 0; base < Bn * B; base += U * 32) {
+    double y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int o = base + u * 32 + lane;
+      y[u] = 0.0;
+      if (o < Bn * B) y[u] = front_value(a, tk, S + o / B, o % B);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int o = base + u * 32 + lane;
+      if (o < Bn * B) {
+        const int r = o / B, s = o - r * B;
+        double acc = 0.0;
+        for (int k = 0; k < S; ++k) acc = fma(Cs[r * S + k], csep[k * B + s], acc);
+        a.ybnd[tk.bnd_off * B + o] = y[u] - acc;
+      }
+    }
+  }
+  __syncwarp();
 }
 
-__global__ void __launch_bounds__(256) solve_backward_kernel(SolveArgs a) {
+__device__ void solve_backward_warp(const SolveArgs& a, const Task tk, double* sm, int lane) {
+  const int B = a.B, S = tk.s, Bn = tk.b;
+  stage_backward<8>(a, tk, sm, lane, 32);
+  __syncwarp();
+  const double* ys = sm;
+  const double* xbn = ys + S * B;
+  const double* Xs = xbn + Bn * B;
+  const double* Gs = Xs + S * S;
+  for (int o = lane; o < S * B; o += 32) {
+    const int r = o / B, s = o - r * B;
+    double acc = 0.0;
+    for (int k = 0; k < S; ++k) acc = fma(Xs[r * S + k], ys[k * B + s], acc);
+    for (int j = 0; j < Bn; ++j) acc = fma(-Gs[r * Bn + j], xbn[j * B + s], acc);
+    a.x[(int64_t)a.sep_nodes[tk.sep_off + r] * B + s] = acc;
+  }
+  __syncwarp();
+}
+
+// The work of one tree level in one direction, as block items: tasks [start, wstart)
+// are block tasks, [wstart, end) warp tasks taken `group` at a time.  Block items
+// come first, so once a block reaches the warp items its warps only touch their
+// own shared-memory slices.
+__device__ void run_level(const SolveArgs& a, const Task* tasks, const int32_t* meta, int levels, int l, bool fwd,
+                          double* sm, int item0, int stride) {
+  const int start = meta[l], end = meta[l + 1], wstart = meta[levels + 1 + l], group = meta[2 * levels + 1 + l];
+  const int nblock = wstart - start;
+  const int nitems = nblock + (end - wstart + group - 1) / group;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int it = item0; it < nitems; it += stride) {
+    if (it < nblock) {
+      if (fwd) solve_forward_task(a, tasks[start + it], sm);
+      else solve_backward_task(a, tasks[start + it], sm);
+    } else {
+      const int w = wstart + (it - nblock) * group + warp;
+      if (warp < group && w < end) {
+        double* wsm = sm + (size_t)warp * a.warp_doubles;
+        if (fwd) solve_forward_warp(a, tasks[w], wsm, lane);
+        else solve_backward_warp(a, tasks[w], wsm, lane);
+      }
+    }
+  }
+}
+
+struct LevelKernelArgs {
+  SolveArgs s;
+  const Task* tasks;
+  const int32_t* meta;
+  int levels, level;
+};
+
+__global__ void __launch_bounds__(256) solve_forward_kernel(LevelKernelArgs a) {
+  extern __shared__ double sm_fwd[];
+  run_level(a.s, a.tasks, a.meta, a.levels, a.level, true, sm_fwd, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) solve_backward_kernel(LevelKernelArgs a) {
   extern __shared__ double sm_bwd[];
-  const Task tk = a.tasks[blockIdx.x];
-  solve_backward_task(a, tk, sm_bwd);
+  run_level(a.s, a.tasks, a.meta, a.levels, a.level, false, sm_bwd, blockIdx.x, gridDim.x);
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
@@ -287,8 +430,8 @@ struct PersistentSolveArgs {
   SolveArgs s;
   const Task* fwd;
   const Task* bwd;
-  const int32_t* fwd_start;   // levels + 1
-  const int32_t* bwd_start;
+  const int32_t* fwd_meta;    // start[L+1] | wstart[L] | group[L]
+  const int32_t* bwd_meta;
   int levels;
   unsigned* bar;              // [2]: arrival count, generation
   int* status;
@@ -306,26 +449,38 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 __global__ void __launch_bounds__(256) solve_persistent_kernel(PersistentSolveArgs a) {
   extern __shared__ double sm_p[];
-  const bool stamp = a.trace && blockIdx.x == 0 && threadIdx.x == 0;
-  unsigned long long t_prev = stamp ? global_ns() : 0ULL;
+  // trace (profiling only): [0, 2L) wall time per phase seen by block 0, [2L, 4L) the
+  // longest time any block spent in its tasks of the phase, [4L, 6L) the sum over
+  // blocks of that time
+  const int L2 = 2 * a.levels;
+  const bool tr = a.trace && threadIdx.x == 0;
+  unsigned long long t_prev = tr ? global_ns() : 0ULL, t_start = t_prev;
   int slot = 0;
+  auto busy = [&]() {
+    if (tr) {
+      const unsigned long long d = global_ns() - t_start;
+      atomicMax(a.trace + L2 + slot, d);
+      atomicAdd(a.trace + 2 * L2 + slot, d);
+    }
+  };
   auto mark = [&]() {
-    if (stamp) {
+    if (tr) {
       const unsigned long long t = global_ns();
-      a.trace[slot] += t - t_prev;
+      if (blockIdx.x == 0) a.trace[slot] += t - t_prev;
       t_prev = t;
+      t_start = t;
     }
     ++slot;
   };
   for (int l = 0; l < a.levels; ++l) {
-    for (int t = a.fwd_start[l] + blockIdx.x; t < a.fwd_start[l + 1]; t += gridDim.x)
-      solve_forward_task(a.s, a.fwd[t], sm_p);
+    run_level(a.s, a.fwd, a.fwd_meta, a.levels, l, true, sm_p, blockIdx.x, gridDim.x);
+    busy();
     if (!grid_barrier(a.bar, a.bar + 1, a.status, a.budget)) return;
     mark();
   }
   for (int l = a.levels - 1; l >= 0; --l) {
-    for (int t = a.bwd_start[l] + blockIdx.x; t < a.bwd_start[l + 1]; t += gridDim.x)
-      solve_backward_task(a.s, a.bwd[t], sm_p);
+    run_level(a.s, a.bwd, a.bwd_meta, a.levels, l, false, sm_p, blockIdx.x, gridDim.x);
+    busy();
     if (l > 0 && !grid_barrier(a.bar, a.bar + 1, a.status, a.budget)) return;
     mark();              // the last one: block 0's own finish
   }
@@ -460,58 +615,119 @@ __global__ void misfit_final_kernel(const double* partial, int nparts, double ha
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// Lanes per output for a dot product of length k: long products of the upper tree
-// levels are split so that few-row fronts still spread over many CTAs.
-static int ksplit_for(int k) {
-  if (k >= 128) return 8;
-  if (k >= 48) return 4;
-  if (k >= 16) return 2;
-  return 1;
+static int pow2_ceil(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+static int pow2_floor(int v) {
+  int p = 1;
+  while (2 * p <= v) p <<= 1;
+  return p;
 }
 
-// B shots; a block task with ksplit 1 covers 256 / B rows
-int build_level_tasks(Model& md, int B) {
-  const int rows_per_task = std::max(1, 256 / B);
+// Small fronts (s <= kWarpS, b <= kWarpB) are warp tasks: one warp does every row.
+static constexpr int kWarpS = 8, kWarpB = 32;
+static bool warp_front(const TreeNodeDev& r) { return r.s <= kWarpS && r.b <= kWarpB; }
+// staging area of one warp task: vectors (s + b) B plus the factors s (s + b)
+size_t solve_warp_doubles(int B) { return (size_t)(kWarpS + kWarpB) * B + (size_t)kWarpS * (kWarpS + kWarpB); }
+// staging area of a block task (see stage_forward / stage_backward)
+static size_t block_task_doubles(const Task& t, int B, bool fwd) {
+  const size_t rows = (size_t)(t.r1 - t.r0);
+  return fwd ? (size_t)t.s * B + rows * t.s : (size_t)(t.s + t.b) * B + rows * (t.s + t.b);
+}
+
+// B shots, `grid` blocks.  Block tasks of a level take a power-of-two number of rows
+// chosen so that the level's rows about fill the grid (the top of the tree has few,
+// long rows: one row per block, its dot products split over up to 32 lanes); the
+// lanes per output fill the block's 256 threads.  Leaves that eliminate nothing get
+// no task (their parents read f_hat directly).  Warp tasks are grouped so that a
+// level's items about fill the grid.
+int build_level_tasks(Model& md, int B, int grid) {
+  const int rows_max = std::max(1, 256 / B);
   const Tree& t = md.mesh->tree;
+  const int L = t.levels;
   std::vector<Task> fwd, bwd;
-  md.tasks.fwd_start.assign(t.levels + 1, 0);
-  md.tasks.bwd_start.assign(t.levels + 1, 0);
-  for (int l = 0; l < t.levels; ++l) {
-    md.tasks.fwd_start[l] = (int32_t)fwd.size();
-    md.tasks.bwd_start[l] = (int32_t)bwd.size();
+  LevelTasks& lt = md.tasks;
+  lt.fwd_start.assign(L + 1, 0); lt.bwd_start.assign(L + 1, 0);
+  lt.fwd_wstart.assign(L, 0); lt.bwd_wstart.assign(L, 0);
+  lt.fwd_group.assign(L, 1); lt.bwd_group.assign(L, 1);
+  auto task = [&](int32_t nd, int32_t r0, int32_t r1, int ks) {
+    const TreeNodeDev& r = t.nodes[nd];
+    Task tk;
+    tk.node = nd; tk.r0 = r0; tk.r1 = r1; tk.ksplit = ks;
+    tk.s = r.s; tk.b = r.b; tk.leaf = r.elem >= 0 ? 1 : 0; tk.pad = 0;
+    tk.sep_off = r.sep_off; tk.bnd_off = r.bnd_off; tk.map_off = r.map_off; tk.X_off = r.X_off;
+    return tk;
+  };
+  auto group_for = [&](int n) { return std::max(1, std::min(8, (n + grid - 1) / std::max(grid, 1))); };
+  // rows per block task and lanes per output for a dot product of length len
+  auto rows_for = [&](int64_t level_rows) {
+    const int64_t per = (level_rows + grid - 1) / std::max(grid, 1);
+    return std::min(rows_max, pow2_ceil((int)std::max<int64_t>(1, per)));
+  };
+  auto lanes_for = [&](int rows, int len) {
+    return std::max(1, std::min({32, pow2_floor(std::max(1, 256 / (B * rows))), pow2_ceil(std::max(1, len))}));
+  };
+  for (int l = 0; l < L; ++l) {
+    lt.fwd_start[l] = (int32_t)fwd.size();
+    lt.bwd_start[l] = (int32_t)bwd.size();
+    int64_t rows_f = 0, rows_b = 0;
     for (int32_t nd : t.nodes_at_level[l]) {
       const TreeNodeDev& r = t.nodes[nd];
-      const int kf = ksplit_for(r.s), kb = ksplit_for(r.s + r.b);
-      const int rf = std::max(1, rows_per_task / kf), rb = std::max(1, rows_per_task / kb);
-      auto task = [&](int32_t r0, int32_t r1, int ks) {
-        Task tk;
-        tk.node = nd; tk.r0 = r0; tk.r1 = r1; tk.ksplit = ks;
-        tk.s = r.s; tk.b = r.b; tk.leaf = r.elem >= 0 ? 1 : 0; tk.pad = 0;
-        tk.sep_off = r.sep_off; tk.bnd_off = r.bnd_off; tk.map_off = r.map_off; tk.X_off = r.X_off;
-        return tk;
-      };
-      if (r.b == 0) fwd.push_back(task(0, 0, 1));
-      for (int32_t r0 = 0; r0 < r.b; r0 += rf) fwd.push_back(task(r0, std::min(r.b, r0 + rf), kf));
-      for (int32_t r0 = 0; r0 < r.s; r0 += rb) bwd.push_back(task(r0, std::min(r.s, r0 + rb), kb));
+      if (!warp_front(r)) { rows_f += r.b; rows_b += r.s; }
     }
+    const int rf = rows_for(rows_f), rb = rows_for(rows_b);
+    for (int32_t nd : t.nodes_at_level[l]) {
+      const TreeNodeDev& r = t.nodes[nd];
+      if (warp_front(r)) continue;
+      const int kf = lanes_for(rf, r.s), kb = lanes_for(rb, r.s + r.b);
+      if (r.b == 0) fwd.push_back(task(nd, 0, 0, 1));
+      for (int32_t r0 = 0; r0 < r.b; r0 += rf) fwd.push_back(task(nd, r0, std::min(r.b, r0 + rf), kf));
+      for (int32_t r0 = 0; r0 < r.s; r0 += rb) bwd.push_back(task(nd, r0, std::min(r.s, r0 + rb), kb));
+    }
+    lt.fwd_wstart[l] = (int32_t)fwd.size();
+    lt.bwd_wstart[l] = (int32_t)bwd.size();
+    for (int32_t nd : t.nodes_at_level[l]) {
+      const TreeNodeDev& r = t.nodes[nd];
+      if (!warp_front(r)) continue;
+      // a leaf that eliminates nothing passes f_hat through (its parent reads f_hat)
+      if (!(r.elem >= 0 && r.s == 0)) fwd.push_back(task(nd, 0, r.b, 1));
+      if (r.s > 0) bwd.push_back(task(nd, 0, r.s, 1));
+    }
+    lt.fwd_group[l] = group_for((int)fwd.size() - lt.fwd_wstart[l]);
+    lt.bwd_group[l] = group_for((int)bwd.size() - lt.bwd_wstart[l]);
   }
-  md.tasks.fwd_start[t.levels] = (int32_t)fwd.size();
-  md.tasks.bwd_start[t.levels] = (int32_t)bwd.size();
-  md.tasks.max_level_tasks = 0;
-  for (int l = 0; l < t.levels; ++l)
-    md.tasks.max_level_tasks = std::max({md.tasks.max_level_tasks, md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l],
-                                         md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l]});
-  SBFWI_CUDA(md.tasks.fwd_start_dev.alloc(sizeof(int32_t) * md.tasks.fwd_start.size()));
-  SBFWI_CUDA(md.tasks.bwd_start_dev.alloc(sizeof(int32_t) * md.tasks.bwd_start.size()));
-  SBFWI_CUDA(cudaMemcpy(md.tasks.fwd_start_dev.p, md.tasks.fwd_start.data(), sizeof(int32_t) * md.tasks.fwd_start.size(),
-                        cudaMemcpyHostToDevice));
-  SBFWI_CUDA(cudaMemcpy(md.tasks.bwd_start_dev.p, md.tasks.bwd_start.data(), sizeof(int32_t) * md.tasks.bwd_start.size(),
-                        cudaMemcpyHostToDevice));
-  SBFWI_CUDA(md.tasks.fwd.alloc(sizeof(Task) * fwd.size()));
-  SBFWI_CUDA(md.tasks.bwd.alloc(sizeof(Task) * std::max<size_t>(bwd.size(), 1)));
-  SBFWI_CUDA(cudaMemcpy(md.tasks.fwd.p, fwd.data(), sizeof(Task) * fwd.size(), cudaMemcpyHostToDevice));
-  if (!bwd.empty()) SBFWI_CUDA(cudaMemcpy(md.tasks.bwd.p, bwd.data(), sizeof(Task) * bwd.size(), cudaMemcpyHostToDevice));
-  md.tasks.shots = B;
+  lt.fwd_start[L] = (int32_t)fwd.size();
+  lt.bwd_start[L] = (int32_t)bwd.size();
+  lt.block_doubles = 1;
+  for (int l = 0; l < L; ++l) {
+    for (int k = lt.fwd_start[l]; k < lt.fwd_wstart[l]; ++k)
+      lt.block_doubles = std::max(lt.block_doubles, block_task_doubles(fwd[k], B, true));
+    for (int k = lt.bwd_start[l]; k < lt.bwd_wstart[l]; ++k)
+      lt.block_doubles = std::max(lt.block_doubles, block_task_doubles(bwd[k], B, false));
+  }
+  lt.max_level_items = 1;
+  for (int l = 0; l < L; ++l) lt.max_level_items = std::max({lt.max_level_items, lt.items(true, l), lt.items(false, l)});
+  auto upload_meta = [&](DevBuf& dst, const std::vector<int32_t>& st, const std::vector<int32_t>& ws,
+                         const std::vector<int32_t>& gr) -> int {
+    std::vector<int32_t> meta(st);
+    meta.insert(meta.end(), ws.begin(), ws.end());
+    meta.insert(meta.end(), gr.begin(), gr.end());
+    SBFWI_CUDA(dst.alloc(sizeof(int32_t) * meta.size()));
+    SBFWI_CUDA(cudaMemcpy(dst.p, meta.data(), sizeof(int32_t) * meta.size(), cudaMemcpyHostToDevice));
+    return SBFWI_OK;
+  };
+  int rc = upload_meta(lt.fwd_meta, lt.fwd_start, lt.fwd_wstart, lt.fwd_group);
+  if (rc) return rc;
+  rc = upload_meta(lt.bwd_meta, lt.bwd_start, lt.bwd_wstart, lt.bwd_group);
+  if (rc) return rc;
+  SBFWI_CUDA(lt.fwd.alloc(sizeof(Task) * std::max<size_t>(fwd.size(), 1)));
+  SBFWI_CUDA(lt.bwd.alloc(sizeof(Task) * std::max<size_t>(bwd.size(), 1)));
+  if (!fwd.empty()) SBFWI_CUDA(cudaMemcpy(lt.fwd.p, fwd.data(), sizeof(Task) * fwd.size(), cudaMemcpyHostToDevice));
+  if (!bwd.empty()) SBFWI_CUDA(cudaMemcpy(lt.bwd.p, bwd.data(), sizeof(Task) * bwd.size(), cudaMemcpyHostToDevice));
+  lt.shots = B;
+  lt.grid = grid;
   return SBFWI_OK;
 }
 
@@ -582,10 +798,14 @@ struct Stepper {
   BoundaryArgs ba;
   const Task* ftasks = nullptr;
   const Task* btasks = nullptr;
-  size_t fwd_smem = 0, bwd_smem = 0, p_smem = 0, e_smem = 0;
+  size_t s_smem = 0, e_smem = 0;
   int e_threads = 0, p_grid = 0;
   unsigned e_blocks = 0, b_blocks = 0;
   DevBuf bar, pstatus;
+  bool use_window = false;
+  cudaAccessPolicyWindow window = {};
+  int setup_l2_window(int device);
+  int launch_solve(const void* fn, unsigned grid, void** args, bool cooperative);
   std::vector<DevBuf*> state_bufs() const;
   int element_launch(int down, int up, int64_t done_step);
   int solve();
@@ -620,18 +840,23 @@ int Stepper::init() {
   }
   int rc = zero_state();
   if (rc) return rc;
-  if (md.tasks.shots != B) {
-    rc = build_level_tasks(md, B);
+  // the solve's tasks are built for 4 blocks per SM; a block task stages its front's
+  // vectors and its rows of the factors in shared memory, a warp task the same for a
+  // whole small front, one slice per warp
+  int device = 0, coop = 0, sms = 0, per_sm = 0;
+  SBFWI_CUDA(cudaGetDevice(&device));
+  SBFWI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
+  SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  const int grid = 4 * sms;
+  if (md.tasks.shots != B || md.tasks.grid != grid) {
+    rc = build_level_tasks(md, B, grid);
     if (rc) return rc;
   }
-  int smax = 0, bmax = 0;
-  for (const TreeNodeDev& r : t.nodes) { smax = std::max(smax, r.s); bmax = std::max(bmax, r.b); }
-  fwd_smem = sizeof(double) * (size_t)smax * B;
-  bwd_smem = sizeof(double) * (size_t)(smax + bmax) * B;
-  if (bwd_smem > 48 * 1024)
-    SBFWI_CUDA(cudaFuncSetAttribute(solve_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem));
-  if (fwd_smem > 48 * 1024)
-    SBFWI_CUDA(cudaFuncSetAttribute(solve_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem));
+  s_smem = sizeof(double) * std::max(md.tasks.block_doubles, 8 * solve_warp_doubles(B));
+  if (s_smem > 200 * 1024) return fail(SBFWI_EUNSUPPORTED, "solve staging area exceeds shared memory");
+  for (const void* f : {(const void*)solve_forward_kernel, (const void*)solve_backward_kernel,
+                        (const void*)solve_persistent_kernel})
+    if (s_smem > 48 * 1024) SBFWI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem));
 
   ea.nb = nb; ea.n = n; ea.B = B; ea.E = E;
   ea.epc = std::max(1, 128 / (nb * B));
@@ -647,26 +872,22 @@ int Stepper::init() {
     SBFWI_CUDA(cudaFuncSetAttribute(element_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem));
 
   const MeshDevice& mdev = md.dev();
-  sa.sep_nodes = mdev.sep_nodes.as<int32_t>(); sa.bnd_nodes = mdev.bnd_nodes.as<int32_t>();
-  sa.src0 = mdev.src0.as<int32_t>(); sa.src1 = mdev.src1.as<int32_t>(); sa.factors = md.factors.as<double>();
+  sa.sep_nodes = md.solve_sep; sa.bnd_nodes = md.solve_bnd;
+  sa.src0 = md.solve_src0; sa.src1 = md.solve_src1; sa.factors = md.factors.as<double>();
   sa.fhat = rb.fhat.as<double>(); sa.ext = rb.ext.as<double>();
   sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
   sa.nb = nb; sa.B = B;
-  ftasks = md.tasks.fwd.as<Task>();
-  btasks = md.tasks.bwd.as<Task>();
+  sa.warp_doubles = (int)solve_warp_doubles(B);
 
   // one cooperative persistent launch per time step for the whole tree, unless the
   // device cannot launch cooperatively or SBFWI_SOLVE=levels asks for one launch per level
-  int device = 0, coop = 0, sms = 0, per_sm = 0;
-  SBFWI_CUDA(cudaGetDevice(&device));
-  SBFWI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
-  SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-  p_smem = std::max(fwd_smem, bwd_smem);
-  if (p_smem > 48 * 1024)
-    SBFWI_CUDA(cudaFuncSetAttribute(solve_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p_smem));
-  SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_persistent_kernel, 256, p_smem));
+  SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_persistent_kernel, 256, s_smem));
   const char* solve_env = std::getenv("SBFWI_SOLVE");
   persistent = coop && per_sm > 0 && !(solve_env && std::strcmp(solve_env, "levels") == 0);
+  ftasks = md.tasks.fwd.as<Task>();
+  btasks = md.tasks.bwd.as<Task>();
+  rc = setup_l2_window(device);
+  if (rc) return rc;
   if (persistent) {
     SBFWI_CUDA(bar.alloc(2 * sizeof(unsigned)));
     SBFWI_CUDA(pstatus.alloc(sizeof(int)));
@@ -674,13 +895,12 @@ int Stepper::init() {
     SBFWI_CUDA(cudaMemsetAsync(pstatus.p, 0, pstatus.bytes, st));
     pa.s = sa;
     pa.fwd = ftasks; pa.bwd = btasks;
-    pa.fwd_start = md.tasks.fwd_start_dev.as<int32_t>(); pa.bwd_start = md.tasks.bwd_start_dev.as<int32_t>();
+    pa.fwd_meta = md.tasks.fwd_meta.as<int32_t>(); pa.bwd_meta = md.tasks.bwd_meta.as<int32_t>();
     pa.levels = t.levels;
     pa.bar = bar.as<unsigned>(); pa.status = pstatus.as<int>();
     pa.budget = 4000000000LL;            // ~2 s at 2 GHz
     pa.trace = nullptr;
-    p_grid = std::min(per_sm, 4) * sms;
-    p_grid = std::max(1, std::min(p_grid, md.tasks.max_level_tasks));
+    p_grid = std::max(1, std::min(std::min(per_sm, 4) * sms, md.tasks.max_level_items));
   }
 
   ba.N = N; ba.B = B; ba.R = 0;
@@ -689,6 +909,63 @@ int Stepper::init() {
   ba.x = rb.x.as<double>(); ba.ub = rb.ub.as<double>(); ba.udb = rb.udb.as<double>(); ba.uddb = rb.uddb.as<double>();
   ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
   b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
+  return SBFWI_OK;
+}
+
+// The solve reads the same factors and index arrays every step, but the element
+// kernel streams gigabytes through L2 in between and would evict them.  Mark that one
+// range persisting (an access policy window on the solve launches) and, if the
+// context's persisting L2 set-aside is smaller, raise it to cover the range (a limit
+// of this process's context; SBFWI_L2_PERSIST=0 leaves L2 alone).
+int Stepper::setup_l2_window(int device) {
+  use_window = false;
+  const char* env = std::getenv("SBFWI_L2_PERSIST");
+  if (env && std::strcmp(env, "0") == 0) return SBFWI_OK;
+  int max_persist = 0, max_window = 0;
+  if (cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, device) != cudaSuccess) {
+    cudaGetLastError();
+    return SBFWI_OK;
+  }
+  if (max_persist <= 0 || max_window <= 0 || md.solve_bytes == 0) return SBFWI_OK;
+  const size_t want = std::min(md.solve_bytes, (size_t)max_persist);
+  size_t cur = 0;
+  SBFWI_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+  if (cur < want) {
+    SBFWI_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+    SBFWI_CUDA(cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+  }
+  if (cur == 0) return SBFWI_OK;
+  window.base_ptr = md.factors.p;
+  window.num_bytes = std::min(md.solve_bytes, (size_t)max_window);
+  window.hitRatio = (float)std::min(1.0, (double)cur / (double)window.num_bytes);
+  window.hitProp = cudaAccessPropertyPersisting;
+  window.missProp = cudaAccessPropertyStreaming;
+  use_window = true;
+  return SBFWI_OK;
+}
+
+int Stepper::launch_solve(const void* fn, unsigned grid, void** args, bool cooperative) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = s_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (cooperative) {
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    ++na;
+  }
+  if (use_window) {
+    attr[na].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[na].val.accessPolicyWindow = window;
+    ++na;
+  }
+  cfg.attrs = attr;
+  cfg.numAttrs = na;
+  SBFWI_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
   return SBFWI_OK;
 }
 
@@ -753,25 +1030,31 @@ int Stepper::solve() {
   const Tree& t = md.mesh->tree;
   prof.begin(kPhaseSolve, st);
   if (persistent) {
-    pa.trace = prof.level_trace(2 * t.levels, st);
+    pa.trace = prof.level_trace(6 * t.levels, st);
     if (pa.trace) ++prof.level_steps;
     void* kargs[] = {&pa};
-    SBFWI_CUDA(cudaLaunchCooperativeKernel((const void*)solve_persistent_kernel, dim3(p_grid), dim3(256), kargs,
-                                           p_smem, st));
+    int rc = launch_solve((const void*)solve_persistent_kernel, (unsigned)p_grid, kargs, true);
+    if (rc) return rc;
     prof.count(kPhaseSolve);
   } else {
+    LevelKernelArgs la;
+    la.s = sa; la.levels = t.levels;
     for (int l = 0; l < t.levels; ++l) {
-      const int cnt = md.tasks.fwd_start[l + 1] - md.tasks.fwd_start[l];
+      const int cnt = md.tasks.items(true, l);
       if (cnt == 0) continue;
-      sa.tasks = ftasks + md.tasks.fwd_start[l];
-      solve_forward_kernel<<<cnt, 256, fwd_smem, st>>>(sa);
+      la.tasks = ftasks; la.meta = md.tasks.fwd_meta.as<int32_t>(); la.level = l;
+      void* kargs[] = {&la};
+      int rc = launch_solve((const void*)solve_forward_kernel, (unsigned)cnt, kargs, false);
+      if (rc) return rc;
       prof.count(kPhaseSolve);
     }
     for (int l = t.levels - 1; l >= 0; --l) {
-      const int cnt = md.tasks.bwd_start[l + 1] - md.tasks.bwd_start[l];
+      const int cnt = md.tasks.items(false, l);
       if (cnt == 0) continue;
-      sa.tasks = btasks + md.tasks.bwd_start[l];
-      solve_backward_kernel<<<cnt, 256, bwd_smem, st>>>(sa);
+      la.tasks = btasks; la.meta = md.tasks.bwd_meta.as<int32_t>(); la.level = l;
+      void* kargs[] = {&la};
+      int rc = launch_solve((const void*)solve_backward_kernel, (unsigned)cnt, kargs, false);
+      if (rc) return rc;
       prof.count(kPhaseSolve);
     }
   }
@@ -794,7 +1077,8 @@ int Stepper::run(int64_t k0, int64_t k1) {
       sources_kernel<<<(B * R + 127) / 128, 128, 0, st>>>(rb.ext.as<double>(), B, R, nodes, values, K, K - 1 - k, 0);
       prof.count(kPhaseOther);
     }
-    solve();
+    int rc = solve();
+    if (rc) return rc;
     ba.k = k;
     if (mode == Mode::Forward) {
       ba.R = R;

@@ -257,7 +257,6 @@ struct ElemTcArgs {
   double* store_int;
   const double* fwd_int;
   double* grad_int;
-  int a2_is_one;        // beta = 1/4: the predictor needs no multiply by a2
 };
 
 namespace tc {
@@ -296,6 +295,7 @@ __device__ __forceinline__ void stage_ops(uint4* dst, int* dexp, const uint4* sr
 // shared memory (cp.async, two stages) while the current point computes, and each
 // point's state is loaded before its products, so the memory latency overlaps the
 // tensor-core and integer work instead of stalling every radial point.
+template <bool kA2One>
 __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
   using namespace tc;
   extern __shared__ __align__(16) unsigned char tc_smem[];
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
           const double udn = fma(a.c2, uddn, fma(a.c1, uddo[j], udo[j]));
           // the interior displacement is not kept: the predictor v carries it
           a.ud[o] = udn; a.udd[o] = uddn;
-          a.v[o] = a.a2_is_one ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+          a.v[o] = kA2One ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
           if (a.store_int) a.store_int[o] = udn;
           if (a.grad_int) a.grad_int[o] = fma(fw[j], udn, gr[j]);    // dt applied at the end
           un[j] = u_new;
@@ -482,8 +482,8 @@ int tc_prepare(Model& md, cudaStream_t st) {
   profiler().count(kPhaseSetup);
   SBFWI_CUDA(cudaGetLastError());
   // the element kernel's two-stage operator pipeline needs more than the default 48 KiB
-  SBFWI_CUDA(cudaFuncSetAttribute(element_step_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(WarpSmem) * kWarpsPerBlock)));
+  for (const void* f : {(const void*)element_step_tc_kernel<true>, (const void*)element_step_tc_kernel<false>})
+    SBFWI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(WarpSmem) * kWarpsPerBlock)));
   md.tc_ready = true;
   return SBFWI_OK;
 }
@@ -500,10 +500,11 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
   a.do_down = down; a.do_up = up;
   a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
-  a.a2_is_one = md.a2 == 1.0;
   const int smem = (int)(sizeof(tc::WarpSmem) * tc::kWarpsPerBlock);   // attribute set by tc_prepare
-  element_step_tc_kernel<<<(unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock), 32 * tc::kWarpsPerBlock,
-                           smem, st>>>(a);
+  const unsigned blocks = (unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock);
+  // beta = 1/4 (a2 = 1): the predictor needs no multiply by a2
+  if (md.a2 == 1.0) element_step_tc_kernel<true><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);
+  else element_step_tc_kernel<false><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);
   return SBFWI_OK;
 }
 

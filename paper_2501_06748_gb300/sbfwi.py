@@ -95,15 +95,18 @@ def profile_read(reset: bool = False) -> dict:
 
 
 def profile_solve_levels(reset: bool = False):
-    """Mean wall time (us) of every barrier-separated phase of the one-launch global
-    solve while profiling was on: forward levels (leaves -> root), then backward
-    levels (root -> leaves).  Returns (array of 2L values, solves recorded)."""
+    """Per-phase timing (us) of the one-launch global solve while profiling was on
+    (phases: forward levels leaves -> root, then backward levels root -> leaves).
+    Returns (dict with 'wall' [2L] mean per solve seen by block 0, 'busy_max' [2L]
+    longest time one block spent in a phase's tasks, 'busy_sum' [2L] mean per solve
+    summed over blocks), solves recorded)."""
     cap = 256
     us = np.zeros(cap)
     n = ctypes.c_int32(0)
     steps = ctypes.c_int64(0)
     _check(_lib.sbfwi_profile_solve_levels(_dptr(us), cap, ctypes.byref(n), ctypes.byref(steps), 1 if reset else 0))
-    return us[:n.value].copy(), int(steps.value)
+    k = n.value // 3
+    return {"wall": us[:k].copy(), "busy_max": us[k:2 * k].copy(), "busy_sum": us[2 * k:3 * k].copy()}, int(steps.value)
 
 
 def _is_torch_cuda(x) -> bool:
