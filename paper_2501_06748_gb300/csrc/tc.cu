@@ -66,6 +66,10 @@ __device__ __forceinline__ int exp_bound(double a) {
   return ex - 1022;
 }
 
+// t * 2^E for results outside the normal range (never met by the path's fields): kept
+// out of line so that its FP64 conversion is not evaluated speculatively on the hot path
+__device__ __noinline__ double int_to_double_scaled_slow(long long t, int E) { return ldexp((double)t, E); }
+
 // t * 2^E as a binary64, rounded to nearest-even like a conversion of t, built with
 // integer operations (the scaling by 2^E is exact unless the result is subnormal)
 __device__ __forceinline__ double int_to_double_scaled(long long t, int E) {
@@ -81,7 +85,7 @@ __device__ __forceinline__ double int_to_double_scaled(long long t, int E) {
   if (hi == (1ULL << 53)) { hi >>= 1; ++bexp; }
   if (bexp >= 1 && bexp <= 2046)
     return __longlong_as_double((long long)(sign | ((unsigned long long)bexp << 52) | (hi & 0x000FFFFFFFFFFFFFULL)));
-  return ldexp((double)t, E);
+  return int_to_double_scaled_slow(t, E);
 }
 
 // six balanced base-512 digits, most significant first, as FP16 bit patterns of 1536 + d
