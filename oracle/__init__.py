@@ -21,6 +21,10 @@ Modules, in the order of the paper:
 * ``bruteforce`` -- the full uncondensed element systems of Eq. (system) plus the
   boundary flux balance, solved densely: an independent route to the same
   discrete solution, and the pencil for free-vibration frequencies.
+* ``modex``      -- the exact derivative of the discrete misfit with respect to the
+  nodal densities, by reverse-mode differentiation of the uncondensed time loop
+  (pinned by central finite differences); the reference the paper's velocity
+  kernel is compared with.
 * ``lfe``        -- Section 3.2: the reduced (constant radial density) equation's
   low-frequency expansion, Riccati stiffness and Lyapunov mass.
 

@@ -98,10 +98,12 @@ class FullSystem:
         self.matrix = sp.coo_matrix((f64(cat(vals)), (cat(rows), cat(cols))), shape=(self.size, self.size)).tocsc()
         self.mass = sp.coo_matrix((f64(cat(mvals)), (cat(mrows), cat(mcols))), shape=(self.size, self.size)).tocsc()
 
-    def _matvec_xp(self, x, mass=False):
+    def _matvec_xp(self, x, mass=False, transpose=False):
         """Extended-precision product of the assembled (uncondensed) matrix, or of the
-        mass pencil matrix, with x (shape (size,) or (size, B))."""
+        mass pencil matrix, or of its transpose, with x (shape (size,) or (size, B))."""
         r, c, v = self._mcoo if mass else self._coo
+        if transpose:
+            r, c = c, r
         x = np.asarray(x)
         out = np.zeros((self.size,) + x.shape[1:], dtype=v.dtype)
         vv = v.reshape((-1,) + (1,) * (x.ndim - 1))
@@ -110,7 +112,32 @@ class FullSystem:
 
     # -- time stepping with a direct solve of the whole system each step --------
 
+    def solve(self, rhs, transpose=False):
+        """x with A x = rhs (or A^T x = rhs): dense LU in float64 (condition number ~1e7
+        from the xi0 = 1e-3 rows), then iterative refinement with residuals in extended
+        precision."""
+        if not hasattr(self, "_lu"):
+            self._lu = sla.lu_factor(self.matrix.toarray())
+        tr = 1 if transpose else 0
+        x = sla.lu_solve(self._lu, rhs, trans=tr).astype(sbfem.XP)
+        for _ in range(3):
+            res = np.asarray(rhs).astype(sbfem.XP) - self._matvec_xp(x, transpose=transpose)
+            x = x + sla.lu_solve(self._lu, np.asarray(res, dtype=np.float64), trans=tr)
+        return np.asarray(x, dtype=np.float64)
+
+    def row_index(self, e, i):
+        """Rows of element e's equation i = -1..n (element rows) or n+1 (flux rows)."""
+        nb, n = self.nb, self.n
+        if i == n + 1:
+            return self.n_elem_unknowns + self.elements[e].dofs
+        return e * (n + 2) * nb + (i + 1) * nb + np.arange(nb)
+
     def step(self, st: fwi.State, f_ext: np.ndarray) -> fwi.State:
+        return self.step_full(st, f_ext)[2]
+
+    def step_full(self, st: fwi.State, f_ext: np.ndarray):
+        """One Newmark step of the whole uncondensed system; returns (x, predictor
+        (E, n+1, n_b, B) at radial points 0..n, new state)."""
         n, nb, E = self.n, self.nb, self.E
         B = st.ub.shape[1]
         rhs = np.zeros((self.size, B))
@@ -118,22 +145,14 @@ class FullSystem:
         u = np.concatenate([st.u, st.ub[dofs][:, None]], axis=1)
         ud = np.concatenate([st.ud, st.udb[dofs][:, None]], axis=1)
         udd = np.concatenate([st.udd, st.uddb[dofs][:, None]], axis=1)
-        pall = sbfem.residual_source(self.xi, self.M0_64, fwi.newmark_predictor(u, ud, udd, self.dt, self.beta))
+        pred = fwi.newmark_predictor(u, ud, udd, self.dt, self.beta)
+        pall = sbfem.residual_source(self.xi, self.M0_64, pred)
         for e in range(E):
             p = pall[e]
             for i in range(n + 1):
-                ridx = e * (n + 2) * nb + (i + 1) * nb + np.arange(nb)
-                rhs[ridx] = p[i]
+                rhs[self.row_index(e, i)] = p[i]
         rhs[self.n_elem_unknowns:] += f_ext
-        if not hasattr(self, "_lu"):
-            self._lu = sla.lu_factor(self.matrix.toarray())
-        # dense LU in float64 (condition number ~1e7 from the xi0 = 1e-3 rows), then
-        # iterative refinement with residuals in extended precision
-        x = sla.lu_solve(self._lu, rhs).astype(sbfem.XP)
-        for _ in range(3):
-            res = rhs.astype(sbfem.XP) - self._matvec_xp(x)
-            x = x + sla.lu_solve(self._lu, np.asarray(res, dtype=np.float64))
-        x = np.asarray(x, dtype=np.float64)
+        x = self.solve(rhs)
         u_int = np.empty((E, n, nb, B))
         for e in range(E):
             for i in range(n):
@@ -141,7 +160,7 @@ class FullSystem:
         ub = x[self.n_elem_unknowns:]
         ud_i, udd_i = fwi.newmark_update(st.u, st.ud, st.udd, u_int, self.dt, self.beta, self.gamma)
         ud_b, udd_b = fwi.newmark_update(st.ub, st.udb, st.uddb, ub, self.dt, self.beta, self.gamma)
-        return fwi.State(u_int, ud_i, udd_i, ub, ud_b, udd_b)
+        return x, pred, fwi.State(u_int, ud_i, udd_i, ub, ud_b, udd_b)
 
     def forward(self, src_nodes, wavelets, rec_nodes, K=None):
         src_nodes = np.asarray(src_nodes)
