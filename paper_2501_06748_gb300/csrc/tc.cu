@@ -9,8 +9,10 @@
 //
 //  * every row r of a matrix A is scaled by 2^(53 - e_r), |A[r][.]| < 2^e_r, and
 //    rounded to an integer of at most 53 bits; every column (shot) of a vector x the
-//    same with its own exponent f; each of the five products has its own exponents
-//    (a shared exponent for P v + Q q loses ~1e-12 relative near the scaling centre);
+//    same with its own exponent f; P v + Q q is one product of [P | Q 2^-a] and
+//    [v ; q 2^a] with a per-point balancing power a (a shared exponent without it
+//    loses ~1e-12 relative near the scaling centre, where |P| << |Q|), H u, R q and
+//    T v are scaled on their own;
 //  * each integer is written in six balanced base-512 digits (|digit| <= 257, exact
 //    in FP16): A_int = sum_k a_k 2^(9(6-k)), x_int = sum_l x_l 2^(9(6-l));
 //  * the digit products of one significance level L = k + l are summed by
@@ -24,7 +26,9 @@
 // The splitting of the vectors and the recombination are integer work; what stays on
 // the FP64 pipe is the conversion of each result and the Newmark arithmetic.
 // Shapes: n_b <= 16 (padded to the 16 rows/columns of one m16n8k16 tile) and B <= 8
-// shots (padded to its 8 columns); one warp per element.
+// shots (padded to its 8 columns); one warp per element.  The joint product sums two
+// k-tiles into each level: at most 12 digit products of <= 257^2 times 16 terms,
+// 1.3e7 < 2^24, still exact in FP32.
 #include <cstdint>
 #include <cuda_fp16.h>
 
@@ -179,10 +183,15 @@ __device__ __forceinline__ void zero(float (&acc)[kLevels][4]) {
 // ---------------------------------------------------------------------------
 // Operators per element and radial point i: P_i, Q_i, H_i (16 x 16 each after
 // padding); per element R and T.  Each is stored as kSlices fragments of 32 lanes x
-// uint4 with its own 16 row exponents.  Every product is scaled on its own: a pair
-// such as P_i v_i + Q_i q_{i-1} is formed as two products recombined separately,
-// because P and Q (and v and q) differ by orders of magnitude near the scaling
-// centre and a shared exponent would cost them significant bits.
+// uint4 with 16 row exponents.
+//
+// P_i v_i + Q_i q_{i-1} is formed as ONE product [P_i | Q_i 2^-a][v_i ; q_{i-1} 2^a]
+// with shared row exponents (over both halves) and a shared column exponent, where the
+// balancing power a_i = e(Q_i) - e(P_i) of the two blocks' largest entries brings them
+// to the same scale (P ~ 1e-4 and Q ~ 0.5 near the scaling centre, and q ~ |P| v, so
+// q 2^a ~ v).  Without the balancing a shared exponent would cost the smaller block a
+// dozen bits.  P's exponent slot holds the joint row exponents, Q's slot holds a_i in
+// its first entry.  H, R and T are scaled on their own.
 struct SliceArgs {
   int nb, n;
   int64_t E;
@@ -218,11 +227,32 @@ __global__ void slice_operators_kernel(SliceArgs a) {
   }
   auto val = [&](int r, int c) { return (r < nb && c < nb) ? h[(int64_t)r * nb + c] : 0.0; };
   int er = -1100;           // lanes 0..15 own one row each
-  if (lane < 16) {
+  if (lane < 16)
     for (int c = 0; c < nb; ++c) er = max(er, exp_bound(val(lane, c)));
-    eout[lane] = er;
+  // P or Q of a radial point: joint row exponents with the balancing power a
+  const int which = w < nmat ? (int)(w % 3) : 2;
+  int shift = 0;            // this operator's digits are taken at row exponent + shift
+  if (which < 2) {
+    const double* hP = which == 0 ? h : h - nn;
+    const double* hQ = hP + nn;
+    auto vP = [&](int r, int c) { return (r < nb && c < nb) ? hP[(int64_t)r * nb + c] : 0.0; };
+    auto vQ = [&](int r, int c) { return (r < nb && c < nb) ? hQ[(int64_t)r * nb + c] : 0.0; };
+    int eP = -1100, eQ = -1100;
+    if (lane < 16)
+      for (int c = 0; c < nb; ++c) { eP = max(eP, exp_bound(vP(lane, c))); eQ = max(eQ, exp_bound(vQ(lane, c))); }
+    int mP = eP, mQ = eQ;
+    for (int off = 16; off > 0; off >>= 1) {
+      mP = max(mP, __shfl_xor_sync(0xffffffffu, mP, off));
+      mQ = max(mQ, __shfl_xor_sync(0xffffffffu, mQ, off));
+    }
+    const int bal = (mP > -1100 && mQ > -1100) ? mQ - mP : 0;
+    er = max(eP, eQ > -1100 ? eQ - bal : -1100);
+    shift = which == 0 ? 0 : bal;
+    if (which == 1 && lane == 0) eout[0] = bal;
+    if (which == 1 && lane > 0 && lane < 16) eout[lane] = 0;
   }
-  const int e_lo = __shfl_sync(0xffffffffu, er, g), e_hi = __shfl_sync(0xffffffffu, er, g + 8);
+  if (lane < 16 && which != 1) eout[lane] = er;
+  const int e_lo = __shfl_sync(0xffffffffu, er, g) + shift, e_hi = __shfl_sync(0xffffffffu, er, g + 8) + shift;
   // fragment entries: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1), then columns + 8
   unsigned short dg[8][kSlices];
 #pragma unroll
@@ -353,6 +383,28 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
     for (int j = 0; j < 4; ++j) y[j] = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
   };
 
+  // y = [P | Q 2^-a][v ; q 2^a] for one radial point: P's and Q's digits in shared
+  // memory, joint row exponents in rexp, a in aexp[0]; returned in C layout
+  auto apply_pq = [&](const uint4* Pf, const uint4* Qf, const int* rexp, const int* aexp, const double (&vbv)[4],
+                      const double (&qbv)[4], double (&y)[4]) {
+    const int bal = aexp[0];
+    int fl = -1100;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) fl = max(fl, max(exp_bound(vbv[j]), exp_bound(qbv[j]) + bal));
+    const int f = column_exponent(fl);
+    BDigits dv, dq;
+    split_b(vbv, f, dv);
+    split_b(qbv, f - bal, dq);
+    float acc[kLevels][4];
+    zero(acc);
+    product(acc, Pf + lane, dv);
+    product(acc, Qf + lane, dq);
+    const int er0 = rexp[g], er1 = rexp[g + 8];
+    const int fc0 = __shfl_sync(0xffffffffu, f, 4 * cc[0]), fc1 = __shfl_sync(0xffffffffu, f, 4 * cc[1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) y[j] = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
+  };
+
   double xb[4];       // the operand of the next product, B layout
   if (a.do_down) {
     const int64_t hop = (int64_t)3 * kSlices * 32;       // uint4 between radial points
@@ -430,13 +482,12 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
     }
     cp_async_wait<1>();
     __syncwarp();
-    double pv[4], qq[4] = {0.0, 0.0, 0.0, 0.0};
-    apply(W.frag[buf], W.exps[buf], vb, pv);
-    if (i > 0) apply(W.frag[buf] + kSlices * 32, W.exps[buf] + 16, qb, qq);
+    double pq[4];
+    apply_pq(W.frag[buf], W.frag[buf] + kSlices * 32, W.exps[buf], W.exps[buf] + 16, vb, qb, pq);
     double qc[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      qc[j] = -(pv[j] + qq[j]);
+      qc[j] = -pq[j];
       if (cok[j]) a.q[base + (int64_t)i * per + cr[j] * B + cc[j]] = qc[j];
       else qc[j] = 0.0;
     }
