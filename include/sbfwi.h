@@ -238,9 +238,10 @@ int sbfwi_profile_enable(int on);
 int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int reset);
 
 /*
- * Per-level tracing of the one-launch global solve (a diagnostic of this
- * implementation; the paper does not specify the solver).  While profiling is on,
- * every persistent solve launch reads the global timer around each phase (a tree
+ * Per-level tracing of the one-launch global solve with grid barriers between
+ * levels (SBFWI_SOLVE=barrier; a diagnostic of this implementation, the paper does
+ * not specify the solver; the default dataflow solve has no levels to time).
+ * While profiling is on, every such launch reads the global timer around each phase (a tree
  * level of one pass, between two grid barriers).  Phases 0..L-1 are the forward
  * (leaves -> root) levels, L..2L-1 the backward levels (root -> leaves).  Slots
  * [0, 2L): wall time of the phase seen by block 0 (the last phase ends when block

@@ -151,6 +151,11 @@ struct LevelTasks {
   int grid = 0;                                 // and this many blocks
   int max_level_items = 0;
   size_t block_doubles = 0;                     // largest staging area of a block task
+  // the same tasks as one dataflow: items {first task, count, block?, direction} in
+  // topological order, and per tree node [forward tasks | backward tasks | child0 |
+  // child1 | nearest ancestor with backward tasks]
+  DevBuf flow_items, node_info;
+  int n_items = 0, nodes = 0;
   int items(bool fwd, int l) const {
     const auto& st = fwd ? fwd_start : bwd_start;
     const auto& ws = fwd ? fwd_wstart : bwd_wstart;

@@ -486,6 +486,117 @@ __global__ void __launch_bounds__(256) solve_persistent_kernel(PersistentSolveAr
   }
 }
 
+// ---------------------------------------------------------------------------
+// the same solve as a dataflow: no grid barriers.  Blocks claim work items in a
+// topological order (forward items leaves -> root, then backward items root ->
+// leaves) from one counter; an item waits only for the tasks it reads from: a
+// forward task for every forward task of its children, a backward task for the
+// forward tasks of its own node and the backward tasks of its nearest ancestor that
+// has any.  Counters are cumulative over the launches of one time loop: after g
+// solves a node has g * n tasks done.  Every dependency of an item lies in an item
+// claimed earlier and all blocks are co-resident, so the earliest unfinished claimed
+// item can always proceed; every wait is still bounded and reports SBFWI_ETIMEOUT.
+// ---------------------------------------------------------------------------
+struct FlowArgs {
+  SolveArgs s;
+  const Task* fwd;
+  const Task* bwd;
+  const int4* items;          // {first task, count, block (1) or warp group (0), direction (0 fwd, 1 bwd)}
+  int n_items;
+  const int32_t* node_info;   // [5][nodes]: forward tasks, backward tasks, child0, child1, backward dependency
+  int nodes;
+  unsigned* done_f;           // [nodes] forward tasks completed (cumulative)
+  unsigned* done_b;           // [nodes] backward tasks completed (cumulative)
+  unsigned long long* claim;  // item counter (cumulative)
+  unsigned long long base;    // counter value at the start of this launch
+  unsigned gen;               // this launch's number in the time loop, from 1
+  int* status;
+  long long budget;
+};
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(volatile const unsigned*)p; }
+
+// one thread: wait until counter >= target; false if the budget ran out or another
+// wait gave up
+__device__ bool wait_count(const unsigned* counter, unsigned target, int* status, long long budget) {
+  if (ld_volatile(counter) >= target) return true;
+  const long long t0 = clock64();
+  while (ld_volatile(counter) < target) {
+    if (clock64() - t0 > budget || *(volatile int*)status != 0) {
+      atomicCAS(status, 0, SBFWI_ETIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+  return true;
+}
+
+__device__ bool wait_deps(const FlowArgs& a, const Task& tk, int dir) {
+  const int T = a.nodes;
+  const int32_t* nf = a.node_info;
+  const int32_t* nbk = a.node_info + T;
+  const int32_t* c0 = a.node_info + 2 * T;
+  const int32_t* c1 = a.node_info + 3 * T;
+  const int32_t* dep = a.node_info + 4 * T;
+  bool ok = true;
+  if (dir == 0) {
+    const int ch[2] = {c0[tk.node], c1[tk.node]};
+    for (int k = 0; k < 2 && ok; ++k)
+      if (ch[k] >= 0) ok = wait_count(a.done_f + ch[k], a.gen * (unsigned)nf[ch[k]], a.status, a.budget);
+  } else {
+    ok = wait_count(a.done_f + tk.node, a.gen * (unsigned)nf[tk.node], a.status, a.budget);
+    const int d = dep[tk.node];
+    if (ok && d >= 0) ok = wait_count(a.done_b + d, a.gen * (unsigned)nbk[d], a.status, a.budget);
+  }
+  __threadfence();
+  return ok;
+}
+
+__global__ void __launch_bounds__(256) solve_flow_kernel(FlowArgs a) {
+  extern __shared__ double sm_f[];
+  __shared__ long long s_item;
+  __shared__ int s_ok;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    // a wait that gave up anywhere stops every block at its next claim
+    if (threadIdx.x == 0)
+      s_item = *(volatile int*)a.status != 0 ? (long long)a.n_items
+                                            : (long long)(atomicAdd(a.claim, 1ULL) - a.base);
+    __syncthreads();
+    const long long it = s_item;
+    __syncthreads();
+    if (it >= a.n_items) return;
+    const int4 im = a.items[it];
+    const Task* tasks = im.w ? a.bwd : a.fwd;
+    if (im.z) {                                            // block task
+      const Task tk = tasks[im.x];
+      if (threadIdx.x == 0) s_ok = wait_deps(a, tk, im.w) ? 1 : 0;
+      __syncthreads();
+      if (!s_ok) return;
+      if (im.w) solve_backward_task(a.s, tk, sm_f);
+      else solve_forward_task(a.s, tk, sm_f);          // both end with __syncthreads
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd((im.w ? a.done_b : a.done_f) + tk.node, 1u);
+      }
+    } else if (warp < im.y) {                              // warp task
+      const Task tk = tasks[im.x + warp];
+      int ok = 1;
+      if (lane == 0) ok = wait_deps(a, tk, im.w) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (ok) {                                            // else: the status stops the block at its next claim
+        double* wsm = sm_f + (size_t)warp * a.s.warp_doubles;
+        if (im.w) solve_backward_warp(a.s, tk, wsm, lane);
+        else solve_forward_warp(a.s, tk, wsm, lane);    // both end with __syncwarp
+        if (lane == 0) {
+          __threadfence();
+          atomicAdd((im.w ? a.done_b : a.done_f) + tk.node, 1u);
+        }
+      }
+    }
+  }
+}
+
 // Self-test of the bounded grid barrier: blocks with index >= gridDim.x - absent
 // return at once and never arrive, so with absent > 0 every other block gives up
 // after `budget` cycles and the status reads SBFWI_ETIMEOUT.
@@ -709,6 +820,39 @@ int build_level_tasks(Model& md, int B, int grid) {
   }
   lt.max_level_items = 1;
   for (int l = 0; l < L; ++l) lt.max_level_items = std::max({lt.max_level_items, lt.items(true, l), lt.items(false, l)});
+  // dataflow items: forward levels leaves -> root, then backward levels root -> leaves
+  {
+    std::vector<int4> items;
+    auto add_level = [&](const std::vector<int32_t>& st, const std::vector<int32_t>& ws,
+                         const std::vector<int32_t>& gr, int l, int dir) {
+      for (int k = st[l]; k < ws[l]; ++k) items.push_back(make_int4(k, 1, 1, dir));
+      for (int k = ws[l]; k < st[l + 1]; k += gr[l]) items.push_back(make_int4(k, std::min(gr[l], st[l + 1] - k), 0, dir));
+    };
+    for (int l = 0; l < L; ++l) add_level(lt.fwd_start, lt.fwd_wstart, lt.fwd_group, l, 0);
+    for (int l = L - 1; l >= 0; --l) add_level(lt.bwd_start, lt.bwd_wstart, lt.bwd_group, l, 1);
+    const int T = (int)t.nodes.size();
+    std::vector<int32_t> info(5 * (size_t)T, 0), parent(T, -1);
+    for (const Task& tk : fwd) info[tk.node] += 1;
+    for (const Task& tk : bwd) info[T + tk.node] += 1;
+    for (int nd = 0; nd < T; ++nd) {
+      info[2 * T + nd] = t.nodes[nd].child0;
+      info[3 * T + nd] = t.nodes[nd].child1;
+      if (t.nodes[nd].child0 >= 0) parent[t.nodes[nd].child0] = nd;
+      if (t.nodes[nd].child1 >= 0) parent[t.nodes[nd].child1] = nd;
+    }
+    for (int nd = 0; nd < T; ++nd) {
+      int a = parent[nd];
+      while (a >= 0 && info[T + a] == 0) a = parent[a];
+      info[4 * T + nd] = a;
+    }
+    SBFWI_CUDA(lt.flow_items.alloc(sizeof(int4) * std::max<size_t>(items.size(), 1)));
+    if (!items.empty())
+      SBFWI_CUDA(cudaMemcpy(lt.flow_items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+    SBFWI_CUDA(lt.node_info.alloc(sizeof(int32_t) * info.size()));
+    SBFWI_CUDA(cudaMemcpy(lt.node_info.p, info.data(), sizeof(int32_t) * info.size(), cudaMemcpyHostToDevice));
+    lt.n_items = (int)items.size();
+    lt.nodes = T;
+  }
   auto upload_meta = [&](DevBuf& dst, const std::vector<int32_t>& st, const std::vector<int32_t>& ws,
                          const std::vector<int32_t>& gr) -> int {
     std::vector<int32_t> meta(st);
@@ -802,6 +946,10 @@ struct Stepper {
   int e_threads = 0, p_grid = 0;
   unsigned e_blocks = 0, b_blocks = 0;
   DevBuf bar, pstatus;
+  bool flow = false;                 // dataflow solve (default) instead of level barriers
+  DevBuf flow_counters;              // done_f [nodes] | done_b [nodes] | item counter (u64)
+  FlowArgs fa;
+  unsigned flow_gen = 0;
   bool use_window = false;
   cudaAccessPolicyWindow window = {};
   int setup_l2_window(int device);
@@ -855,7 +1003,7 @@ int Stepper::init() {
   s_smem = sizeof(double) * std::max(md.tasks.block_doubles, 8 * solve_warp_doubles(B));
   if (s_smem > 200 * 1024) return fail(SBFWI_EUNSUPPORTED, "solve staging area exceeds shared memory");
   for (const void* f : {(const void*)solve_forward_kernel, (const void*)solve_backward_kernel,
-                        (const void*)solve_persistent_kernel})
+                        (const void*)solve_persistent_kernel, (const void*)solve_flow_kernel})
     if (s_smem > 48 * 1024) SBFWI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem));
 
   ea.nb = nb; ea.n = n; ea.B = B; ea.E = E;
@@ -882,8 +1030,11 @@ int Stepper::init() {
   // one cooperative persistent launch per time step for the whole tree, unless the
   // device cannot launch cooperatively or SBFWI_SOLVE=levels asks for one launch per level
   SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_persistent_kernel, 256, s_smem));
+  // SBFWI_SOLVE=levels: one launch per tree level; =barrier: one launch with grid
+  // barriers between levels; default: one dataflow launch
   const char* solve_env = std::getenv("SBFWI_SOLVE");
   persistent = coop && per_sm > 0 && !(solve_env && std::strcmp(solve_env, "levels") == 0);
+  flow = persistent && !(solve_env && std::strcmp(solve_env, "barrier") == 0);
   ftasks = md.tasks.fwd.as<Task>();
   btasks = md.tasks.bwd.as<Task>();
   rc = setup_l2_window(device);
@@ -901,6 +1052,25 @@ int Stepper::init() {
     pa.budget = 4000000000LL;            // ~2 s at 2 GHz
     pa.trace = nullptr;
     p_grid = std::max(1, std::min(std::min(per_sm, 4) * sms, md.tasks.max_level_items));
+  }
+  if (flow) {
+    int per_sm_flow = 0;
+    SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, solve_flow_kernel, 256, s_smem));
+    if (per_sm_flow < 1) return fail(SBFWI_EUNSUPPORTED, "the dataflow solve does not fit on an SM");
+    const int T = md.tasks.nodes;
+    const size_t cb = ((sizeof(unsigned) * 2 * (size_t)T + 15) / 16) * 16;
+    SBFWI_CUDA(flow_counters.alloc(cb + sizeof(unsigned long long)));
+    SBFWI_CUDA(cudaMemsetAsync(flow_counters.p, 0, flow_counters.bytes, st));
+    fa.s = sa;
+    fa.fwd = ftasks; fa.bwd = btasks;
+    fa.items = md.tasks.flow_items.as<int4>(); fa.n_items = md.tasks.n_items;
+    fa.node_info = md.tasks.node_info.as<int32_t>(); fa.nodes = T;
+    fa.done_f = flow_counters.as<unsigned>(); fa.done_b = fa.done_f + T;
+    fa.claim = reinterpret_cast<unsigned long long*>(flow_counters.as<char>() + cb);
+    fa.status = pstatus.as<int>();
+    fa.budget = 4000000000LL;
+    p_grid = std::max(1, std::min(per_sm_flow, 4) * sms);    // every block co-resident (cooperative launch)
+    flow_gen = 0;
   }
 
   ba.N = N; ba.B = B; ba.R = 0;
@@ -1029,7 +1199,15 @@ int Stepper::solve() {
   Profiler& prof = profiler();
   const Tree& t = md.mesh->tree;
   prof.begin(kPhaseSolve, st);
-  if (persistent) {
+  if (flow) {
+    ++flow_gen;
+    fa.gen = flow_gen;
+    fa.base = (unsigned long long)(flow_gen - 1) * (unsigned long long)(fa.n_items + p_grid);
+    void* kargs[] = {&fa};
+    int rc = launch_solve((const void*)solve_flow_kernel, (unsigned)p_grid, kargs, true);
+    if (rc) return rc;
+    prof.count(kPhaseSolve);
+  } else if (persistent) {
     pa.trace = prof.level_trace(6 * t.levels, st);
     if (pa.trace) ++prof.level_steps;
     void* kargs[] = {&pa};

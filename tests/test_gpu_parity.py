@@ -172,16 +172,30 @@ def test_full_size_workload_few_steps(lib):
     assert rel(g, go) <= GRAD_TOL
 
 
-def test_persistent_and_per_level_global_solves_agree(lib, tiny, monkeypatch):
-    """The cooperative one-launch solve and the one-launch-per-tree-level solve give the
-    same traces (same arithmetic, different launch structure)."""
-    mesh, rho, srcs, recs, wav, dt = _ragged_case()
-    M = lib.Mesh.from_inputs(mesh, 6)
-    md = lib.Model(M, 1.3, rho, dt, lx=1.2, ly=1.0)
-    t_persistent, _ = lib.forward(md, srcs, wav, recs, keep=False)
+@pytest.mark.parametrize("case", ["ragged", "size8"])
+def test_dataflow_barrier_and_per_level_global_solves_agree(lib, monkeypatch, case):
+    """The one-launch dataflow solve (default), the one-launch solve with grid barriers
+    between levels and the one-launch-per-level solve give the same traces (same
+    arithmetic, different launch structure)."""
+    if case == "ragged":
+        mesh, rho, srcs, recs, wav, dt = _ragged_case()
+        n_r, c, lx, ly = 6, 1.3, 1.2, 1.0
+    else:
+        w = size_workload(K=8)
+        mesh, rho, srcs, recs, wav, dt = w.mesh, w.rho_true, w.src_nodes, w.rec_nodes, w.wavelets, w.dt
+        n_r, c, lx, ly = w.n_r, w.c, 1.0, 1.0
+    M = lib.Mesh.from_inputs(mesh, n_r)
+    md = lib.Model(M, c, rho, dt, lx=lx, ly=ly)
+    t_flow, _ = lib.forward(md, srcs, wav, recs, keep=False)
+    t_flow2, _ = lib.forward(md, srcs, wav, recs, keep=False)
+    monkeypatch.setenv("SBFWI_SOLVE", "barrier")
+    t_barrier, _ = lib.forward(md, srcs, wav, recs, keep=False)
     monkeypatch.setenv("SBFWI_SOLVE", "levels")
     t_levels, _ = lib.forward(md, srcs, wav, recs, keep=False)
-    assert np.array_equal(t_persistent, t_levels)
+    assert np.abs(t_flow).max() > 0
+    assert np.array_equal(t_flow, t_flow2)
+    assert np.array_equal(t_flow, t_barrier)
+    assert np.array_equal(t_flow, t_levels)
 
 
 @pytest.mark.parametrize("case", ["tiny", "ragged"])
