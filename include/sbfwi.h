@@ -221,7 +221,19 @@ int sbfwi_misfit_noalloc(const double* traces, const double* observed, int64_t n
  */
 int sbfwi_adjoint_gradient(sbfwi_model* model, sbfwi_fwdstate* fwdstate, const double* residual,
                            int mode, double* grad, int mem, void* stream);
+
+/*
+ * sbfwi_destroy_fwdstate -- frees a forward state.  Its velocity or checkpoint
+ * store (the largest allocation of the library, K * n_nodal * n_shots * 8 bytes
+ * for a stored field) is kept in a one-slot cache instead of being freed, and the
+ * next sbfwi_forward on the same device whose store is at least as large and at
+ * most a third larger reuses it (an evaluation loop then allocates it once).
+ * sbfwi_release_cache() frees the cached store; a forward that needs a store that
+ * the cached one does not fit frees the cached one first.  (A service of the
+ * library; the paper has no counterpart.)
+ */
 void sbfwi_destroy_fwdstate(sbfwi_fwdstate* state);
+int sbfwi_release_cache(void);
 
 /*
  * Tracing of the library's kernels (process-wide, not thread-safe).

@@ -58,6 +58,14 @@ struct DevBuf {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// One cached device allocation for the forward-field store (hundreds of GB at the
+// bench size): freeing and re-allocating it every evaluation costs ~0.2 s, so a
+// destroyed forward state hands its store to the cache and the next forward state
+// of a similar size on the same device takes it over.  sbfwi_release_cache() frees it.
+cudaError_t store_alloc(DevBuf& b, size_t bytes);
+void store_release(DevBuf& b);
+void store_cache_clear();
+
 // ---------------------------------------------------------------------------
 // elimination tree of the global boundary system (nested dissection by
 // recursive coordinate bisection of the elements)
@@ -216,6 +224,7 @@ struct FwdState {
   // ckpt_every == c > 0: [ceil(K/c) - 1][state_doubles] Newmark states before steps c, 2c, ...
   DevBuf store;
   DevBuf values, nodes;         // wavelets and source nodes, for the recompute (c > 0)
+  ~FwdState() { store_release(store); }
 };
 
 }  // namespace sbfwi

@@ -207,6 +207,66 @@ int build_tree(Mesh& m) {
 using namespace sbfwi;
 
 namespace sbfwi {
+
+namespace {
+std::mutex g_cache_mu;
+void* g_cache_p = nullptr;
+size_t g_cache_bytes = 0;
+int g_cache_device = -1;
+
+void cache_free_locked() {
+  if (g_cache_p) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != g_cache_device) cudaSetDevice(g_cache_device);
+    cudaFree(g_cache_p);
+    if (cur != g_cache_device) cudaSetDevice(cur);
+  }
+  g_cache_p = nullptr;
+  g_cache_bytes = 0;
+  g_cache_device = -1;
+}
+}  // namespace
+
+cudaError_t store_alloc(DevBuf& b, size_t bytes) {
+  b.release();
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  {
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    // take the cached buffer if it fits without wasting more than a quarter of it
+    if (g_cache_p && g_cache_device == dev && g_cache_bytes >= bytes && g_cache_bytes <= bytes + bytes / 3) {
+      b.p = g_cache_p;
+      b.bytes = g_cache_bytes;
+      g_cache_p = nullptr;
+      g_cache_bytes = 0;
+      g_cache_device = -1;
+      return cudaSuccess;
+    }
+    cache_free_locked();          // the new allocation may need its memory
+  }
+  return b.alloc(bytes);
+}
+
+void store_release(DevBuf& b) {
+  if (!b.p) return;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) { b.release(); return; }
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  cache_free_locked();
+  g_cache_p = b.p;
+  g_cache_bytes = b.bytes;
+  g_cache_device = dev;
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+void store_cache_clear() {
+  std::lock_guard<std::mutex> lock(g_cache_mu);
+  cache_free_locked();
+}
+
 Profiler& profiler() {
   static Profiler p;
   return p;
@@ -257,6 +317,11 @@ int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_
     if (e != cudaSuccess) return cuda_fail(e, "reset solve trace");
     p.level_steps = 0;
   }
+  return SBFWI_OK;
+}
+
+int sbfwi_release_cache(void) {
+  store_cache_clear();
   return SBFWI_OK;
 }
 

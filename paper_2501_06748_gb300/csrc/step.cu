@@ -1397,11 +1397,11 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     double gb = 0;
     if (c == 0) {
       gb = (double)K * np * B * 8 / 1e9;
-      e = fs->store.alloc(sizeof(double) * (size_t)K * np * B);
+      e = store_alloc(fs->store, sizeof(double) * (size_t)K * np * B);
     } else {
       const int64_t nseg = (K + c - 1) / c;
       gb = (double)(nseg - 1) * sd * 8 / 1e9;
-      if (nseg > 1) e = fs->store.alloc(sizeof(double) * (size_t)(nseg - 1) * sd);
+      if (nseg > 1) e = store_alloc(fs->store, sizeof(double) * (size_t)(nseg - 1) * sd);
     }
     if (e != cudaSuccess) {
       cudaGetLastError();

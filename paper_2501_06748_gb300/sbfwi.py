@@ -60,6 +60,8 @@ def _load():
     lib.sbfwi_profile_read.argtypes = [pd, pi64, pi64, ctypes.c_int]
     lib.sbfwi_profile_solve_levels.argtypes = [pd, I32, P(I32), pi64, ctypes.c_int]
     lib.sbfwi_profile_solve_levels.restype = ctypes.c_int
+    lib.sbfwi_release_cache.argtypes = []
+    lib.sbfwi_release_cache.restype = ctypes.c_int
     lib.sbfwi_selftest_barrier.argtypes = [I32, I32, I64, I32, VP]
     lib.sbfwi_selftest_barrier.restype = ctypes.c_int
     for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
@@ -296,6 +298,11 @@ def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
     _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
                                      arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
     return E_out, residual_out
+
+
+def release_cache() -> None:
+    """Free the cached forward-field store that destroyed forward states leave behind."""
+    _check(_lib.sbfwi_release_cache())
 
 
 def selftest_barrier(n_blocks, n_absent=0, budget_cycles=2_000_000, rounds=8, stream=None) -> int:

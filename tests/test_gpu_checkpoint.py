@@ -67,3 +67,21 @@ def test_negative_interval_is_rejected(lib, ragged):
     with pytest.raises(lib.SbfwiError) as ei:
         lib.forward(md, srcs, wav, recs, ckpt_every=-2)
     assert ei.value.code == lib.EINVAL
+
+
+def test_cached_store_gives_identical_results(lib, ragged):
+    """A destroyed forward state leaves its store in the library's cache; the next
+    forward state of the same size takes it over.  Results do not depend on it."""
+    md, srcs, recs, wav, res = ragged
+    lib.release_cache()
+    t1, s1 = lib.forward(md, srcs, wav, recs)
+    g1 = lib.adjoint_gradient(md, s1, res)
+    del s1                                   # store goes to the cache
+    t2, s2 = lib.forward(md, srcs, wav, recs)  # takes it over
+    g2 = lib.adjoint_gradient(md, s2, res)
+    assert np.array_equal(t1, t2) and np.array_equal(g1, g2)
+    del s2
+    lib.release_cache()
+    t3, s3 = lib.forward(md, srcs, wav, recs, ckpt_every=5)
+    assert np.array_equal(t3, t1)
+    assert np.array_equal(lib.adjoint_gradient(md, s3, res), g1)
