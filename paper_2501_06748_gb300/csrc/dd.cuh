@@ -2,11 +2,11 @@
 // about 106 significant bits), written from the error-free transformations of
 // Knuth (TwoSum), Dekker (FastTwoSum) and the FMA form of TwoProduct.
 //
-// The set-up of the path runs in this arithmetic: the algorithmic condensation
-// amplifies rounding errors of the coefficient matrices by about four orders of
-// magnitude (its first pivot is -xi0 E0 / (2h) with xi0 = 1e-3), which in plain
-// binary64 would move receiver traces by ~1e-10 relative.  Results are rounded
-// to binary64 (the hi part) before the time loop uses them.
+// The set-up of the path runs in this arithmetic next to the scaling centre: the
+// algorithmic condensation amplifies rounding errors of the coefficient matrices by
+// about four orders of magnitude through its first pivot -xi0 E0 / (2h) (xi0 = 1e-3),
+// which in plain binary64 would move receiver traces by ~1e-10 relative.  Results
+// are rounded to binary64 (the hi part) before the time loop uses them.
 #pragma once
 
 #include <cmath>

@@ -224,7 +224,38 @@ struct ElemSmem {
 
 __device__ __forceinline__ dd ldd(const double* hi, const double* lo, int64_t k) { return dd{hi[k], lo[k]}; }
 
+// Arithmetic of one radial point of the set-up.  Only the points next to the scaling
+// centre need more than binary64: there the first pivot -xi0 E0 / (2h) amplifies
+// rounding of the coefficient matrices and blocks by ~1e4.  Points 0..3 (their
+// coefficient matrices) and rows 0, 1 (blocks, first elimination, first Thomas step)
+// run in double-double; everything farther out in binary64 (the hi part of the dd
+// storage, lo = 0), which moves receiver traces by ~1e-13 against an all-extended
+// set-up (measured on the CPU with the oracle's extended-precision arithmetic).
+struct DDOps {
+  static __device__ __forceinline__ dd make(double a) { return dd_make(a); }
+  static __device__ __forceinline__ dd add(dd x, dd y) { return dd_add(x, y); }
+  static __device__ __forceinline__ dd sub(dd x, dd y) { return dd_sub(x, y); }
+  static __device__ __forceinline__ dd mul(dd x, dd y) { return dd_mul(x, y); }
+  static __device__ __forceinline__ dd mul_d(dd x, double y) { return dd_mul_d(x, y); }
+  static __device__ __forceinline__ dd fma(dd acc, dd x, dd y) { return dd_fma(acc, x, y); }
+  static __device__ __forceinline__ dd div(dd x, dd y) { return dd_div(x, y); }
+  static __device__ __forceinline__ dd neg(dd x) { return dd_neg(x); }
+};
+struct F64Ops {
+  static __device__ __forceinline__ dd make(double a) { return dd{a, 0.0}; }
+  static __device__ __forceinline__ dd add(dd x, dd y) { return dd{x.hi + y.hi, 0.0}; }
+  static __device__ __forceinline__ dd sub(dd x, dd y) { return dd{x.hi - y.hi, 0.0}; }
+  static __device__ __forceinline__ dd mul(dd x, dd y) { return dd{x.hi * y.hi, 0.0}; }
+  static __device__ __forceinline__ dd mul_d(dd x, double y) { return dd{x.hi * y, 0.0}; }
+  static __device__ __forceinline__ dd fma(dd acc, dd x, dd y) { return dd{::fma(x.hi, y.hi, acc.hi), 0.0}; }
+  static __device__ __forceinline__ dd div(dd x, dd y) { return dd{x.hi / y.hi, 0.0}; }
+  static __device__ __forceinline__ dd neg(dd x) { return dd{-x.hi, 0.0}; }
+};
+constexpr int kExtendedPoints = 4;   // coefficient matrices of points 0..3 in double-double
+constexpr int kExtendedRows = 2;     // rows 0, 1 of the condensation in double-double
+
 // E0, E1, E2, M0 of element e at radial point i into the four given matrices
+template <class Op>
 __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int64_t e, int i,
                                      dd* E0, dd* E1, dd* E2, dd* M0) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -232,28 +263,28 @@ __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int6
   // density at the Gauss points of every line, times the geometry factors
   for (int t = tid; t < L * ng; t += nt) {
     const int l = t / ng, g = t - l * ng;
-    dd r = dd_make(0.0);
+    dd r = Op::make(0.0);
     for (int q = 0; q < pp; ++q) {
       const int j = a.line_local[(e * L + l) * pp + q];
       const int64_t idx = (i < a.n) ? e * (int64_t)a.n * nb + (int64_t)i * nb + j : a.n_int + a.dofs[e * nb + j];
-      r = dd_fma(r, sm.phi[g * pp + q], ldd(a.rho_hi, a.rho_lo, idx));
+      r = Op::fma(r, sm.phi[g * pp + q], ldd(a.rho_hi, a.rho_lo, idx));
     }
-    for (int k = 0; k < 4; ++k) sm.KR[(l * ng + g) * 4 + k] = dd_mul(sm.K[(l * ng + g) * 4 + k], r);
+    for (int k = 0; k < 4; ++k) sm.KR[(l * ng + g) * 4 + k] = Op::mul(sm.K[(l * ng + g) * 4 + k], r);
   }
   __syncthreads();
   // per-line matrices: sum over Gauss points
   for (int t = tid; t < L * pp * pp; t += nt) {
     const int l = t / (pp * pp), ab = t - l * pp * pp, aa = ab / pp, bb = ab - aa * pp;
-    dd s0 = dd_make(0.0), s1 = s0, s2 = s0, sm0 = s0;
+    dd s0 = Op::make(0.0), s1 = s0, s2 = s0, sm0 = s0;
     for (int g = 0; g < ng; ++g) {
       const dd* kr = sm.KR + (l * ng + g) * 4;
       const dd pa = sm.phi[g * pp + aa], pb = sm.phi[g * pp + bb];
       const dd da = sm.dphi[g * pp + aa], db = sm.dphi[g * pp + bb];
-      const dd papb = dd_mul(pa, pb);
-      s0 = dd_fma(s0, kr[0], papb);
-      s1 = dd_fma(s1, kr[1], dd_mul(da, pb));
-      s2 = dd_fma(s2, kr[2], dd_mul(da, db));
-      sm0 = dd_fma(sm0, kr[3], papb);
+      const dd papb = Op::mul(pa, pb);
+      s0 = Op::fma(s0, kr[0], papb);
+      s1 = Op::fma(s1, kr[1], Op::mul(da, pb));
+      s2 = Op::fma(s2, kr[2], Op::mul(da, db));
+      sm0 = Op::fma(sm0, kr[3], papb);
     }
     dd* out = sm.Eline + (size_t)t * 4;
     out[0] = s0; out[1] = s1; out[2] = s2; out[3] = sm0;
@@ -262,7 +293,7 @@ __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int6
   // assemble the element matrices from the lines
   for (int t = tid; t < nb * nb; t += nt) {
     const int A = t / nb, B = t - A * nb;
-    dd s0 = dd_make(0.0), s1 = s0, s2 = s0, s3 = s0;
+    dd s0 = Op::make(0.0), s1 = s0, s2 = s0, s3 = s0;
     for (int l = 0; l < L; ++l) {
       int pa = -1, pb = -1;
       for (int q = 0; q < pp; ++q) {
@@ -272,7 +303,7 @@ __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int6
       }
       if (pa < 0 || pb < 0) continue;
       const dd* v = sm.Eline + ((size_t)(l * pp + pa) * pp + pb) * 4;
-      s0 = dd_add(s0, v[0]); s1 = dd_add(s1, v[1]); s2 = dd_add(s2, v[2]); s3 = dd_add(s3, v[3]);
+      s0 = Op::add(s0, v[0]); s1 = Op::add(s1, v[1]); s2 = Op::add(s2, v[2]); s3 = Op::add(s3, v[3]);
     }
     E0[t] = s0; E1[t] = s1; E2[t] = s2; M0[t] = s3;
   }
@@ -280,9 +311,10 @@ __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int6
 }
 
 // Inv = A^{-1} by Gauss-Jordan with partial pivoting; A is destroyed.
+template <class Op>
 __device__ void gj_inverse(int nb, dd* A, dd* Inv, dd* col, int* piv, int* status) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < nb * nb; t += nt) Inv[t] = dd_make((t / nb) == (t % nb) ? 1.0 : 0.0);
+  for (int t = tid; t < nb * nb; t += nt) Inv[t] = Op::make((t / nb) == (t % nb) ? 1.0 : 0.0);
   __syncthreads();
   for (int k = 0; k < nb; ++k) {
     if (tid == 0) {
@@ -306,32 +338,33 @@ __device__ void gj_inverse(int nb, dd* A, dd* Inv, dd* col, int* piv, int* statu
     __syncthreads();
     for (int r = tid; r < nb; r += nt) col[r] = A[r * nb + k];
     __syncthreads();
-    const dd pinv = dd_div(dd_make(1.0), col[k]);
+    const dd pinv = Op::div(Op::make(1.0), col[k]);
     for (int t = tid; t < nb * nb; t += nt) {
       const int r = t / nb, c = t - r * nb;
       // row k is only read here; it is normalised after the barrier below
-      const dd ak = dd_mul(A[k * nb + c], pinv), ik = dd_mul(Inv[k * nb + c], pinv);
+      const dd ak = Op::mul(A[k * nb + c], pinv), ik = Op::mul(Inv[k * nb + c], pinv);
       if (r != k) {
         const dd f = col[r];
-        A[t] = dd_sub(A[t], dd_mul(f, ak));
-        Inv[t] = dd_sub(Inv[t], dd_mul(f, ik));
+        A[t] = Op::sub(A[t], Op::mul(f, ak));
+        Inv[t] = Op::sub(Inv[t], Op::mul(f, ik));
       }
     }
     __syncthreads();
     for (int c = tid; c < nb; c += nt) {
-      A[k * nb + c] = dd_mul(A[k * nb + c], pinv);
-      Inv[k * nb + c] = dd_mul(Inv[k * nb + c], pinv);
+      A[k * nb + c] = Op::mul(A[k * nb + c], pinv);
+      Inv[k * nb + c] = Op::mul(Inv[k * nb + c], pinv);
     }
     __syncthreads();
   }
 }
 
 // C = A * B (all nb x nb, distinct buffers)
+template <class Op>
 __device__ void mm(int nb, const dd* A, const dd* B, dd* C) {
   for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
     const int r = t / nb, c = t - r * nb;
-    dd s = dd_make(0.0);
-    for (int k = 0; k < nb; ++k) s = dd_fma(s, A[r * nb + k], B[k * nb + c]);
+    dd s = Op::make(0.0);
+    for (int k = 0; k < nb; ++k) s = Op::fma(s, A[r * nb + k], B[k * nb + c]);
     C[t] = s;
   }
   __syncthreads();
@@ -410,130 +443,135 @@ __global__ void element_setup_kernel(ElemArgs a) {
   // radial window: slots of E0/E1 hold i-1, i, i+1; E2/M0 hold i, i+1
   int s_prev = 0, s_cur = 1, s_next = 2;
   int w_cur = 0, w_next = 1;
-  coefficient_matrices(a, sm, e, 0, E0w[s_cur], E1w[s_cur], E2w[w_cur], M0w[w_cur]);
-  coefficient_matrices(a, sm, e, 1, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
+  coefficient_matrices<DDOps>(a, sm, e, 0, E0w[s_cur], E1w[s_cur], E2w[w_cur], M0w[w_cur]);
+  coefficient_matrices<DDOps>(a, sm, e, 1, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
 
   for (int i = 0; i <= n; ++i) {
-    const dd xi = dd{a.xi_hi[i], a.xi_lo[i]};
-    const dd x2 = dd_mul(xi, xi);
-    // blocks of row i (Eq. (discretized) with Eq. (FD); dE by one-sided differences at the ends)
-    for (int t = tid; t < nn; t += nt) {
-      const int r = t / nb, cc = t - r * nb, tt = cc * nb + r;
-      const dd E0 = E0w[s_cur][t], E1 = E1w[s_cur][t], E1T = E1w[s_cur][tt];
-      dd dE0, dE1T;
+    auto point = [&](auto ops) {
+      using Op = decltype(ops);
+      const dd xi = dd{a.xi_hi[i], a.xi_lo[i]};
+      const dd x2 = Op::mul(xi, xi);
+      // blocks of row i (Eq. (discretized) with Eq. (FD); dE by one-sided differences at the ends)
+      for (int t = tid; t < nn; t += nt) {
+        const int r = t / nb, cc = t - r * nb, tt = cc * nb + r;
+        const dd E0 = E0w[s_cur][t], E1 = E1w[s_cur][t], E1T = E1w[s_cur][tt];
+        dd dE0, dE1T;
+        if (i == 0) {
+          dE0 = Op::mul(Op::sub(E0w[s_next][t], E0), inv_h);
+          dE1T = Op::mul(Op::sub(E1w[s_next][tt], E1T), inv_h);
+        } else if (i == n) {
+          dE0 = Op::mul(Op::sub(E0, E0w[s_prev][t]), inv_h);
+          dE1T = Op::mul(Op::sub(E1T, E1w[s_prev][tt]), inv_h);
+        } else {
+          dE0 = Op::mul(Op::sub(E0w[s_next][t], E0w[s_prev][t]), inv_2h);
+          dE1T = Op::mul(Op::sub(E1w[s_next][tt], E1w[s_prev][tt]), inv_2h);
+        }
+        const dd D = Op::add(Op::sub(Op::add(E0, E1T), E1), Op::mul(xi, dE0));
+        const dd a2 = Op::mul(Op::mul(x2, E0), inv_h2);
+        const dd a1 = Op::mul(Op::mul(xi, D), inv_2h);
+        th[t] = Op::sub(a2, a1);
+        ps[t] = Op::add(a2, a1);
+        dd f = Op::neg(Op::add(a2, a2));
+        f = Op::sub(f, E2w[w_cur][t]);
+        f = Op::add(f, Op::mul(xi, dE1T));
+        f = Op::sub(f, Op::mul(a.mass, Op::mul(x2, M0w[w_cur][t])));
+        ph[t] = f;
+      }
+      __syncthreads();
       if (i == 0) {
-        dE0 = dd_mul(dd_sub(E0w[s_next][t], E0), inv_h);
-        dE1T = dd_mul(dd_sub(E1w[s_next][tt], E1T), inv_h);
-      } else if (i == n) {
-        dE0 = dd_mul(dd_sub(E0, E0w[s_prev][t]), inv_h);
-        dE1T = dd_mul(dd_sub(E1T, E1w[s_prev][tt]), inv_h);
+        // row -1: theta = -xi_0 E0/(2h), phi = E1^T, psi = xi_0 E0/(2h).  rho_0 = theta_0 theta_{-1}^{-1}
+        for (int t = tid; t < nn; t += nt) T1[t] = Op::mul(Op::neg(Op::mul(xi, E0w[s_cur][t])), inv_2h);
+        __syncthreads();
+        gj_inverse<Op>(nb, T1, Gm, sm.col, sm.piv, a.status);
+        mm<Op>(nb, th, Gm, Hp);                                   // Hp <- rho_0
+        // phi_0 -= rho_0 phi_{-1}; psi_0 -= rho_0 psi_{-1}
+        for (int t = tid; t < nn; t += nt) {
+          const int r = t / nb, cc = t - r * nb;
+          dd s1 = Op::make(0.0), s2 = Op::make(0.0);
+          for (int k = 0; k < nb; ++k) {
+            const dd rk = Hp[r * nb + k];
+            s1 = Op::fma(s1, rk, E1w[s_cur][cc * nb + k]);               // phi_{-1}[k][c] = E1[c][k]
+            s2 = Op::fma(s2, rk, Op::mul(Op::mul(xi, E0w[s_cur][k * nb + cc]), inv_2h));
+          }
+          T1[t] = s1;
+          Gm[t] = s2;
+        }
+        __syncthreads();
+        for (int t = tid; t < nn; t += nt) {
+          ph[t] = Op::sub(ph[t], T1[t]);
+          ps[t] = Op::sub(ps[t], Gm[t]);
+        }
+        __syncthreads();
       } else {
-        dE0 = dd_mul(dd_sub(E0w[s_next][t], E0w[s_prev][t]), inv_2h);
-        dE1T = dd_mul(dd_sub(E1w[s_next][tt], E1w[s_prev][tt]), inv_2h);
+        // Thomas sweep: phi_i -= theta_i phi_{i-1}^{-1} psi_{i-1} = theta_i H_{i-1}
+        mm<Op>(nb, th, Hp, T1);
+        for (int t = tid; t < nn; t += nt) ph[t] = Op::sub(ph[t], T1[t]);
+        __syncthreads();
       }
-      const dd D = dd_add(dd_sub(dd_add(E0, E1T), E1), dd_mul(xi, dE0));
-      const dd a2 = dd_mul(dd_mul(x2, E0), inv_h2);
-      const dd a1 = dd_mul(dd_mul(xi, D), inv_2h);
-      th[t] = dd_sub(a2, a1);
-      ps[t] = dd_add(a2, a1);
-      dd f = dd_neg(dd_add(a2, a2));
-      f = dd_sub(f, E2w[w_cur][t]);
-      f = dd_add(f, dd_mul(xi, dE1T));
-      f = dd_sub(f, dd_mul(a.mass, dd_mul(x2, M0w[w_cur][t])));
-      ph[t] = f;
-    }
-    __syncthreads();
-    if (i == 0) {
-      // row -1: theta = -xi_0 E0/(2h), phi = E1^T, psi = xi_0 E0/(2h).  rho_0 = theta_0 theta_{-1}^{-1}
-      for (int t = tid; t < nn; t += nt) T1[t] = dd_mul(dd_neg(dd_mul(xi, E0w[s_cur][t])), inv_2h);
-      __syncthreads();
-      gj_inverse(nb, T1, Gm, sm.col, sm.piv, a.status);
-      mm(nb, th, Gm, Hp);                                   // Hp <- rho_0
-      // phi_0 -= rho_0 phi_{-1}; psi_0 -= rho_0 psi_{-1}
-      for (int t = tid; t < nn; t += nt) {
-        const int r = t / nb, cc = t - r * nb;
-        dd s1 = dd_make(0.0), s2 = dd_make(0.0);
-        for (int k = 0; k < nb; ++k) {
-          const dd rk = Hp[r * nb + k];
-          s1 = dd_fma(s1, rk, E1w[s_cur][cc * nb + k]);               // phi_{-1}[k][c] = E1[c][k]
-          s2 = dd_fma(s2, rk, dd_mul(dd_mul(xi, E0w[s_cur][k * nb + cc]), inv_2h));
+      if (i < n) {
+        gj_inverse<Op>(nb, ph, Gm, sm.col, sm.piv, a.status);     // G_i, destroys ph
+        double* Pi = mats_e + (int64_t)i * matstride;
+        for (int t = tid; t < nn; t += nt) {
+          const int r = t / nb, cc = t - r * nb;
+          dd sp = Op::make(0.0), sq = Op::make(0.0), sh = Op::make(0.0);
+          for (int k = 0; k < nb; ++k) {
+            const dd gk = Gm[r * nb + k];
+            sp = Op::fma(sp, gk, M0w[w_cur][k * nb + cc]);
+            sq = Op::fma(sq, gk, th[k * nb + cc]);
+            sh = Op::fma(sh, gk, ps[k * nb + cc]);
+          }
+          sp = Op::mul(sp, x2);
+          Pi[t] = sp.hi;
+          Pi[nn + t] = (i == 0) ? 0.0 : sq.hi;
+          Pi[2 * nn + t] = sh.hi;
+          T1[t] = sh;                                         // H_i kept in double-double
         }
-        T1[t] = s1;
-        Gm[t] = s2;
-      }
-      __syncthreads();
-      for (int t = tid; t < nn; t += nt) {
-        ph[t] = dd_sub(ph[t], T1[t]);
-        ps[t] = dd_sub(ps[t], Gm[t]);
-      }
-      __syncthreads();
-    } else {
-      // Thomas sweep: phi_i -= theta_i phi_{i-1}^{-1} psi_{i-1} = theta_i H_{i-1}
-      mm(nb, th, Hp, T1);
-      for (int t = tid; t < nn; t += nt) ph[t] = dd_sub(ph[t], T1[t]);
-      __syncthreads();
-    }
-    if (i < n) {
-      gj_inverse(nb, ph, Gm, sm.col, sm.piv, a.status);     // G_i, destroys ph
-      double* Pi = mats_e + (int64_t)i * matstride;
-      for (int t = tid; t < nn; t += nt) {
-        const int r = t / nb, cc = t - r * nb;
-        dd sp = dd_make(0.0), sq = dd_make(0.0), sh = dd_make(0.0);
-        for (int k = 0; k < nb; ++k) {
-          const dd gk = Gm[r * nb + k];
-          sp = dd_fma(sp, gk, M0w[w_cur][k * nb + cc]);
-          sq = dd_fma(sq, gk, th[k * nb + cc]);
-          sh = dd_fma(sh, gk, ps[k * nb + cc]);
+        __syncthreads();
+        for (int t = tid; t < nn; t += nt) Hp[t] = T1[t];
+        __syncthreads();
+      } else {
+        // i == n: th = theta_n, ph = modified phi_n, ps = psi_n, Hp = H_{n-1}
+        for (int t = tid; t < nn; t += nt) T1[t] = ps[t];
+        __syncthreads();
+        gj_inverse<Op>(nb, T1, Gm, sm.col, sm.piv, a.status);     // Gm = psi_n^{-1}
+        // W = psi_{n+1} psi_n^{-1}, psi_{n+1} = xi_n E0_n / (2h)
+        for (int t = tid; t < nn; t += nt) {
+          const int r = t / nb, cc = t - r * nb;
+          dd s = Op::make(0.0);
+          for (int k = 0; k < nb; ++k)
+            s = Op::fma(s, Op::mul(Op::mul(xi, E0w[s_cur][r * nb + k]), inv_2h), Gm[k * nb + cc]);
+          T1[t] = s;
         }
-        sp = dd_mul(sp, x2);
-        Pi[t] = sp.hi;
-        Pi[nn + t] = (i == 0) ? 0.0 : sq.hi;
-        Pi[2 * nn + t] = sh.hi;
-        T1[t] = sh;                                         // H_i kept in double-double
-      }
-      __syncthreads();
-      for (int t = tid; t < nn; t += nt) Hp[t] = T1[t];
-      __syncthreads();
-    } else {
-      // i == n: th = theta_n, ph = modified phi_n, ps = psi_n, Hp = H_{n-1}
-      for (int t = tid; t < nn; t += nt) T1[t] = ps[t];
-      __syncthreads();
-      gj_inverse(nb, T1, Gm, sm.col, sm.piv, a.status);     // Gm = psi_n^{-1}
-      // W = psi_{n+1} psi_n^{-1}, psi_{n+1} = xi_n E0_n / (2h)
-      for (int t = tid; t < nn; t += nt) {
-        const int r = t / nb, cc = t - r * nb;
-        dd s = dd_make(0.0);
-        for (int k = 0; k < nb; ++k)
-          s = dd_fma(s, dd_mul(dd_mul(xi, E0w[s_cur][r * nb + k]), inv_2h), Gm[k * nb + cc]);
-        T1[t] = s;
-      }
-      __syncthreads();
-      // phi_{n+1} modified = E1_n^T - theta_{n+1} H_{n-1}, theta_{n+1} = -xi_n E0_n/(2h)
-      for (int t = tid; t < nn; t += nt) {
-        const int r = t / nb, cc = t - r * nb;
-        dd s = E1w[s_cur][cc * nb + r];
-        for (int k = 0; k < nb; ++k)
-          s = dd_add(s, dd_mul(dd_mul(dd_mul(xi, E0w[s_cur][r * nb + k]), inv_2h), Hp[k * nb + cc]));
-        Gm[t] = s;
-      }
-      __syncthreads();
-      double* Se = a.S + e * (int64_t)nn;
-      double* Re = a.rt + e * (int64_t)2 * nn;
-      for (int t = tid; t < nn; t += nt) {
-        const int r = t / nb, cc = t - r * nb;
-        dd s = Gm[t], rr = dd_mul(dd_mul(xi, E0w[s_cur][t]), inv_2h), tt = dd_make(0.0);  // -theta_{n+1} = xi E0/(2h)
-        for (int k = 0; k < nb; ++k) {
-          const dd wk = T1[r * nb + k];
-          s = dd_sub(s, dd_mul(wk, ph[k * nb + cc]));
-          rr = dd_fma(rr, wk, th[k * nb + cc]);
-          tt = dd_fma(tt, wk, M0w[w_cur][k * nb + cc]);
+        __syncthreads();
+        // phi_{n+1} modified = E1_n^T - theta_{n+1} H_{n-1}, theta_{n+1} = -xi_n E0_n/(2h)
+        for (int t = tid; t < nn; t += nt) {
+          const int r = t / nb, cc = t - r * nb;
+          dd s = E1w[s_cur][cc * nb + r];
+          for (int k = 0; k < nb; ++k)
+            s = Op::add(s, Op::mul(Op::mul(Op::mul(xi, E0w[s_cur][r * nb + k]), inv_2h), Hp[k * nb + cc]));
+          Gm[t] = s;
         }
-        Se[t] = s.hi;
-        Re[t] = rr.hi;
-        Re[nn + t] = dd_mul(tt, x2).hi;
+        __syncthreads();
+        double* Se = a.S + e * (int64_t)nn;
+        double* Re = a.rt + e * (int64_t)2 * nn;
+        for (int t = tid; t < nn; t += nt) {
+          const int r = t / nb, cc = t - r * nb;
+          dd s = Gm[t], rr = Op::mul(Op::mul(xi, E0w[s_cur][t]), inv_2h), tt = Op::make(0.0);  // -theta_{n+1} = xi E0/(2h)
+          for (int k = 0; k < nb; ++k) {
+            const dd wk = T1[r * nb + k];
+            s = Op::sub(s, Op::mul(wk, ph[k * nb + cc]));
+            rr = Op::fma(rr, wk, th[k * nb + cc]);
+            tt = Op::fma(tt, wk, M0w[w_cur][k * nb + cc]);
+          }
+          Se[t] = s.hi;
+          Re[t] = rr.hi;
+          Re[nn + t] = Op::mul(tt, x2).hi;
+        }
+        __syncthreads();
       }
-      __syncthreads();
-    }
+    };
+    if (i < kExtendedRows) point(DDOps{});
+    else point(F64Ops{});
     // advance the radial window
     if (i + 1 <= n) {
       const int old_prev = s_prev;
@@ -543,7 +581,12 @@ __global__ void element_setup_kernel(ElemArgs a) {
       const int ow = w_cur;
       w_cur = w_next;
       w_next = ow;
-      if (i + 2 <= n) coefficient_matrices(a, sm, e, i + 2, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
+      if (i + 2 <= n) {
+        if (i + 2 < kExtendedPoints)
+          coefficient_matrices<DDOps>(a, sm, e, i + 2, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
+        else
+          coefficient_matrices<F64Ops>(a, sm, e, i + 2, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
+      }
     }
   }
 }
