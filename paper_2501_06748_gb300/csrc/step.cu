@@ -969,9 +969,10 @@ int Stepper::init() {
   // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
   const char* elem_env = std::getenv("SBFWI_ELEMENT");
   use_tc = md.tc_ready && tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
-  SBFWI_CUDA(rb.u.alloc(sizeof(double) * (use_tc ? 1 : si)));     // the tensor-core path carries v, not u
+  // the tensor-core path carries the predictor v and z = u' + dt (1 - gamma) u'' (in ud), not u, u''
+  SBFWI_CUDA(rb.u.alloc(sizeof(double) * (use_tc ? 1 : si)));
   SBFWI_CUDA(rb.ud.alloc(sizeof(double) * si));
-  SBFWI_CUDA(rb.udd.alloc(sizeof(double) * si));
+  SBFWI_CUDA(rb.udd.alloc(sizeof(double) * (use_tc ? 1 : si)));
   SBFWI_CUDA(rb.q.alloc(sizeof(double) * si));
   if (use_tc) SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
   SBFWI_CUDA(rb.ub.alloc(sizeof(double) * sb));
@@ -1146,7 +1147,7 @@ int Stepper::zero_state() {
 }
 
 std::vector<DevBuf*> Stepper::state_bufs() const {
-  if (use_tc) return {&rb.v, &rb.ud, &rb.udd, &rb.ub, &rb.udb, &rb.uddb};
+  if (use_tc) return {&rb.v, &rb.ud, &rb.ub, &rb.udb, &rb.uddb};
   return {&rb.u, &rb.ud, &rb.udd, &rb.ub, &rb.udb, &rb.uddb};
 }
 

@@ -283,7 +283,9 @@ struct ElemTcArgs {
   const int* exps;
   const int* exps_rt;
   const int32_t* dofs;
-  double* u; double* ud; double* udd; double* v;          // interior state [E][n][nb][B]
+  double* u; double* ud; double* udd; double* v;          // interior state [E][n][nb][B]: this kernel
+                                                          // keeps v (predictor) in v and z = u' + dt (1 - gamma) u''
+                                                          // in ud; u and udd are unused
   const double* ub; const double* udb; const double* uddb;
   double* q;
   double* fhat;
@@ -420,12 +422,11 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
                            Hexp - (int64_t)(n - i) * 48, 1, lane);
       cp_async_commit();
       // the state of this radial point, loaded ahead of the product
-      double udo[4], uddo[4], vo[4], qo[4], fw[4], gr[4];
+      double zo[4], vo[4], qo[4], fw[4], gr[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int64_t o = base + (int64_t)i * per + cr[j] * B + cc[j];
-        udo[j] = cok[j] ? a.ud[o] : 0.0;
-        uddo[j] = cok[j] ? a.udd[o] : 0.0;
+        zo[j] = cok[j] ? a.ud[o] : 0.0;
         vo[j] = cok[j] ? a.v[o] : 0.0;
         qo[j] = cok[j] ? a.q[o] : 0.0;
         fw[j] = (cok[j] && a.grad_int) ? a.fwd_int[o] : 0.0;
@@ -443,9 +444,12 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
           const int64_t o = base + (int64_t)i * per + cr[j] * B + cc[j];
           const double u_new = qo[j] - hu[j];
           const double uddn = fma(a.a0, u_new, -vo[j]);
-          const double udn = fma(a.c2, uddn, fma(a.c1, uddo[j], udo[j]));
+          const double udn = fma(a.c2, uddn, zo[j]);
           // the interior displacement is not kept: the predictor v carries it
-          a.ud[o] = udn; a.udd[o] = uddn;
+          // the interior u', u'' are not kept either: the Newmark update needs only
+          // z = u' + dt (1 - gamma) u'' of the old state, the same value the update
+          // would form from u' and u'' (same rounding)
+          a.ud[o] = fma(a.c1, uddn, udn);
           a.v[o] = kA2One ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
           if (a.store_int) a.store_int[o] = udn;
           if (a.grad_int) a.grad_int[o] = fma(fw[j], udn, gr[j]);    // dt applied at the end
