@@ -167,7 +167,7 @@ def run_ours(args, rank, world):
     build.build()
     from paper_2501_06748_gb300 import sbfwi as lib
     from paper_2501_06748_gb300.shots import shard, allreduce_misfit_gradient
-    from sbfwi_inputs import size_workload
+    from sbfwi_inputs import size_workload, diff_workload
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
@@ -177,7 +177,13 @@ def run_ours(args, rank, world):
         dist.init_process_group("nccl", device_id=dev)
 
     # weak scaling: the job has shots x ranks sources; each rank takes its shard
-    w = size_workload(K=args.time_steps, n_shots=args.shots * world)
+    diff = args.config == "diff"
+    K_steps = args.time_steps or (8000 if diff else 2000)
+    if diff:
+        w = diff_workload(K=K_steps, n_shots=(args.shots or 16) * world)
+    else:
+        w = size_workload(K=K_steps, n_shots=(args.shots or 8) * world)
+    ckpt = lib.CKPT_AUTO if diff else 0
     mine = shard(w.n_shots, rank, world)
     src_nodes = w.src_nodes[mine.start:mine.stop]
     wav_host = np.ascontiguousarray(w.wavelets[mine.start:mine.stop])
@@ -197,7 +203,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
 
     observed_host = observed.cpu().numpy()
-    chunk = args.shots_per_pass or B
+    chunk = args.shots_per_pass or min(B, 8)
     chunks = [slice(s, min(B, s + chunk)) for s in range(0, B, chunk)]
 
     def step(host=False):
@@ -211,7 +217,7 @@ def run_ours(args, rank, world):
         model = lib.Model(M, w.c, rho_in, w.dt)
         E_tot = 0.0
         for c in chunks:
-            tr, st = lib.forward(model, src_nodes[c], wav_in[c], w.rec_nodes)
+            tr, st = lib.forward(model, src_nodes[c], wav_in[c], w.rec_nodes, ckpt_every=ckpt)
             Ec, res = lib.misfit(tr, obs_in[c], w.dt)
             lib.adjoint_gradient(model, st, res, grad_out=grad, accumulate=True)
             E_tot += Ec
@@ -295,7 +301,7 @@ def run_ours(args, rank, world):
 
     # the same path one shot at a time (B = 1 per pass), for comparison with the batched pass
     one_shot = None
-    if args.one_shot:
+    if args.one_shot and not diff:
         def step_one():
             model = lib.Model(M, w.c, rho_start, w.dt)
             tr, st = lib.forward(model, src_nodes[:1], wav[:1], w.rec_nodes)
@@ -349,13 +355,16 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"size: {w.mesh.nx}x{w.mesh.ny} square S-elements, p=4 (n_b={nb}), N_r={N_r}, "
+        "config": {"workload": f"{w.name}: {w.mesh.nx}x{w.mesh.ny} square S-elements, p=4 (n_b={nb}), N_r={N_r}, "
                                f"{B} Ricker shots, {R} receivers, {K} Newmark steps, {w.gx}x{w.gy} density grid; "
-                               "per step: set-up + forward + misfit + adjoint + gradient",
+                               "per step: set-up + forward + misfit + adjoint + gradient"
+                               + ("; checkpoints at the memory-optimal interval, forward recomputed in the adjoint"
+                                  if diff else ""),
                    "elements": E, "n_b": nb, "N_r": N_r, "shots": B, "shots_per_pass": Bc, "time_steps": K,
                    "global_nodes": M.n_nodes, "units_per_step": units_per_step,
                    "flaw_factor": w.info["flaws"]["factor"],
-                   "l2": "inputs larger than L2 (forward velocity store %.0f GB per pass)" % (K * M.n_nodal * Bc * 8 / 1e9),
+                   "l2": ("inputs larger than L2 (forward velocity store %.0f GB per pass)" % (K * M.n_nodal * Bc * 8 / 1e9)
+                          if not diff else "inputs larger than L2 (checkpoints + recompute window > 100 GB per pass)"),
                    "parallelism": f"shots per GPU, {world} GPU(s)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "per_step": [float(x) for x in per_step]},
@@ -395,8 +404,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--time-steps", type=int, default=2000, help="Newmark steps of the workload")
-    ap.add_argument("--shots", type=int, default=8)
+    ap.add_argument("--config", choices=["size", "diff"], default="size",
+                    help="size: 64x64 elements, 8 shots, 2000 steps, stored forward field (the default); "
+                         "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint")
+    ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")
+    ap.add_argument("--shots", type=int, default=0, help="shots per rank (0: the config's)")
     ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

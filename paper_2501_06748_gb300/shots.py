@@ -54,14 +54,15 @@ def allreduce_misfit_gradient(E: float, grad, group=None):
     return float(buf[-1].item()), grad
 
 
-def misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed, shots_per_pass: int = 8, group=None):
+def misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed, shots_per_pass: int = 8, group=None,
+                        ckpt_every: int = 0):
     """Misfit and density gradient of all shots, sharded over the ranks of `group`.
 
     `src_nodes` [S], `wavelets` [S][K] and `observed` [S][R][K] hold every shot; each
     rank takes its `shard`, runs it through the library in passes of at most
-    `shots_per_pass` shots (forward with the velocity store, misfit, adjoint with the
-    gradient accumulated), then joins the one all-reduce.  Host arrays in, host
-    arrays out; CUDA tensors in, CUDA tensors out."""
+    `shots_per_pass` shots (forward with the velocity store, or with checkpoints every
+    `ckpt_every` steps, misfit, adjoint with the gradient accumulated), then joins the
+    one all-reduce.  Host arrays in, host arrays out; CUDA tensors in, CUDA tensors out."""
     from . import sbfwi
     dist = _dist()
     rank = dist.get_rank(group) if dist else 0
@@ -77,7 +78,7 @@ def misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed, shots_p
     E = 0.0
     for lo in range(mine.start, mine.stop, max(1, shots_per_pass)):
         hi = min(mine.stop, lo + max(1, shots_per_pass))
-        tr, st = sbfwi.forward(model, src[lo:hi], wavelets[lo:hi], rec_nodes)
+        tr, st = sbfwi.forward(model, src[lo:hi], wavelets[lo:hi], rec_nodes, ckpt_every=ckpt_every)
         Ec, res = sbfwi.misfit(tr, observed[lo:hi], model.dt)
         sbfwi.adjoint_gradient(model, st, res, grad_out=grad, accumulate=True)
         E += Ec

@@ -128,9 +128,22 @@ def size_workload(seed: int = 1, K: int = 2000, n_shots: int = 8, nx: int = 64, 
                     dt, K, f0, info={"flaws": finfo, "seed": seed})
 
 
+def diff_workload(seed: int = 2, K: int = 8000, n_shots: int = 16, nx: int = 128, n_r: int = 32,
+                  grid: int = 512, n_rec: int = 64, flaw_factor: float = FLAW_FACTOR) -> Workload:
+    """The differentiation-scale recipe: 128x128 square S-elements, p = 4, N_r = 32, 16
+    sources on the top edge, 64 receivers along the perimeter, 8000 steps, 512x512
+    density grid (the forward field no longer fits in memory: checkpoints)."""
+    w = size_workload(seed=seed, K=K, n_shots=n_shots, nx=nx, n_r=n_r, grid=grid, n_rec=n_rec,
+                      flaw_factor=flaw_factor)
+    w.name = "diff"
+    return w
+
+
 def workload_by_name(name: str, **kw) -> Workload:
     if name == "tiny":
         return tiny_workload(**kw)
     if name == "size":
         return size_workload(**kw)
+    if name == "diff":
+        return diff_workload(**kw)
     raise KeyError(name)
