@@ -377,6 +377,92 @@ def run_ours(args, rank, world):
     return out
 
 
+def run_serving(args, rank, world):
+    """Forward-modelling requests with Poisson arrivals through the serving engine
+    (continuous batching of shots that share a model, step count and receivers)."""
+    import torch
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi as lib, serving
+    from sbfwi_inputs import structured_mesh, boundary_nodes, flawed_density_ellipses, ricker
+    if rank != 0:
+        return None
+    torch.cuda.set_device(0)
+    specs = [(16, 2, 8), (32, 3, 16), (32, 4, 16), (64, 4, 32)]      # (elements per side, p, N_r)
+    meshes, recs, dts = {}, {}, {}
+    for nx, p, n_r in specs:
+        m = structured_mesh(nx, nx, p)
+        meshes[(nx, p, n_r)] = (m, lib.Mesh.from_inputs(m, n_r))
+        bnd = np.unique(np.concatenate([boundary_nodes(m, s) for s in ("bottom", "left", "right")]))
+        recs[(nx, p, n_r)] = bnd[np.linspace(0, len(bnd) - 1, 16).astype(int)]
+        dts[(nx, p, n_r)] = 0.5 / (nx * p)
+
+    def build_model(key):
+        nx, p, n_r, seed = key
+        rho, _ = flawed_density_ellipses(128, 128, n=2, factor=0.5, seed=seed)
+        return lib.Model(meshes[(nx, p, n_r)][1], 1.0, rho, dts[(nx, p, n_r)])
+
+    rng = np.random.default_rng(7)
+    n_req = args.requests
+    keys = [spec + (int(seed),) for spec in specs for seed in (0, 1)]
+    reqs, units = [], 0
+    for rid in range(n_req):
+        key = keys[int(rng.integers(len(keys)))]
+        spec = key[:3]
+        m = meshes[spec][0]
+        K = int(rng.choice([500, 1000]))
+        h = 1.0 / (spec[0] * spec[1])
+        top = boundary_nodes(m, "top")
+        wav = ricker(1.0 / (10 * h), dts[spec], K)
+        reqs.append(serving.Request(rid, key, int(rng.choice(top)), wav, recs[spec], arrival=0.0))
+        units += m.n_elem * spec[2] * K
+    # arrival rate: 70 % of the rate one request at a time could sustain (service times
+    # of single-shot requests measured once per model, after its set-up)
+    eng0 = serving.Engine(build_model, max_batch=1, cache_capacity=len(keys))
+    probe = []
+    for k, key in enumerate(keys):
+        top = boundary_nodes(meshes[key[:3]][0], "top")
+        probe.append(serving.Request(-1 - k, key, int(top[len(top) // 2]),
+                                     ricker(1.0 / (10 / (key[0] * key[1])), dts[key[:3]], 500), recs[key[:3]], 0.0))
+    eng0.run(probe)                              # set-ups + warm-up
+    t_one = {}
+    for r in probe:
+        t0 = time.perf_counter()
+        lib.forward(eng0.cache.get(r.model_key), [r.src_node], r.wavelet[None], r.rec_nodes, keep=False)
+        torch.cuda.synchronize()
+        t_one[r.model_key] = (time.perf_counter() - t0) / 500.0           # seconds per step, one shot
+    mean_service = float(np.mean([t_one[r.model_key] * r.K for r in reqs]))
+    rate = 0.7 / mean_service
+    t = 0.0
+    for r in reqs:
+        t += float(rng.exponential(1.0 / rate))
+        r.arrival = t
+    eng = serving.Engine(build_model, max_batch=8, cache_capacity=len(keys))
+    for key in keys:                             # models set up before the clock starts
+        eng.cache.get(key)
+    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_serving.csv")
+                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/sbfwi_clocks_serving.csv")
+    clocks.start()
+    t0 = time.perf_counter()
+    eng.run(reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop(0)
+    st = serving.latency_stats(reqs)
+    return {"metric": "serving: forward element-radial-node-steps/s; p50/p99 request latency",
+            "value": units / wall, "unit": "element-radial-node-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serving: %d forward requests (one Ricker shot each, 16 receivers) on 8 seeded "
+                                   "flawed models over meshes %s (elements per side, p, N_r), K in {500, 1000}, Poisson "
+                                   "arrivals at 70%% of the one-request-at-a-time capacity; continuous batching of "
+                                   "up to 8 shots that share a model, K and receivers" % (n_req, specs),
+                       "requests": n_req, "arrival_rate_per_s": rate, "batches": len(eng.batches),
+                       "mean_batch": float(np.mean(eng.batches)), "l2": "models and traces stay on the device"},
+            "latency_ms": {"p50": st["p50_s"] * 1e3, "p99": st["p99_s"] * 1e3, "mean": st["mean_s"] * 1e3},
+            "clocks": clk}
+
+
 def run_reference(args, rank, world):
     """The oracle (the only reference this path has) on the host cores, rank 0 only."""
     if rank != 0:
@@ -404,9 +490,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["size", "diff"], default="size",
+    ap.add_argument("--requests", type=int, default=64, help="serving config: number of requests")
+    ap.add_argument("--config", choices=["size", "diff", "serving"], default="size",
                     help="size: 64x64 elements, 8 shots, 2000 steps, stored forward field (the default); "
-                         "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint")
+                         "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint; "
+                         "serving: forward-modelling requests with continuous batching")
     ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")
     ap.add_argument("--shots", type=int, default=0, help="shots per rank (0: the config's)")
     ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")
@@ -419,6 +507,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.config == "serving":
+        out = run_serving(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if out is not None:
