@@ -93,14 +93,26 @@ __device__ __forceinline__ double int_to_double_scaled(long long t, int E) {
 }
 
 // six balanced base-512 digits, most significant first, as FP16 bit patterns of 1536 + d
+// The 54-bit recurrence runs on two 32-bit halves: the low 27 bits give the three
+// least significant digits and a carry (0 or 1) into the high half, which gives the
+// rest -- the same digits as the recurrence on the whole integer.
 __device__ __forceinline__ void digits(long long v, unsigned short (&h)[kSlices]) {
+  int lo = (int)(v & ((1LL << 27) - 1));      // 0 .. 2^27 - 1
+  int hi = (int)(v >> 27);                    // |hi| < 2^26 (arithmetic shift)
 #pragma unroll
-  for (int k = kSlices - 1; k >= 1; --k) {
-    const int d = (int)(((v + 256) & 511) - 256);
-    v = (v - d) >> 9;
+  for (int k = kSlices - 1; k >= kSlices - 3; --k) {
+    const int d = ((lo + 256) & 511) - 256;
+    lo = (lo - d) >> 9;
     h[k] = (unsigned short)(0x6600 + d);
   }
-  h[0] = (unsigned short)(0x6600 + (int)v);
+  hi += lo;                                   // carry of the low half
+#pragma unroll
+  for (int k = kSlices - 4; k >= 1; --k) {
+    const int d = ((hi + 256) & 511) - 256;
+    hi = (hi - d) >> 9;
+    h[k] = (unsigned short)(0x6600 + d);
+  }
+  h[0] = (unsigned short)(0x6600 + hi);
 }
 
 // two FP16 patterns of 1536 + d packed in a register -> the pair (d0, d1) as half2
