@@ -552,7 +552,7 @@ __device__ bool wait_deps(const FlowArgs& a, const Task& tk, int dir) {
   return ok;
 }
 
-__global__ void __launch_bounds__(256) solve_flow_kernel(FlowArgs a) {
+__global__ void __launch_bounds__(256, 4) solve_flow_kernel(FlowArgs a) {
   extern __shared__ double sm_f[];
   __shared__ long long s_item;
   __shared__ int s_ok;
