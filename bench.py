@@ -463,6 +463,66 @@ def run_serving(args, rank, world):
             "clocks": clk}
 
 
+# the paper's Tables 1-2: seconds per L-BFGS epoch (forward + adjoint + gradient of 2 sources, 200
+# steps) on 12 CPU threads, Voronoi meshes; hole specimen, 5 and 7 radial intervals
+PAPER_EPOCH_S = {(1000, 5): 0.95, (2000, 5): 2.39, (4000, 5): 5.49, (8000, 5): 11.19,
+                 (1000, 7): 1.32, (2000, 7): 3.21, (4000, 7): 6.82, (8000, 7): 13.92}
+
+
+def run_paper(args, rank, world):
+    """The paper's plate recipe on square S-elements: one evaluation (set-up + forward,
+    misfit, adjoint and gradient of both sources) per element count and interval count,
+    with the paper's seconds per epoch beside it (context: its meshes are Voronoi
+    polygons and it ran on a laptop CPU)."""
+    import torch
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi as lib
+    from sbfwi_inputs import paper_workload
+    if rank != 0:
+        return None
+    torch.cuda.set_device(0)
+    rows = []
+    units_all, secs_all = 0, 0.0
+    for (n_elem, intervals) in sorted(PAPER_EPOCH_S):
+        w = paper_workload(n_elem=n_elem, intervals=intervals)
+        L = w.mesh.lx
+        M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+        mt = lib.Model(M, w.c, w.rho_true, w.dt, lx=L, ly=L)
+        obs, _ = lib.forward(mt, w.src_nodes, w.wavelets, w.rec_nodes, keep=False)
+        del mt
+
+        def epoch():
+            md = lib.Model(M, w.c, w.rho_start, w.dt, lx=L, ly=L)
+            tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+            E, res = lib.misfit(tr, obs, w.dt)
+            return E, lib.adjoint_gradient(md, st, res)
+
+        for _ in range(max(1, args.warmup)):
+            epoch()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            epoch()
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / args.steps
+        units = w.mesh.n_elem * w.n_r * w.K * w.n_shots
+        units_all += units
+        secs_all += sec
+        rows.append({"elements": w.mesh.n_elem, "intervals": intervals, "N_r": w.n_r, "receivers": int(len(w.rec_nodes)),
+                     "s_per_epoch": sec, "units_per_s": units / sec,
+                     "paper_s_per_epoch": PAPER_EPOCH_S[(n_elem, intervals)],
+                     "paper_over_ours": PAPER_EPOCH_S[(n_elem, intervals)] / sec})
+    return {"metric": "paper-shaped plate: seconds per epoch (set-up + fwd + adj + grad, 2 sources, 200 steps)",
+            "value": units_all / secs_all, "unit": "element-radial-node-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs_all / len(rows), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "paper: 100 mm plate, c = 6000 m/s, rho = 2700 with one circular flaw, 2 sine-burst "
+                                   "sources (2 cycles, 500 kHz) 30 mm apart, receivers every 1 mm on 4 edges, 200 steps "
+                                   "of 0.2 us; square S-elements of order 2 instead of the paper's Voronoi polygons",
+                       "rows": rows, "l2": "small workloads: latency-bound, inputs fit L2"}}
+
+
 def run_reference(args, rank, world):
     """The oracle (the only reference this path has) on the host cores, rank 0 only."""
     if rank != 0:
@@ -491,10 +551,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=64, help="serving config: number of requests")
-    ap.add_argument("--config", choices=["size", "diff", "serving"], default="size",
+    ap.add_argument("--config", choices=["size", "diff", "serving", "paper"], default="size",
                     help="size: 64x64 elements, 8 shots, 2000 steps, stored forward field (the default); "
                          "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint; "
-                         "serving: forward-modelling requests with continuous batching")
+                         "serving: forward-modelling requests with continuous batching; "
+                         "paper: the paper's plate recipe at its Table 1 element counts")
     ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")
     ap.add_argument("--shots", type=int, default=0, help="shots per rank (0: the config's)")
     ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")
@@ -509,6 +570,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.config == "serving":
         out = run_serving(args, rank, world)
+    elif args.config == "paper":
+        out = run_paper(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if out is not None:

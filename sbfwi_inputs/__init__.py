@@ -15,11 +15,11 @@ meshes), a void/flaw density contrast, and Ricker sources.
 
 from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node
 from .fields import flawed_density_circle, flawed_density_ellipses
-from .wavelet import ricker
-from .configs import Workload, tiny_workload, size_workload, diff_workload, workload_by_name
+from .wavelet import ricker, sine_burst
+from .configs import Workload, tiny_workload, size_workload, diff_workload, paper_workload, workload_by_name
 
 __all__ = [
     "StructuredMesh", "structured_mesh", "boundary_nodes", "nearest_node",
-    "flawed_density_circle", "flawed_density_ellipses", "ricker",
-    "Workload", "tiny_workload", "size_workload", "diff_workload", "workload_by_name",
+    "flawed_density_circle", "flawed_density_ellipses", "ricker", "sine_burst",
+    "Workload", "tiny_workload", "size_workload", "diff_workload", "paper_workload", "workload_by_name",
 ]

@@ -21,7 +21,7 @@ import numpy as np
 
 from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node
 from .fields import flawed_density_circle, flawed_density_ellipses
-from .wavelet import ricker
+from .wavelet import ricker, sine_burst
 
 FLAW_FACTOR = 0.5
 
@@ -139,6 +139,39 @@ def diff_workload(seed: int = 2, K: int = 8000, n_shots: int = 16, nx: int = 128
     return w
 
 
+def paper_workload(n_elem: int = 2000, intervals: int = 5, seed: int = 3, p: int = 2, K: int = 200,
+                   flaw_factor: float = FLAW_FACTOR) -> Workload:
+    """The shape of the paper's plate experiments (Section 4) on square S-elements: a
+    100 mm x 100 mm plate, c = 6000 m/s, rho = 2700 with one circular flaw, two
+    sources 30 mm apart on the top edge driven by a 2-cycle sine burst (f0 = 500 kHz),
+    receivers every 1 mm along all four edges, dt = 0.2 us, 200 steps (40 us), and
+    `intervals` radial intervals (N_r = intervals + 1).  The paper's Voronoi meshes of
+    1000..8000 elements become about `n_elem` squares."""
+    nx = max(1, int(round(np.sqrt(n_elem))))
+    L = 0.1
+    mesh = structured_mesh(nx, nx, p, lx=L, ly=L)
+    c = 6000.0
+    f0, dt = 500e3, 0.2e-6
+    grid = 256
+    rho_rel, finfo = flawed_density_circle(grid, grid, radius=0.08, factor=flaw_factor, seed=seed)
+    rho_true = 2700.0 * rho_rel
+    rho_start = np.full_like(rho_true, 2700.0)
+    top = boundary_nodes(mesh, "top")
+    srcs = [nearest_node(mesh, top, (x, L)) for x in (0.035, 0.065)]
+    recs = []
+    for side, pts in (("bottom", [(x, 0.0) for x in np.arange(0.0005, L, 0.001)]),
+                      ("right", [(L, y) for y in np.arange(0.0005, L, 0.001)]),
+                      ("top", [(x, L) for x in np.arange(0.0005, L, 0.001)]),
+                      ("left", [(0.0, y) for y in np.arange(0.0005, L, 0.001)])):
+        cand = boundary_nodes(mesh, side)
+        recs += [nearest_node(mesh, cand, pt) for pt in pts]
+    recs = [r for r in dict.fromkeys(recs) if r not in srcs]
+    wav = np.stack([sine_burst(f0, dt, K, cycles=2, amplitude=1e12) for _ in srcs])
+    return Workload("paper", mesh, intervals + 1, c, grid, grid, rho_true, rho_start,
+                    np.array(srcs, dtype=np.int64), wav, np.array(recs, dtype=np.int64),
+                    dt, K, f0, info={"flaws": finfo, "seed": seed, "plate_m": L, "intervals": intervals})
+
+
 def workload_by_name(name: str, **kw) -> Workload:
     if name == "tiny":
         return tiny_workload(**kw)
@@ -146,4 +179,6 @@ def workload_by_name(name: str, **kw) -> Workload:
         return size_workload(**kw)
     if name == "diff":
         return diff_workload(**kw)
+    if name == "paper":
+        return paper_workload(**kw)
     raise KeyError(name)

@@ -15,3 +15,12 @@ def ricker(f0: float, dt: float, K: int, t0: float | None = None, amplitude: flo
     t = np.arange(1, K + 1, dtype=np.float64) * dt
     a = (np.pi * f0 * (t - t0)) ** 2
     return amplitude * (1.0 - 2.0 * a) * np.exp(-a)
+
+
+def sine_burst(f0: float, dt: float, K: int, cycles: int = 2, amplitude: float = 1.0) -> np.ndarray:
+    """Tone burst a sin(2 pi f0 t) sin^2(pi f0 t / cycles) for 0 <= t <= cycles/f0, zero after
+    (a sine carrier under a sin^2 window of `cycles` carrier periods), sampled at
+    t_k = k*dt for k = 1..K like ``ricker``."""
+    t = np.arange(1, K + 1, dtype=np.float64) * dt
+    w = np.where(t <= cycles / f0, np.sin(np.pi * f0 * t / cycles) ** 2, 0.0)
+    return amplitude * np.sin(2.0 * np.pi * f0 * t) * w

@@ -73,3 +73,24 @@ def test_no_receivers_gives_empty_traces_and_zero_gradient(lib):
     assert np.all(g == 0)
     E, _ = lib.misfit(tr, tr, dt)
     assert E == 0.0
+
+
+@pytest.mark.parametrize("intervals", [5, 7])
+def test_paper_shaped_workload_matches_oracle(lib, intervals):
+    """The paper's plate recipe (100 mm plate, c = 6000 m/s, rho = 2700 with a flaw, two
+    2-cycle sine-burst sources, receivers every 1 mm, 200 steps of 0.2 us) with 5 and 7
+    radial intervals, on about 100 square elements."""
+    from sbfwi_inputs import paper_workload
+    w = paper_workload(n_elem=100, intervals=intervals)
+    L = w.mesh.lx
+    om = fwi.build_model(w.mesh, w.n_r, w.c, w.rho_true, w.dt, lx=L, ly=L)
+    to, store, _ = fwi.forward(om, w.src_nodes, w.wavelets, w.rec_nodes)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_true, w.dt, lx=L, ly=L)
+    tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+    assert np.abs(to).max() > 0
+    assert rel(tr, to) <= TRACE_TOL
+    res = -to
+    g = lib.adjoint_gradient(md, st, res)
+    go = fwi.gradient_to_grid(om, fwi.adjoint_gradient(om, store, res, w.rec_nodes), w.gx, w.gy, L, L)
+    assert rel(g, go) <= GRAD_TOL
