@@ -25,6 +25,9 @@ Modules, in the order of the paper:
   nodal densities, by reverse-mode differentiation of the uncondensed time loop
   (pinned by central finite differences); the reference the paper's velocity
   kernel is compared with.
+* ``uneven``     -- the condensed path of ``fwi`` on meshes whose elements have
+  different numbers of boundary nodes (elements grouped by n_b), with its own
+  uncondensed direct solve for pinning.
 * ``lfe``        -- Section 3.2: the reduced (constant radial density) equation's
   low-frequency expansion, Riccati stiffness and Lyapunov mass.
 

@@ -117,3 +117,147 @@ def boundary_nodes(mesh, side: str) -> np.ndarray:
 def nearest_node(mesh, ids: np.ndarray, point) -> int:
     d = np.hypot(mesh.node_xy[ids, 0] - point[0], mesh.node_xy[ids, 1] - point[1])
     return int(ids[int(np.argmin(d))])
+
+
+@dataclass
+class QuadtreeMesh:
+    """Square S-elements of a 2:1-balanced quadtree, same arrays as ``StructuredMesh``.
+
+    Where a cell borders two cells of the next finer level, the side is split at
+    the shared (hanging) vertex into two line elements, so an element has 4 to 8
+    line elements and p * (number of lines) boundary nodes.  ``cells`` holds
+    (level, ix, iy) of every element (ix, iy in units of that level's cell size).
+    """
+    node_xy: np.ndarray
+    elem_ptr: np.ndarray
+    line_nodes: np.ndarray
+    centre_xy: np.ndarray
+    p: int
+    lx: float
+    ly: float
+    base: int
+    levels: int
+    cells: np.ndarray
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.node_xy.shape[0])
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.centre_xy.shape[0])
+
+    @property
+    def n_b(self) -> np.ndarray:
+        """Boundary nodes of every element."""
+        return self.p * np.diff(self.elem_ptr)
+
+
+def quadtree_mesh(base: int, levels: int, refine, p: int, lx: float = 1.0, ly: float = 1.0) -> QuadtreeMesh:
+    """Quadtree of square S-elements on [0, lx] x [0, ly] with ``base`` x ``base`` root cells.
+
+    ``refine(x0, y0, x1, y1, level)`` decides whether a cell of the given level
+    (0 = root) is split; cells are split up to ``levels`` times, then further
+    cells are split until every pair of cells sharing a side differs by at most
+    one level (2:1 balance).  Scaling centres are the cell centres; lines run
+    counter-clockwise from the lower-left corner; nodes inside a line element are
+    equally spaced.
+    """
+    if base < 1 or levels < 0 or p < 1:
+        raise ValueError("base >= 1, levels >= 0, p >= 1")
+    F = 1 << levels                       # fine-lattice units per root cell
+    M = base * F                          # fine cells per side
+    leaves = {(0, i, j) for i in range(base) for j in range(base)}
+
+    def box(c):
+        l, i, j = c
+        s = F >> l
+        return i * s, j * s, s
+
+    for lvl in range(levels):
+        for c in sorted(x for x in leaves if x[0] == lvl):
+            X, Y, s = box(c)
+            if refine(X * lx / M, Y * ly / M, (X + s) * lx / M, (Y + s) * ly / M, lvl):
+                leaves.remove(c)
+                leaves.update({(lvl + 1, 2 * c[1] + a, 2 * c[2] + b) for a in (0, 1) for b in (0, 1)})
+
+    def level_map():
+        lev = np.zeros((M, M), dtype=np.int64)          # [fine x][fine y] -> level of the covering leaf
+        for c in leaves:
+            X, Y, s = box(c)
+            lev[X:X + s, Y:Y + s] = c[0]
+        return lev
+
+    while True:                                          # 2:1 balance
+        lev = level_map()
+        split = []
+        for c in leaves:
+            X, Y, s = box(c)
+            nb_levels = []
+            if X > 0: nb_levels.append(lev[X - 1, Y:Y + s].max())
+            if X + s < M: nb_levels.append(lev[X + s, Y:Y + s].max())
+            if Y > 0: nb_levels.append(lev[X:X + s, Y - 1].max())
+            if Y + s < M: nb_levels.append(lev[X:X + s, Y + s].max())
+            if nb_levels and max(nb_levels) > c[0] + 1:
+                split.append(c)
+        if not split:
+            break
+        for c in split:
+            leaves.remove(c)
+            leaves.update({(c[0] + 1, 2 * c[1] + a, 2 * c[2] + b) for a in (0, 1) for b in (0, 1)})
+    lev = level_map()
+
+    vid = {}                                             # fine-lattice vertex -> node id
+    xy = []
+
+    def vertex(X, Y):
+        if (X, Y) not in vid:
+            vid[(X, Y)] = len(xy)
+            xy.append((X * lx / M, Y * ly / M))
+        return vid[(X, Y)]
+
+    inner = {}                                           # segment -> its p-1 inner nodes, from the lower endpoint
+
+    def segment(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in inner:
+            (Xa, Ya), (Xb, Yb) = key
+            ids = []
+            for k in range(1, p):
+                ids.append(len(xy))
+                xy.append(((Xa + (Xb - Xa) * k / p) * lx / M, (Ya + (Yb - Ya) * k / p) * ly / M))
+            inner[key] = ids
+        ids = inner[key]
+        return [vertex(*a)] + (ids if a < b else ids[::-1]) + [vertex(*b)]
+
+    cells = sorted(leaves, key=lambda c: (box(c)[1], box(c)[0], c[0]))   # rows bottom to top
+    lines, ptr, centres = [], [0], []
+    for c in cells:
+        X, Y, s = box(c)
+        h = s // 2
+        corners = [(X, Y), (X + s, Y), (X + s, Y + s), (X, Y + s)]
+        # a side gets its midpoint when the cell across it is finer
+        finer = [Y > 0 and lev[X, Y - 1] > c[0],
+                 X + s < M and lev[X + s, Y] > c[0],
+                 Y + s < M and lev[X, Y + s] > c[0],
+                 X > 0 and lev[X - 1, Y] > c[0]]
+        mids = [(X + h, Y), (X + s, Y + h), (X + h, Y + s), (X, Y + h)]
+        loop = []
+        for k in range(4):
+            loop.append(corners[k])
+            if finer[k]:
+                loop.append(mids[k])
+        for k in range(len(loop)):
+            lines.append(segment(loop[k], loop[(k + 1) % len(loop)]))
+        ptr.append(len(lines))
+        centres.append(((X + s / 2) * lx / M, (Y + s / 2) * ly / M))
+    return QuadtreeMesh(np.asarray(xy, dtype=np.float64), np.asarray(ptr, dtype=np.int64),
+                        np.asarray(lines, dtype=np.int64), np.asarray(centres, dtype=np.float64), p, lx, ly,
+                        base, levels, np.asarray(cells, dtype=np.int64))
+
+
+def min_spacing(mesh) -> float:
+    """Smallest distance between consecutive nodes of any line element."""
+    ln = mesh.line_nodes
+    d = np.hypot(*(mesh.node_xy[ln[:, 1:]] - mesh.node_xy[ln[:, :-1]]).transpose(2, 0, 1))
+    return float(d.min())
