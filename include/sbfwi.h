@@ -90,16 +90,22 @@ int sbfwi_version(void);
  *
  * Checks: ids in range, closed CCW loops, straight lines with equally spaced
  * nodes, det J_b > 0 (scaling centre sees every line from its left).  Returns
- * SBFWI_EINVAL with the offending element in the message.  This build requires
- * the same number of boundary nodes n_b (<= 24) for every element
- * (SBFWI_EUNSUPPORTED otherwise).  All arrays are host memory, copied.
+ * SBFWI_EINVAL with the offending element in the message.  Elements may have
+ * different numbers of line elements, hence of boundary nodes n_b(e) = p L(e)
+ * (quadtree meshes whose sides are split at hanging vertices, polygons); at most
+ * 40 per element (SBFWI_EUNSUPPORTED beyond).  The library pads every element to
+ * the mesh's largest n_b internally; the nodal points seen by callers (nodal
+ * densities and gradients) are unpadded: the N_r - 1 interior radial points of
+ * each element's n_b(e) rays in element order, radial index major, then the
+ * global nodes.  All arrays are host memory, copied.
  */
 int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes,
                      const int64_t* elem_ptr, const int64_t* line_nodes, int64_t n_lines,
                      const double* centre_xy, int64_t n_elem, int32_t p, int32_t n_r, double xi0);
 
-/* info[0..7] = n_elem, n_nodes, n_b, N_r, n_nodal (= n_int + n_nodes), n_int,
- * levels of the global elimination tree, nonzeros kept by the global factors. */
+/* info[0..7] = n_elem, n_nodes, n_b (the largest), N_r, n_nodal (= n_int + n_nodes),
+ * n_int (= (N_r - 1) x the sum of n_b(e)), levels of the global elimination tree,
+ * nonzeros kept by the global factors. */
 int sbfwi_mesh_info(const sbfwi_mesh* mesh, int64_t* info);
 void sbfwi_destroy_mesh(sbfwi_mesh* mesh);
 

@@ -126,18 +126,34 @@ struct MeshDevice {
   int64_t gx = 0, gy = 0;
   double lx = 0, ly = 0;
   DevBuf cell, clamp, cell_ptr, cell_list;
+  DevBuf nbe, lptr, api_map;         // n_b per element, first line per element, Mesh::api_to_lib
 };
 
+constexpr int kMaxBoundaryNodes = 40;   // largest n_b of an element
+
+// Elements may have different numbers of boundary nodes n_b(e).  Every per-element array
+// is laid out with the largest count, nb, as its stride: local dofs j >= n_b(e) are
+// padding, mapped to the extra global node n_nodes, whose state stays zero, and their
+// rows and columns of every element operator are zero, so they stay zero through the
+// time loop and never reach the global system.
 struct Mesh {
   int64_t n_elem = 0, n_nodes = 0, n_lines = 0;
-  int p = 0, n_r = 0, nb = 0, n = 0, L = 0;   // n = N_r - 1 intervals, L lines per element
+  int p = 0, n_r = 0, nb = 0, n = 0, L = 0;   // n = N_r - 1 intervals; nb, L: largest n_b, lines per element
   double xi0 = 1e-3;
   std::vector<double> node_xy, centre_xy;
   std::vector<int64_t> elem_ptr, line_nodes;
-  std::vector<int32_t> dofs;        // [n_elem][nb] global node of each local dof
-  std::vector<int32_t> line_local;  // [n_elem][L][p+1] local dof of each line position
+  std::vector<int32_t> nbe;         // [n_elem] n_b of each element
+  std::vector<int32_t> dofs;        // [n_elem][nb] global node of each local dof (n_nodes for padding)
+  std::vector<int32_t> line_local;  // [n_lines][p+1] local dof of each line position
+  bool uneven = false;              // some element has fewer than nb boundary nodes
   Tree tree;
+  // nodal points in the library's layout: interior (e, i, j) at (e n + i) nb + j for
+  // j < nb (padding included), then the global nodes
   int64_t n_int = 0, n_nodal = 0;
+  // nodal points in the caller's layout: interior points of every element without
+  // padding (n n_b(e) per element), then the global nodes; api_to_lib maps them
+  int64_t n_int_api = 0, n_nodal_api = 0;
+  std::vector<int64_t> api_to_lib;  // [n_nodal_api] (empty when !uneven: the layouts agree)
   mutable std::unique_ptr<MeshDevice> dev;   // set-up cache (set_model calls on one mesh must not overlap)
 };
 

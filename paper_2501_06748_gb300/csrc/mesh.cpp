@@ -90,7 +90,7 @@ int build_tree(Mesh& m) {
   // smallest subtree containing all elements of each node
   std::vector<int32_t> pmin(m.n_nodes, INT32_MAX), pmax(m.n_nodes, -1);
   for (int64_t e = 0; e < m.n_elem; ++e)
-    for (int j = 0; j < m.nb; ++j) {
+    for (int j = 0; j < m.nbe[e]; ++j) {
       int32_t g = m.dofs[e * m.nb + j];
       pmin[g] = std::min(pmin[g], pos_of[e]);
       pmax[g] = std::max(pmax[g], pos_of[e]);
@@ -114,7 +114,7 @@ int build_tree(Mesh& m) {
     std::vector<int32_t> cand;
     if (bd.c0[nd] < 0) {
       int32_t e = bd.order[bd.lo[nd]];
-      for (int j = 0; j < m.nb; ++j) cand.push_back(m.dofs[(int64_t)e * m.nb + j]);
+      for (int j = 0; j < m.nbe[e]; ++j) cand.push_back(m.dofs[(int64_t)e * m.nb + j]);
     } else {
       cand = bnd[bd.c0[nd]];
       cand.insert(cand.end(), bnd[bd.c1[nd]].begin(), bnd[bd.c1[nd]].end());
@@ -156,7 +156,7 @@ int build_tree(Mesh& m) {
     front.insert(front.end(), bnd[nd].begin(), bnd[nd].end());
     if (r.elem >= 0) {
       std::map<int32_t, int32_t> local;
-      for (int j = 0; j < m.nb; ++j) local[m.dofs[(int64_t)r.elem * m.nb + j]] = j;
+      for (int j = 0; j < m.nbe[r.elem]; ++j) local[m.dofs[(int64_t)r.elem * m.nb + j]] = j;
       for (int32_t g : front) {
         const int32_t j = local.at(g);
         t.map0.push_back(j);
@@ -350,7 +350,7 @@ int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes, c
   auto bad = [&](int code, const std::string& msg) { delete m; return fail(code, msg); };
   for (int64_t k = 0; k < n_lines * (p + 1); ++k)
     if (line_nodes[k] < 0 || line_nodes[k] >= n_nodes) return bad(SBFWI_EINVAL, "line node id out of range");
-  int nb_all = -1, L_all = -1;
+  int nb_max = 0, L_max = 0;
   for (int64_t e = 0; e < n_elem; ++e) {
     const int64_t l0 = elem_ptr[e], l1 = elem_ptr[e + 1];
     const std::string tag = "element " + std::to_string(e) + ": ";
@@ -378,9 +378,11 @@ int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes, c
     }
     const int L = (int)(l1 - l0);
     if ((int)order.size() != L * p) return bad(SBFWI_EINVAL, tag + "boundary nodes repeat along the loop");
-    if (nb_all < 0) { nb_all = (int)order.size(); L_all = L; }
-    if ((int)order.size() != nb_all || L != L_all)
-      return bad(SBFWI_EUNSUPPORTED, "elements with different numbers of boundary nodes are not supported by this build");
+    if (L * p > kMaxBoundaryNodes)
+      return bad(SBFWI_EUNSUPPORTED, tag + "more than " + std::to_string(kMaxBoundaryNodes) + " boundary nodes");
+    nb_max = std::max(nb_max, L * p);
+    L_max = std::max(L_max, L);
+    m->nbe.push_back(L * p);
     m->dofs.insert(m->dofs.end(), order.begin(), order.end());
     for (int64_t l = l0; l < l1; ++l)
       for (int k = 0; k <= p; ++k) {
@@ -388,11 +390,31 @@ int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes, c
         m->line_local.push_back((int32_t)(std::find(order.begin(), order.end(), g) - order.begin()));
       }
   }
-  m->nb = nb_all;
-  m->L = L_all;
-  if (m->nb > 24) return bad(SBFWI_EUNSUPPORTED, "this build supports at most 24 boundary nodes per element");
+  m->nb = nb_max;
+  m->L = L_max;
+  // padded dof table: padding points at the extra zero node n_nodes
+  {
+    std::vector<int32_t> padded((size_t)n_elem * nb_max, (int32_t)n_nodes);
+    int64_t k = 0;
+    for (int64_t e = 0; e < n_elem; ++e)
+      for (int j = 0; j < m->nbe[e]; ++j) padded[(size_t)e * nb_max + j] = m->dofs[k++];
+    m->dofs.swap(padded);
+  }
   m->n_int = m->n_elem * (int64_t)m->n * m->nb;
   m->n_nodal = m->n_int + m->n_nodes;
+  m->n_int_api = 0;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    m->n_int_api += (int64_t)m->n * m->nbe[e];
+    if (m->nbe[e] != m->nb) m->uneven = true;
+  }
+  m->n_nodal_api = m->n_int_api + m->n_nodes;
+  if (m->uneven) {
+    m->api_to_lib.reserve(m->n_nodal_api);
+    for (int64_t e = 0; e < n_elem; ++e)
+      for (int i = 0; i < m->n; ++i)
+        for (int j = 0; j < m->nbe[e]; ++j) m->api_to_lib.push_back((e * m->n + i) * m->nb + j);
+    for (int64_t g = 0; g < n_nodes; ++g) m->api_to_lib.push_back(m->n_int + g);
+  }
   int rc = build_tree(*m);
   if (rc != SBFWI_OK) { delete m; return rc; }
   *out = m;
@@ -405,8 +427,8 @@ int sbfwi_mesh_info(const sbfwi_mesh* m, int64_t* info) {
   info[1] = m->n_nodes;
   info[2] = m->nb;
   info[3] = m->n_r;
-  info[4] = m->n_nodal;
-  info[5] = m->n_int;
+  info[4] = m->n_nodal_api;
+  info[5] = m->n_int_api;
   info[6] = m->tree.levels;
   info[7] = m->tree.X_total;
   return SBFWI_OK;

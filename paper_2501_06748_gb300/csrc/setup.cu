@@ -111,6 +111,7 @@ __device__ __forceinline__ void atomic_flag(int* status, int code) { atomicCAS(s
 struct DensityArgs {
   int64_t n_elem, n_nodes, n_int;
   int nb, n;
+  const int32_t* nbe;        // n_b of each element: padding points get density 1 at the centre
   const double* node_xy;
   const double* centre_xy;
   const int32_t* dofs;
@@ -137,9 +138,15 @@ __global__ void density_kernel(DensityArgs a) {
       const int64_t e = q / ((int64_t)a.n * a.nb);
       const int64_t rem = q - e * (int64_t)a.n * a.nb;
       const int i = (int)(rem / a.nb), j = (int)(rem - (int64_t)i * a.nb);
+      const double x0 = a.centre_xy[2 * e], y0 = a.centre_xy[2 * e + 1];
+      if (j >= a.nbe[e]) {                 // padding: never used by the method
+        a.pts_hi[2 * q] = x0; a.pts_lo[2 * q] = 0.0;
+        a.pts_hi[2 * q + 1] = y0; a.pts_lo[2 * q + 1] = 0.0;
+        a.rho_hi[q] = 1.0; a.rho_lo[q] = 0.0;
+        continue;
+      }
       const int32_t g = a.dofs[e * a.nb + j];
       const dd xi{a.xi_hi[i], a.xi_lo[i]};
-      const double x0 = a.centre_xy[2 * e], y0 = a.centre_xy[2 * e + 1];
       // x0 + xi (x_j - x0)
       px = dd_add(dd_make(x0), dd_mul(xi, two_sum(a.node_xy[2 * g], -x0)));
       py = dd_add(dd_make(y0), dd_mul(xi, two_sum(a.node_xy[2 * g + 1], -y0)));
@@ -186,26 +193,40 @@ __global__ void density_kernel(DensityArgs a) {
   }
 }
 
+__global__ void fill_kernel(double* x, int64_t n, double v) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) x[q] = v;
+}
+
+// lib[map[q]] = api[q]: nodal values from the caller's layout to the padded one
+__global__ void scatter_nodal_kernel(const double* api, const int64_t* map, int64_t n, double* lib) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    lib[map[q]] = api[q];
+}
+
 // ---------------------------------------------------------------------------
 // 2. element set-up (double-double, one CTA per element, one thread per entry)
 // ---------------------------------------------------------------------------
 struct ElemArgs {
-  int nb, n, L, p, ng;
+  int nb, n, L, p, ng;        // nb, L: largest n_b and line count (strides of the outputs and smem)
+  int64_t e0;                 // first element of this launch
+  const int32_t* nbe;         // [E] n_b of each element
+  const int64_t* lptr;        // [E+1] first line of each element
+  dd* mat_ws;                 // global workspace for the 16 matrices (nullptr: shared memory)
   int64_t n_elem, n_int;
   double c;
   dd mass;                    // 1 / (beta dt^2)
   dd h;                       // radial spacing (1 - xi0) / n
   const double* node_xy;
   const double* centre_xy;
-  const int64_t* line_nodes;  // [E*L][p+1] (elements own consecutive lines)
-  const int32_t* line_local;  // [E][L][p+1]
+  const int64_t* line_nodes;  // [n_lines][p+1] (elements own consecutive lines)
+  const int32_t* line_local;  // [n_lines][p+1]
   const int32_t* dofs;
   const double* rho_hi;
   const double* rho_lo;
   const double* xi_hi;        // [n+1]
   const double* xi_lo;
   const double* tab;          // dd tables (hi,lo pairs): w[ng], phi[ng][p+1], dphi[ng][p+1]
-  double* mats;               // [E][n][3][nb][nb]
+  double* mats;               // [E][n][3][nb][nb], zero beyond n_b(e)
   double* rt;                 // [E][2][nb][nb]
   double* S;                  // [E][nb][nb]
   int* status;
@@ -217,9 +238,11 @@ struct ElemSmem {
   dd* Eline;  // [L][p+1][p+1][4] per-line contributions
   dd* phi;    // [ng][p+1]
   dd* dphi;   // [ng][p+1]
-  dd* mat;    // 16 matrices of nb*nb
+  dd* mat;    // 16 matrices of n_b(e)^2 (placed nb*nb apart)
   dd* col;    // [nb] Gauss-Jordan factor column
   int* piv;
+  int nb, L;  // this element's boundary nodes and lines
+  int64_t l0; // its first line
 };
 
 __device__ __forceinline__ dd ldd(const double* hi, const double* lo, int64_t k) { return dd{hi[k], lo[k]}; }
@@ -259,14 +282,14 @@ template <class Op>
 __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int64_t e, int i,
                                      dd* E0, dd* E1, dd* E2, dd* M0) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int nb = a.nb, L = a.L, p = a.p, ng = a.ng, pp = p + 1;
+  const int nb = sm.nb, L = sm.L, p = a.p, ng = a.ng, pp = p + 1, nbs = a.nb;
   // density at the Gauss points of every line, times the geometry factors
   for (int t = tid; t < L * ng; t += nt) {
     const int l = t / ng, g = t - l * ng;
     dd r = Op::make(0.0);
     for (int q = 0; q < pp; ++q) {
-      const int j = a.line_local[(e * L + l) * pp + q];
-      const int64_t idx = (i < a.n) ? e * (int64_t)a.n * nb + (int64_t)i * nb + j : a.n_int + a.dofs[e * nb + j];
+      const int j = a.line_local[(sm.l0 + l) * pp + q];
+      const int64_t idx = (i < a.n) ? e * (int64_t)a.n * nbs + (int64_t)i * nbs + j : a.n_int + a.dofs[e * nbs + j];
       r = Op::fma(r, sm.phi[g * pp + q], ldd(a.rho_hi, a.rho_lo, idx));
     }
     for (int k = 0; k < 4; ++k) sm.KR[(l * ng + g) * 4 + k] = Op::mul(sm.K[(l * ng + g) * 4 + k], r);
@@ -297,7 +320,7 @@ __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int6
     for (int l = 0; l < L; ++l) {
       int pa = -1, pb = -1;
       for (int q = 0; q < pp; ++q) {
-        const int j = a.line_local[(e * L + l) * pp + q];
+        const int j = a.line_local[(sm.l0 + l) * pp + q];
         if (j == A) pa = q;
         if (j == B) pb = q;
       }
@@ -372,30 +395,38 @@ __device__ void mm(int nb, const dd* A, const dd* B, dd* C) {
 
 __global__ void element_setup_kernel(ElemArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int nb = a.nb, L = a.L, p = a.p, ng = a.ng, pp = p + 1, n = a.n;
-  const int nn = nb * nb;
-  const int64_t e = blockIdx.x;
+  const int64_t e = a.e0 + blockIdx.x;
+  const int p = a.p, ng = a.ng, pp = p + 1, n = a.n, nbs = a.nb;
+  const int nb = a.nbe[e], L = (int)(a.lptr[e + 1] - a.lptr[e]);
+  const int nn = nb * nb;                 // this element's matrices are dense nb x nb
+  const int64_t nns = (int64_t)nbs * nbs; // stride of the padded outputs
   const int tid = threadIdx.x, nt = blockDim.x;
   ElemSmem sm;
+  sm.nb = nb; sm.L = L; sm.l0 = a.lptr[e];
   dd* base = reinterpret_cast<dd*>(smem_raw);
-  sm.K = base;                     base += L * ng * 4;
-  sm.KR = base;                    base += L * ng * 4;
-  sm.Eline = base;                 base += L * pp * pp * 4;
+  sm.K = base;                     base += a.L * ng * 4;
+  sm.KR = base;                    base += a.L * ng * 4;
+  sm.Eline = base;                 base += a.L * pp * pp * 4;
   sm.phi = base;                   base += ng * pp;
   sm.dphi = base;                  base += ng * pp;
-  sm.col = base;                   base += nb;
-  sm.mat = base;                   base += 16 * nn;
+  sm.col = base;                   base += nbs;
+  if (a.mat_ws) {
+    sm.mat = a.mat_ws + (int64_t)blockIdx.x * 16 * nns;
+  } else {
+    sm.mat = base;                 base += 16 * nns;
+  }
   sm.piv = reinterpret_cast<int*>(base);
-  dd* E0w[3] = {sm.mat + 0 * nn, sm.mat + 1 * nn, sm.mat + 2 * nn};
-  dd* E1w[3] = {sm.mat + 3 * nn, sm.mat + 4 * nn, sm.mat + 5 * nn};
-  dd* E2w[2] = {sm.mat + 6 * nn, sm.mat + 7 * nn};
-  dd* M0w[2] = {sm.mat + 8 * nn, sm.mat + 9 * nn};
-  dd* th = sm.mat + 10 * nn;
-  dd* ph = sm.mat + 11 * nn;
-  dd* ps = sm.mat + 12 * nn;
-  dd* Hp = sm.mat + 13 * nn;
-  dd* Gm = sm.mat + 14 * nn;
-  dd* T1 = sm.mat + 15 * nn;
+  const int ms = (int)nns;
+  dd* E0w[3] = {sm.mat + 0 * ms, sm.mat + 1 * ms, sm.mat + 2 * ms};
+  dd* E1w[3] = {sm.mat + 3 * ms, sm.mat + 4 * ms, sm.mat + 5 * ms};
+  dd* E2w[2] = {sm.mat + 6 * ms, sm.mat + 7 * ms};
+  dd* M0w[2] = {sm.mat + 8 * ms, sm.mat + 9 * ms};
+  dd* th = sm.mat + 10 * ms;
+  dd* ph = sm.mat + 11 * ms;
+  dd* ps = sm.mat + 12 * ms;
+  dd* Hp = sm.mat + 13 * ms;
+  dd* Gm = sm.mat + 14 * ms;
+  dd* T1 = sm.mat + 15 * ms;
 
   // Lagrange tables and line geometry (Section 3 preamble)
   for (int t = tid; t < ng * pp; t += nt) {
@@ -408,7 +439,7 @@ __global__ void element_setup_kernel(ElemArgs a) {
   const dd c2 = two_prod(a.c, a.c);
   for (int t = tid; t < L * ng; t += nt) {
     const int l = t / ng, g = t - l * ng;
-    const int64_t* ln = a.line_nodes + (e * L + l) * pp;
+    const int64_t* ln = a.line_nodes + (sm.l0 + l) * pp;
     dd xb = dd_make(0.0), yb = xb, xe = xb, ye = xb;
     for (int q = 0; q < pp; ++q) {
       const double nx = a.node_xy[2 * ln[q]], ny = a.node_xy[2 * ln[q] + 1];
@@ -437,7 +468,7 @@ __global__ void element_setup_kernel(ElemArgs a) {
   const dd inv_h = dd_div(dd_make(1.0), h);
   const dd inv_2h = dd_div(dd_make(0.5), h);
   const dd inv_h2 = dd_mul(inv_h, inv_h);
-  const int64_t matstride = (int64_t)3 * nn;
+  const int64_t matstride = 3 * nns;
   double* mats_e = a.mats + e * (int64_t)n * matstride;
 
   // radial window: slots of E0/E1 hold i-1, i, i+1; E2/M0 hold i, i+1
@@ -521,9 +552,10 @@ __global__ void element_setup_kernel(ElemArgs a) {
             sh = Op::fma(sh, gk, ps[k * nb + cc]);
           }
           sp = Op::mul(sp, x2);
-          Pi[t] = sp.hi;
-          Pi[nn + t] = (i == 0) ? 0.0 : sq.hi;
-          Pi[2 * nn + t] = sh.hi;
+          const int64_t to = (int64_t)r * nbs + cc;
+          Pi[to] = sp.hi;
+          Pi[nns + to] = (i == 0) ? 0.0 : sq.hi;
+          Pi[2 * nns + to] = sh.hi;
           T1[t] = sh;                                         // H_i kept in double-double
         }
         __syncthreads();
@@ -552,8 +584,8 @@ __global__ void element_setup_kernel(ElemArgs a) {
           Gm[t] = s;
         }
         __syncthreads();
-        double* Se = a.S + e * (int64_t)nn;
-        double* Re = a.rt + e * (int64_t)2 * nn;
+        double* Se = a.S + e * nns;
+        double* Re = a.rt + e * 2 * nns;
         for (int t = tid; t < nn; t += nt) {
           const int r = t / nb, cc = t - r * nb;
           dd s = Gm[t], rr = Op::mul(Op::mul(xi, E0w[s_cur][t]), inv_2h), tt = Op::make(0.0);  // -theta_{n+1} = xi E0/(2h)
@@ -563,9 +595,10 @@ __global__ void element_setup_kernel(ElemArgs a) {
             rr = Op::fma(rr, wk, th[k * nb + cc]);
             tt = Op::fma(tt, wk, M0w[w_cur][k * nb + cc]);
           }
-          Se[t] = s.hi;
-          Re[t] = rr.hi;
-          Re[nn + t] = Op::mul(tt, x2).hi;
+          const int64_t to = (int64_t)r * nbs + cc;
+          Se[to] = s.hi;
+          Re[to] = rr.hi;
+          Re[nns + to] = Op::mul(tt, x2).hi;
         }
         __syncthreads();
       }
@@ -783,6 +816,9 @@ static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
   if ((rc = upload(d->lines, m.line_nodes, st))) return rc;
   if ((rc = upload(d->lloc, m.line_local, st))) return rc;
   if ((rc = upload(d->dofs, m.dofs, st))) return rc;
+  if ((rc = upload(d->nbe, m.nbe, st))) return rc;
+  if ((rc = upload(d->lptr, m.elem_ptr, st))) return rc;
+  if (m.uneven && (rc = upload(d->api_map, m.api_to_lib, st))) return rc;
   if ((rc = upload(d->xih, xi_hi, st))) return rc;
   if ((rc = upload(d->xil, xi_lo, st))) return rc;
   if ((rc = upload(d->tab, tab, st))) return rc;
@@ -817,9 +853,20 @@ static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, double lx, dou
   std::vector<int32_t> cell(np, 0);
   std::vector<int8_t> clamp(np, 0);
   const long double h = (1.0L - (long double)m.xi0) / n;
+  // padding points of uneven meshes sit at their element's centre and are left out of
+  // the transpose (their gradient is zero)
+  auto padding = [&](int64_t q) {
+    if (q >= m.n_int) return false;
+    const int64_t e = q / ((int64_t)n * nb);
+    return (int)(q % nb) >= m.nbe[e];
+  };
   for (int64_t q = 0; q < np; ++q) {
     long double x, y;
-    if (q < m.n_int) {
+    if (padding(q)) {
+      const int64_t e = q / ((int64_t)n * nb);
+      x = m.centre_xy[2 * e];
+      y = m.centre_xy[2 * e + 1];
+    } else if (q < m.n_int) {
       const int64_t e = q / ((int64_t)n * nb), rem = q - e * (int64_t)n * nb;
       const int i = (int)(rem / nb), j = (int)(rem - (int64_t)i * nb);
       const int32_t g = m.dofs[e * nb + j];
@@ -847,12 +894,14 @@ static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, double lx, dou
     return (iy + (k >> 1)) * gx + ix + (k & 1);
   };
   for (int64_t q = 0; q < np; ++q)
-    for (int k = 0; k < 4; ++k) cnt[corner_cell(q, k) + 1]++;
+    if (!padding(q))
+      for (int k = 0; k < 4; ++k) cnt[corner_cell(q, k) + 1]++;
   for (int64_t c = 0; c < gx * gy; ++c) cnt[c + 1] += cnt[c];
   std::vector<int64_t> list(cnt.back());
   std::vector<int64_t> fillp(cnt.begin(), cnt.end() - 1);
   for (int64_t q = 0; q < np; ++q)
-    for (int k = 0; k < 4; ++k) list[fillp[corner_cell(q, k)]++] = q * 4 + k;
+    if (!padding(q))
+      for (int k = 0; k < 4; ++k) list[fillp[corner_cell(q, k)]++] = q * 4 + k;
   int rc;
   if ((rc = upload(d.cell, cell, st))) return rc;
   if ((rc = upload(d.clamp, clamp, st))) return rc;
@@ -879,12 +928,26 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   Profiler& prof = profiler();
   prof.begin(kPhaseSetup, st);
 
-  // density input
-  DevBuf d_rho_in;
-  const int64_t nrho = (md.rho_kind == SBFWI_RHO_NODAL) ? np : md.gx * md.gy;
-  SBFWI_CUDA(d_rho_in.alloc(sizeof(double) * nrho));
-  SBFWI_CUDA(cudaMemcpyAsync(d_rho_in.p, rho, sizeof(double) * nrho,
-                             mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  // density input (nodal values arrive in the caller's layout; uneven meshes spread
+  // them to the library's padded layout, padding points get 1)
+  DevBuf d_rho_in, d_rho_api;
+  const bool nodal = md.rho_kind == SBFWI_RHO_NODAL;
+  const int64_t nrho = nodal ? m.n_nodal_api : md.gx * md.gy;
+  const cudaMemcpyKind kind = mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (nodal && m.uneven) {
+    SBFWI_CUDA(d_rho_api.alloc(sizeof(double) * nrho));
+    SBFWI_CUDA(cudaMemcpyAsync(d_rho_api.p, rho, sizeof(double) * nrho, kind, st));
+    SBFWI_CUDA(d_rho_in.alloc(sizeof(double) * np));
+    const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
+    fill_kernel<<<blocks, 256, 0, st>>>(d_rho_in.as<double>(), np, 1.0);
+    scatter_nodal_kernel<<<blocks, 256, 0, st>>>(d_rho_api.as<double>(), d.api_map.as<int64_t>(), nrho,
+                                                 d_rho_in.as<double>());
+    prof.count(kPhaseSetup, 2);
+    SBFWI_CUDA(cudaGetLastError());
+  } else {
+    SBFWI_CUDA(d_rho_in.alloc(sizeof(double) * nrho));
+    SBFWI_CUDA(cudaMemcpyAsync(d_rho_in.p, rho, sizeof(double) * nrho, kind, st));
+  }
   DevBuf rho_hi, rho_lo;
   SBFWI_CUDA(rho_hi.alloc(sizeof(double) * np));
   SBFWI_CUDA(rho_lo.alloc(sizeof(double) * np));
@@ -892,7 +955,7 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   SBFWI_CUDA(md.pts_lo.alloc(sizeof(double) * 2 * np));
   {
     DensityArgs a;
-    a.n_elem = E; a.n_nodes = N; a.n_int = m.n_int; a.nb = nb; a.n = n;
+    a.n_elem = E; a.n_nodes = N; a.n_int = m.n_int; a.nb = nb; a.n = n; a.nbe = d.nbe.as<int32_t>();
     a.node_xy = d.xy.as<double>(); a.centre_xy = d.ctr.as<double>(); a.dofs = d.dofs.as<int32_t>();
     a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>();
     a.grid = d_rho_in.as<double>(); a.rho_kind = md.rho_kind; a.gx = md.gx; a.gy = md.gy; a.lx = md.lx; a.ly = md.ly;
@@ -914,9 +977,15 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   SBFWI_CUDA(md.mats.alloc(sizeof(double) * E * n * 3 * nn));
   SBFWI_CUDA(md.rt.alloc(sizeof(double) * E * 2 * nn));
   SBFWI_CUDA(md.S.alloc(sizeof(double) * E * nn));
+  if (m.uneven) {   // rows and columns beyond an element's n_b stay zero
+    SBFWI_CUDA(cudaMemsetAsync(md.mats.p, 0, md.mats.bytes, st));
+    SBFWI_CUDA(cudaMemsetAsync(md.rt.p, 0, md.rt.bytes, st));
+    SBFWI_CUDA(cudaMemsetAsync(md.S.p, 0, md.S.bytes, st));
+  }
   {
     ElemArgs a;
     a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
+    a.nbe = d.nbe.as<int32_t>(); a.lptr = d.lptr.as<int64_t>(); a.mat_ws = nullptr; a.e0 = 0;
     a.c = md.c;
     a.mass = dd_div(dd_make(1.0), dd_mul(dd_make(md.beta), two_prod(md.dt, md.dt)));
     a.h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
@@ -925,13 +994,30 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>();
     a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>(); a.tab = d.tab.as<double>();
     a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>(); a.S = md.S.as<double>(); a.status = status.as<int>();
-    const size_t smem = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb + 16 * nn) + 16;
+    // the 16 working matrices live in shared memory up to n_b = 24; beyond, in a global
+    // workspace, with the elements set up in chunks that bound its size
+    const size_t small = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb) + 16;
+    const size_t mat_bytes = sizeof(dd) * 16 * (size_t)nn;
+    const bool in_smem = small + mat_bytes <= 160 * 1024;
+    const size_t smem = in_smem ? small + mat_bytes : small;
     SBFWI_CUDA(cudaFuncSetAttribute(element_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int threads = (int)((nn + 31) / 32 * 32);
+    cudaFuncAttributes fattr;
+    SBFWI_CUDA(cudaFuncGetAttributes(&fattr, element_setup_kernel));
+    int threads = (int)std::min<int64_t>((nn + 31) / 32 * 32, fattr.maxThreadsPerBlock / 32 * 32);
     if (threads < 64) threads = 64;
-    element_setup_kernel<<<(unsigned)E, threads, smem, st>>>(a);
-    prof.count(kPhaseSetup);
-    SBFWI_CUDA(cudaGetLastError());
+    const int64_t chunk = in_smem ? E : std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)((256u << 20) / mat_bytes)));
+    DevBuf ws;
+    if (!in_smem) {
+      SBFWI_CUDA(ws.alloc(mat_bytes * chunk));
+      a.mat_ws = ws.as<dd>();
+    }
+    for (int64_t e0 = 0; e0 < E; e0 += chunk) {
+      a.e0 = e0;
+      element_setup_kernel<<<(unsigned)std::min(chunk, E - e0), threads, smem, st>>>(a);
+      prof.count(kPhaseSetup);
+      SBFWI_CUDA(cudaGetLastError());
+    }
+    if (!in_smem) SBFWI_CUDA(cudaStreamSynchronize(st));   // the workspace is freed on return
   }
 
   // the per-step operators split for the tensor cores

@@ -668,6 +668,12 @@ __global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double dt
   }
 }
 
+// out[q] (+)= lib[map[q]]: nodal values from the padded layout to the caller's
+__global__ void gather_nodal_kernel(const double* lib, const int64_t* map, int64_t n, double* out, int accumulate) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = accumulate ? out[q] + lib[map[q]] : lib[map[q]];
+}
+
 __global__ void grid_transpose_kernel(const double* g_nodal, const double* pts, const int32_t* cell_of_point,
                                       const int8_t* clamp, const int64_t* cell_ptr, const int64_t* cell_list,
                                       int64_t gx, int64_t gy, double lx, double ly, double* out, int accumulate) {
@@ -964,7 +970,8 @@ int Stepper::init() {
   const Tree& t = m.tree;
   nb = md.nb; n = md.n;
   E = md.E; N = md.N; np = m.n_nodal; nint = m.n_int;
-  const int64_t si = nint * B, sb = N * B;
+  // boundary state has one extra zero row: the padding dofs of uneven meshes read it
+  const int64_t si = nint * B, sb = N * B, sb1 = (N + 1) * B;
   // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
   // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
   const char* elem_env = std::getenv("SBFWI_ELEMENT");
@@ -975,9 +982,9 @@ int Stepper::init() {
   SBFWI_CUDA(rb.udd.alloc(sizeof(double) * (use_tc ? 1 : si)));
   SBFWI_CUDA(rb.q.alloc(sizeof(double) * si));
   if (use_tc) SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
-  SBFWI_CUDA(rb.ub.alloc(sizeof(double) * sb));
-  SBFWI_CUDA(rb.udb.alloc(sizeof(double) * sb));
-  SBFWI_CUDA(rb.uddb.alloc(sizeof(double) * sb));
+  SBFWI_CUDA(rb.ub.alloc(sizeof(double) * sb1));
+  SBFWI_CUDA(rb.udb.alloc(sizeof(double) * sb1));
+  SBFWI_CUDA(rb.uddb.alloc(sizeof(double) * sb1));
   SBFWI_CUDA(rb.ext.alloc(sizeof(double) * sb));
   SBFWI_CUDA(rb.x.alloc(sizeof(double) * sb));
   SBFWI_CUDA(rb.fhat.alloc(sizeof(double) * E * nb * B));
@@ -1017,6 +1024,10 @@ int Stepper::init() {
   e_threads = ea.epc * nb * B;
   e_blocks = (unsigned)((E + ea.epc - 1) / ea.epc);
   e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
+  cudaFuncAttributes eattr;
+  SBFWI_CUDA(cudaFuncGetAttributes(&eattr, element_step_kernel));
+  if (!use_tc && (e_threads > eattr.maxThreadsPerBlock || e_smem > 227 * 1024))
+    return fail(SBFWI_EUNSUPPORTED, "n_b x shots x radial points too large for one element block: run fewer shots per pass");
   if (e_smem > 48 * 1024)
     SBFWI_CUDA(cudaFuncSetAttribute(element_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem));
 
@@ -1497,7 +1508,8 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   if (rc == SBFWI_OK) rc = adj.check_status();
   if (rc) return rc;
   DevBuf gn, gout;
-  const int64_t nout = (md->rho_kind == SBFWI_RHO_GRID) ? md->gx * md->gy : np;
+  const Mesh& msh = *md->mesh;
+  const int64_t nout = (md->rho_kind == SBFWI_RHO_GRID) ? md->gx * md->gy : msh.n_nodal_api;
   double* dst = nullptr;
   if (mem == SBFWI_MEM_DEVICE) dst = grad;
   else {
@@ -1508,10 +1520,18 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   SBFWI_CUDA(gn.alloc(sizeof(double) * np));
   const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
   const bool grid = md->rho_kind == SBFWI_RHO_GRID;
-  // nodal output: shots summed straight into the output (accumulating if asked)
-  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, md->dt, grid ? gn.as<double>() : dst,
-                                           (!grid && accumulate) ? 1 : 0);
+  // nodal output: shots summed straight into the output (accumulating if asked); on
+  // uneven meshes into the padded layout first, then gathered to the caller's
+  const bool direct = !grid && !msh.uneven;
+  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, md->dt, direct ? dst : gn.as<double>(),
+                                           (direct && accumulate) ? 1 : 0);
   profiler().count(kPhaseOther);
+  if (!grid && msh.uneven) {
+    const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
+    gather_nodal_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->dev().api_map.as<int64_t>(), nout, dst,
+                                            accumulate ? 1 : 0);
+    profiler().count(kPhaseOther);
+  }
   if (grid) {
     const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
     const MeshDevice& mdev = md->dev();

@@ -13,13 +13,15 @@ meshes are not available.  They use square S-elements (structured or quadtree
 meshes), a void/flaw density contrast, and Ricker sources.
 """
 
-from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node
+from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node, QuadtreeMesh, quadtree_mesh, min_spacing
 from .fields import flawed_density_circle, flawed_density_ellipses
 from .wavelet import ricker, sine_burst
-from .configs import Workload, tiny_workload, size_workload, diff_workload, paper_workload, workload_by_name
+from .configs import (Workload, tiny_workload, size_workload, diff_workload, paper_workload, batching_workload,
+                      workload_by_name)
 
 __all__ = [
-    "StructuredMesh", "structured_mesh", "boundary_nodes", "nearest_node",
+    "StructuredMesh", "structured_mesh", "boundary_nodes", "nearest_node", "QuadtreeMesh", "quadtree_mesh",
+    "min_spacing", "batching_workload",
     "flawed_density_circle", "flawed_density_ellipses", "ricker", "sine_burst",
     "Workload", "tiny_workload", "size_workload", "diff_workload", "paper_workload", "workload_by_name",
 ]

@@ -19,7 +19,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node
+from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node, quadtree_mesh, min_spacing
 from .fields import flawed_density_circle, flawed_density_ellipses
 from .wavelet import ricker, sine_burst
 
@@ -53,7 +53,9 @@ class Workload:
 
     def summary(self) -> dict:
         m = self.mesh
-        return {"workload": self.name, "elements": m.n_elem, "p": m.p, "n_b": 4 * m.p,
+        nb = getattr(m, "n_b", None)
+        nb = 4 * m.p if nb is None else [int(nb.min()), int(nb.max())]
+        return {"workload": self.name, "elements": m.n_elem, "p": m.p, "n_b": nb,
                 "N_r": self.n_r, "global_nodes": m.n_nodes, "shots": self.n_shots,
                 "receivers": int(self.rec_nodes.shape[0]), "steps": self.K,
                 "grid": [self.gy, self.gx], "dt": self.dt, "f0": self.f0}
@@ -170,6 +172,51 @@ def paper_workload(n_elem: int = 2000, intervals: int = 5, seed: int = 3, p: int
     return Workload("paper", mesh, intervals + 1, c, grid, grid, rho_true, rho_start,
                     np.array(srcs, dtype=np.int64), wav, np.array(recs, dtype=np.int64),
                     dt, K, f0, info={"flaws": finfo, "seed": seed, "plate_m": L, "intervals": intervals})
+
+
+BATCHING_MESHES = ((2, 16), (3, 32), (5, 48))     # (p, N_r) of the three quadtree meshes
+
+
+def batching_workload(index: int, seed: int = 4, base: int = 16, levels: int = 2, K: int = 1500,
+                      n_shots: int | None = None, total_shots: int = 64, grid: int = 256, n_rec: int = 32,
+                      flaw_factor: float = FLAW_FACTOR) -> Workload:
+    """Mesh ``index`` (0, 1, 2) of the batching recipe: a quadtree of square S-elements,
+    ``base`` x ``base`` root cells refined ``levels`` times around two elliptical flaws
+    (seed + index) and 2:1 balanced, so that elements carry 4 to 8 line elements of order
+    p = 2, 3, 5 (n_b from 8 to 40) with N_r = 16, 32, 48 radial points.  The 64 shots of
+    the recipe are split over the three meshes (22, 21, 21), sources equally spaced on
+    the top edge, ``n_rec`` receivers equally spaced along the perimeter, 1500 steps."""
+    p, n_r = BATCHING_MESHES[index]
+    rho_true, finfo = flawed_density_ellipses(grid, grid, n=2, factor=flaw_factor, seed=seed + index)
+    flaw = rho_true != rho_true.max()
+    h = 1.0 / grid
+
+    def refine(x0, y0, x1, y1, lvl):
+        m = 0.5 * (x1 - x0)                        # refine where a flaw is within half a cell
+        i0, i1 = max(0, int((x0 - m) / h)), min(grid, int(np.ceil((x1 + m) / h)))
+        j0, j1 = max(0, int((y0 - m) / h)), min(grid, int(np.ceil((y1 + m) / h)))
+        return bool(flaw[j0:j1, i0:i1].any())
+
+    mesh = quadtree_mesh(base, levels, refine, p)
+    c = 1.0
+    s_min = min_spacing(mesh)
+    f0, dt = c / (10.0 * s_min), 0.5 * s_min / c
+    if n_shots is None:
+        n_shots = total_shots // 3 + (1 if index < total_shots % 3 else 0)
+    top = boundary_nodes(mesh, "top")
+    srcs = list(dict.fromkeys(nearest_node(mesh, top, ((s + 0.5) / n_shots, 1.0)) for s in range(n_shots)))
+    recs = []
+    for k in range(n_rec):
+        t = 4.0 * (k + 0.5) / n_rec
+        side, u = int(t), t - int(t)
+        side_name, pt = [("bottom", (u, 0.0)), ("right", (1.0, u)),
+                         ("top", (1.0 - u, 1.0)), ("left", (0.0, 1.0 - u))][side]
+        recs.append(nearest_node(mesh, boundary_nodes(mesh, side_name), pt))
+    recs = list(dict.fromkeys(recs))
+    wav = np.stack([ricker(f0, dt, K) for _ in srcs])
+    return Workload(f"batching[{index}]", mesh, n_r, c, grid, grid, rho_true, np.ones_like(rho_true),
+                    np.array(srcs, dtype=np.int64), wav, np.array(recs, dtype=np.int64),
+                    dt, K, f0, info={"flaws": finfo, "seed": seed + index, "base": base, "levels": levels})
 
 
 def workload_by_name(name: str, **kw) -> Workload:

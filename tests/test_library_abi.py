@@ -47,6 +47,23 @@ def test_mesh_info_and_elimination_tree(binding):
     assert big.factor_entries < 0.02 * big.n_nodes ** 2
 
 
+def test_mesh_info_of_elements_with_different_boundary_node_counts(binding):
+    """Quadtree mesh with hanging vertices: n_b is the largest count, and the nodal
+    layout seen by callers has no padding (n_int = n * sum of n_b(e))."""
+    from sbfwi_inputs import quadtree_mesh
+    m = quadtree_mesh(3, 1, lambda x0, y0, x1, y1, lvl: not (1 / 3 <= x0 < 0.5 and 1 / 3 <= y0 < 0.5), 5)
+    nbs = m.n_b
+    assert nbs.max() == 40 and nbs.min() == 20        # the centre cell has four finer neighbours
+    M = binding.Mesh.from_inputs(m, 6)
+    assert (M.n_elem, M.n_nodes, M.n_b) == (m.n_elem, m.n_nodes, 40)
+    assert M.n_int == 5 * int(nbs.sum()) and M.n_nodal == M.n_int + m.n_nodes
+    # more than 40 boundary nodes is outside this build
+    m9 = quadtree_mesh(3, 1, lambda x0, y0, x1, y1, lvl: not (1 / 3 <= x0 < 0.5 and 1 / 3 <= y0 < 0.5), 6)
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.Mesh.from_inputs(m9, 6)
+    assert ei.value.code == binding.EUNSUPPORTED
+
+
 def _bad(binding, **kw):
     m = structured_mesh(2, 2, 2)
     args = dict(node_xy=m.node_xy.copy(), elem_ptr=m.elem_ptr.copy(), line_nodes=m.line_nodes.copy(),
