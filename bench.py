@@ -523,6 +523,73 @@ def run_paper(args, rank, world):
                        "rows": rows, "l2": "small workloads: latency-bound, inputs fit L2"}}
 
 
+def run_batching(args, rank, world):
+    """The batching recipe: 64 shots over three seeded quadtree meshes (p = 2, 3, 5 with
+    N_r = 16, 32, 48; elements with 4 to 8 line elements, so n_b varies inside each mesh
+    and every mesh runs as one launch per step padded to its largest n_b), 1500 steps.
+    One step = set-up of the starting model + forward, misfit, adjoint and gradient of
+    every shot of the three meshes, in passes of 8 shots; the meshes run one after another."""
+    import torch
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi as lib
+    from paper_2501_06748_gb300 import shots
+    from sbfwi_inputs import batching_workload
+    if rank != 0:
+        return None
+    torch.cuda.set_device(0)
+    K = args.time_steps or 1500
+    per_pass = args.shots_per_pass or 8
+    meshes = []
+    for i in range(3):
+        w = batching_workload(i, K=K)
+        M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+        mt = lib.Model(M, w.c, w.rho_true, w.dt)
+        obs = np.concatenate([lib.forward(mt, w.src_nodes[lo:lo + per_pass], w.wavelets[lo:lo + per_pass],
+                                          w.rec_nodes, keep=False)[0]
+                              for lo in range(0, w.n_shots, per_pass)])
+        del mt
+        meshes.append((w, M, obs))
+
+    def epoch(times=None):
+        for k, (w, M, obs) in enumerate(meshes):
+            t0 = time.perf_counter()
+            md = lib.Model(M, w.c, w.rho_start, w.dt)
+            shots.misfit_and_gradient(md, w.src_nodes, w.wavelets, w.rec_nodes, obs, shots_per_pass=per_pass)
+            if times is not None:
+                times[k] += time.perf_counter() - t0
+
+    for _ in range(max(3, args.warmup)):
+        epoch()
+    clocks = ClockSampler(os.path.join("gpurun_out" if os.path.isdir("gpurun_out") else ".", "clocks_batching.csv"))
+    clocks.start()
+    times = [0.0] * 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        epoch(times)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    units = [w.mesh.n_elem * w.n_r * w.K * w.n_shots for w, _, _ in meshes]
+    rows = []
+    for (w, M, _), u, t in zip(meshes, units, times):
+        nb = w.mesh.n_b
+        rows.append({"mesh": w.name, "elements": w.mesh.n_elem, "p": w.mesh.p, "N_r": w.n_r,
+                     "n_b": {str(v): int(c) for v, c in zip(*np.unique(nb, return_counts=True))},
+                     "padded_n_b": int(M.n_b), "global_nodes": w.mesh.n_nodes, "shots": w.n_shots,
+                     "s_per_step": t / args.steps, "units_per_s": u / (t / args.steps)})
+    return {"metric": "batching: element-radial-node-steps/s fwd+adj+grad over 3 uneven quadtree meshes",
+            "value": sum(units) / sec, "unit": "element-radial-node-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"batching: 64 shots over 3 seeded quadtree meshes (16x16 root cells refined 2 "
+                                   f"levels around two elliptical flaws, 2:1 balanced, hanging vertices), p = 2, 3, 5, "
+                                   f"N_r = 16, 32, 48, {K} steps, {per_pass} shots per pass",
+                       "rows": rows, "l2": "inputs larger than L2 (forward velocity store 12-89 GB per pass)"},
+            "clocks": clk}
+
+
 def run_reference(args, rank, world):
     """The oracle (the only reference this path has) on the host cores, rank 0 only."""
     if rank != 0:
@@ -551,11 +618,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=64, help="serving config: number of requests")
-    ap.add_argument("--config", choices=["size", "diff", "serving", "paper"], default="size",
+    ap.add_argument("--config", choices=["size", "diff", "serving", "paper", "batching"], default="size",
                     help="size: 64x64 elements, 8 shots, 2000 steps, stored forward field (the default); "
                          "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint; "
                          "serving: forward-modelling requests with continuous batching; "
-                         "paper: the paper's plate recipe at its Table 1 element counts")
+                         "paper: the paper's plate recipe at its Table 1 element counts; "
+                         "batching: 64 shots over 3 quadtree meshes with uneven elements")
     ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")
     ap.add_argument("--shots", type=int, default=0, help="shots per rank (0: the config's)")
     ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")
@@ -572,6 +640,8 @@ def main():
         out = run_serving(args, rank, world)
     elif args.config == "paper":
         out = run_paper(args, rank, world)
+    elif args.config == "batching":
+        out = run_batching(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if out is not None:
