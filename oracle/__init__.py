@@ -20,7 +20,8 @@ Modules, in the order of the paper:
   and the zero-lag cross-correlation kernel with the gradient term dropped.
 * ``bruteforce`` -- the full uncondensed element systems of Eq. (system) plus the
   boundary flux balance, solved densely: an independent route to the same
-  discrete solution, and the pencil for free-vibration frequencies.
+  discrete solution, the pencil for free-vibration frequencies, and the time loop
+  on the transposed pencil (source-receiver reciprocity).
 * ``modex``      -- the exact derivative of the discrete misfit with respect to the
   nodal densities, by reverse-mode differentiation of the uncondensed time loop
   (pinned by central finite differences); the reference the paper's velocity
@@ -29,7 +30,8 @@ Modules, in the order of the paper:
   different numbers of boundary nodes (elements grouped by n_b), with its own
   uncondensed direct solve for pinning.
 * ``lfe``        -- Section 3.2: the reduced (constant radial density) equation's
-  low-frequency expansion, Riccati stiffness and Lyapunov mass.
+  low-frequency expansion, Riccati stiffness and Lyapunov mass (the paper's
+  comparison method), against which the radial finite differences converge.
 
 Parity status of each function is stated in its docstring ("pinned by ..." or
 "parity unpinned").

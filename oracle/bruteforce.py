@@ -180,6 +180,31 @@ class FullSystem:
             traces[:, :, k] = st.ub[np.asarray(rec_nodes)].T
         return traces, st
 
+    def forward_pencil(self, src_nodes, wavelets, rec_nodes, K=None, transpose=False):
+        """The same time loop written for the assembled pencil: with M the assembled mass
+        rows (xi_i^2 M0_i at element row i, unknown u_i) and A the assembled matrix, every
+        step solves A x = -M (a0 u + a1 u' + a2 u'') + f and updates u, u', u'' of every
+        entry by Eq. (Newmark).  ``transpose=True`` runs the transposed pencil (A^T, M^T),
+        whose state lives on the equations' index set; sources act on the flux rows and
+        receivers read the boundary unknowns of the same global node numbers."""
+        src_nodes = np.asarray(src_nodes)
+        rec_nodes = np.asarray(rec_nodes)
+        wavelets = np.atleast_2d(wavelets)
+        B = src_nodes.size
+        K = wavelets.shape[1] if K is None else K
+        M = self.mass.T.tocsc() if transpose else self.mass
+        u, ud, udd = (np.zeros((self.size, B)) for _ in range(3))
+        traces = np.zeros((B, len(rec_nodes), K))
+        for k in range(K):
+            rhs = -(M @ fwi.newmark_predictor(u, ud, udd, self.dt, self.beta))
+            for s in range(B):
+                rhs[self.n_elem_unknowns + src_nodes[s], s] += wavelets[s, k]
+            x = self.solve(rhs, transpose=transpose)
+            ud, udd = fwi.newmark_update(u, ud, udd, x, self.dt, self.beta, self.gamma)
+            u = x
+            traces[:, :, k] = x[self.n_elem_unknowns + rec_nodes].T
+        return traces
+
     # -- free vibration ---------------------------------------------------------
 
     def refine_mode(self, x, omega2, iters=4):

@@ -1,0 +1,53 @@
+"""Low-frequency expansion of the reduced element equation (Section 3.2), the paper's
+comparison method.  TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+With the density held constant along every radial line (it varies with eta only),
+E0, E1, E2, M0 no longer depend on xi and the radial ODE reduces to Eq. (simplified).
+Its dynamic stiffness S(omega) at the boundary is expanded as S ~ K - omega^2 M
+(Eq. (S)):
+
+* K solves the algebraic Riccati equation (K - E1) E0^-1 (K - E1^T) - E2 = 0.  With
+  q = xi E0 u_xi + E1^T u (Eq. (internal)) the static ODE is the first-order system
+  xi d/dxi [u; q] = -Z [u; q] with
+      Z = [[E0^-1 E1^T, -E0^-1], [-E2 + E1 E0^-1 E1^T, -E1 E0^-1]];
+  its solutions are eigenvectors of Z times xi^-lambda, and those bounded at the
+  scaling centre (Re lambda < 0, plus the constant mode u = 1, q = 0 of the double
+  zero eigenvalue, exact because E1^T 1 = E2 1 = 0) span q = K u, so K = Q_q Q_u^-1.
+* M solves the Lyapunov equation (K - E1) E0^-1 M + M E0^-1 (K - E1^T) + 2 M - M0 = 0,
+  as one dense linear system in the n_b^2 entries of M.
+
+Pinned by ``tests/test_oracle_lfe.py``: the radial finite-difference condensation of
+the same reduced element (``oracle.sbfem``, density constant in xi) converges to K
+(static S) and to M (derivative of S with respect to the Newmark mass factor) as N_r
+grows -- two independent discretisations of one equation.
+"""
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def riccati_stiffness(E0, E1, E2):
+    """K with (K - E1) E0^-1 (K - E1^T) - E2 = 0 from the bounded solutions of Z."""
+    nb = E0.shape[0]
+    E0i = np.linalg.inv(E0)
+    Z = np.block([[E0i @ E1.T, -E0i], [-E2 + E1 @ E0i @ E1.T, -E1 @ E0i]])
+    lam, V = np.linalg.eig(Z)
+    order = np.argsort(lam.real)
+    # the two eigenvalues closest to zero are the constant mode and its unbounded
+    # (log xi) partner; the n_b - 1 most negative ones decay towards the centre
+    near_zero = set(np.argsort(np.abs(lam))[:2])
+    keep = [k for k in order if k not in near_zero][:nb - 1]
+    Q = np.concatenate([V[:, keep], np.concatenate([np.ones(nb), np.zeros(nb)])[:, None]], axis=1)
+    K = Q[nb:] @ np.linalg.inv(Q[:nb])
+    return K.real, float(np.abs(K.imag).max() / np.abs(K.real).max())
+
+
+def lyapunov_mass(K, E0, E1, M0):
+    """M with (K - E1) E0^-1 M + M E0^-1 (K - E1^T) + 2 M - M0 = 0 (row-major vec)."""
+    nb = E0.shape[0]
+    E0i = np.linalg.inv(E0)
+    A = (K - E1) @ E0i
+    B = E0i @ (K - E1.T)
+    I = np.eye(nb)
+    L = np.kron(A, I) + np.kron(I, B.T) + 2.0 * np.eye(nb * nb)
+    return np.linalg.solve(L, M0.reshape(-1)).reshape(nb, nb)
