@@ -7,8 +7,11 @@ set-up models (the set-up is paid once per model), queues requests as they arriv
 and, whenever the device is free, launches the oldest waiting request together
 with up to ``max_batch - 1`` other waiting requests that share its model, step
 count and receivers: they run as one batch of shots through ``sbfwi.forward``
-(every operator read once for all of them).  Latency is measured from a request's
-arrival to the end of the batch that served it.
+(every operator read once for all of them).  Admission is also bounded by device
+memory: with ``mem_budget`` set, a batch takes requests only while the device memory
+their shots need (the stepper's per-shot state and the traces, ``request_bytes``) fits
+the budget; a request that does not fit waits for the next batch.  Latency is measured
+from a request's arrival to the end of the batch that served it.
 """
 
 from __future__ import annotations
@@ -56,17 +59,34 @@ class ModelCache:
         return m
 
 
+def request_bytes(model, r: Request) -> int:
+    """Device memory one shot of a forward pass needs: the interior state of every
+    element at the padded n_b (predictor, z, q and their neighbours: 5 arrays), the
+    boundary state and solution (6 arrays), the effective sources and the traces."""
+    mesh = model.mesh
+    interior = mesh.n_elem * (mesh.n_r - 1) * mesh.n_b
+    return 8 * (5 * interior + 6 * (mesh.n_nodes + 1) + mesh.n_elem * mesh.n_b + r.rec_nodes.size * r.K)
+
+
 class Engine:
-    def __init__(self, build_model, max_batch=8, cache_capacity=8):
+    def __init__(self, build_model, max_batch=8, cache_capacity=8, mem_budget=None):
         self.cache = ModelCache(build_model, cache_capacity)
         self.max_batch = max_batch
+        self.mem_budget = mem_budget
         self.batches = []
 
-    def _pick(self, waiting):
+    def _pick(self, waiting, model):
         head = waiting[0]
         same = [r for r in waiting if r.model_key == head.model_key and r.K == head.K
                 and np.array_equal(r.rec_nodes, head.rec_nodes)]
-        return same[:self.max_batch]
+        batch, used = [], 0
+        for r in same[:self.max_batch]:
+            need = request_bytes(model, r)
+            if batch and self.mem_budget is not None and used + need > self.mem_budget:
+                break
+            batch.append(r)
+            used += need
+        return batch
 
     def run(self, requests, clock=time.perf_counter):
         """Serve ``requests`` (sorted by arrival, arrival times relative to the start);
@@ -84,8 +104,8 @@ class Engine:
             if not waiting:
                 time.sleep(max(0.0, min(pending[i].arrival - now(), 0.01)))
                 continue
-            batch = self._pick(waiting)
-            model = self.cache.get(batch[0].model_key)
+            model = self.cache.get(waiting[0].model_key)
+            batch = self._pick(waiting, model)
             src = np.array([r.src_node for r in batch], dtype=np.int64)
             wav = np.stack([r.wavelet for r in batch])
             tr, _ = sbfwi.forward(model, src, wav, batch[0].rec_nodes, keep=False)

@@ -9,7 +9,10 @@ from sbfwi_inputs import structured_mesh, boundary_nodes, ricker, flawed_density
 pytestmark = pytest.mark.gpu
 
 
-def test_batched_requests_match_single_shot_forwards(lib):
+@pytest.mark.parametrize("budget_requests", [None, 2])
+def test_batched_requests_match_single_shot_forwards(lib, budget_requests):
+    """Results are the same alone and in the mix; with a memory budget of two requests'
+    worth, no batch holds more than two."""
     from paper_2501_06748_gb300 import serving
     meshes = {}
 
@@ -32,10 +35,16 @@ def test_batched_requests_match_single_shot_forwards(lib):
         dt = 0.5 / (nx * p)
         wav = ricker(1.0 / (10 / (nx * p)), dt, 40 + 10 * (rid % 2))
         reqs.append(serving.Request(rid, key, int(rng.choice(top)), wav, recs, arrival=0.0))
-    eng = serving.Engine(build, max_batch=4)
+    budget = None
+    if budget_requests:
+        need = max(serving.request_bytes(build(r.model_key), r) for r in reqs)
+        budget = budget_requests * need
+    eng = serving.Engine(build, max_batch=4, mem_budget=budget)
     eng.run(reqs)
     assert all(r.done >= 0 for r in reqs)
     assert max(eng.batches) > 1 and sum(eng.batches) == len(reqs)
+    if budget_requests:
+        assert max(eng.batches) <= budget_requests
     for r in reqs:
         md = build(r.model_key)
         tr, _ = lib.forward(md, [r.src_node], r.wavelet[None], r.rec_nodes, keep=False)
