@@ -34,161 +34,9 @@
 
 #include "internal.h"
 #include "prof.h"
+#include "tc_digits.cuh"
 
 namespace sbfwi {
-
-namespace tc {
-
-constexpr int kSlices = 6;      // base-512 digits per operand
-constexpr int kLevels = 7;      // significance levels kept: k + l = 2..8
-constexpr int kTile = 16;       // rows / inner dimension of one mma tile
-constexpr int kCols = 8;        // shots of one mma tile
-
-// round(a * 2^(53 - e)) for |a| < 2^e, from the binary64 fields (integer work only)
-__device__ __forceinline__ long long to_fixed(double a, int e) {
-  const long long bits = __double_as_longlong(a);
-  if ((bits & 0x7FFFFFFFFFFFFFFFLL) == 0) return 0;
-  const int ex = (int)((bits >> 52) & 0x7FF);
-  long long mant = bits & 0x000FFFFFFFFFFFFFLL;
-  int ex_eff = ex;
-  if (ex == 0) ex_eff = 1;              // subnormal
-  else mant |= 0x0010000000000000LL;
-  // right shift of the 53-bit significand; |a| < 2^e makes it >= 0
-  const int sh = e + 1022 - ex_eff;
-  long long v;
-  if (sh <= 0) v = mant;
-  else if (sh >= 60) v = 0;
-  else v = (mant + (1LL << (sh - 1))) >> sh;
-  return bits < 0 ? -v : v;
-}
-
-// exponent e with |a| < 2^e (for a != 0); very small for a == 0 (integer work only)
-__device__ __forceinline__ int exp_bound(double a) {
-  const long long bits = __double_as_longlong(a);
-  const int ex = (int)((bits >> 52) & 0x7FF);
-  if (ex == 0) return (bits & 0x7FFFFFFFFFFFFFFFLL) == 0 ? -1100 : -1021;
-  return ex - 1022;
-}
-
-// t * 2^E for results outside the normal range (never met by the path's fields): kept
-// out of line so that its FP64 conversion is not evaluated speculatively on the hot path
-__device__ __noinline__ double int_to_double_scaled_slow(long long t, int E) { return ldexp((double)t, E); }
-
-// t * 2^E as a binary64, rounded to nearest-even like a conversion of t, built with
-// integer operations (the scaling by 2^E is exact unless the result is subnormal)
-__device__ __forceinline__ double int_to_double_scaled(long long t, int E) {
-  if (t == 0) return 0.0;
-  const unsigned long long sign = t < 0 ? 0x8000000000000000ULL : 0ULL;
-  unsigned long long m = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
-  const int lz = __clzll((long long)m);
-  m <<= lz;                                   // top bit at position 63
-  unsigned long long hi = m >> 11;            // 53 bits
-  const unsigned long long rem = m & 0x7FFULL;
-  if (rem > 0x400ULL || (rem == 0x400ULL && (hi & 1ULL))) ++hi;
-  int bexp = E - lz + 11 + 52 + 1023;
-  if (hi == (1ULL << 53)) { hi >>= 1; ++bexp; }
-  if (bexp >= 1 && bexp <= 2046)
-    return __longlong_as_double((long long)(sign | ((unsigned long long)bexp << 52) | (hi & 0x000FFFFFFFFFFFFFULL)));
-  return int_to_double_scaled_slow(t, E);
-}
-
-// six balanced base-512 digits, most significant first, as FP16 bit patterns of 1536 + d
-// The 54-bit recurrence runs on two 32-bit halves: the low 27 bits give the three
-// least significant digits and a carry (0 or 1) into the high half, which gives the
-// rest -- the same digits as the recurrence on the whole integer.
-__device__ __forceinline__ void digits(long long v, unsigned short (&h)[kSlices]) {
-  int lo = (int)(v & ((1LL << 27) - 1));      // 0 .. 2^27 - 1
-  int hi = (int)(v >> 27);                    // |hi| < 2^26 (arithmetic shift)
-#pragma unroll
-  for (int k = kSlices - 1; k >= kSlices - 3; --k) {
-    const int d = ((lo + 256) & 511) - 256;
-    lo = (lo - d) >> 9;
-    h[k] = (unsigned short)(0x6600 + d);
-  }
-  hi += lo;                                   // carry of the low half
-#pragma unroll
-  for (int k = kSlices - 4; k >= 1; --k) {
-    const int d = ((hi + 256) & 511) - 256;
-    hi = (hi - d) >> 9;
-    h[k] = (unsigned short)(0x6600 + d);
-  }
-  h[0] = (unsigned short)(0x6600 + hi);
-}
-
-// two FP16 patterns of 1536 + d packed in a register -> the pair (d0, d1) as half2
-__device__ __forceinline__ unsigned pack_digits(unsigned short lo, unsigned short hi) {
-  const unsigned u = (unsigned)lo | ((unsigned)hi << 16);
-  __half2 h = *reinterpret_cast<const __half2*>(&u);
-  h = __hsub2(h, __halves2half2(__ushort_as_half(0x6600), __ushort_as_half(0x6600)));
-  return *reinterpret_cast<const unsigned*>(&h);
-}
-
-__device__ __forceinline__ void mma16816(float (&c)[4], const uint4& a, unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-
-// Sum of the levels as an int64 with weight 2^-52 relative to 2^(e_r + f).  Levels
-// 2..6 are added exactly; levels 7 and 8 are summed exactly apart and rounded once to
-// the nearest unit (flooring them with shifts biases every product by about -1 unit,
-// which the energy-conserving time loop then accumulates).
-__device__ __forceinline__ double recombine(const float (&acc)[kLevels][4], int j, int e) {
-  long long t = 0;
-  t += (long long)__float2int_rn(acc[0][j]) << 36;
-  t += (long long)__float2int_rn(acc[1][j]) << 27;
-  t += (long long)__float2int_rn(acc[2][j]) << 18;
-  t += (long long)__float2int_rn(acc[3][j]) << 9;
-  t += (long long)__float2int_rn(acc[4][j]);
-  const long long low = ((long long)__float2int_rn(acc[5][j]) << 9) + (long long)__float2int_rn(acc[6][j]);
-  t += (low + (1LL << 17)) >> 18;
-  return int_to_double_scaled(t, e - 52);
-}
-
-// Digits of an operand held in the B-fragment layout of m16n8k16: lane (g, t) holds
-// rows 2t, 2t+1, 2t+8, 2t+9 of column g.  f is that column's exponent.
-struct BDigits {
-  unsigned r[kSlices][2];
-};
-
-__device__ __forceinline__ void split_b(const double (&x)[4], int f, BDigits& d) {
-  unsigned short h[4][kSlices];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) digits(to_fixed(x[j], f), h[j]);
-#pragma unroll
-  for (int k = 0; k < kSlices; ++k) {
-    d.r[k][0] = pack_digits(h[0][k], h[1][k]);
-    d.r[k][1] = pack_digits(h[2][k], h[3][k]);
-  }
-}
-
-// column exponent: max over the four lanes of a column group (lanes 4g..4g+3)
-__device__ __forceinline__ int column_exponent(int e) {
-  e = max(e, __shfl_xor_sync(0xffffffffu, e, 1));
-  e = max(e, __shfl_xor_sync(0xffffffffu, e, 2));
-  return e;
-}
-
-// acc[L] += sum_{k + l = L} A_k x_l over the kept levels; A slices in fragment layout
-__device__ __forceinline__ void product(float (&acc)[kLevels][4], const uint4* Aslices, const BDigits& x) {
-#pragma unroll
-  for (int k = 0; k < kSlices; ++k) {
-    const uint4 a = Aslices[k * 32];
-#pragma unroll
-    for (int l = 0; l < kSlices; ++l)
-      if (k + l < kLevels) mma16816(acc[k + l], a, x.r[l][0], x.r[l][1]);
-  }
-}
-
-__device__ __forceinline__ void zero(float (&acc)[kLevels][4]) {
-#pragma unroll
-  for (int L = 0; L < kLevels; ++L)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[L][j] = 0.f;
-}
-
-}  // namespace tc
 
 // ---------------------------------------------------------------------------
 // set-up: slices of the per-step operators in mma fragment layout
@@ -204,16 +52,6 @@ __device__ __forceinline__ void zero(float (&acc)[kLevels][4]) {
 // q 2^a ~ v).  Without the balancing a shared exponent would cost the smaller block a
 // dozen bits.  P's exponent slot holds the joint row exponents, Q's slot holds a_i in
 // its first entry.  H, R and T are scaled on their own.
-struct SliceArgs {
-  int nb, n;
-  int64_t E;
-  const double* mats;     // [E][n][3][nb][nb]
-  const double* rt;       // [E][2][nb][nb]
-  uint4* frag;            // [E][n][3: P, Q, H][kSlices][32]
-  uint4* frag_rt;         // [E][2: R, T][kSlices][32]
-  int* exps;              // [E][n][3][16]
-  int* exps_rt;           // [E][2][16]
-};
 
 __global__ void slice_operators_kernel(SliceArgs a) {
   using namespace tc;
@@ -286,41 +124,8 @@ __global__ void slice_operators_kernel(SliceArgs a) {
 // ---------------------------------------------------------------------------
 // element step on the tensor cores (one warp per element)
 // ---------------------------------------------------------------------------
-struct ElemTcArgs {
-  int nb, n, B;
-  int64_t E;
-  double a0, a1, a2, c1, c2, dt;
-  const uint4* frag;
-  const uint4* frag_rt;
-  const int* exps;
-  const int* exps_rt;
-  const int32_t* dofs;
-  double* u; double* ud; double* udd; double* v;          // interior state [E][n][nb][B]: this kernel
-                                                          // keeps v (predictor) in v and z = u' + dt (1 - gamma) u''
-                                                          // in ud; u and udd are unused
-  const double* ub; const double* udb; const double* uddb;
-  double* q;
-  double* fhat;
-  int do_down, do_up;
-  double* store_int;
-  const double* fwd_int;
-  double* grad_int;
-};
 
 namespace tc {
-
-// asynchronous global -> shared copies (Ampere-style cp.async; completion per thread)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // One pipeline stage: the digit fragments of one or two operators and their row
 // exponents.  Each lane copies its own fragments; lanes 0..16*nops-1 the exponents.
@@ -533,10 +338,17 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
 // ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
-bool tc_supported(int nb, int B) { return nb <= tc::kTile && B <= tc::kCols; }
+// Padded n_b 17..20 stays on the FP64 kernel: two 16-row tiles then do 4x the digit work
+// of one for at most 1.6x the entries, and on the batching meshes the FP64 kernel was
+// faster at n_b = 18 (6.6 s against 8.0 s per step of the p = 3 mesh) while the two-tile
+// kernel was faster at n_b = 30 (12.5 s against 21.9 s of the p = 5 mesh).
+bool tc_supported(int nb, int B) {
+  return (nb <= tc::kTile || (nb >= kTwoTileMinNb && nb <= 2 * tc::kTile)) && B <= tc::kCols;
+}
 
 int tc_prepare(Model& md, cudaStream_t st) {
   using namespace tc;
+  if (md.nb > kTile) return tc2_prepare(md, st);
   const int nb = md.nb, n = md.n;
   const int64_t E = md.E;
   SBFWI_CUDA(md.tc_frag.alloc(sizeof(uint4) * (size_t)E * n * 3 * kSlices * 32));
@@ -571,6 +383,7 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
   a.do_down = down; a.do_up = up;
   a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
+  if (md.nb > tc::kTile) return tc2_element_launch(a, md.a2, st);
   const int smem = (int)(sizeof(tc::WarpSmem) * tc::kWarpsPerBlock);   // attribute set by tc_prepare
   const unsigned blocks = (unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock);
   // beta = 1/4 (a2 = 1): the predictor needs no multiply by a2

@@ -1,7 +1,7 @@
 """Edge cases of the GPU path against the oracle: a single element, the lowest
 Lagrange order, the fewest radial points, one time step, no receivers, the largest
-shot batch (16, FP64 element kernel), a boundary-node count above the tensor-core
-tile (n_b = 20, FP64 element kernel)."""
+shot batch (16, FP64 element kernel), boundary-node counts above one tensor-core
+tile (n_b = 20: FP64 element kernel; n_b = 24 and the largest, 32: two-tile kernel)."""
 
 import numpy as np
 import pytest
@@ -41,6 +41,8 @@ CASES = {
     "one_time_step": (3, 2, 2, 5, 2, 1, 4),
     "sixteen_shots_fp64_kernel": (3, 3, 2, 5, 16, 30, 4),
     "nb20_fp64_kernel": (2, 2, 5, 5, 3, 30, 4),
+    "nb24_two_tile_kernel": (2, 2, 6, 5, 3, 30, 4),
+    "nb32_two_tile_kernel": (2, 2, 8, 4, 3, 20, 4),
 }
 
 

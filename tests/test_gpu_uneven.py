@@ -64,25 +64,28 @@ def _compare(lib, m, n_r, rho, dt, src, wav, rec, rho_kind="grid"):
 
 
 @pytest.mark.parametrize("element", ["tensor", "fp64"])
-def test_quadtree_order2_both_element_kernels(lib, element, monkeypatch):
-    """n_b 8 and 10 padded to 10: the tensor-core kernel (n_b <= 16) and the FP64 kernel."""
+@pytest.mark.parametrize("p", [2, 5])
+def test_quadtree_both_element_kernels(lib, p, element, monkeypatch):
+    """p = 2: n_b 8 and 10 padded to 10 (one-tile tensor-core kernel); p = 5: n_b 20 and
+    25 padded to 25 (two-tile tensor-core kernel); and the FP64 kernel on both."""
     if element == "fp64":
         monkeypatch.setenv("SBFWI_ELEMENT", "fp64")
-    m, n_r, rho, dt, src, wav, rec = _case(2, 6)
-    assert set(m.n_b) == {8, 10}
+    m, n_r, rho, dt, src, wav, rec = _case(p, 6 if p < 5 else 5, K=40 if p < 5 else 25)
+    assert set(m.n_b) == {4 * p, 5 * p}
     _compare(lib, m, n_r, rho, dt, src, wav, rec)
 
 
 @pytest.mark.parametrize("rho_kind", ["grid", "nodal"])
 def test_quadtree_order3_grid_and_nodal_density(lib, rho_kind):
-    """n_b 12 and 15 (padded to 15, FP64 element kernel); nodal density in the caller's
-    unpadded layout, and the nodal gradient returned in it."""
+    """n_b 12 and 15 (padded to 15); nodal density in the caller's unpadded layout, and
+    the nodal gradient returned in it."""
     m, n_r, rho, dt, src, wav, rec = _case(3, 5, shots=2, seed=1)
     _compare(lib, m, n_r, rho, dt, src, wav, rec, rho_kind)
 
 
 def test_quadtree_order5_up_to_forty_boundary_nodes(lib):
-    """A cell with four finer neighbours: n_b = 40 next to n_b = 20 and 25."""
+    """A cell with four finer neighbours: n_b = 40 next to n_b = 20 and 25 (padded to 40:
+    the FP64 element kernel)."""
     m, n_r, rho, dt, src, wav, rec = _case(5, 5, shots=2, K=25, seed=2, ring=True)
     assert m.n_b.max() == 40 and m.n_b.min() == 20
     _compare(lib, m, n_r, rho, dt, src, wav, rec)
@@ -91,8 +94,10 @@ def test_quadtree_order5_up_to_forty_boundary_nodes(lib):
 @pytest.mark.parametrize("index", [0, 1, 2])
 def test_batching_meshes_full_size_few_steps(lib, index):
     """Each mesh of the batching recipe at full size (about 700 elements, p = 2, 3, 5,
-    N_r = 16, 32, 48) with 8 shots in one pass, the launch configuration of the
-    benchmark, for 4 steps: traces and the grid gradient against the oracle."""
+    N_r = 16, 32, 48, padded n_b 12, 18, 30: one-tile tensor-core, FP64 and two-tile
+    tensor-core element kernels)
+    with 8 shots in one pass, the launch configuration of the benchmark, for 4 steps:
+    traces and the grid gradient against the oracle."""
     w = batching_workload(index, K=4)
     src = w.src_nodes[:8]
     wav = np.stack([ricker(w.f0, w.dt, 4, t0=(2 + k) * w.dt) for k in range(src.size)])  # active from step 1
