@@ -148,7 +148,7 @@ __device__ __forceinline__ void stage_ops(uint4* dst, int* dexp, const uint4* sr
 // shared memory (cp.async, two stages) while the current point computes, and each
 // point's state is loaded before its products, so the memory latency overlaps the
 // tensor-core and integer work instead of stalling every radial point.
-template <bool kA2One>
+template <bool kAvgAccel>
 __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
   using namespace tc;
   extern __shared__ __align__(16) unsigned char tc_smem[];
@@ -202,8 +202,9 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
     for (int j = 0; j < 4; ++j) y[j] = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
   };
 
-  // y = [P | Q 2^-a][v ; q 2^a] for one radial point: P's and Q's digits in shared
-  // memory, joint row exponents in rexp, a in aexp[0]; returned in C layout
+  // -y = -[P | Q 2^-a][v ; q 2^a] for one radial point (the sweep's q_i directly): P's
+  // and Q's digits in shared memory, joint row exponents in rexp, a in aexp[0]; returned
+  // in C layout
   auto apply_pq = [&](const uint4* Pf, const uint4* Qf, const int* rexp, const int* aexp, const double (&vbv)[4],
                       const double (&qbv)[4], double (&y)[4]) {
     const int bal = aexp[0];
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
     const int er0 = rexp[g], er1 = rexp[g + 8];
     const int fc0 = __shfl_sync(0xffffffffu, f, 4 * cc[0]), fc1 = __shfl_sync(0xffffffffu, f, 4 * cc[1]);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) y[j] = recombine(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
+    for (int j = 0; j < 4; ++j) y[j] = recombine<true>(acc, j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
   };
 
   double xb[4];       // the operand of the next product, B layout
@@ -266,8 +267,16 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
           // the interior u', u'' are not kept either: the Newmark update needs only
           // z = u' + dt (1 - gamma) u'' of the old state, the same value the update
           // would form from u' and u'' (same rounding)
-          a.ud[o] = fma(a.c1, uddn, udn);
-          a.v[o] = kA2One ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+          // average acceleration (beta = 1/4, gamma = 1/2): z' = z + dt u''_new and the new
+          // predictor a0 u_new + a1 u'_new + u''_new equals v + a1 z' (one FMA instead of two)
+          if (kAvgAccel) {
+            const double zn = fma(a.dt, uddn, zo[j]);
+            a.ud[o] = zn;
+            a.v[o] = fma(a.a1, zn, vo[j]);
+          } else {
+            a.ud[o] = fma(a.c1, uddn, udn);
+            a.v[o] = fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+          }
           if (a.store_int) a.store_int[o] = udn;
           if (a.grad_int) a.grad_int[o] = fma(fw[j], udn, gr[j]);    // dt applied at the end
           un[j] = u_new;
@@ -303,12 +312,10 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
     }
     cp_async_wait<1>();
     __syncwarp();
-    double pq[4];
-    apply_pq(W.frag[buf], W.frag[buf] + kSlices * 32, W.exps[buf], W.exps[buf] + 16, vb, qb, pq);
     double qc[4];
+    apply_pq(W.frag[buf], W.frag[buf] + kSlices * 32, W.exps[buf], W.exps[buf] + 16, vb, qb, qc);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      qc[j] = -pq[j];
       if (cok[j]) a.q[base + (int64_t)i * per + cr[j] * B + cc[j]] = qc[j];
       else qc[j] = 0.0;
     }
@@ -383,11 +390,11 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
   a.do_down = down; a.do_up = up;
   a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
-  if (md.nb > tc::kTile) return tc2_element_launch(a, md.a2, st);
+  if (md.nb > tc::kTile) return tc2_element_launch(a, md.a2 == 1.0 && md.c1 == md.c2, st);
   const int smem = (int)(sizeof(tc::WarpSmem) * tc::kWarpsPerBlock);   // attribute set by tc_prepare
   const unsigned blocks = (unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock);
-  // beta = 1/4 (a2 = 1): the predictor needs no multiply by a2
-  if (md.a2 == 1.0) element_step_tc_kernel<true><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);
+  // average acceleration (beta = 1/4, gamma = 1/2): the shorter predictor update
+  if (md.a2 == 1.0 && md.c1 == md.c2) element_step_tc_kernel<true><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);
   else element_step_tc_kernel<false><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);
   return SBFWI_OK;
 }

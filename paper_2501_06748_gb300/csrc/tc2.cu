@@ -5,6 +5,8 @@
 // y = A x sums, per row tile, the levels of both k-tiles before one recombination; the
 // row exponents span all 32 rows, the column exponent all 32 entries of a shot, so the
 // scaling (and the result) is that of one 32 x 32 product.
+#include <type_traits>
+
 #include "internal.h"
 #include "prof.h"
 #include "tc_digits.cuh"
@@ -109,7 +111,7 @@ __global__ void slice_operators2_kernel(SliceArgs a) {
 // The element step of element_step_tc_kernel with 2 x 2 operator tiles: fused
 // back-substitution + Newmark (+ velocity store or gradient) of one step and the forward
 // sweep of the next, operator digits of the next radial point prefetched by cp.async.
-template <bool kA2One>
+template <bool kAvgAccel>
 __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
   using namespace tc2;
   extern __shared__ __align__(16) unsigned char tc2_smem[];
@@ -148,13 +150,14 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
       for (int j = 0; j < 4; ++j) b[r][j] = X[(r * kTile + br[j]) * kCols + g];
     __syncwarp();
   };
-  auto finish = [&](float (&acc)[kRT][kLevels][4], const int* rexp, int f, double (&y)[kRT][4]) {
+  auto finish = [&](auto neg, float (&acc)[kRT][kLevels][4], const int* rexp, int f, double (&y)[kRT][4]) {
     const int fc0 = __shfl_sync(0xffffffffu, f, 4 * cc[0]), fc1 = __shfl_sync(0xffffffffu, f, 4 * cc[1]);
 #pragma unroll
     for (int r = 0; r < kRT; ++r) {
       const int er0 = rexp[r * kTile + g], er1 = rexp[r * kTile + g + 8];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) y[r][j] = recombine(acc[r], j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
+      for (int j = 0; j < 4; ++j)
+        y[r][j] = recombine<decltype(neg)::value>(acc[r], j, (j < 2 ? er0 : er1) + ((j & 1) ? fc1 : fc0));
     }
   };
   // y = A x, A's 2 x 2 tiles of digits in shared memory
@@ -175,9 +178,9 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
 #pragma unroll
       for (int r = 0; r < kRT; ++r) product(acc[r], tile(A, r, k) + lane, d);
     }
-    finish(acc, rexp, f, y);
+    finish(std::false_type{}, acc, rexp, f, y);
   };
-  // y = [P | Q 2^-a][v ; q 2^a]
+  // -y = -[P | Q 2^-a][v ; q 2^a] (the sweep's q_i directly)
   auto apply_pq = [&](const uint4* Pf, const uint4* Qf, const int* rexp, const int* aexp, const double (&vb)[kRT][4],
                       const double (&qb)[kRT][4], double (&y)[kRT][4]) {
     const int bal = aexp[0];
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
 #pragma unroll
       for (int r = 0; r < kRT; ++r) product(acc[r], tile(Qf, r, k) + lane, d);
     }
-    finish(acc, rexp, f, y);
+    finish(std::true_type{}, acc, rexp, f, y);
   };
 
   double xb[kRT][4];
@@ -249,8 +252,14 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
             const double u_new = qo[r][j] - hu[r][j];
             const double uddn = fma(a.a0, u_new, -vo[r][j]);
             const double udn = fma(a.c2, uddn, zo[r][j]);
-            a.ud[o] = fma(a.c1, uddn, udn);
-            a.v[o] = kA2One ? fma(a.a0, u_new, fma(a.a1, udn, uddn)) : fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+            if (kAvgAccel) {                 // z' = z + dt u''_new, v' = v + a1 z' (as tc.cu)
+              const double zn = fma(a.dt, uddn, zo[r][j]);
+              a.ud[o] = zn;
+              a.v[o] = fma(a.a1, zn, vo[r][j]);
+            } else {
+              a.ud[o] = fma(a.c1, uddn, udn);
+              a.v[o] = fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
+            }
             if (a.store_int) a.store_int[o] = udn;
             if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);   // dt applied at the end
             un[r][j] = u_new;
@@ -286,14 +295,12 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
         vb[k][j] = bok[k][j] ? a.v[base + (int64_t)i * per + (k * kTile + br[j]) * B + g] : 0.0;
     cp_async_wait<1>();
     __syncwarp();
-    double pq[kRT][4];
-    apply_pq(W.frag[buf], W.frag[buf] + kOpFrags, W.exps[buf], W.exps[buf] + kR, vb, qb, pq);
     double qc[kRT][4];
+    apply_pq(W.frag[buf], W.frag[buf] + kOpFrags, W.exps[buf], W.exps[buf] + kR, vb, qb, qc);
 #pragma unroll
     for (int r = 0; r < kRT; ++r)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        qc[r][j] = -pq[r][j];
         if (cok[r][j]) a.q[base + (int64_t)i * per + (r * kTile + cr[j]) * B + cc[j]] = qc[r][j];
         else qc[r][j] = 0.0;
       }
@@ -348,11 +355,11 @@ int tc2_prepare(Model& md, cudaStream_t st) {
   return SBFWI_OK;
 }
 
-int tc2_element_launch(const ElemTcArgs& a, double a2, cudaStream_t st) {
+int tc2_element_launch(const ElemTcArgs& a, bool avg_accel, cudaStream_t st) {
   using namespace tc2;
   const int smem = (int)(sizeof(WarpSmem) * kWarps);
   const unsigned blocks = (unsigned)((a.E + kWarps - 1) / kWarps);
-  if (a2 == 1.0) element_step_tc2_kernel<true><<<blocks, 32 * kWarps, smem, st>>>(a);
+  if (avg_accel) element_step_tc2_kernel<true><<<blocks, 32 * kWarps, smem, st>>>(a);
   else element_step_tc2_kernel<false><<<blocks, 32 * kWarps, smem, st>>>(a);
   return SBFWI_OK;
 }

@@ -107,6 +107,9 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint4& a, unsigned
 // 2..6 are added exactly; levels 7 and 8 are summed exactly apart and rounded once to
 // the nearest unit (flooring them with shifts biases every product by about -1 unit,
 // which the energy-conserving time loop then accumulates).
+// (kNeg: the negated sum, negated in the integer domain -- rounding is symmetric, so the
+// result is bit for bit the negation of the kNeg = false one.)
+template <bool kNeg = false>
 __device__ __forceinline__ double recombine(const float (&acc)[kLevels][4], int j, int e) {
   long long t = 0;
   t += (long long)__float2int_rn(acc[0][j]) << 36;
@@ -116,7 +119,7 @@ __device__ __forceinline__ double recombine(const float (&acc)[kLevels][4], int 
   t += (long long)__float2int_rn(acc[4][j]);
   const long long low = ((long long)__float2int_rn(acc[5][j]) << 9) + (long long)__float2int_rn(acc[6][j]);
   t += (low + (1LL << 17)) >> 18;
-  return int_to_double_scaled(t, e - 52);
+  return int_to_double_scaled(kNeg ? -t : t, e - 52);
 }
 
 // Digits of an operand held in the B-fragment layout of m16n8k16: lane (g, t) holds
@@ -213,6 +216,6 @@ struct ElemTcArgs {
 // elements padded to 21..32 boundary nodes (tc2.cu)
 constexpr int kTwoTileMinNb = 21;
 int tc2_prepare(Model& md, cudaStream_t st);
-int tc2_element_launch(const ElemTcArgs& a, double a2, cudaStream_t st);
+int tc2_element_launch(const ElemTcArgs& a, bool avg_accel, cudaStream_t st);
 
 }  // namespace sbfwi
