@@ -60,16 +60,16 @@ def profiled_traffic(kernel):
     except OSError:
         return None, "no ncu summary"
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    m_h = re.search(r"source_sha256:\s*(\S+)\s+(\S+)", text)
-    if not m_b or not m_h:
+    hashes = re.findall(r"source_sha256:\s*(\S+)\s+(\S+)", text)    # every file the kernel is built from
+    if not m_b or not hashes:
         return None, "ncu summary without traffic"
-    src = os.path.join(ROOT, m_h.group(1))
-    try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None, "kernel source missing"
-    if digest != m_h.group(2):
-        return None, "kernel changed since the ncu capture"
+    for rel, want in hashes:
+        try:
+            digest = hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()
+        except OSError:
+            return None, "kernel source missing"
+        if digest != want:
+            return None, "kernel changed since the ncu capture"
     return float(m_b.group(1)), os.path.relpath(path, ROOT)
 
 
