@@ -470,8 +470,8 @@ PAPER_EPOCH_S = {(1000, 5): 0.95, (2000, 5): 2.39, (4000, 5): 5.49, (8000, 5): 1
 
 
 def run_paper(args, rank, world):
-    """The paper's plate recipe on square S-elements: one evaluation (set-up + forward,
-    misfit, adjoint and gradient of both sources) per element count and interval count,
+    """The paper's plate recipe on its centroidal Voronoi meshes (or squares): one evaluation
+    (set-up + forward, misfit, adjoint and gradient of both sources) per element count and interval count,
     with the paper's seconds per epoch beside it (context: its meshes are Voronoi
     polygons and it ran on a laptop CPU)."""
     import torch
@@ -484,8 +484,10 @@ def run_paper(args, rank, world):
     torch.cuda.set_device(0)
     rows = []
     units_all, secs_all = 0, 0.0
+    meshes = {}
     for (n_elem, intervals) in sorted(PAPER_EPOCH_S):
-        w = paper_workload(n_elem=n_elem, intervals=intervals)
+        w = paper_workload(n_elem=n_elem, intervals=intervals, mesh_kind=args.paper_mesh, mesh=meshes.get(n_elem))
+        meshes[n_elem] = w.mesh
         L = w.mesh.lx
         M = lib.Mesh.from_inputs(w.mesh, w.n_r)
         mt = lib.Model(M, w.c, w.rho_true, w.dt, lx=L, ly=L)
@@ -509,7 +511,9 @@ def run_paper(args, rank, world):
         units = w.mesh.n_elem * w.n_r * w.K * w.n_shots
         units_all += units
         secs_all += sec
+        nb = getattr(w.mesh, "n_b", None)
         rows.append({"elements": w.mesh.n_elem, "intervals": intervals, "N_r": w.n_r, "receivers": int(len(w.rec_nodes)),
+                     "n_b": [int(nb.min()), int(nb.max())] if nb is not None else 4 * w.mesh.p,
                      "s_per_epoch": sec, "units_per_s": units / sec,
                      "paper_s_per_epoch": PAPER_EPOCH_S[(n_elem, intervals)],
                      "paper_over_ours": PAPER_EPOCH_S[(n_elem, intervals)] / sec})
@@ -519,7 +523,9 @@ def run_paper(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "paper: 100 mm plate, c = 6000 m/s, rho = 2700 with one circular flaw, 2 sine-burst "
                                    "sources (2 cycles, 500 kHz) 30 mm apart, receivers every 1 mm on 4 edges, 200 steps "
-                                   "of 0.2 us; square S-elements of order 2 instead of the paper's Voronoi polygons",
+                                   "of 0.2 us; " + ("centroidal Voronoi polygons (the paper's mesh type), line order 2"
+                                                    if args.paper_mesh == "voronoi" else
+                                                    "square S-elements of order 2 instead of the paper's Voronoi polygons"),
                        "rows": rows, "l2": "small workloads: latency-bound, inputs fit L2"}}
 
 
@@ -624,6 +630,8 @@ def main():
                          "serving: forward-modelling requests with continuous batching; "
                          "paper: the paper's plate recipe at its Table 1 element counts; "
                          "batching: 64 shots over 3 quadtree meshes with uneven elements")
+    ap.add_argument("--paper-mesh", choices=["voronoi", "square"], default="voronoi",
+                    help="paper config: centroidal Voronoi polygons (the paper's) or squares")
     ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")
     ap.add_argument("--shots", type=int, default=0, help="shots per rank (0: the config's)")
     ap.add_argument("--shots-per-pass", type=int, default=0, help="0 = all shots in one pass")

@@ -10,10 +10,12 @@ The workloads stand in for the paper's flawed-specimen experiments
 (Section 4: a plate with a hole and a plate with a weak inclusion, sources on the
 top surface, receivers along the edges), whose FEM-generated data and Voronoi
 meshes are not available.  They use square S-elements (structured or quadtree
-meshes), a void/flaw density contrast, and Ricker sources.
+meshes, and the paper's centroidal Voronoi polygons), a void/flaw density contrast,
+and Ricker or sine-burst sources.
 """
 
-from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node, QuadtreeMesh, quadtree_mesh, min_spacing
+from .mesh import (StructuredMesh, structured_mesh, boundary_nodes, nearest_node, QuadtreeMesh, quadtree_mesh,
+                   min_spacing, PolygonMesh, voronoi_mesh)
 from .fields import flawed_density_circle, flawed_density_ellipses
 from .wavelet import ricker, sine_burst
 from .configs import (Workload, tiny_workload, size_workload, diff_workload, paper_workload, batching_workload,
@@ -21,7 +23,7 @@ from .configs import (Workload, tiny_workload, size_workload, diff_workload, pap
 
 __all__ = [
     "StructuredMesh", "structured_mesh", "boundary_nodes", "nearest_node", "QuadtreeMesh", "quadtree_mesh",
-    "min_spacing", "batching_workload",
+    "min_spacing", "PolygonMesh", "voronoi_mesh", "batching_workload",
     "flawed_density_circle", "flawed_density_ellipses", "ricker", "sine_burst",
     "Workload", "tiny_workload", "size_workload", "diff_workload", "paper_workload", "workload_by_name",
 ]

@@ -19,7 +19,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .mesh import StructuredMesh, structured_mesh, boundary_nodes, nearest_node, quadtree_mesh, min_spacing
+from .mesh import (StructuredMesh, structured_mesh, boundary_nodes, nearest_node, quadtree_mesh, min_spacing,
+                   voronoi_mesh)
 from .fields import flawed_density_circle, flawed_density_ellipses
 from .wavelet import ricker, sine_burst
 
@@ -142,16 +143,25 @@ def diff_workload(seed: int = 2, K: int = 8000, n_shots: int = 16, nx: int = 128
 
 
 def paper_workload(n_elem: int = 2000, intervals: int = 5, seed: int = 3, p: int = 2, K: int = 200,
-                   flaw_factor: float = FLAW_FACTOR) -> Workload:
+                   flaw_factor: float = FLAW_FACTOR, mesh_kind: str = "square", lloyd_iters: int = 40,
+                   mesh=None) -> Workload:
     """The shape of the paper's plate experiments (Section 4) on square S-elements: a
     100 mm x 100 mm plate, c = 6000 m/s, rho = 2700 with one circular flaw, two
     sources 30 mm apart on the top edge driven by a 2-cycle sine burst (f0 = 500 kHz),
     receivers every 1 mm along all four edges, dt = 0.2 us, 200 steps (40 us), and
-    `intervals` radial intervals (N_r = intervals + 1).  The paper's Voronoi meshes of
-    1000..8000 elements become about `n_elem` squares."""
-    nx = max(1, int(round(np.sqrt(n_elem))))
+    `intervals` radial intervals (N_r = intervals + 1).  ``mesh_kind="voronoi"`` gives the
+    paper's mesh type, `n_elem` centroidal Voronoi polygons (seeded, Lloyd iterations);
+    ``"square"`` about `n_elem` squares."""
     L = 0.1
-    mesh = structured_mesh(nx, nx, p, lx=L, ly=L)
+    if mesh is not None:                      # a mesh of this recipe made earlier (reused across intervals)
+        pass
+    elif mesh_kind == "voronoi":
+        mesh = voronoi_mesh(n_elem, p, lx=L, ly=L, seed=seed, lloyd_iters=lloyd_iters)
+    elif mesh_kind == "square":
+        nx = max(1, int(round(np.sqrt(n_elem))))
+        mesh = structured_mesh(nx, nx, p, lx=L, ly=L)
+    else:
+        raise ValueError(mesh_kind)
     c = 6000.0
     f0, dt = 500e3, 0.2e-6
     grid = 256
@@ -171,7 +181,8 @@ def paper_workload(n_elem: int = 2000, intervals: int = 5, seed: int = 3, p: int
     wav = np.stack([sine_burst(f0, dt, K, cycles=2, amplitude=1e12) for _ in srcs])
     return Workload("paper", mesh, intervals + 1, c, grid, grid, rho_true, rho_start,
                     np.array(srcs, dtype=np.int64), wav, np.array(recs, dtype=np.int64),
-                    dt, K, f0, info={"flaws": finfo, "seed": seed, "plate_m": L, "intervals": intervals})
+                    dt, K, f0, info={"flaws": finfo, "seed": seed, "plate_m": L, "intervals": intervals,
+                                     "mesh": mesh_kind})
 
 
 BATCHING_MESHES = ((2, 16), (3, 32), (5, 48))     # (p, N_r) of the three quadtree meshes

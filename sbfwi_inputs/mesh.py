@@ -261,3 +261,145 @@ def min_spacing(mesh) -> float:
     ln = mesh.line_nodes
     d = np.hypot(*(mesh.node_xy[ln[:, 1:]] - mesh.node_xy[ln[:, :-1]]).transpose(2, 0, 1))
     return float(d.min())
+
+
+@dataclass
+class PolygonMesh:
+    """Convex polygonal S-elements (centroidal Voronoi cells), same arrays as
+    ``StructuredMesh``: element e owns one straight line element of order p per polygon
+    side, counter-clockwise around its centroid."""
+    node_xy: np.ndarray
+    elem_ptr: np.ndarray
+    line_nodes: np.ndarray
+    centre_xy: np.ndarray
+    p: int
+    lx: float
+    ly: float
+    seeds: np.ndarray
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.node_xy.shape[0])
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.centre_xy.shape[0])
+
+    @property
+    def n_b(self) -> np.ndarray:
+        return self.p * np.diff(self.elem_ptr)
+
+
+def _polygon_centroid(V):
+    x, y = V[:, 0], V[:, 1]
+    xs, ys = np.roll(x, -1), np.roll(y, -1)
+    cr = x * ys - xs * y
+    a = cr.sum() / 2
+    return np.array([((x + xs) * cr).sum() / (6 * a), ((y + ys) * cr).sum() / (6 * a)])
+
+
+def voronoi_mesh(n_cells: int, p: int, lx: float = 1.0, ly: float = 1.0, seed: int = 0, lloyd_iters: int = 40,
+                 min_edge: float = 0.2) -> PolygonMesh:
+    """Centroidal Voronoi tessellation of [0, lx] x [0, ly] into ``n_cells`` convex polygons
+    (the mesh type of the paper's experiments, Section 4).
+
+    Seeds are drawn uniformly and moved to their cells' centroids ``lloyd_iters`` times
+    (Lloyd's algorithm); cells are bounded by mirroring the seeds across the four sides.
+    Sides shorter than ``min_edge`` times the mean cell size sqrt(lx ly / n) are collapsed
+    (their two vertices merged: at a domain vertex or side if one lies there, else at the
+    midpoint), so no line element is much shorter than the rest.  Each polygon side is one
+    line element of order p with equally spaced nodes; scaling centres are the centroids.
+    """
+    from scipy.spatial import Voronoi
+
+    if n_cells < 2 or p < 1:
+        raise ValueError("n_cells >= 2, p >= 1")
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n_cells, 2)) * [lx, ly]
+    for it in range(lloyd_iters + 1):
+        allp = np.concatenate([pts, pts * [-1, 1], pts * [1, -1], np.c_[2 * lx - pts[:, 0], pts[:, 1]],
+                               np.c_[pts[:, 0], 2 * ly - pts[:, 1]]])
+        vor = Voronoi(allp)
+        regions = [vor.regions[vor.point_region[i]] for i in range(n_cells)]
+        if it == lloyd_iters:
+            break
+        pts = np.array([_polygon_centroid(vor.vertices[r]) for r in regions])
+    V = vor.vertices.copy()
+    tol = 1e-9 * max(lx, ly)
+    V[np.abs(V[:, 0]) < tol, 0] = 0.0
+    V[np.abs(V[:, 0] - lx) < tol, 0] = lx
+    V[np.abs(V[:, 1]) < tol, 1] = 0.0
+    V[np.abs(V[:, 1] - ly) < tol, 1] = ly
+    # counter-clockwise vertex loops
+    cells = []
+    for r in regions:
+        c = V[r].mean(axis=0)
+        ang = np.arctan2(V[r, 1] - c[1], V[r, 0] - c[0])
+        cells.append([r[k] for k in np.argsort(ang)])
+    on_x = lambda v: V[v, 0] == 0.0 or V[v, 0] == lx
+    on_y = lambda v: V[v, 1] == 0.0 or V[v, 1] == ly
+    # collapse short sides
+    h = np.sqrt(lx * ly / n_cells)
+    parent = list(range(V.shape[0]))
+
+    def find(v):
+        while parent[v] != v:
+            parent[v] = parent[parent[v]]
+            v = parent[v]
+        return v
+
+    changed = True
+    while changed:
+        changed = False
+        for cell in cells:
+            loop = [find(v) for v in cell]
+            loop = [v for k, v in enumerate(loop) if v != loop[k - 1]] if len(set(loop)) > 1 else loop
+            for k in range(len(loop)):
+                a, b = loop[k], loop[(k + 1) % len(loop)]
+                if a == b or np.hypot(*(V[a] - V[b])) >= min_edge * h:
+                    continue
+                ca, cb = on_x(a) + on_y(a), on_x(b) + on_y(b)    # 2: domain vertex, 1: on a side
+                if ca == 2 and cb == 2:
+                    continue
+                if ca > cb or (ca == cb and ca == 1 and (on_x(a) != on_x(b))):
+                    keep, drop = a, b
+                elif cb > ca:
+                    keep, drop = b, a
+                else:
+                    keep, drop = a, b
+                    if ca == 0:
+                        V[a] = 0.5 * (V[a] + V[b])
+                parent[drop] = keep
+                changed = True
+                break
+    loops = []
+    for cell in cells:
+        loop = [find(v) for v in cell]
+        loop = [v for k, v in enumerate(loop) if v != loop[k - 1]]
+        loops.append(loop)
+    used = sorted({v for loop in loops for v in loop})
+    ren = {v: k for k, v in enumerate(used)}
+    xy = [tuple(V[v]) for v in used]
+    inner = {}
+
+    def segment(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in inner:
+            (xa, ya), (xb, yb) = xy[key[0]], xy[key[1]]
+            ids = []
+            for k in range(1, p):
+                ids.append(len(xy))
+                xy.append((xa + (xb - xa) * k / p, ya + (yb - ya) * k / p))
+            inner[key] = ids
+        ids = inner[key]
+        return [a] + (ids if a < b else ids[::-1]) + [b]
+
+    lines, ptr, centres = [], [0], []
+    for loop in loops:
+        lp = [ren[v] for v in loop]
+        for k in range(len(lp)):
+            lines.append(segment(lp[k], lp[(k + 1) % len(lp)]))
+        ptr.append(len(lines))
+        centres.append(_polygon_centroid(np.array([xy[v] for v in lp])))
+    return PolygonMesh(np.asarray(xy, dtype=np.float64), np.asarray(ptr, dtype=np.int64),
+                       np.asarray(lines, dtype=np.int64), np.asarray(centres, dtype=np.float64), p, lx, ly, pts)

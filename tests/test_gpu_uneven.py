@@ -112,3 +112,41 @@ def test_batching_meshes_full_size_few_steps(lib, index):
     g = lib.adjoint_gradient(md, st, res)
     go = uneven.gradient_to_grid(om, uneven.adjoint_gradient(om, store, obs - to, w.rec_nodes), w.gx, w.gy)
     assert rel(g, go) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("intervals", [5, 7])
+def test_voronoi_paper_plate(lib, intervals):
+    """The paper's plate recipe on its own mesh type: about 100 centroidal Voronoi
+    polygons (4 to 7 sides, n_b 8..14), 5 and 7 radial intervals, two sine-burst
+    sources, receivers every 1 mm, all 200 steps: traces and gradient."""
+    from sbfwi_inputs import paper_workload
+    w = paper_workload(n_elem=100, intervals=intervals, mesh_kind="voronoi")
+    assert len(set(w.mesh.n_b)) > 1
+    L = w.mesh.lx
+    om = uneven.build_model(w.mesh, w.n_r, w.c, w.rho_true, w.dt, lx=L, ly=L)
+    to, store, _ = uneven.forward(om, w.src_nodes, w.wavelets, w.rec_nodes)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_true, w.dt, lx=L, ly=L)
+    tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+    assert np.abs(to).max() > 0
+    assert rel(tr, to) <= TRACE_TOL
+    g = lib.adjoint_gradient(md, st, -tr)
+    go = uneven.gradient_to_grid(om, uneven.adjoint_gradient(om, store, -to, w.rec_nodes), w.gx, w.gy, L, L)
+    assert rel(g, go) <= GRAD_TOL
+
+
+def test_voronoi_paper_plate_full_size_few_steps(lib):
+    """1000 Voronoi polygons (the paper's smallest mesh), 5 intervals, 6 steps."""
+    from sbfwi_inputs import paper_workload
+    w = paper_workload(n_elem=1000, intervals=5, K=6, mesh_kind="voronoi")
+    L = w.mesh.lx
+    om = uneven.build_model(w.mesh, w.n_r, w.c, w.rho_true, w.dt, lx=L, ly=L)
+    to, store, _ = uneven.forward(om, w.src_nodes, w.wavelets, w.rec_nodes)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_true, w.dt, lx=L, ly=L)
+    tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+    assert np.abs(to).max() > 0
+    assert rel(tr, to) <= TRACE_TOL
+    g = lib.adjoint_gradient(md, st, -tr)
+    go = uneven.gradient_to_grid(om, uneven.adjoint_gradient(om, store, -to, w.rec_nodes), w.gx, w.gy, L, L)
+    assert rel(g, go) <= GRAD_TOL

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import fwi, sbfem, uneven
-from sbfwi_inputs.mesh import min_spacing, quadtree_mesh, structured_mesh
+from sbfwi_inputs.mesh import min_spacing, quadtree_mesh, structured_mesh, voronoi_mesh
 from sbfwi_inputs.wavelet import ricker
 
 
@@ -107,3 +107,54 @@ def test_uneven_path_equals_uniform_oracle_on_structured_mesh():
     ga = fwi.adjoint_gradient(a, sta, res, rec)
     gb = uneven.adjoint_gradient(b, stb, res, rec)
     assert np.linalg.norm(ga - gb) <= 1e-12 * np.linalg.norm(ga)
+
+
+def test_voronoi_mesh_is_a_conforming_ccw_tiling():
+    m = voronoi_mesh(60, 2, seed=3)
+    sides = np.diff(m.elem_ptr)
+    assert sides.min() >= 3 and sides.max() > sides.min()
+    seen = set()
+    area = 0.0
+    for e in range(m.n_elem):
+        ls = m.line_nodes[m.elem_ptr[e]:m.elem_ptr[e + 1]]
+        c = m.centre_xy[e]
+        for k, ln in enumerate(ls):
+            assert ln[-1] == ls[(k + 1) % len(ls)][0]                  # closed loop
+            a, b = m.node_xy[ln[0]], m.node_xy[ln[-1]]
+            assert (a[0] - c[0]) * (b[1] - a[1]) - (a[1] - c[1]) * (b[0] - a[0]) > 0   # centre sees it CCW
+            assert (ln[0], ln[-1]) not in seen
+            seen.add((int(ln[0]), int(ln[-1])))
+        P = m.node_xy[[ln[0] for ln in ls]]
+        area += 0.5 * np.sum(P[:, 0] * np.roll(P[:, 1], -1) - np.roll(P[:, 0], -1) * P[:, 1])
+    assert abs(area - 1.0) < 1e-12
+    for a, b in seen:                                                   # interior sides shared, reversed
+        if (b, a) not in seen:
+            mid = 0.5 * (m.node_xy[a] + m.node_xy[b])
+            assert np.isclose(mid, 0).any() or np.isclose(mid, 1).any()
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_polygon_element_static_stiffness_annihilates_constants(p):
+    m = voronoi_mesh(12, p, seed=5)
+    for el in sbfem.elements_from_mesh(m)[:4]:
+        xi = sbfem.radial_grid(5, 1e-3, sbfem.XP)
+        mats = sbfem.coefficient_matrices(el, m.node_xy, p, 1.0, np.ones((6, el.dofs.size), dtype=sbfem.XP))
+        cd = sbfem.condense(sbfem.element_system(*(q[None] for q in mats), xi, 1.0, 0.25, static=True))
+        S = np.asarray(cd.S[0], dtype=np.float64)
+        assert np.abs(S @ np.ones(el.dofs.size)).max() < 1e-10 * np.abs(S).max()
+
+
+def test_voronoi_condensed_path_equals_uncondensed_system():
+    m = voronoi_mesh(8, 2, seed=7)
+    assert len(set(m.n_b)) > 1
+    n_r, c = 5, 1.0
+    s = min_spacing(m)
+    dt, f0, K = 0.5 * s / c, c / (10 * s), 30
+    w = np.stack([ricker(f0, dt, K, t0=1.0 / f0)])
+    rho = 1.0 + 0.3 * np.random.default_rng(2).random((16, 16))
+    src, rec = np.array([0]), np.array([1, 5, 9])
+    md = uneven.build_model(m, n_r, c, rho, dt)
+    tr, _, st = uneven.forward(md, src, w, rec)
+    tr2, u2 = uneven.FullSystem(m, n_r, c, md.rho_nodal, dt).forward(src, w, rec)
+    assert np.linalg.norm(tr) > 0
+    assert np.linalg.norm(tr - tr2) <= 1e-11 * np.linalg.norm(tr)
