@@ -21,6 +21,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -245,8 +246,7 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup - 1):
         step()
     torch.cuda.synchronize()
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/sbfwi_clocks_{rank}.csv")
+    clocks = ClockSampler(os.path.join(args.clock_log, f"clocks_rank{rank}.csv"))
     lib.profile_read(reset=True)
     lib.profile_enable(True)
     stream = torch.cuda.current_stream(dev)
@@ -440,8 +440,7 @@ def run_serving(args, rank, world):
     eng = serving.Engine(build_model, max_batch=8, cache_capacity=len(keys))
     for key in keys:                             # models set up before the clock starts
         eng.cache.get(key)
-    clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", "clocks_serving.csv")
-                          if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/sbfwi_clocks_serving.csv")
+    clocks = ClockSampler(os.path.join(args.clock_log, "clocks_serving.csv"))
     clocks.start()
     t0 = time.perf_counter()
     eng.run(reqs)
@@ -567,7 +566,7 @@ def run_batching(args, rank, world):
 
     for _ in range(max(3, args.warmup)):
         epoch()
-    clocks = ClockSampler(os.path.join("gpurun_out" if os.path.isdir("gpurun_out") else ".", "clocks_batching.csv"))
+    clocks = ClockSampler(os.path.join(args.clock_log, "clocks_batching.csv"))
     clocks.start()
     times = [0.0] * 3
     torch.cuda.synchronize()
@@ -630,6 +629,8 @@ def main():
                          "serving: forward-modelling requests with continuous batching; "
                          "paper: the paper's plate recipe at its Table 1 element counts; "
                          "batching: 64 shots over 3 quadtree meshes with uneven elements")
+    ap.add_argument("--clock-log", default=tempfile.gettempdir(),
+                    help="directory for the raw nvidia-smi clock samples of the timed region")
     ap.add_argument("--paper-mesh", choices=["voronoi", "square"], default="voronoi",
                     help="paper config: centroidal Voronoi polygons (the paper's) or squares")
     ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")
