@@ -556,10 +556,24 @@ def run_batching(args, rank, world):
         del mt
         meshes.append((w, M, obs))
 
+    # schedule per mesh: element kernel x solve schedule timed on 16 steps of the first pass
+    choices = []
+    for w, M, _ in meshes:
+        if args.autotune:
+            from paper_2501_06748_gb300 import autotune
+            mt = lib.Model(M, w.c, w.rho_start, w.dt)
+            choices.append(autotune.tune(mt, w.src_nodes[:per_pass], w.wavelets[:per_pass], w.rec_nodes))
+            del mt
+        else:
+            choices.append(None)
+
     def epoch(times=None):
         for k, (w, M, obs) in enumerate(meshes):
             t0 = time.perf_counter()
             md = lib.Model(M, w.c, w.rho_start, w.dt)
+            if choices[k] is not None:
+                from paper_2501_06748_gb300 import autotune
+                autotune.apply(md, choices[k])
             shots.misfit_and_gradient(md, w.src_nodes, w.wavelets, w.rec_nodes, obs, shots_per_pass=per_pass)
             if times is not None:
                 times[k] += time.perf_counter() - t0
@@ -584,6 +598,12 @@ def run_batching(args, rank, world):
                      "n_b": {str(v): int(c) for v, c in zip(*np.unique(nb, return_counts=True))},
                      "padded_n_b": int(M.n_b), "global_nodes": w.mesh.n_nodes, "shots": w.n_shots,
                      "s_per_step": t / args.steps, "units_per_s": u / (t / args.steps)})
+    for row, ch in zip(rows, choices):
+        if ch is not None:
+            row["schedule"] = {"element": ch["element"], "solve": ch["solve"],
+                               "candidates_ms_per_step": {f'{c["element"]}/{c["solve"]}': (
+                                   None if c["s_per_step"] is None else round(1e3 * c["s_per_step"], 4))
+                                   for c in ch["candidates"]}}
     return {"metric": "batching: element-radial-node-steps/s fwd+adj+grad over 3 uneven quadtree meshes",
             "value": sum(units) / sec, "unit": "element-radial-node-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
@@ -631,6 +651,8 @@ def main():
                          "batching: 64 shots over 3 quadtree meshes with uneven elements")
     ap.add_argument("--clock-log", default=tempfile.gettempdir(),
                     help="directory for the raw nvidia-smi clock samples of the timed region")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="batching config: keep the default schedule instead of timing the candidates per mesh")
     ap.add_argument("--paper-mesh", choices=["voronoi", "square"], default="voronoi",
                     help="paper config: centroidal Voronoi polygons (the paper's) or squares")
     ap.add_argument("--time-steps", type=int, default=0, help="Newmark steps (0: the config's)")

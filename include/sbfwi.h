@@ -137,6 +137,36 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
 void sbfwi_destroy_model(sbfwi_model* model);
 
 /*
+ * sbfwi_set_schedule -- how the time loops of later sbfwi_forward and
+ * sbfwi_adjoint_gradient calls on `model` run.  Not part of the paper: a
+ * performance choice between kernels that compute the same method (results agree
+ * within rounding, ~1e-13 relative on traces).  An autotuner times the candidates
+ * and keeps the fastest (paper_2501_06748_gb300/autotune.py).
+ *
+ *   element  SBFWI_ELEMENT_AUTO: the tensor-core element kernel for a padded n_b of
+ *            at most 16 or 21..32 with at most 8 shots per pass, else FP64 (the
+ *            SBFWI_ELEMENT=fp64 environment variable forces FP64);
+ *            SBFWI_ELEMENT_TENSOR: the tensor-core kernel wherever one exists
+ *            (padded n_b <= 32, <= 8 shots; SBFWI_EUNSUPPORTED at the time-loop
+ *            call otherwise; its operator digits are prepared on first use);
+ *            SBFWI_ELEMENT_FP64: the FP64 kernel.
+ *   solve    SBFWI_SOLVE_AUTO: the dataflow solve (SBFWI_SOLVE=barrier|levels in
+ *            the environment selects the others); SBFWI_SOLVE_DATAFLOW: one
+ *            cooperative launch, tasks ordered by dependencies; SBFWI_SOLVE_BARRIER:
+ *            one cooperative launch, grid barriers between tree levels;
+ *            SBFWI_SOLVE_LEVELS: one launch per tree level and direction.  The
+ *            cooperative schedules need a device that launches cooperatively
+ *            (SBFWI_EUNSUPPORTED at the time-loop call otherwise).
+ *
+ * A checkpointed forward state must be consumed by an adjoint with the same
+ * element kernel (SBFWI_ESTATE otherwise).  Errors: SBFWI_EINVAL for a NULL model
+ * or an unknown value.
+ */
+enum { SBFWI_ELEMENT_AUTO = 0, SBFWI_ELEMENT_TENSOR = 1, SBFWI_ELEMENT_FP64 = 2 };
+enum { SBFWI_SOLVE_AUTO = 0, SBFWI_SOLVE_DATAFLOW = 1, SBFWI_SOLVE_BARRIER = 2, SBFWI_SOLVE_LEVELS = 3 };
+int sbfwi_set_schedule(sbfwi_model* model, int element, int solve);
+
+/*
  * sbfwi_forward -- forward solve of n_shots independent shots on the model
  * (Section 2, Eq. (main); zero initial state), K Newmark steps.  Each step:
  * residual sources (Eq. (ODE_Newmark)), forward condensation sweep and

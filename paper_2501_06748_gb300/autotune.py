@@ -1,0 +1,57 @@
+"""Schedule autotuner (a harness around the library; not part of the paper's method).
+
+For one model and one shot batch, ``tune`` times every element kernel (tensor-core,
+FP64) with every global-solve schedule (dataflow, barrier, per-level launches) on a
+few steps of the caller's own forward problem, keeps the fastest on the model
+(``sbfwi.set_schedule``) and reports all candidates.  Candidates the shapes do not
+allow (no tensor-core kernel for this n_b or shot count) are reported as such.  Every
+candidate computes the same method; results agree within rounding.
+"""
+
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import sbfwi
+
+ELEMENTS = {"tensor": sbfwi.ELEMENT_TENSOR, "fp64": sbfwi.ELEMENT_FP64}
+SOLVES = {"dataflow": sbfwi.SOLVE_DATAFLOW, "barrier": sbfwi.SOLVE_BARRIER, "levels": sbfwi.SOLVE_LEVELS}
+
+
+def tune(model, src_nodes, wavelets, rec_nodes, steps: int = 16, repeats: int = 3,
+         elements=("tensor", "fp64"), solves=("dataflow", "barrier", "levels")) -> dict:
+    """Time the candidates on ``steps`` steps of a forward pass of these shots and set the
+    fastest; returns {"element", "solve", "s_per_step", "candidates": [...]}."""
+    wav = wavelets[:, :max(1, min(steps, wavelets.shape[1]))]
+    K = wav.shape[1]
+    out = []
+    for en in elements:
+        for sn in solves:
+            sbfwi.set_schedule(model, ELEMENTS[en], SOLVES[sn])
+            try:
+                sbfwi.forward(model, src_nodes, wav, rec_nodes, keep=False)      # warm-up, first-use preparation
+            except sbfwi.SbfwiError as err:
+                if err.code != sbfwi.EUNSUPPORTED:
+                    raise
+                out.append({"element": en, "solve": sn, "s_per_step": None, "note": str(err)})
+                continue
+            best = np.inf
+            for _ in range(repeats):
+                t0 = time.perf_counter()
+                sbfwi.forward(model, src_nodes, wav, rec_nodes, keep=False)   # synchronous: traces come back
+                best = min(best, time.perf_counter() - t0)
+            out.append({"element": en, "solve": sn, "s_per_step": best / K})
+    ok = [c for c in out if c["s_per_step"] is not None]
+    if not ok:
+        sbfwi.set_schedule(model)
+        raise RuntimeError("no schedule ran")
+    win = min(ok, key=lambda c: c["s_per_step"])
+    sbfwi.set_schedule(model, ELEMENTS[win["element"]], SOLVES[win["solve"]])
+    return {"element": win["element"], "solve": win["solve"], "s_per_step": win["s_per_step"], "candidates": out}
+
+
+def apply(model, choice: dict) -> None:
+    """Set a choice returned by ``tune`` on another model of the same mesh."""
+    sbfwi.set_schedule(model, ELEMENTS[choice["element"]], SOLVES[choice["solve"]])

@@ -215,6 +215,8 @@ struct Model {
   // the same operators split into FP16 digits for the tensor-core element kernel
   DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
   bool tc_ready = false;
+  int elem_pref = SBFWI_ELEMENT_AUTO;     // sbfwi_set_schedule
+  int solve_pref = SBFWI_SOLVE_AUTO;
   LevelTasks tasks;        // built for tasks.shots
   const MeshDevice& dev() const { return *mesh->dev; }
 };
@@ -222,7 +224,8 @@ struct Model {
 int build_level_tasks(Model& md, int shots, int grid);
 
 // tensor-core element operators (tc.cu)
-bool tc_supported(int nb, int B);
+bool tc_supported(int nb, int B);   // the tensor-core kernel is the default for these shapes
+bool tc_available(int nb, int B);   // a tensor-core kernel exists for these shapes
 int tc_prepare(Model& md, cudaStream_t st);
 int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
                       const double* ub, const double* udb, const double* uddb, double* q, double* fhat,

@@ -975,7 +975,19 @@ int Stepper::init() {
   // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
   // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
   const char* elem_env = std::getenv("SBFWI_ELEMENT");
-  use_tc = md.tc_ready && tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
+  if (md.elem_pref == SBFWI_ELEMENT_TENSOR) {
+    if (!tc_available(nb, B))
+      return fail(SBFWI_EUNSUPPORTED, "no tensor-core element kernel for this n_b and shot count");
+    use_tc = true;
+  } else if (md.elem_pref == SBFWI_ELEMENT_FP64) {
+    use_tc = false;
+  } else {
+    use_tc = tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
+  }
+  if (use_tc && !md.tc_ready) {
+    const int rc_tc = tc_prepare(md, st);
+    if (rc_tc) return rc_tc;
+  }
   // the tensor-core path carries the predictor v and z = u' + dt (1 - gamma) u'' (in ud), not u, u''
   SBFWI_CUDA(rb.u.alloc(sizeof(double) * (use_tc ? 1 : si)));
   SBFWI_CUDA(rb.ud.alloc(sizeof(double) * si));
@@ -1045,8 +1057,16 @@ int Stepper::init() {
   // SBFWI_SOLVE=levels: one launch per tree level; =barrier: one launch with grid
   // barriers between levels; default: one dataflow launch
   const char* solve_env = std::getenv("SBFWI_SOLVE");
-  persistent = coop && per_sm > 0 && !(solve_env && std::strcmp(solve_env, "levels") == 0);
-  flow = persistent && !(solve_env && std::strcmp(solve_env, "barrier") == 0);
+  const bool can_coop = coop && per_sm > 0;
+  if (md.solve_pref == SBFWI_SOLVE_AUTO) {
+    persistent = can_coop && !(solve_env && std::strcmp(solve_env, "levels") == 0);
+    flow = persistent && !(solve_env && std::strcmp(solve_env, "barrier") == 0);
+  } else {
+    if (md.solve_pref != SBFWI_SOLVE_LEVELS && !can_coop)
+      return fail(SBFWI_EUNSUPPORTED, "this device cannot launch the cooperative solve schedules");
+    persistent = md.solve_pref != SBFWI_SOLVE_LEVELS;
+    flow = md.solve_pref == SBFWI_SOLVE_DATAFLOW;
+  }
   ftasks = md.tasks.fwd.as<Task>();
   btasks = md.tasks.bwd.as<Task>();
   rc = setup_l2_window(device);
@@ -1342,6 +1362,15 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
 }
 
 void sbfwi_destroy_model(sbfwi_model* m) { delete m; }
+
+int sbfwi_set_schedule(sbfwi_model* m, int element, int solve) {
+  if (!m) return fail(SBFWI_EINVAL, "model is NULL");
+  if (element < SBFWI_ELEMENT_AUTO || element > SBFWI_ELEMENT_FP64) return fail(SBFWI_EINVAL, "unknown element kernel");
+  if (solve < SBFWI_SOLVE_AUTO || solve > SBFWI_SOLVE_LEVELS) return fail(SBFWI_EINVAL, "unknown solve schedule");
+  m->elem_pref = element;
+  m->solve_pref = solve;
+  return SBFWI_OK;
+}
 void sbfwi_destroy_fwdstate(sbfwi_fwdstate* s) { delete s; }
 
 int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, const double* src_wavelet, int32_t n_rec,

@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
 bool tc_supported(int nb, int B) {
   return (nb <= tc::kTile || (nb >= kTwoTileMinNb && nb <= 2 * tc::kTile)) && B <= tc::kCols;
 }
+bool tc_available(int nb, int B) { return nb <= 2 * tc::kTile && B <= tc::kCols; }
 
 int tc_prepare(Model& md, cudaStream_t st) {
   using namespace tc;

@@ -21,6 +21,8 @@ RHO_GRID, RHO_NODAL = 0, 1
 GRAD_KERNEL, GRAD_EXACT = 0, 1
 GRAD_ACCUMULATE = 0x100
 CKPT_AUTO = -1
+ELEMENT_AUTO, ELEMENT_TENSOR, ELEMENT_FP64 = 0, 1, 2
+SOLVE_AUTO, SOLVE_DATAFLOW, SOLVE_BARRIER, SOLVE_LEVELS = 0, 1, 2, 3
 PHASES = ("setup", "element", "solve", "other")
 
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE",
@@ -62,6 +64,8 @@ def _load():
     lib.sbfwi_profile_solve_levels.restype = ctypes.c_int
     lib.sbfwi_release_cache.argtypes = []
     lib.sbfwi_release_cache.restype = ctypes.c_int
+    lib.sbfwi_set_schedule.argtypes = [VP, ctypes.c_int, ctypes.c_int]
+    lib.sbfwi_set_schedule.restype = ctypes.c_int
     lib.sbfwi_selftest_barrier.argtypes = [I32, I32, I64, I32, VP]
     lib.sbfwi_selftest_barrier.restype = ctypes.c_int
     for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
@@ -298,6 +302,11 @@ def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
     _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
                                      arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
     return E_out, residual_out
+
+
+def set_schedule(model: Model, element: int = ELEMENT_AUTO, solve: int = SOLVE_AUTO) -> None:
+    """Element kernel and global-solve schedule of the model's later time loops."""
+    _check(_lib.sbfwi_set_schedule(model._h, int(element), int(solve)))
 
 
 def release_cache() -> None:
