@@ -48,7 +48,7 @@ def test_every_schedule_gives_the_same_traces(lib):
 def test_tensor_kernel_on_request_where_the_default_is_fp64(lib):
     """Padded n_b = 18 runs the FP64 kernel by default; asking for the tensor-core kernel
     prepares its operator digits on first use, and both match the oracle."""
-    m = quadtree_mesh(4, 1, lambda x0, y0, x1, y1, lvl: (x0 < 0.5 and y0 < 0.5) or (x0 >= 0.75 and y0 >= 0.75), 3)
+    m = quadtree_mesh(4, 1, lambda x0, y0, x1, y1, lvl: x0 < 0.25 or y0 < 0.25, 3)    # corner cell: n_b 18
     assert m.n_b.max() == 18
     _, rho, dt, src, wav, rec = _problem()
     om = uneven.build_model(m, 5, 1.0, rho, dt)
