@@ -2,7 +2,9 @@
 
 For one model and one shot batch, ``tune`` times every element kernel (tensor-core,
 FP64) with every global-solve schedule (dataflow, barrier, per-level launches) on a
-few steps of the caller's own forward problem, keeps the fastest on the model
+few steps of the caller's own problem -- a forward pass that stores its velocities and
+the adjoint pass with the gradient, the two time loops of a misfit-and-gradient
+evaluation, whose element launches differ (store vs gradient) -- keeps the fastest on the model
 (``sbfwi.set_schedule``) and reports all candidates.  Candidates the shapes do not
 allow (no tensor-core kernel for this n_b or shot count) are reported as such.  Every
 candidate computes the same method; results agree within rounding.
@@ -22,16 +24,23 @@ SOLVES = {"dataflow": sbfwi.SOLVE_DATAFLOW, "barrier": sbfwi.SOLVE_BARRIER, "lev
 
 def tune(model, src_nodes, wavelets, rec_nodes, steps: int = 16, repeats: int = 3,
          elements=("tensor", "fp64"), solves=("dataflow", "barrier", "levels")) -> dict:
-    """Time the candidates on ``steps`` steps of a forward pass of these shots and set the
-    fastest; returns {"element", "solve", "s_per_step", "candidates": [...]}."""
+    """Time the candidates on ``steps`` steps (forward with stored velocities + adjoint
+    with the gradient) of these shots and set the fastest; returns {"element", "solve",
+    "s_per_step" (both passes), "candidates": [...]}."""
     wav = wavelets[:, :max(1, min(steps, wavelets.shape[1]))]
     K = wav.shape[1]
     out = []
     for en in elements:
         for sn in solves:
             sbfwi.set_schedule(model, ELEMENTS[en], SOLVES[sn])
+
+            def evaluation():
+                tr, st = sbfwi.forward(model, src_nodes, wav, rec_nodes)
+                sbfwi.adjoint_gradient(model, st, tr)     # synchronous: the gradient comes back
+                del st
+
             try:
-                sbfwi.forward(model, src_nodes, wav, rec_nodes, keep=False)      # warm-up, first-use preparation
+                evaluation()                               # warm-up, first-use preparation
             except sbfwi.SbfwiError as err:
                 if err.code != sbfwi.EUNSUPPORTED:
                     raise
@@ -40,7 +49,7 @@ def tune(model, src_nodes, wavelets, rec_nodes, steps: int = 16, repeats: int = 
             best = np.inf
             for _ in range(repeats):
                 t0 = time.perf_counter()
-                sbfwi.forward(model, src_nodes, wav, rec_nodes, keep=False)   # synchronous: traces come back
+                evaluation()
                 best = min(best, time.perf_counter() - t0)
             out.append({"element": en, "solve": sn, "s_per_step": best / K})
     ok = [c for c in out if c["s_per_step"] is not None]
