@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
       if (i > 0) stage_ops(W.frag[buf ^ 1], W.exps[buf ^ 1], Hsrc - (int64_t)(n - i) * hop,
                            Hexp - (int64_t)(n - i) * 3 * kR, 1, lane);
       cp_async_commit();
-      double qo[kRT][4], zo[kRT][4], vo[kRT][4];
+      double qo[kRT][4], zo[kRT][4], vo[kRT][4], fw[kRT][4], gr[kRT][4];
 #pragma unroll
       for (int r = 0; r < kRT; ++r)
 #pragma unroll
@@ -236,6 +236,8 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
           qo[r][j] = cok[r][j] ? a.q[o] : 0.0;
           zo[r][j] = cok[r][j] ? a.ud[o] : 0.0;
           vo[r][j] = cok[r][j] ? a.v[o] : 0.0;
+          fw[r][j] = (cok[r][j] && a.grad_int) ? a.fwd_int[o] : 0.0;
+          gr[r][j] = (cok[r][j] && a.grad_int) ? a.grad_int[o] : 0.0;
         }
       cp_async_wait<1>();
       __syncwarp();
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
               a.v[o] = fma(a.a0, u_new, fma(a.a1, udn, a.a2 * uddn));
             }
             if (a.store_int) a.store_int[o] = udn;
-            if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);   // dt applied at the end
+            if (a.grad_int) a.grad_int[o] = fma(fw[r][j], udn, gr[r][j]);   // dt applied at the end
             un[r][j] = u_new;
           }
         }
