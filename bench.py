@@ -556,13 +556,13 @@ def run_batching(args, rank, world):
         del mt
         meshes.append((w, M, obs))
 
-    # schedule per mesh: element kernel x solve schedule timed on 16 steps of the first pass
+    # schedule per mesh: element kernel x solve schedule timed on 16 steps of all its passes
     choices = []
     for w, M, _ in meshes:
         if args.autotune:
             from paper_2501_06748_gb300 import autotune
             mt = lib.Model(M, w.c, w.rho_start, w.dt)
-            choices.append(autotune.tune(mt, w.src_nodes[:per_pass], w.wavelets[:per_pass], w.rec_nodes))
+            choices.append(autotune.tune(mt, w.src_nodes, w.wavelets, w.rec_nodes, shots_per_pass=per_pass))
             del mt
         else:
             choices.append(None)

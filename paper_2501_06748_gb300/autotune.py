@@ -23,10 +23,11 @@ SOLVES = {"dataflow": sbfwi.SOLVE_DATAFLOW, "barrier": sbfwi.SOLVE_BARRIER, "lev
 
 
 def tune(model, src_nodes, wavelets, rec_nodes, steps: int = 16, repeats: int = 3,
-         elements=("tensor", "fp64"), solves=("dataflow", "barrier", "levels")) -> dict:
-    """Time the candidates on ``steps`` steps (forward with stored velocities + adjoint
-    with the gradient) of these shots and set the fastest; returns {"element", "solve",
-    "s_per_step" (both passes), "candidates": [...]}."""
+         elements=("tensor", "fp64"), solves=("dataflow", "barrier", "levels"), shots_per_pass: int = 8) -> dict:
+    """Time the candidates on ``steps`` steps of a misfit-and-gradient evaluation of these
+    shots (passes of ``shots_per_pass``: forward with stored velocities + adjoint with the
+    gradient) and set the fastest; returns {"element", "solve", "s_per_step" (the whole
+    evaluation per step), "candidates": [...]}."""
     wav = wavelets[:, :max(1, min(steps, wavelets.shape[1]))]
     K = wav.shape[1]
     out = []
@@ -34,10 +35,12 @@ def tune(model, src_nodes, wavelets, rec_nodes, steps: int = 16, repeats: int = 
         for sn in solves:
             sbfwi.set_schedule(model, ELEMENTS[en], SOLVES[sn])
 
-            def evaluation():
-                tr, st = sbfwi.forward(model, src_nodes, wav, rec_nodes)
-                sbfwi.adjoint_gradient(model, st, tr)     # synchronous: the gradient comes back
-                del st
+            def evaluation():                          # the passes of a misfit-and-gradient evaluation
+                for lo in range(0, len(src_nodes), max(1, shots_per_pass)):
+                    hi = min(len(src_nodes), lo + max(1, shots_per_pass))
+                    tr, st = sbfwi.forward(model, src_nodes[lo:hi], wav[lo:hi], rec_nodes)
+                    sbfwi.adjoint_gradient(model, st, tr)   # synchronous: the gradient comes back
+                    del st
 
             try:
                 evaluation()                               # warm-up, first-use preparation
