@@ -64,6 +64,17 @@ def test_mesh_info_of_elements_with_different_boundary_node_counts(binding):
     assert ei.value.code == binding.EUNSUPPORTED
 
 
+def test_voronoi_mesh_builds_with_its_elimination_tree(binding):
+    """A centroidal Voronoi mesh (4 to 8 sides per polygon) passes the library's checks
+    (closed CCW loops, straight equally spaced lines, det J_b > 0) and gets a tree."""
+    from sbfwi_inputs import voronoi_mesh
+    m = voronoi_mesh(400, 2, seed=2)
+    M = binding.Mesh.from_inputs(m, 6)
+    assert (M.n_elem, M.n_nodes, M.n_b) == (400, m.n_nodes, int(m.n_b.max()))
+    assert M.n_int == 5 * int(m.n_b.sum())
+    assert 8 <= M.tree_levels <= 12 and M.factor_entries > 0
+
+
 def _bad(binding, **kw):
     m = structured_mesh(2, 2, 2)
     args = dict(node_xy=m.node_xy.copy(), elem_ptr=m.elem_ptr.copy(), line_nodes=m.line_nodes.copy(),
