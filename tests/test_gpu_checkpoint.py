@@ -85,3 +85,28 @@ def test_cached_store_gives_identical_results(lib, ragged):
     t3, s3 = lib.forward(md, srcs, wav, recs, ckpt_every=5)
     assert np.array_equal(t3, t1)
     assert np.array_equal(lib.adjoint_gradient(md, s3, res), g1)
+
+
+def test_differentiation_recipe_at_full_size(lib):
+    """The differentiation recipe at its full mesh size (128 x 128 elements, p = 4, N_r = 32,
+    512^2 grid) in the benchmark's launch configuration (8 shots per pass), 24 steps:
+    properties that hold at any size -- the checkpointed adjoint gradient is bitwise the
+    stored-field one, traces are exactly linear in the wavelets (scaling by 2), and one
+    shot alone gives its traces in the batch to rounding."""
+    from sbfwi_inputs import diff_workload
+    w = diff_workload(K=24)
+    src, wav = w.src_nodes[:8], w.wavelets[:8]
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_start, w.dt)
+    tr, st = lib.forward(md, src, wav, w.rec_nodes)
+    assert np.abs(tr).max() > 0
+    res = -tr
+    g_store = lib.adjoint_gradient(md, st, res)
+    tr_c, st_c = lib.forward(md, src, wav, w.rec_nodes, ckpt_every=lib.CKPT_AUTO)
+    assert np.array_equal(tr, tr_c)
+    g_ckpt = lib.adjoint_gradient(md, st_c, res)
+    assert np.array_equal(g_store, g_ckpt)
+    tr2, _ = lib.forward(md, src, 2.0 * wav, w.rec_nodes, keep=False)
+    assert np.array_equal(tr2, 2.0 * tr)
+    tr1, _ = lib.forward(md, src[3:4], wav[3:4], w.rec_nodes, keep=False)
+    assert np.linalg.norm(tr1[0] - tr[3]) <= 1e-13 * np.linalg.norm(tr[3])
