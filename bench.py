@@ -87,6 +87,9 @@ import numpy as np
 from sbfwi_inputs import size_workload
 from oracle import fwi
 w = size_workload(nx={nx}, K={K})
+lo, hi = {lo}, {hi}
+w.src_nodes, w.wavelets = w.src_nodes[lo:hi], w.wavelets[lo:hi]
+wall0 = time.time()
 t0 = time.perf_counter()
 om = fwi.build_model(w.mesh, w.n_r, w.c, w.rho_start, w.dt)
 tr, store, _ = fwi.forward(om, w.src_nodes, w.wavelets, w.rec_nodes)
@@ -94,14 +97,14 @@ E, res = fwi.misfit(tr, np.zeros_like(tr), w.dt)
 g = fwi.gradient_to_grid(om, fwi.adjoint_gradient(om, store, res, w.rec_nodes), w.gx, w.gy)
 t1 = time.perf_counter()
 units = w.mesh.n_elem * w.n_r * w.K * w.n_shots
-print(json.dumps({{"seconds": t1 - t0, "units": units}}))
+print(json.dumps({{"seconds": t1 - t0, "units": units, "wall0": wall0, "wall1": time.time()}}))
 """
 
 
 def run_oracle_sample(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
     """The oracle as it stands, single-threaded, in a fresh process (never forked from CUDA)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _CPU_CODE.format(root=ROOT, nx=nx, K=K)
+    code = _CPU_CODE.format(root=ROOT, nx=nx, K=K, lo=0, hi=8)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
@@ -109,6 +112,31 @@ def run_oracle_sample(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
     sample = (f"oracle set-up + {K} Newmark steps forward, misfit, adjoint and gradient of 8 shots on a "
               f"{nx}x{nx} sub-mesh of the same recipe (p=4, N_r=32), float64 time loop, extended-precision set-up")
     return r["units"] / r["seconds"], r["seconds"], sample
+
+
+def run_oracle_sample_all_cores(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
+    """The same sample on several host cores: the 8 shots split over concurrent fresh
+    single-threaded processes (one shot each, up to the core count), each with its own
+    set-up; the rate is all processes' units over the wall time of the slowest."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs_n = max(1, min(8, os.cpu_count() or 1))
+    bounds = [(k * 8 // procs_n, (k + 1) * 8 // procs_n) for k in range(procs_n)]
+    procs = [subprocess.Popen([sys.executable, "-c", _CPU_CODE.format(root=ROOT, nx=nx, K=K, lo=lo, hi=hi)],
+                              env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+             for lo, hi in bounds]
+    units, starts, ends = 0, [], []
+    for p in procs:
+        out, err = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + err[-2000:])
+        r = json.loads(out.strip().splitlines()[-1])
+        units += r["units"]
+        starts.append(r["wall0"])
+        ends.append(r["wall1"])
+    wall = max(ends) - min(starts)        # from the first process's set-up to the last one's end
+    sample = (f"the single-core sample's 8 shots split over {procs_n} concurrent single-threaded oracle "
+              f"processes (set-up repeated in each)")
+    return units / wall, wall, procs_n, sample
 
 
 # ---------------------------------------------------------------------------
@@ -346,10 +374,13 @@ def run_ours(args, rank, world):
 
     if rank != 0:
         return None
-    cpu = None
+    cpu = cpu_all = None
     if not args.no_cpu_baseline:
         rate, secs, sample = run_oracle_sample()
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs}
+        rate_all, wall_all, cores_all, sample_all = run_oracle_sample_all_cores()
+        cpu_all = {"value": rate_all, "unit": UNIT, "cores": cores_all, "kind": "oracle", "sample": sample_all,
+                   "seconds": wall_all}
     lat = np.array(per_step)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -369,7 +400,7 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "per_step": [float(x) for x in per_step]},
         "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "one_shot_path": one_shot, "gpu_launches": int(launches),
+        "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "one_shot_path": one_shot, "gpu_launches": int(launches),
         "clocks": clk,
     }
     if dist:
