@@ -16,10 +16,16 @@ Its dynamic stiffness S(omega) at the boundary is expanded as S ~ K - omega^2 M
 * M solves the Lyapunov equation (K - E1) E0^-1 M + M E0^-1 (K - E1^T) + 2 M - M0 = 0,
   as one dense linear system in the n_b^2 entries of M.
 
+The comparison method's time loop assembles K and M (symmetric) over the mesh and
+steps M u'' + K u = f with Newmark (``element_matrices``, ``assemble``, ``newmark``).
+
 Pinned by ``tests/test_oracle_lfe.py``: the radial finite-difference condensation of
 the same reduced element (``oracle.sbfem``, density constant in xi) converges to K
 (static S) and to M (derivative of S with respect to the Newmark mass factor) as N_r
-grows -- two independent discretisations of one equation.
+grows -- two independent discretisations of one equation; 1^T M 1 is the element's
+(and the plate's) mass; K and M are symmetric with one rigid mode; the Newmark loop
+conserves the discrete energy; and on a homogeneous plate the radial-FD traces approach
+the expansion's as N_r grows at a low source frequency.
 """
 
 import numpy as np
@@ -51,3 +57,54 @@ def lyapunov_mass(K, E0, E1, M0):
     I = np.eye(nb)
     L = np.kron(A, I) + np.kron(I, B.T) + 2.0 * np.eye(nb * nb)
     return np.linalg.solve(L, M0.reshape(-1)).reshape(nb, nb)
+
+
+# ----------------------------------------------------------------------------
+# The low-frequency-expansion time loop (the paper's comparison method)
+# ----------------------------------------------------------------------------
+
+def element_matrices(mesh, c, rho_boundary_nodal, xi0=1e-3):
+    """K_e, M_e of every element with its density taken constant along xi (the values at
+    its boundary nodes, Section 3.2): E0..M0 at xi = 1 (any xi: they do not depend on it
+    then) -> Riccati K, Lyapunov M."""
+    from . import sbfem
+    els = sbfem.elements_from_mesh(mesh)
+    out = []
+    for el in els:
+        rho = np.tile(np.asarray(rho_boundary_nodal, dtype=sbfem.XP)[el.dofs], (2, 1))
+        E0, E1, E2, M0 = (np.asarray(q[-1], dtype=np.float64)
+                          for q in sbfem.coefficient_matrices(el, mesh.node_xy, mesh.p, c, rho))
+        K, _ = riccati_stiffness(E0, E1, E2)
+        out.append((el.dofs, K, lyapunov_mass(K, E0, E1, M0)))
+    return out
+
+
+def assemble(mesh, elem):
+    """Global K and M (dense; tiny meshes) from the element matrices."""
+    N = mesh.n_nodes
+    K, M = np.zeros((N, N)), np.zeros((N, N))
+    for dofs, Ke, Me in elem:
+        K[np.ix_(dofs, dofs)] += Ke
+        M[np.ix_(dofs, dofs)] += Me
+    return K, M
+
+
+def newmark(K, M, f, dt, beta=0.25, gamma=0.5, u0=None, v0=None):
+    """M u'' + K u = f by Newmark (Eq. (Newmark)) from rest, or from u0, v0 with the
+    consistent initial acceleration; f[k] (steps, N) is the load at the end of step k.
+    Returns u, u' after every step."""
+    N = K.shape[0]
+    u = np.zeros(N) if u0 is None else np.array(u0, dtype=np.float64)
+    v = np.zeros(N) if v0 is None else np.array(v0, dtype=np.float64)
+    a = np.linalg.solve(M, -K @ u)               # at rest, or free vibration from u0 (no load at t = 0)
+    a0, a1, a2 = 1 / (beta * dt * dt), 1 / (beta * dt), 1 / (2 * beta) - 1
+    lu = sla.lu_factor(K + a0 * M)
+    us, vs = [], []
+    for k in range(f.shape[0]):
+        un = sla.lu_solve(lu, f[k] + M @ (a0 * u + a1 * v + a2 * a))
+        an = a0 * (un - u) - a1 * v - a2 * a
+        v = v + dt * ((1 - gamma) * a + gamma * an)
+        u, a = un, an
+        us.append(u.copy())
+        vs.append(v.copy())
+    return np.array(us), np.array(vs)

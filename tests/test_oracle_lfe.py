@@ -77,3 +77,63 @@ def test_lyapunov_mass_carries_the_element_mass():
     M = lfe.lyapunov_mass(K, E0, E1, M0)
     one = np.ones(4 * p)
     assert one @ M @ one == pytest.approx(rho0 * 0.25, rel=1e-12)
+
+
+def _plate(nx=3, p=2, rho=None):
+    m = structured_mesh(nx, nx, p)
+    rho = np.ones(m.n_nodes) if rho is None else rho(m)
+    K, M = lfe.assemble(m, lfe.element_matrices(m, 1.0, rho))
+    return m, K, M
+
+
+def test_lfe_global_matrices_are_symmetric_and_definite():
+    m, K, M = _plate(rho=lambda m: 1.0 + 0.3 * np.random.default_rng(0).random(m.n_nodes))
+    assert np.abs(K - K.T).max() < 1e-12 * np.abs(K).max()
+    assert np.abs(M - M.T).max() < 1e-12 * np.abs(M).max()
+    assert np.linalg.eigvalsh(M).min() > 0
+    ev = np.sort(np.linalg.eigvalsh(K))
+    assert abs(ev[0]) < 1e-12 * ev[-1] and ev[1] > 1e-3 * ev[-1]      # one rigid (constant) mode
+
+
+def test_lfe_total_mass_of_a_homogeneous_plate():
+    m, K, M = _plate(rho=lambda m: np.full(m.n_nodes, 1.7))
+    one = np.ones(m.n_nodes)
+    assert one @ M @ one == pytest.approx(1.7 * 1.0, rel=1e-12)    # unit square
+    assert np.abs(K @ one).max() < 1e-12 * np.abs(K).max()
+
+
+def test_lfe_newmark_conserves_the_discrete_energy():
+    """Average-acceleration Newmark on a symmetric pencil: 1/2 u'^T M u' + 1/2 u^T K u stays
+    at its initial value in free vibration (400 steps)."""
+    m, K, M = _plate(rho=lambda m: 1.0 + 0.3 * np.random.default_rng(0).random(m.n_nodes))
+    u0 = np.random.default_rng(1).standard_normal(m.n_nodes)
+    us, vs = lfe.newmark(K, M, np.zeros((400, m.n_nodes)), 0.05, u0=u0, v0=np.zeros(m.n_nodes))
+    E = 0.5 * np.einsum("ki,ij,kj->k", vs, M, vs) + 0.5 * np.einsum("ki,ij,kj->k", us, K, us)
+    E0 = 0.5 * u0 @ K @ u0
+    assert np.abs(E / E0 - 1).max() < 1e-12
+
+
+def test_fd_traces_approach_the_lfe_traces_at_low_frequency():
+    """Homogeneous plate (density constant along xi, so both methods solve the same
+    equation): the radial-FD receiver traces converge towards the low-frequency expansion's
+    as N_r grows when the source frequency is low, and stay apart at a higher frequency
+    where the one-term expansion itself is inaccurate (a trend, not a number)."""
+    from oracle import fwi
+    from sbfwi_inputs import boundary_nodes, ricker
+    m = structured_mesh(4, 4, 2)
+    src = int(boundary_nodes(m, "top")[4])
+    rec = np.array([int(boundary_nodes(m, "bottom")[3]), int(boundary_nodes(m, "left")[5])])
+    K, M = lfe.assemble(m, lfe.element_matrices(m, 1.0, np.ones(m.n_nodes)))
+    dt, steps = 0.0625, 300
+    err = {}
+    for f0 in (0.2, 0.4):
+        w = ricker(f0, dt, steps)
+        F = np.zeros((steps, m.n_nodes))
+        F[:, src] = w
+        tl = lfe.newmark(K, M, F, dt)[0][:, rec].T
+        for n_r in (5, 9, 17):
+            tr, _, _ = fwi.forward(fwi.build_model(m, n_r, 1.0, np.ones((8, 8)), dt), [src], w[None], rec, keep=False)
+            err[(f0, n_r)] = np.linalg.norm(tr[0] - tl) / np.linalg.norm(tl)
+    assert err[(0.2, 5)] > err[(0.2, 9)] > err[(0.2, 17)]
+    assert err[(0.2, 17)] < 0.05
+    assert err[(0.4, 17)] > 3 * err[(0.2, 17)]
