@@ -268,12 +268,14 @@ def nodal_vector(model: Model, interior: np.ndarray, boundary: np.ndarray) -> np
     return np.concatenate([interior.reshape(-1, B), boundary], axis=0)
 
 
-def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True, state=None):
+def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True, state=None, keep_u=False):
     """Forward solve of B shots (Section 2, Eq. (main)); shot s has one point source.
 
     Returns traces (B, R, K) with sample k = u(t_{k+1}) at the receivers and, if
     ``keep``, the nodal velocities (K, n_nodal, B) after every step (stored for the
-    adjoint, the memory strategy of Section 4).
+    adjoint, the memory strategy of Section 4).  With ``keep_u`` the nodal
+    displacements of every step are returned as well (a 4th result), for the gradient
+    term of the full Frechet kernel (``adjoint_gradient(..., store_u=...)``).
     """
     src_nodes = np.asarray(src_nodes)
     rec_nodes = np.asarray(rec_nodes)
@@ -283,6 +285,7 @@ def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True, sta
     st = zero_state(model, B) if state is None else state
     traces = np.zeros((B, rec_nodes.size, K))
     store = np.zeros((K, model.n_int + model.n_nodes, B)) if keep else None
+    store_u = np.zeros((K, model.n_int + model.n_nodes, B)) if keep_u else None
     for k in range(K):
         f = np.zeros((model.n_nodes, B))
         for s in range(B):
@@ -291,6 +294,10 @@ def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True, sta
         traces[:, :, k] = st.ub[rec_nodes].T
         if keep:
             store[k] = nodal_vector(model, st.ud, st.udb)
+        if keep_u:
+            store_u[k] = nodal_vector(model, st.u, st.ub)
+    if keep_u:
+        return traces, store, st, store_u
     return traces, store, st
 
 
@@ -302,7 +309,57 @@ def misfit(traces, observed, dt):
     return 0.5 * dt * float(np.sum(res * res)), res
 
 
-def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_nodes):
+def gradient_operator(model: Model):
+    """Sparse G: (G u)[2q + d] is component d (x, y) of grad u at nodal point q, from nodal
+    values u (the full Frechet kernel's c^2 grad(lambda).grad(u) term, Section 2).
+
+    Readings (the paper gives no discretisation of the term it drops): at radial point
+    xi_i of node j on one of the element's line elements, [u_xi; u_eta] = J [u_x; u_y]
+    with J = [[x_b - x0, y_b - y0], [xi x_b,eta, xi y_b,eta]] (the coordinate map x = x0 +
+    xi (x_b(eta) - x0), Section 3); u_xi by second-order finite differences on the radial
+    grid (central inside, one-sided at xi_0 and xi_n = 1), u_eta by the derivative of the
+    line's Lagrange interpolant at the node.  A point met by several (element, line)
+    pairs -- a vertex node, or a boundary node shared by elements -- gets the mean of their
+    gradients."""
+    import scipy.sparse as sp_
+    mesh, n, xi = model.mesh, model.n, model.xi
+    h = float(xi[1] - xi[0])
+    p = mesh.p
+    _, dphi = sbfem.lagrange(p, sbfem.lagrange_nodes(p))
+    n_int = model.n_int
+    rows, cols, vals = [], [], []
+    count = np.zeros(n_int + model.n_nodes)
+    for e, el in enumerate(model.elements):
+        nb = el.dofs.size
+        idx = lambda i, j: model.int_ptr[e] + i * nb + j if i < n else n_int + el.dofs[j]
+        x0 = el.centre
+        for ln, loc in zip(el.lines, el.line_local):
+            X = mesh.node_xy[ln]
+            dX = dphi @ X
+            for i in range(n + 1):
+                if i == 0:
+                    st = ((0, -3.0), (1, 4.0), (2, -1.0))
+                elif i == n:
+                    st = ((n, 3.0), (n - 1, -4.0), (n - 2, 1.0))
+                else:
+                    st = ((i + 1, 1.0), (i - 1, -1.0))
+                for k in range(p + 1):
+                    j = int(loc[k])
+                    Jinv = np.linalg.inv(np.array([X[k] - x0, xi[i] * dX[k]]))
+                    q = idx(i, j)
+                    for d in range(2):
+                        for ii, wgt in st:
+                            rows.append(2 * q + d); cols.append(idx(ii, j)); vals.append(Jinv[d, 0] * wgt / (2 * h))
+                        for mm in range(p + 1):
+                            rows.append(2 * q + d); cols.append(idx(i, int(loc[mm]))); vals.append(Jinv[d, 1] * dphi[k, mm])
+                    count[q] += 1
+    rows = np.asarray(rows)
+    vals = np.asarray(vals) / np.repeat(count, 2)[rows]
+    npt = n_int + model.n_nodes
+    return sp_.csr_matrix((vals, (rows, np.asarray(cols))), shape=(2 * npt, npt))
+
+
+def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_nodes, store_u=None):
     """Adjoint solve in reversed time and zero-lag cross-correlation (Sections 2 and 4).
 
     The adjoint field lambda(T - t) is the forward operator run from a zero state
@@ -318,11 +375,20 @@ def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_
     (reading of the sign of the reversed-time kernel).  Returns g on nodal points
     (n_nodal,).  Parity of this kernel against the paper is unpinned (the paper
     prints no values); its parts are pinned through the forward solver.
+
+    With ``store_u`` (the forward displacements of every step, ``forward(...,
+    keep_u=True)``) the gradient term the paper drops is added: the same reversed-time
+    pairing of c^2 grad(u_fwd) . grad(lambda) (``gradient_operator``).  In reversed time
+    the velocity term changes sign and the gradient term does not, so relative to the
+    velocity term as computed here it enters with a plus sign (Section 2's kernel
+    d_t lambda d_t u - c^2 grad lambda . grad u, with d_t lambda = -d lambda / d tau).
     """
     residual = np.asarray(residual)
     B, R, K = residual.shape
     st = zero_state(model, B)
     g = np.zeros(model.n_int + model.n_nodes)
+    G = gradient_operator(model) if store_u is not None else None
+    npt = model.n_int + model.n_nodes
     for m in range(K):
         j = K - 1 - m
         f = np.zeros((model.n_nodes, B))
@@ -331,6 +397,10 @@ def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_
         st = step(model, st, f)
         lam_dot = nodal_vector(model, st.ud, st.udb)
         g += model.dt * np.sum(store[j] * lam_dot, axis=1)
+        if G is not None:
+            gu = (G @ store_u[j]).reshape(npt, 2, B)
+            gl = (G @ nodal_vector(model, st.u, st.ub)).reshape(npt, 2, B)
+            g += model.dt * model.c ** 2 * np.sum(gu * gl, axis=(1, 2))
     return g
 
 
