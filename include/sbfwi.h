@@ -162,6 +162,23 @@ void sbfwi_destroy_model(sbfwi_model* model);
  * element kernel (SBFWI_ESTATE otherwise).  Errors: SBFWI_EINVAL for a NULL model
  * or an unknown value.
  */
+/*
+ * sbfwi_set_kernel_terms -- which terms of the Frechet kernel (Section 2:
+ * K_rho = int d_t lambda d_t u - c^2 grad lambda . grad u dt) later adjoint gradients
+ * on `model` accumulate.
+ *   SBFWI_TERMS_VELOCITY (default): the velocity term only, as the paper does
+ *     (Section 4).
+ *   SBFWI_TERMS_FULL: both terms.  The gradient at a nodal point comes from the
+ *     coordinate map of each element line through it (second-order differences along
+ *     the radial grid, the line's Lagrange derivative along it; the mean over the
+ *     element lines that meet at the point).  Forward passes then also keep the
+ *     nodal displacements of every step (twice the stored field); checkpointed
+ *     forward passes (ckpt_every != 0) return SBFWI_EUNSUPPORTED.
+ * Errors: SBFWI_EINVAL for a NULL model or an unknown value.
+ */
+enum { SBFWI_TERMS_VELOCITY = 0, SBFWI_TERMS_FULL = 1 };
+int sbfwi_set_kernel_terms(sbfwi_model* model, int terms);
+
 enum { SBFWI_ELEMENT_AUTO = 0, SBFWI_ELEMENT_TENSOR = 1, SBFWI_ELEMENT_FP64 = 2 };
 enum { SBFWI_SOLVE_AUTO = 0, SBFWI_SOLVE_DATAFLOW = 1, SBFWI_SOLVE_BARRIER = 2, SBFWI_SOLVE_LEVELS = 3 };
 int sbfwi_set_schedule(sbfwi_model* model, int element, int solve);

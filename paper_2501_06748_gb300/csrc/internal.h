@@ -127,6 +127,9 @@ struct MeshDevice {
   double lx = 0, ly = 0;
   DevBuf cell, clamp, cell_ptr, cell_list;
   DevBuf nbe, lptr, api_map;         // n_b per element, first line per element, Mesh::api_to_lib
+  // nodal gradient operator (CSR, rows 2q and 2q+1: x and y components at nodal point q)
+  bool grad_ready = false;
+  DevBuf grad_ptr, grad_col, grad_val;
 };
 
 constexpr int kMaxBoundaryNodes = 40;   // largest n_b of an element
@@ -158,6 +161,7 @@ struct Mesh {
 };
 
 int build_tree(Mesh& m);
+int ensure_gradient_operator(const Mesh& m, cudaStream_t st);   // MeshDevice::grad_* (setup.cu)
 
 // ---------------------------------------------------------------------------
 // model (device resident)
@@ -215,6 +219,7 @@ struct Model {
   // the same operators split into FP16 digits for the tensor-core element kernel
   DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
   bool tc_ready = false;
+  int kernel_terms = SBFWI_TERMS_VELOCITY;  // sbfwi_set_kernel_terms
   int elem_pref = SBFWI_ELEMENT_AUTO;     // sbfwi_set_schedule
   int solve_pref = SBFWI_SOLVE_AUTO;
   LevelTasks tasks;        // built for tasks.shots
@@ -229,7 +234,7 @@ bool tc_available(int nb, int B);   // a tensor-core kernel exists for these sha
 int tc_prepare(Model& md, cudaStream_t st);
 int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
                       const double* ub, const double* udb, const double* uddb, double* q, double* fhat,
-                      double* store_int, const double* fwd_int, double* grad_int, cudaStream_t st);
+                      double* store_int, const double* fwd_int, double* grad_int, double* u_out, cudaStream_t st);
 
 struct FwdState {
   Model* model = nullptr;
@@ -242,6 +247,7 @@ struct FwdState {
   // ckpt_every == 0: [K][n_nodal][B] nodal velocities after every step;
   // ckpt_every == c > 0: [ceil(K/c) - 1][state_doubles] Newmark states before steps c, 2c, ...
   DevBuf store;
+  DevBuf store_u;               // full kernel: [K][n_nodal][B] nodal displacements after every step
   DevBuf values, nodes;         // wavelets and source nodes, for the recompute (c > 0)
   ~FwdState() { store_release(store); }
 };

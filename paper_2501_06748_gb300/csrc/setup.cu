@@ -913,6 +913,100 @@ static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, double lx, dou
   return SBFWI_OK;
 }
 
+// The nodal gradient operator of the full Frechet kernel, in the library's padded nodal
+// layout: at radial point xi_i of local node j on one line element of element e,
+// [u_xi; u_eta] = J [u_x; u_y] with J = [[x_b - x0, y_b - y0], [xi x_b,eta, xi y_b,eta]]
+// (the coordinate map x = x0 + xi (x_b(eta) - x0)); u_xi by second-order differences on
+// the radial grid (central inside, one-sided at xi_0 and xi_n = 1), u_eta by the line's
+// Lagrange derivative at the node; a point met by several (element, line) pairs takes
+// the mean of their gradients.
+int ensure_gradient_operator(const Mesh& m, cudaStream_t st) {
+  MeshDevice& d = *m.dev;
+  if (d.grad_ready) return SBFWI_OK;
+  const int n = m.n, nb = m.nb, p = m.p, pp = p + 1;
+  const int64_t npt = m.n_nodal;
+  const double h = (1.0 - m.xi0) / n;
+  std::vector<double> eta(pp), D((size_t)pp * pp, 0.0);    // D[k][a] = d phi_a / d eta at node k
+  for (int k = 0; k < pp; ++k) eta[k] = -1.0 + 2.0 * k / p;
+  for (int a = 0; a < pp; ++a) {
+    double denom = 1.0;
+    for (int b = 0; b < pp; ++b) if (b != a) denom *= eta[a] - eta[b];
+    for (int k = 0; k < pp; ++k) {
+      double sum = 0.0;
+      for (int b = 0; b < pp; ++b) {
+        if (b == a) continue;
+        double prod = 1.0;
+        for (int c = 0; c < pp; ++c) if (c != a && c != b) prod *= eta[k] - eta[c];
+        sum += prod;
+      }
+      D[(size_t)k * pp + a] = sum / denom;
+    }
+  }
+  std::vector<int64_t> R;
+  std::vector<int32_t> C;
+  std::vector<double> V;
+  std::vector<int32_t> cnt(npt, 0);
+  for (int64_t e = 0; e < m.n_elem; ++e) {
+    const double x0 = m.centre_xy[2 * e], y0 = m.centre_xy[2 * e + 1];
+    auto idx = [&](int i, int j) -> int64_t {
+      return i < n ? (e * n + i) * (int64_t)nb + j : m.n_int + m.dofs[(size_t)e * nb + j];
+    };
+    for (int64_t l = m.elem_ptr[e]; l < m.elem_ptr[e + 1]; ++l) {
+      const int64_t* ln = m.line_nodes.data() + l * pp;
+      const int32_t* loc = m.line_local.data() + l * pp;
+      std::vector<double> dx(pp, 0.0), dy(pp, 0.0);
+      for (int k = 0; k < pp; ++k)
+        for (int a = 0; a < pp; ++a) {
+          dx[k] += D[(size_t)k * pp + a] * m.node_xy[2 * ln[a]];
+          dy[k] += D[(size_t)k * pp + a] * m.node_xy[2 * ln[a] + 1];
+        }
+      for (int i = 0; i <= n; ++i) {
+        const double xi = i == n ? 1.0 : m.xi0 + i * h;
+        int si[3], ns;
+        double sw[3];
+        if (i == 0) { si[0] = 0; si[1] = 1; si[2] = 2; sw[0] = -3; sw[1] = 4; sw[2] = -1; ns = 3; }
+        else if (i == n) { si[0] = n; si[1] = n - 1; si[2] = n - 2; sw[0] = 3; sw[1] = -4; sw[2] = 1; ns = 3; }
+        else { si[0] = i + 1; si[1] = i - 1; sw[0] = 1; sw[1] = -1; ns = 2; }
+        for (int k = 0; k < pp; ++k) {
+          const int j = loc[k];
+          const double j00 = m.node_xy[2 * ln[k]] - x0, j01 = m.node_xy[2 * ln[k] + 1] - y0;
+          const double j10 = xi * dx[k], j11 = xi * dy[k];
+          const double det = j00 * j11 - j01 * j10;
+          const double inv[2][2] = {{j11 / det, -j01 / det}, {-j10 / det, j00 / det}};
+          const int64_t q = idx(i, j);
+          for (int dd = 0; dd < 2; ++dd) {
+            for (int t = 0; t < ns; ++t) {
+              R.push_back(2 * q + dd); C.push_back((int32_t)idx(si[t], j)); V.push_back(inv[dd][0] * sw[t] / (2 * h));
+            }
+            for (int a = 0; a < pp; ++a) {
+              R.push_back(2 * q + dd); C.push_back((int32_t)idx(i, loc[a])); V.push_back(inv[dd][1] * D[(size_t)k * pp + a]);
+            }
+          }
+          ++cnt[q];
+        }
+      }
+    }
+  }
+  std::vector<int64_t> ptr(2 * npt + 1, 0);
+  for (size_t t = 0; t < R.size(); ++t) ++ptr[R[t] + 1];
+  for (int64_t r = 0; r < 2 * npt; ++r) ptr[r + 1] += ptr[r];
+  std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+  std::vector<int32_t> col(R.size());
+  std::vector<double> val(R.size());
+  for (size_t t = 0; t < R.size(); ++t) {
+    const int64_t at = fill[R[t]]++;
+    col[at] = C[t];
+    val[at] = V[t] / cnt[R[t] / 2];
+  }
+  int rc;
+  if ((rc = upload(d.grad_ptr, ptr, st))) return rc;
+  if ((rc = upload(d.grad_col, col, st))) return rc;
+  if ((rc = upload(d.grad_val, val, st))) return rc;
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  d.grad_ready = true;
+  return SBFWI_OK;
+}
+
 int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st) {
   const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
   const int ng = (3 * p + 2) / 2;

@@ -51,6 +51,7 @@ struct ElemStepArgs {
   double* store_int;    // forward: velocities of this step, interior part [E][n][nb][B]
   const double* fwd_int;// adjoint: paired forward velocities, interior part
   double* grad_int;     // adjoint: accumulators [E][n][nb][B]
+  double* u_out;        // full Frechet kernel: the new interior displacements [E][n][nb][B]
 };
 
 __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
         a.u[o] = un; a.ud[o] = udn; a.udd[o] = uddn;
         if (a.store_int) a.store_int[o] = udn;
         if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);   // dt applied at the end
+        if (a.u_out) a.u_out[o] = un;
         if (a.do_up) vbuf[i * per + r * B + s] = fma(a.a0, un, fma(a.a1, udn, a.a2 * uddn));
       }
       __syncthreads();
@@ -619,6 +621,7 @@ struct BoundaryArgs {
   const int64_t* rec;
   double* traces;         // [B][R][K]
   double* store_b;        // forward: velocities of this step at the boundary nodes [N][B]
+  double* store_ub;       // forward, full kernel: displacements of this step at the boundary nodes [N][B]
   const double* fwd_b;    // adjoint: paired forward velocities [N][B]
   double* grad_b;         // adjoint accumulators [N][B]
 };
@@ -633,6 +636,7 @@ __global__ void boundary_update_kernel(BoundaryArgs a) {
     const double udn = fma(a.c2, uddn, fma(a.c1, uddo, udo));
     a.ub[t] = un; a.udb[t] = udn; a.uddb[t] = uddn;
     if (a.store_b) a.store_b[t] = udn;
+    if (a.store_ub) a.store_ub[t] = un;
     if (a.grad_b) a.grad_b[t] = fma(a.fwd_b[t], udn, a.grad_b[t]);          // dt applied at the end
   }
   if (a.traces) {
@@ -669,6 +673,33 @@ __global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double dt
 }
 
 // out[q] (+)= lib[map[q]]: nodal values from the padded layout to the caller's
+// Gradient term of the full Frechet kernel at one adjoint step, for every nodal point q and
+// shot s: grad[q][s] += c^2 (G u_fwd)(q, s) . (G lambda)(q, s), G the nodal gradient operator
+// (CSR rows 2q, 2q+1); lambda's interior part from lam_int, its boundary part from lam_b.
+// dt is applied at the end with the velocity term.
+__global__ void gradient_term_kernel(const int64_t* ptr, const int32_t* col, const double* val, int64_t np,
+                                     int64_t n_int, int B, const double* u_fwd, const double* lam_int,
+                                     const double* lam_b, double c2, double* grad) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < np * B; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / B;
+    const int s = (int)(t - q * B);
+    double gu[2], gl[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      double au = 0.0, al = 0.0;
+      for (int64_t k = ptr[2 * q + d]; k < ptr[2 * q + d + 1]; ++k) {
+        const int64_t c = col[k];
+        const double v = val[k];
+        au = fma(v, u_fwd[c * B + s], au);
+        al = fma(v, c < n_int ? lam_int[c * B + s] : lam_b[(c - n_int) * B + s], al);
+      }
+      gu[d] = au;
+      gl[d] = al;
+    }
+    grad[t] = fma(c2, fma(gu[0], gl[0], gu[1] * gl[1]), grad[t]);
+  }
+}
+
 __global__ void gather_nodal_kernel(const double* lib, const int64_t* map, int64_t n, double* out, int accumulate) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
     out[q] = accumulate ? out[q] + lib[map[q]] : lib[map[q]];
@@ -885,6 +916,7 @@ namespace {
 
 struct RunBuffers {
   DevBuf u, ud, udd, v, ub, udb, uddb, q, fhat, ext, ysep, ybnd, x;
+  DevBuf lam;                       // full kernel, adjoint: interior displacements of the current step
   DevBuf grad_int;                  // grad accumulators [n_nodal][B] (adjoint)
 };
 
@@ -914,9 +946,11 @@ struct Stepper {
   const cudaStream_t st;
   // forward: velocities of step k go to store + (k - store_k0) * n_nodal * B
   double* store = nullptr;
+  double* store_u = nullptr;        // full kernel: displacements of step k at store_u + (k - store_k0) * n_nodal * B
   int64_t store_k0 = 0;
   // adjoint: forward velocities of step j are read at fwd + (j - fwd_k0) * n_nodal * B
   const double* fwd = nullptr;
+  const double* fwd_u = nullptr;    // full kernel: forward displacements, paired like fwd
   int64_t fwd_k0 = 0;
   // source values and nodes (forward: wavelets [B][K], nodes = B sources then R
   // receivers; adjoint: residuals [B][R][K], nodes = R receivers) and the device
@@ -1033,6 +1067,13 @@ int Stepper::init() {
   ea.u = rb.u.as<double>(); ea.ud = rb.ud.as<double>(); ea.udd = rb.udd.as<double>();
   ea.ub = rb.ub.as<double>(); ea.udb = rb.udb.as<double>(); ea.uddb = rb.uddb.as<double>();
   ea.q = rb.q.as<double>(); ea.fhat = rb.fhat.as<double>();
+  ea.u_out = nullptr;
+  if (mode == Mode::Adjoint && md.kernel_terms == SBFWI_TERMS_FULL) {
+    SBFWI_CUDA(rb.lam.alloc(sizeof(double) * std::max<int64_t>(si, 1)));
+    SBFWI_CUDA(cudaMemsetAsync(rb.lam.p, 0, rb.lam.bytes, st));
+    int rc_g = ensure_gradient_operator(*md.mesh, st);
+    if (rc_g) return rc_g;
+  }
   e_threads = ea.epc * nb * B;
   e_blocks = (unsigned)((E + ea.epc - 1) / ea.epc);
   e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
@@ -1109,7 +1150,7 @@ int Stepper::init() {
   ba.K = K;
   ba.a0 = md.a0; ba.a1 = md.a1; ba.a2 = md.a2; ba.c1 = md.c1; ba.c2 = md.c2; ba.dt = md.dt;
   ba.x = rb.x.as<double>(); ba.ub = rb.ub.as<double>(); ba.udb = rb.udb.as<double>(); ba.uddb = rb.uddb.as<double>();
-  ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
+  ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.store_ub = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
   b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
   return SBFWI_OK;
 }
@@ -1210,8 +1251,11 @@ int Stepper::element_launch(int down, int up, int64_t done_step) {
   // done_step: the step whose back-substitution runs in this launch (if down)
   Profiler& prof = profiler();
   ea.do_down = down; ea.do_up = up;
-  ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr;
+  ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr; ea.u_out = nullptr;
   if (down && mode == Mode::Forward && store) ea.store_int = store + (done_step - store_k0) * np * B;
+  if (down && mode == Mode::Forward && store_u) ea.u_out = store_u + (done_step - store_k0) * np * B;
+  const bool grad_term = down && mode == Mode::Adjoint && fwd_u != nullptr;
+  if (grad_term) ea.u_out = rb.lam.as<double>();
   if (down && mode == Mode::Adjoint) {
     ea.fwd_int = fwd + (K - 1 - done_step - fwd_k0) * np * B;
     ea.grad_int = rb.grad_int.as<double>();
@@ -1219,11 +1263,23 @@ int Stepper::element_launch(int down, int up, int64_t done_step) {
   prof.begin(kPhaseElement, st);
   if (use_tc)
     tc_element_launch(md, B, down, up, ea.u, ea.ud, ea.udd, rb.v.as<double>(), ea.ub, ea.udb, ea.uddb, ea.q, ea.fhat,
-                      ea.store_int, ea.fwd_int, ea.grad_int, st);
+                      ea.store_int, ea.fwd_int, ea.grad_int, ea.u_out, st);
   else
     element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
   prof.end(kPhaseElement, st);
   prof.count(kPhaseElement);
+  if (grad_term) {
+    // the full kernel's gradient term of this step: the interior adjoint field was just
+    // written to lam, its boundary part is the current boundary state
+    const MeshDevice& mdev = md.dev();
+    const int64_t tot = np * B;
+    const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+    gradient_term_kernel<<<blocks, 256, 0, st>>>(mdev.grad_ptr.as<int64_t>(), mdev.grad_col.as<int32_t>(),
+                                                 mdev.grad_val.as<double>(), np, nint, B,
+                                                 fwd_u + (K - 1 - done_step - fwd_k0) * np * B, rb.lam.as<double>(),
+                                                 rb.ub.as<double>(), md.c * md.c, rb.grad_int.as<double>());
+    prof.count(kPhaseOther);
+  }
   return SBFWI_OK;
 }
 
@@ -1295,6 +1351,7 @@ int Stepper::run(int64_t k0, int64_t k1) {
       ba.rec = nodes + B;
       ba.traces = R > 0 ? traces : nullptr;
       ba.store_b = store ? store + (k - store_k0) * np * B + nint * B : nullptr;
+      ba.store_ub = store_u ? store_u + (k - store_k0) * np * B + nint * B : nullptr;
     } else {
       ba.fwd_b = fwd + (K - 1 - k - fwd_k0) * np * B + nint * B;
       ba.grad_b = rb.grad_int.as<double>() + nint * B;
@@ -1362,6 +1419,13 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
 }
 
 void sbfwi_destroy_model(sbfwi_model* m) { delete m; }
+
+int sbfwi_set_kernel_terms(sbfwi_model* m, int terms) {
+  if (!m) return fail(SBFWI_EINVAL, "model is NULL");
+  if (terms != SBFWI_TERMS_VELOCITY && terms != SBFWI_TERMS_FULL) return fail(SBFWI_EINVAL, "unknown kernel terms");
+  m->kernel_terms = terms;
+  return SBFWI_OK;
+}
 
 int sbfwi_set_schedule(sbfwi_model* m, int element, int solve) {
   if (!m) return fail(SBFWI_EINVAL, "model is NULL");
@@ -1431,6 +1495,8 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
       c = (int64_t)std::ceil(std::sqrt((double)K * (double)sd / ((double)np * B)));
     }
     c = std::min<int64_t>(c, K);
+    if (md->kernel_terms == SBFWI_TERMS_FULL && c != 0)
+      return fail(SBFWI_EUNSUPPORTED, "the full Frechet kernel needs the stored forward field (ckpt_every = 0)");
     fs->ckpt_every = c;
     fs->state_doubles = sd;
     fs->tensor_core_path = f.tensor_core_path();
@@ -1439,6 +1505,10 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     if (c == 0) {
       gb = (double)K * np * B * 8 / 1e9;
       e = store_alloc(fs->store, sizeof(double) * (size_t)K * np * B);
+      if (e == cudaSuccess && md->kernel_terms == SBFWI_TERMS_FULL) {
+        gb *= 2;
+        e = fs->store_u.alloc(sizeof(double) * (size_t)K * np * B);
+      }
     } else {
       const int64_t nseg = (K + c - 1) / c;
       gb = (double)(nseg - 1) * sd * 8 / 1e9;
@@ -1451,6 +1521,7 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
   }
   if (!keep || c == 0) {
     f.store = fs ? fs->store.as<double>() : nullptr;
+    f.store_u = (fs && fs->store_u.p) ? fs->store_u.as<double>() : nullptr;
     rc = f.run(0, K);
   } else {
     // checkpoints: the Newmark state before steps c, 2c, ... (before step 0 it is zero)
@@ -1503,6 +1574,11 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   int rc = adj.init();
   if (rc) return rc;
   const int64_t c = fs->ckpt_every;
+  if (md->kernel_terms == SBFWI_TERMS_FULL) {
+    if (!fs->store_u.p)
+      return fail(SBFWI_ESTATE, "the forward pass kept no displacements: set the full kernel before the forward pass");
+    adj.fwd_u = fs->store_u.as<double>();
+  }
   if (c == 0) {
     adj.fwd = fs->store.as<double>();
     rc = adj.run(0, K);

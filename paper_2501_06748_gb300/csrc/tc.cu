@@ -279,6 +279,7 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
           }
           if (a.store_int) a.store_int[o] = udn;
           if (a.grad_int) a.grad_int[o] = fma(fw[j], udn, gr[j]);    // dt applied at the end
+          if (a.u_out) a.u_out[o] = u_new;
           un[j] = u_new;
         }
       }
@@ -381,7 +382,7 @@ int tc_prepare(Model& md, cudaStream_t st) {
 
 int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
                       const double* ub, const double* udb, const double* uddb, double* q, double* fhat,
-                      double* store_int, const double* fwd_int, double* grad_int, cudaStream_t st) {
+                      double* store_int, const double* fwd_int, double* grad_int, double* u_out, cudaStream_t st) {
   ElemTcArgs a;
   a.nb = md.nb; a.n = md.n; a.B = B; a.E = md.E;
   a.a0 = md.a0; a.a1 = md.a1; a.a2 = md.a2; a.c1 = md.c1; a.c2 = md.c2; a.dt = md.dt;
@@ -390,7 +391,7 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.dofs = md.dev().dofs.as<int32_t>();
   a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
   a.do_down = down; a.do_up = up;
-  a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int;
+  a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int; a.u_out = u_out;
   if (md.nb > tc::kTile) return tc2_element_launch(a, md.a2 == 1.0 && md.c1 == md.c2, st);
   const int smem = (int)(sizeof(tc::WarpSmem) * tc::kWarpsPerBlock);   // attribute set by tc_prepare
   const unsigned blocks = (unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock);

@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
             }
             if (a.store_int) a.store_int[o] = udn;
             if (a.grad_int) a.grad_int[o] = fma(fw[r][j], udn, gr[r][j]);   // dt applied at the end
+            if (a.u_out) a.u_out[o] = u_new;
             un[r][j] = u_new;
           }
         }

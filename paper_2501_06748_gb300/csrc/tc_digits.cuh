@@ -211,6 +211,7 @@ struct ElemTcArgs {
   double* store_int;
   const double* fwd_int;
   double* grad_int;
+  double* u_out;          // full Frechet kernel: the new interior displacements (store or adjoint field)
 };
 
 // elements padded to 21..32 boundary nodes (tc2.cu)

@@ -23,6 +23,7 @@ GRAD_ACCUMULATE = 0x100
 CKPT_AUTO = -1
 ELEMENT_AUTO, ELEMENT_TENSOR, ELEMENT_FP64 = 0, 1, 2
 SOLVE_AUTO, SOLVE_DATAFLOW, SOLVE_BARRIER, SOLVE_LEVELS = 0, 1, 2, 3
+TERMS_VELOCITY, TERMS_FULL = 0, 1
 PHASES = ("setup", "element", "solve", "other")
 
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE",
@@ -64,6 +65,8 @@ def _load():
     lib.sbfwi_profile_solve_levels.restype = ctypes.c_int
     lib.sbfwi_release_cache.argtypes = []
     lib.sbfwi_release_cache.restype = ctypes.c_int
+    lib.sbfwi_set_kernel_terms.argtypes = [VP, ctypes.c_int]
+    lib.sbfwi_set_kernel_terms.restype = ctypes.c_int
     lib.sbfwi_set_schedule.argtypes = [VP, ctypes.c_int, ctypes.c_int]
     lib.sbfwi_set_schedule.restype = ctypes.c_int
     lib.sbfwi_selftest_barrier.argtypes = [I32, I32, I64, I32, VP]
@@ -302,6 +305,12 @@ def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
     _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
                                      arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
     return E_out, residual_out
+
+
+def set_kernel_terms(model: Model, terms: int = TERMS_VELOCITY) -> None:
+    """Velocity term only (the paper's kernel) or the full Frechet kernel for later
+    forward/adjoint pairs on the model."""
+    _check(_lib.sbfwi_set_kernel_terms(model._h, int(terms)))
 
 
 def set_schedule(model: Model, element: int = ELEMENT_AUTO, solve: int = SOLVE_AUTO) -> None:

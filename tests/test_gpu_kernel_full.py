@@ -1,0 +1,71 @@
+"""The full Frechet kernel (velocity term + the gradient term the paper drops) on the GPU
+against the oracle's, through the C ABI: grid and nodal parameters, both element
+kernels, and the errors of the states it needs."""
+
+import numpy as np
+import pytest
+
+from oracle import fwi
+from sbfwi_inputs import tiny_workload, structured_mesh, boundary_nodes, ricker
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-8
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _oracle_full(w, rho, obs, rho_kind="grid"):
+    om = fwi.build_model(w.mesh, w.n_r, w.c, rho, w.dt, rho_kind=rho_kind)
+    to, store, _, su = fwi.forward(om, w.src_nodes, w.wavelets, w.rec_nodes, keep_u=True)
+    g = fwi.adjoint_gradient(om, store, obs - to, w.rec_nodes, store_u=su)
+    gv = fwi.adjoint_gradient(om, store, obs - to, w.rec_nodes)
+    return om, g, gv
+
+
+@pytest.mark.parametrize("element", ["tensor", "fp64"])
+@pytest.mark.parametrize("rho_kind", ["grid", "nodal"])
+def test_full_kernel_matches_the_oracle(lib, element, rho_kind):
+    w = tiny_workload(K=120)
+    wf = tiny_workload(refine=2, K=120)
+    mt = fwi.build_model(wf.mesh, wf.n_r, 1.0, wf.rho_true, w.dt)
+    obs, _, _ = fwi.forward(mt, wf.src_nodes, wf.wavelets, wf.rec_nodes, keep=False)
+    rho = w.rho_start * (1.0 + 0.2 * np.sin(np.linspace(0, 3, w.rho_start.size)).reshape(w.rho_start.shape))
+    om, go, gvo = _oracle_full(w, rho, obs)
+    if rho_kind == "nodal":
+        rho = np.asarray(om.rho_nodal, dtype=np.float64)
+        om, go, gvo = _oracle_full(w, rho, obs, "nodal")
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, rho, w.dt, rho_kind=lib.RHO_GRID if rho_kind == "grid" else lib.RHO_NODAL)
+    lib.set_schedule(md, lib.ELEMENT_TENSOR if element == "tensor" else lib.ELEMENT_FP64)
+    lib.set_kernel_terms(md, lib.TERMS_FULL)
+    tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+    _, res = lib.misfit(tr, obs, w.dt)
+    g = lib.adjoint_gradient(md, st, res)
+    if rho_kind == "grid":
+        go = fwi.gradient_to_grid(om, go, w.gx, w.gy)
+        gvo = fwi.gradient_to_grid(om, gvo, w.gx, w.gy)
+    assert rel(g, go) <= GRAD_TOL
+    assert rel(go, gvo) > 1e-3              # the gradient term is not negligible here
+
+
+def test_full_kernel_state_errors(lib):
+    w = tiny_workload(K=40)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_start, w.dt)
+    tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)          # velocities only
+    lib.set_kernel_terms(md, lib.TERMS_FULL)
+    with pytest.raises(lib.SbfwiError) as ei:
+        lib.adjoint_gradient(md, st, -tr)
+    assert ei.value.code == lib.ESTATE
+    with pytest.raises(lib.SbfwiError) as ei:
+        lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes, ckpt_every=5)
+    assert ei.value.code == lib.EUNSUPPORTED
+    with pytest.raises(lib.SbfwiError) as ei:
+        lib.set_kernel_terms(md, 5)
+    assert ei.value.code == lib.EINVAL
+    lib.set_kernel_terms(md, lib.TERMS_VELOCITY)
+    g = lib.adjoint_gradient(md, st, -tr)                                     # back to the paper's kernel
+    assert np.isfinite(g).all()
