@@ -184,9 +184,10 @@ def nodal_vector(model: Model, interior: list, boundary: np.ndarray) -> np.ndarr
     return out
 
 
-def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True):
+def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True, keep_u=False):
     """Traces (B, R, K), the nodal velocities after every step (if ``keep``) and the
-    final state; the conventions of ``oracle.fwi.forward``."""
+    final state; the conventions of ``oracle.fwi.forward`` (``keep_u``: the nodal
+    displacements of every step as a 4th result, for the full kernel)."""
     src_nodes = np.asarray(src_nodes)
     rec_nodes = np.asarray(rec_nodes)
     wavelets = np.atleast_2d(wavelets)
@@ -195,6 +196,7 @@ def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True):
     st = zero_state(model, B)
     traces = np.zeros((B, rec_nodes.size, K))
     store = np.zeros((K, model.n_int + model.n_nodes, B)) if keep else None
+    store_u = np.zeros((K, model.n_int + model.n_nodes, B)) if keep_u else None
     for k in range(K):
         f = np.zeros((model.n_nodes, B))
         for s in range(B):
@@ -203,16 +205,24 @@ def forward(model: Model, src_nodes, wavelets, rec_nodes, K=None, keep=True):
         traces[:, :, k] = st.ub[rec_nodes].T
         if keep:
             store[k] = nodal_vector(model, st.ud, st.udb)
+        if keep_u:
+            store_u[k] = nodal_vector(model, st.u, st.ub)
+    if keep_u:
+        return traces, store, st, store_u
     return traces, store, st
 
 
-def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_nodes):
+def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_nodes, store_u=None):
     """Time-reversed adjoint and zero-lag velocity correlation on the nodal points, the
-    conventions of ``oracle.fwi.adjoint_gradient`` (the gradient term dropped)."""
+    conventions of ``oracle.fwi.adjoint_gradient``; with ``store_u`` the full kernel's
+    gradient term too (``oracle.fwi.gradient_operator``, which takes each element's own
+    n_b)."""
     residual = np.asarray(residual)
     B, R, K = residual.shape
     st = zero_state(model, B)
-    g = np.zeros(model.n_int + model.n_nodes)
+    npt = model.n_int + model.n_nodes
+    g = np.zeros(npt)
+    G = fwi.gradient_operator(model) if store_u is not None else None
     for m in range(K):
         j = K - 1 - m
         f = np.zeros((model.n_nodes, B))
@@ -220,6 +230,10 @@ def adjoint_gradient(model: Model, store: np.ndarray, residual: np.ndarray, rec_
             np.add.at(f[:, s], rec_nodes, residual[s, :, j])
         st = step(model, st, f)
         g += model.dt * np.sum(store[j] * nodal_vector(model, st.ud, st.udb), axis=1)
+        if G is not None:
+            gu = (G @ store_u[j]).reshape(npt, 2, B)
+            gl = (G @ nodal_vector(model, st.u, st.ub)).reshape(npt, 2, B)
+            g += model.dt * model.c ** 2 * np.sum(gu * gl, axis=(1, 2))
     return g
 
 

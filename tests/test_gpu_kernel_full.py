@@ -69,3 +69,31 @@ def test_full_kernel_state_errors(lib):
     lib.set_kernel_terms(md, lib.TERMS_VELOCITY)
     g = lib.adjoint_gradient(md, st, -tr)                                     # back to the paper's kernel
     assert np.isfinite(g).all()
+
+
+@pytest.mark.parametrize("p", [3, 5])
+def test_full_kernel_on_uneven_meshes(lib, p):
+    """Quadtree meshes with hanging vertices (p = 3: n_b 12 and 15; p = 5 with a cell of
+    four finer neighbours: n_b 20..40, FP64 kernel): the padded layout's gradient operator
+    against the grouped oracle's."""
+    from oracle import uneven
+    from sbfwi_inputs import min_spacing, nearest_node, quadtree_mesh
+    if p == 3:
+        m = quadtree_mesh(4, 1, lambda x0, y0, x1, y1, lvl: x0 < 0.5 and y0 < 0.5, 3)
+    else:
+        m = quadtree_mesh(3, 1, lambda x0, y0, x1, y1, lvl: not (1 / 3 <= x0 < 0.5 and 1 / 3 <= y0 < 0.5), 5)
+    rho = 0.8 + 0.4 * np.random.default_rng(p).random((15, 15))
+    s = min_spacing(m)
+    dt, f0, K = 0.5 * s, 1.0 / (10 * s), 30
+    src = np.array([nearest_node(m, boundary_nodes(m, "top"), (0.4, 1.0))])
+    wav = ricker(f0, dt, K, t0=1.2 / f0)[None]
+    rec = boundary_nodes(m, "bottom")[::2]
+    om = uneven.build_model(m, 5, 1.0, rho, dt)
+    to, store, _, su = uneven.forward(om, src, wav, rec, keep_u=True)
+    go = uneven.gradient_to_grid(om, uneven.adjoint_gradient(om, store, -to, rec, store_u=su), 15, 15)
+    M = lib.Mesh.from_inputs(m, 5)
+    md = lib.Model(M, 1.0, rho, dt)
+    lib.set_kernel_terms(md, lib.TERMS_FULL)
+    tr, st = lib.forward(md, src, wav, rec)
+    g = lib.adjoint_gradient(md, st, -tr)
+    assert rel(g, go) <= GRAD_TOL
