@@ -925,6 +925,7 @@ int ensure_gradient_operator(const Mesh& m, cudaStream_t st) {
   if (d.grad_ready) return SBFWI_OK;
   const int n = m.n, nb = m.nb, p = m.p, pp = p + 1;
   const int64_t npt = m.n_nodal;
+  if (npt > INT32_MAX) return fail(SBFWI_EUNSUPPORTED, "the full kernel's gradient operator needs fewer than 2^31 nodal points");
   const double h = (1.0 - m.xi0) / n;
   std::vector<double> eta(pp), D((size_t)pp * pp, 0.0);    // D[k][a] = d phi_a / d eta at node k
   for (int k = 0; k < pp; ++k) eta[k] = -1.0 + 2.0 * k / p;
