@@ -163,6 +163,23 @@ void sbfwi_destroy_model(sbfwi_model* model);
  * or an unknown value.
  */
 /*
+ * sbfwi_lfe_element_matrices -- the element stiffness K and mass M of the paper's
+ * comparison method, the low-frequency expansion of the reduced element equation
+ * (Section 3.2: density constant along xi, S ~ K - omega^2 M): K from the Riccati
+ * equation (K - E1) E0^-1 (K - E1^T) - E2 = 0 (the solution whose modes are bounded at
+ * the scaling centre, with the constant mode), M from the Lyapunov equation
+ * (K - E1) E0^-1 M + M E0^-1 (K - E1^T) + 2 M - M0 = 0.
+ *   E0, E1, E2, M0  [n_b][n_b] host, row-major, the element's coefficient matrices
+ *                   (Eq. (Es)) for its density along the boundary
+ *   K, M            [n_b][n_b] host outputs
+ * Host computation in FP64 (matrix sign function for the Riccati subspace, dense
+ * solve for the Lyapunov equation); no device use.  Errors: SBFWI_EINVAL (NULL,
+ * n_b outside 2..40), SBFWI_ESINGULAR (a singular E0 or a failed iteration).
+ */
+int sbfwi_lfe_element_matrices(const double* E0, const double* E1, const double* E2, const double* M0,
+                               int32_t n_b, double* K, double* M);
+
+/*
  * sbfwi_set_kernel_terms -- which terms of the Frechet kernel (Section 2:
  * K_rho = int d_t lambda d_t u - c^2 grad lambda . grad u dt) later adjoint gradients
  * on `model` accumulate.

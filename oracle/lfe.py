@@ -108,3 +108,37 @@ def newmark(K, M, f, dt, beta=0.25, gamma=0.5, u0=None, v0=None):
         us.append(u.copy())
         vs.append(v.copy())
     return np.array(us), np.array(vs)
+
+
+def forward_and_gradient(mesh, c, rho_boundary_nodal, dt, src_nodes, wavelets, rec_nodes, observed, beta=0.25,
+                         gamma=0.5):
+    """The comparison method's misfit pipeline on the boundary nodes: Newmark traces of
+    every shot, E = 1/2 dt sum (d - u)^2, and the reversed-time adjoint (the same
+    symmetric pencil driven by the residuals, last sample first) correlated with the
+    forward velocities: g(node) = dt sum_m sum_shots u'_fwd[K-1-m] lambda'[m] (the
+    conventions of ``oracle.fwi``; the expansion has nodal points on the boundary only).
+    Returns (traces (B, R, K), E, g (n_nodes,))."""
+    K_, M_ = assemble(mesh, element_matrices(mesh, c, rho_boundary_nodal))
+    src_nodes, rec_nodes = np.asarray(src_nodes), np.asarray(rec_nodes)
+    wavelets = np.atleast_2d(wavelets)
+    B, K = wavelets.shape
+    N = mesh.n_nodes
+    traces = np.zeros((B, rec_nodes.size, K))
+    vel = np.zeros((B, K, N))
+    for s in range(B):
+        F = np.zeros((K, N))
+        F[:, src_nodes[s]] = wavelets[s]
+        us, vs = newmark(K_, M_, F, dt, beta, gamma)
+        traces[s] = us[:, rec_nodes].T
+        vel[s] = vs
+    res = np.asarray(observed, dtype=np.float64) - traces
+    E = 0.5 * dt * float(np.sum(res * res))
+    g = np.zeros(N)
+    for s in range(B):
+        F = np.zeros((K, N))
+        for m in range(K):
+            np.add.at(F[m], rec_nodes, res[s, :, K - 1 - m])
+        _, lv = newmark(K_, M_, F, dt, beta, gamma)
+        for m in range(K):
+            g += dt * vel[s, K - 1 - m] * lv[m]
+    return traces, E, g

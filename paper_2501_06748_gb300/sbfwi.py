@@ -65,6 +65,8 @@ def _load():
     lib.sbfwi_profile_solve_levels.restype = ctypes.c_int
     lib.sbfwi_release_cache.argtypes = []
     lib.sbfwi_release_cache.restype = ctypes.c_int
+    lib.sbfwi_lfe_element_matrices.argtypes = [pd, pd, pd, pd, I32, pd, pd]
+    lib.sbfwi_lfe_element_matrices.restype = ctypes.c_int
     lib.sbfwi_set_kernel_terms.argtypes = [VP, ctypes.c_int]
     lib.sbfwi_set_kernel_terms.restype = ctypes.c_int
     lib.sbfwi_set_schedule.argtypes = [VP, ctypes.c_int, ctypes.c_int]
@@ -305,6 +307,15 @@ def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
     _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
                                      arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
     return E_out, residual_out
+
+
+def lfe_element_matrices(E0, E1, E2, M0):
+    """(K, M) of the low-frequency expansion for one element's coefficient matrices (host)."""
+    mats = [np.ascontiguousarray(x, dtype=np.float64) for x in (E0, E1, E2, M0)]
+    nb = mats[0].shape[0]
+    K, M = np.empty((nb, nb)), np.empty((nb, nb))
+    _check(_lib.sbfwi_lfe_element_matrices(*(_dptr(x) for x in mats), nb, _dptr(K), _dptr(M)))
+    return K, M
 
 
 def set_kernel_terms(model: Model, terms: int = TERMS_VELOCITY) -> None:

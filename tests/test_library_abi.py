@@ -75,6 +75,32 @@ def test_voronoi_mesh_builds_with_its_elimination_tree(binding):
     assert 8 <= M.tree_levels <= 12 and M.factor_entries > 0
 
 
+def test_lfe_element_matrices_match_the_oracle(binding):
+    """The comparison method's element K (Riccati, by the matrix sign function) and M
+    (Lyapunov) computed by the library on the host agree with the oracle's (eigenvector
+    Riccati basis, dense Kronecker Lyapunov) on square, quadtree, Voronoi and n_b = 40
+    elements with a density that varies along the boundary."""
+    from oracle import lfe, sbfem
+    from sbfwi_inputs import quadtree_mesh, voronoi_mesh
+    meshes = [structured_mesh(2, 2, 2), quadtree_mesh(4, 1, lambda *a: a[0] < 0.5 and a[1] < 0.5, 3),
+              voronoi_mesh(30, 2, seed=1),
+              quadtree_mesh(3, 1, lambda x0, y0, x1, y1, lvl: not (1 / 3 <= x0 < 0.5 and 1 / 3 <= y0 < 0.5), 5)]
+    for m in meshes:
+        for el in sbfem.elements_from_mesh(m)[:4]:
+            nb = el.dofs.size
+            rho = np.tile((1 + 0.3 * np.random.default_rng(nb).random(nb)).astype(sbfem.XP), (2, 1))
+            E0, E1, E2, M0 = (np.asarray(q[-1], dtype=np.float64)
+                              for q in sbfem.coefficient_matrices(el, m.node_xy, m.p, 1.0, rho))
+            K, _ = lfe.riccati_stiffness(E0, E1, E2)
+            M = lfe.lyapunov_mass(K, E0, E1, M0)
+            K2, M2 = binding.lfe_element_matrices(E0, E1, E2, M0)
+            assert np.abs(K2 - K).max() <= 1e-12 * np.abs(K).max()
+            assert np.abs(M2 - M).max() <= 1e-12 * np.abs(M).max()
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.lfe_element_matrices(*(np.zeros((1, 1)),) * 4)
+    assert ei.value.code == binding.EINVAL
+
+
 def _bad(binding, **kw):
     m = structured_mesh(2, 2, 2)
     args = dict(node_xy=m.node_xy.copy(), elem_ptr=m.elem_ptr.copy(), line_nodes=m.line_nodes.copy(),
