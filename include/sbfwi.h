@@ -137,6 +137,22 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
 void sbfwi_destroy_model(sbfwi_model* model);
 
 /*
+ * sbfwi_set_model_lfe -- the same set-up for the paper's comparison method, the
+ * low-frequency expansion of the reduced equation (Section 3.2): the density is held
+ * constant along every radial line (its value at the element's boundary node), each
+ * element gets K (Riccati) and M (Lyapunov, sbfwi_lfe_element_matrices), and the global
+ * system sum_e K_e + M_e / (beta dt^2) is factorised.  Forward and adjoint passes on
+ * the model then step M u'' + K u = f with Newmark on the boundary nodes only (no radial
+ * interior); the gradient lives on the boundary nodes (interior nodal points get zero).
+ * Arguments and errors as sbfwi_set_model; SBFWI_ESINGULAR also when an element's
+ * Riccati or Lyapunov solve fails.  The full kernel (sbfwi_set_kernel_terms) does not
+ * apply (SBFWI_EUNSUPPORTED at the forward call).
+ */
+int sbfwi_set_model_lfe(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho,
+                        int rho_kind, int64_t gx, int64_t gy, double lx, double ly,
+                        double dt, double beta, double gamma, int mem, void* stream);
+
+/*
  * sbfwi_set_schedule -- how the time loops of later sbfwi_forward and
  * sbfwi_adjoint_gradient calls on `model` run.  Not part of the paper: a
  * performance choice between kernels that compute the same method (results agree

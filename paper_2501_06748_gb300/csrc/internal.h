@@ -162,6 +162,8 @@ struct Mesh {
 
 int build_tree(Mesh& m);
 int ensure_gradient_operator(const Mesh& m, cudaStream_t st);   // MeshDevice::grad_* (setup.cu)
+int lfe_element(const double* E0, const double* E1, const double* E2, const double* M0, int nb, double* K,
+                double* M);                                        // lfe.cpp
 
 // ---------------------------------------------------------------------------
 // model (device resident)
@@ -219,6 +221,8 @@ struct Model {
   // the same operators split into FP16 digits for the tensor-core element kernel
   DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
   bool tc_ready = false;
+  bool lfe = false;        // the comparison method (low-frequency expansion, sbfwi_set_model_lfe)
+  DevBuf lfe_M;            // its element masses [E][nb][nb]; S holds K + a0 M
   int kernel_terms = SBFWI_TERMS_VELOCITY;  // sbfwi_set_kernel_terms
   int elem_pref = SBFWI_ELEMENT_AUTO;     // sbfwi_set_schedule
   int solve_pref = SBFWI_SOLVE_AUTO;

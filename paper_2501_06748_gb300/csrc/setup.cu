@@ -197,6 +197,20 @@ __global__ void fill_kernel(double* x, int64_t n, double v) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) x[q] = v;
 }
 
+// comparison method: every interior nodal point takes the density of its boundary node
+// (the density constant along each radial line, Section 3.2)
+__global__ void radial_constant_density_kernel(double* rho_hi, double* rho_lo, const int32_t* dofs,
+                                               const int32_t* nbe, int64_t n_int, int n, int nb) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n_int; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / ((int64_t)n * nb);
+    const int j = (int)(q % nb);
+    if (j >= nbe[e]) continue;
+    const int64_t g = n_int + dofs[e * nb + j];
+    rho_hi[q] = rho_hi[g];
+    rho_lo[q] = rho_lo[g];
+  }
+}
+
 // lib[map[q]] = api[q]: nodal values from the caller's layout to the padded one
 __global__ void scatter_nodal_kernel(const double* api, const int64_t* map, int64_t n, double* lib) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
@@ -212,6 +226,7 @@ struct ElemArgs {
   const int32_t* nbe;         // [E] n_b of each element
   const int64_t* lptr;        // [E+1] first line of each element
   dd* mat_ws;                 // global workspace for the 16 matrices (nullptr: shared memory)
+  double* E_out;              // comparison method: E0, E1, E2, M0 of radial point 0 [E][4][nb][nb], then stop
   int64_t n_elem, n_int;
   double c;
   dd mass;                    // 1 / (beta dt^2)
@@ -475,6 +490,20 @@ __global__ void element_setup_kernel(ElemArgs a) {
   int s_prev = 0, s_cur = 1, s_next = 2;
   int w_cur = 0, w_next = 1;
   coefficient_matrices<DDOps>(a, sm, e, 0, E0w[s_cur], E1w[s_cur], E2w[w_cur], M0w[w_cur]);
+  if (a.E_out) {
+    // the comparison method needs only the coefficient matrices (with a density constant
+    // along xi they are the same at every radial point)
+    double* out = a.E_out + e * 4 * nns;
+    for (int t = tid; t < nn; t += nt) {
+      const int r = t / nb, cc = t - r * nb;
+      const int64_t to = (int64_t)r * nbs + cc;
+      out[to] = E0w[s_cur][t].hi;
+      out[nns + to] = E1w[s_cur][t].hi;
+      out[2 * nns + to] = E2w[w_cur][t].hi;
+      out[3 * nns + to] = M0w[w_cur][t].hi;
+    }
+    return;
+  }
   coefficient_matrices<DDOps>(a, sm, e, 1, E0w[s_next], E1w[s_next], E2w[w_next], M0w[w_next]);
 
   for (int i = 0; i <= n; ++i) {
@@ -1067,6 +1096,14 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   SBFWI_CUDA(md.rho_nodal.alloc(sizeof(double) * np));
   SBFWI_CUDA(cudaMemcpyAsync(md.rho_nodal.p, rho_hi.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
 
+  if (md.lfe) {
+    const unsigned blocks = (unsigned)std::min<int64_t>((m.n_int + 255) / 256, 152 * 8);
+    radial_constant_density_kernel<<<blocks, 256, 0, st>>>(rho_hi.as<double>(), rho_lo.as<double>(),
+                                                           d.dofs.as<int32_t>(), d.nbe.as<int32_t>(), m.n_int, n, nb);
+    prof.count(kPhaseSetup);
+    SBFWI_CUDA(cudaGetLastError());
+  }
+
   // element set-up
   const int64_t nn = (int64_t)nb * nb;
   SBFWI_CUDA(md.mats.alloc(sizeof(double) * E * n * 3 * nn));
@@ -1081,6 +1118,13 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     ElemArgs a;
     a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
     a.nbe = d.nbe.as<int32_t>(); a.lptr = d.lptr.as<int64_t>(); a.mat_ws = nullptr; a.e0 = 0;
+    DevBuf E_dev;
+    a.E_out = nullptr;
+    if (md.lfe) {
+      SBFWI_CUDA(E_dev.alloc(sizeof(double) * E * 4 * nn));
+      SBFWI_CUDA(cudaMemsetAsync(E_dev.p, 0, E_dev.bytes, st));
+      a.E_out = E_dev.as<double>();
+    }
     a.c = md.c;
     a.mass = dd_div(dd_make(1.0), dd_mul(dd_make(md.beta), two_prod(md.dt, md.dt)));
     a.h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
@@ -1113,10 +1157,37 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
       SBFWI_CUDA(cudaGetLastError());
     }
     if (!in_smem) SBFWI_CUDA(cudaStreamSynchronize(st));   // the workspace is freed on return
+    if (md.lfe) {
+      // the comparison method's K and M per element on the host; S = K + a0 M for the global
+      // system, M for the per-step effective sources
+      std::vector<double> Eh((size_t)E * 4 * nn), Sh((size_t)E * nn, 0.0), Mh((size_t)E * nn, 0.0);
+      SBFWI_CUDA(cudaMemcpyAsync(Eh.data(), E_dev.p, sizeof(double) * Eh.size(), cudaMemcpyDeviceToHost, st));
+      SBFWI_CUDA(cudaStreamSynchronize(st));
+      for (int64_t e = 0; e < E; ++e) {
+        const int ne = m.nbe[e];
+        std::vector<double> blk(4 * (size_t)ne * ne), K((size_t)ne * ne), M((size_t)ne * ne);
+        for (int k = 0; k < 4; ++k)
+          for (int r = 0; r < ne; ++r)
+            for (int c = 0; c < ne; ++c)
+              blk[(size_t)k * ne * ne + r * ne + c] = Eh[(size_t)(e * 4 + k) * nn + (size_t)r * nb + c];
+        int rc_l = lfe_element(blk.data(), blk.data() + ne * ne, blk.data() + 2 * ne * ne, blk.data() + 3 * ne * ne,
+                               ne, K.data(), M.data());
+        if (rc_l) return rc_l;
+        for (int r = 0; r < ne; ++r)
+          for (int c = 0; c < ne; ++c) {
+            Sh[(size_t)e * nn + (size_t)r * nb + c] = K[(size_t)r * ne + c] + md.a0 * M[(size_t)r * ne + c];
+            Mh[(size_t)e * nn + (size_t)r * nb + c] = M[(size_t)r * ne + c];
+          }
+      }
+      int rc_u;
+      if ((rc_u = upload(md.lfe_M, Mh, st))) return rc_u;
+      SBFWI_CUDA(cudaMemcpyAsync(md.S.p, Sh.data(), sizeof(double) * Sh.size(), cudaMemcpyHostToDevice, st));
+      SBFWI_CUDA(cudaStreamSynchronize(st));
+    }
   }
 
   // the per-step operators split for the tensor cores
-  if (tc_supported(nb, 1) && (rc = tc_prepare(md, st))) return rc;
+  if (!md.lfe && tc_supported(nb, 1) && (rc = tc_prepare(md, st))) return rc;
 
   // global factorisation along the elimination tree
   const Tree& t = m.tree;

@@ -672,6 +672,26 @@ __global__ void sum_shots_kernel(const double* acc, int64_t np, int B, double dt
   }
 }
 
+// Comparison method (low-frequency expansion): the effective source of every element for
+// the next step, f_hat_e = M_e (a0 u + a1 u' + a2 u'') at its boundary nodes, so that the
+// global system (sum of K_e + a0 M_e) u = f + sum f_hat_e is Newmark on M u'' + K u = f.
+__global__ void lfe_source_kernel(const double* M, const int32_t* dofs, const double* ub, const double* udb,
+                                  const double* uddb, int64_t E, int nb, int B, double a0, double a1, double a2,
+                                  double* fhat) {
+  const int64_t tot = E * nb * B;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = t / ((int64_t)nb * B);
+    const int r = (int)((t / B) % nb), s = (int)(t % B);
+    const double* Mr = M + (e * nb + r) * (int64_t)nb;
+    double acc = 0.0;
+    for (int c = 0; c < nb; ++c) {
+      const int64_t g = (int64_t)dofs[e * nb + c] * B + s;
+      acc = fma(Mr[c], fma(a0, ub[g], fma(a1, udb[g], a2 * uddb[g])), acc);
+    }
+    fhat[t] = acc;
+  }
+}
+
 // out[q] (+)= lib[map[q]]: nodal values from the padded layout to the caller's
 // Gradient term of the full Frechet kernel at one adjoint step, for every nodal point q and
 // shot s: grad[q][s] += c^2 (G u_fwd)(q, s) . (G lambda)(q, s), G the nodal gradient operator
@@ -1009,7 +1029,9 @@ int Stepper::init() {
   // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
   // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
   const char* elem_env = std::getenv("SBFWI_ELEMENT");
-  if (md.elem_pref == SBFWI_ELEMENT_TENSOR) {
+  if (md.lfe) {
+    use_tc = false;                  // the comparison method has no radial interior
+  } else if (md.elem_pref == SBFWI_ELEMENT_TENSOR) {
     if (!tc_available(nb, B))
       return fail(SBFWI_EUNSUPPORTED, "no tensor-core element kernel for this n_b and shot count");
     use_tc = true;
@@ -1079,9 +1101,9 @@ int Stepper::init() {
   e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
   cudaFuncAttributes eattr;
   SBFWI_CUDA(cudaFuncGetAttributes(&eattr, element_step_kernel));
-  if (!use_tc && (e_threads > eattr.maxThreadsPerBlock || e_smem > 227 * 1024))
+  if (!use_tc && !md.lfe && (e_threads > eattr.maxThreadsPerBlock || e_smem > 227 * 1024))
     return fail(SBFWI_EUNSUPPORTED, "n_b x shots x radial points too large for one element block: run fewer shots per pass");
-  if (e_smem > 48 * 1024)
+  if (e_smem > 48 * 1024 && !md.lfe)
     SBFWI_CUDA(cudaFuncSetAttribute(element_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e_smem));
 
   const MeshDevice& mdev = md.dev();
@@ -1250,6 +1272,19 @@ int Stepper::restore_state(const double* src) {
 int Stepper::element_launch(int down, int up, int64_t done_step) {
   // done_step: the step whose back-substitution runs in this launch (if down)
   Profiler& prof = profiler();
+  if (md.lfe) {                      // comparison method: only the effective sources of the next step
+    if (up) {
+      prof.begin(kPhaseElement, st);
+      const int64_t tot = E * nb * B;
+      const unsigned blocks = (unsigned)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+      lfe_source_kernel<<<blocks, 256, 0, st>>>(md.lfe_M.as<double>(), md.dev().dofs.as<int32_t>(), rb.ub.as<double>(),
+                                                 rb.udb.as<double>(), rb.uddb.as<double>(), E, nb, B, md.a0, md.a1,
+                                                 md.a2, rb.fhat.as<double>());
+      prof.end(kPhaseElement, st);
+      prof.count(kPhaseElement);
+    }
+    return SBFWI_OK;
+  }
   ea.do_down = down; ea.do_up = up;
   ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr; ea.u_out = nullptr;
   if (down && mode == Mode::Forward && store) ea.store_int = store + (done_step - store_k0) * np * B;
@@ -1385,9 +1420,25 @@ using namespace sbfwi;
 
 extern "C" {
 
+static int set_model_impl(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
+                          int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
+                          void* stream, bool lfe);
+
 int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
                     int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
                     void* stream) {
+  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, lx, ly, dt, beta, gamma, mem, stream, false);
+}
+
+int sbfwi_set_model_lfe(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
+                        int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
+                        void* stream) {
+  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, lx, ly, dt, beta, gamma, mem, stream, true);
+}
+
+static int set_model_impl(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
+                          int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
+                          void* stream, bool lfe) {
   if (!out) return fail(SBFWI_EINVAL, "out is NULL");
   *out = nullptr;
   if (!mesh || !rho) return fail(SBFWI_EINVAL, "NULL argument");
@@ -1406,6 +1457,7 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
   md->c1 = dt * (1.0 - gamma);
   md->c2 = dt * gamma;
   md->rho_kind = rho_kind; md->gx = gx; md->gy = gy; md->lx = lx; md->ly = ly;
+  md->lfe = lfe;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = setup_model(*md, *mesh, rho, mem, st);
   if (rc == SBFWI_OK) {
@@ -1495,6 +1547,8 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
       c = (int64_t)std::ceil(std::sqrt((double)K * (double)sd / ((double)np * B)));
     }
     c = std::min<int64_t>(c, K);
+    if (md->kernel_terms == SBFWI_TERMS_FULL && md->lfe)
+      return fail(SBFWI_EUNSUPPORTED, "the comparison method has no radial field for the full kernel's gradient term");
     if (md->kernel_terms == SBFWI_TERMS_FULL && c != 0)
       return fail(SBFWI_EUNSUPPORTED, "the full Frechet kernel needs the stored forward field (ckpt_every = 0)");
     fs->ckpt_every = c;

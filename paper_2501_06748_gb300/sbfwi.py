@@ -50,6 +50,8 @@ def _load():
     lib.sbfwi_destroy_mesh.argtypes = [VP]
     lib.sbfwi_destroy_mesh.restype = None
     lib.sbfwi_set_model.argtypes = [P(VP), VP, D, VP, ctypes.c_int, I64, I64, D, D, D, D, D, ctypes.c_int, VP]
+    lib.sbfwi_set_model_lfe.argtypes = lib.sbfwi_set_model.argtypes
+    lib.sbfwi_set_model_lfe.restype = ctypes.c_int
     lib.sbfwi_destroy_model.argtypes = [VP]
     lib.sbfwi_destroy_model.restype = None
     lib.sbfwi_forward.argtypes = [VP, I32, pi64, VP, I32, pi64, I64, VP, P(VP), I64, ctypes.c_int, VP]
@@ -196,11 +198,14 @@ class Mesh:
 
 
 class Model:
-    def __init__(self, mesh: Mesh, c, rho, dt, beta=0.25, gamma=0.5, rho_kind=RHO_GRID, lx=1.0, ly=1.0):
+    def __init__(self, mesh: Mesh, c, rho, dt, beta=0.25, gamma=0.5, rho_kind=RHO_GRID, lx=1.0, ly=1.0, lfe=False):
+        """``lfe=True``: the paper's comparison method (low-frequency expansion) instead of
+        the radial finite differences."""
         r = _Arr(rho)
         gy, gx = (r.obj.shape if rho_kind == RHO_GRID else (0, 0))
         h = ctypes.c_void_p()
-        _check(_lib.sbfwi_set_model(ctypes.byref(h), mesh._h, float(c), r.ptr, int(rho_kind), int(gx), int(gy),
+        setup = _lib.sbfwi_set_model_lfe if lfe else _lib.sbfwi_set_model
+        _check(setup(ctypes.byref(h), mesh._h, float(c), r.ptr, int(rho_kind), int(gx), int(gy),
                                     float(lx), float(ly), float(dt), float(beta), float(gamma), r.mem, r.stream))
         self._h = h
         self.mesh = mesh                 # keeps the mesh alive for the model's lifetime
