@@ -86,7 +86,7 @@ sys.path.insert(0, {root!r})
 import numpy as np
 from sbfwi_inputs import size_workload
 from oracle import fwi
-w = size_workload(nx={nx}, K={K})
+w = size_workload(nx={nx}, K={K}, n_shots={ns})
 lo, hi = {lo}, {hi}
 w.src_nodes, w.wavelets = w.src_nodes[lo:hi], w.wavelets[lo:hi]
 wall0 = time.time()
@@ -97,14 +97,18 @@ E, res = fwi.misfit(tr, np.zeros_like(tr), w.dt)
 g = fwi.gradient_to_grid(om, fwi.adjoint_gradient(om, store, res, w.rec_nodes), w.gx, w.gy)
 t1 = time.perf_counter()
 units = w.mesh.n_elem * w.n_r * w.K * w.n_shots
+if {save!r}:
+    np.savez({save!r}, traces=tr, grad=g, misfit=E)
 print(json.dumps({{"seconds": t1 - t0, "units": units, "wall0": wall0, "wall1": time.time()}}))
 """
 
 
-def run_oracle_sample(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
-    """The oracle as it stands, single-threaded, in a fresh process (never forked from CUDA)."""
+def run_oracle_sample(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K, save=""):
+    """The oracle as it stands, single-threaded, in a fresh process (never forked from CUDA).
+    With `save`, the sample's traces, gradient and misfit are written there (npz) for the
+    accuracy check of the GPU path on the same inputs."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = _CPU_CODE.format(root=ROOT, nx=nx, K=K, lo=0, hi=8)
+    code = _CPU_CODE.format(root=ROOT, nx=nx, K=K, ns=8, lo=0, hi=8, save=save)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
@@ -114,16 +118,32 @@ def run_oracle_sample(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
     return r["units"] / r["seconds"], r["seconds"], sample
 
 
+def host_cpu():
+    """Core count and CPU model of this host (lscpu's model name, else the platform's)."""
+    import platform
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model or platform.processor() or platform.machine()}
+
+
 def run_oracle_sample_all_cores(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
-    """The same sample on several host cores: the 8 shots split over concurrent fresh
-    single-threaded processes (one shot each, up to the core count), each with its own
-    set-up; the rate is all processes' units over the wall time of the slowest."""
+    """The same recipe on every host core: one fresh single-threaded oracle process per core,
+    each running one shot (its own set-up) of a version of the sample with one top-edge
+    source per core; the rate is all processes' units over the wall time from the first
+    set-up to the last end."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    procs_n = max(1, min(8, os.cpu_count() or 1))
-    bounds = [(k * 8 // procs_n, (k + 1) * 8 // procs_n) for k in range(procs_n)]
-    procs = [subprocess.Popen([sys.executable, "-c", _CPU_CODE.format(root=ROOT, nx=nx, K=K, lo=lo, hi=hi)],
+    procs_n = max(1, min(4 * nx, os.cpu_count() or 1))      # distinct top-edge nodes of the sub-mesh
+    procs = [subprocess.Popen([sys.executable, "-c", _CPU_CODE.format(root=ROOT, nx=nx, K=K, ns=procs_n, lo=k,
+                                                                      hi=k + 1, save="")],
                               env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
-             for lo, hi in bounds]
+             for k in range(procs_n)]
     units, starts, ends = 0, [], []
     for p in procs:
         out, err = p.communicate(timeout=900)
@@ -134,9 +154,37 @@ def run_oracle_sample_all_cores(nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
         starts.append(r["wall0"])
         ends.append(r["wall1"])
     wall = max(ends) - min(starts)        # from the first process's set-up to the last one's end
-    sample = (f"the single-core sample's 8 shots split over {procs_n} concurrent single-threaded oracle "
-              f"processes (set-up repeated in each)")
+    sample = (f"{procs_n} concurrent single-threaded oracle processes, one shot each (set-up repeated in each), "
+              f"of the single-core sample's recipe with {procs_n} top-edge sources")
     return units / wall, wall, procs_n, sample
+
+
+TRACE_TOL, GRAD_TOL = 1e-10, 1e-8
+
+
+def accuracy_check(lib, dev, oracle_npz, nx=CPU_SAMPLE_NX, K=CPU_SAMPLE_K):
+    """The GPU path on the oracle sample's inputs (the same sub-mesh, shots, steps and
+    starting model; one pass of 8 shots with the default kernels, as in the timed step):
+    relative L2 error of traces, misfit and gradient against the oracle's."""
+    import torch
+    from sbfwi_inputs import size_workload
+    ref = np.load(oracle_npz)
+    w = size_workload(nx=nx, K=K, n_shots=8)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, torch.tensor(w.rho_start, device=dev), w.dt)
+    tr, st = lib.forward(md, w.src_nodes, torch.tensor(w.wavelets, device=dev), w.rec_nodes)
+    E, res = lib.misfit(tr, torch.zeros_like(tr), w.dt)
+    g = lib.adjoint_gradient(md, st, res)
+    torch.cuda.synchronize()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    e_tr = rel(tr.cpu().numpy(), ref["traces"])
+    e_g = rel(g.cpu().numpy(), ref["grad"])
+    e_E = abs(E - float(ref["misfit"])) / abs(float(ref["misfit"]))
+    return {"traces_rel_l2": e_tr, "grad_rel_l2": e_g, "misfit_rel": e_E,
+            "tol": {"traces": TRACE_TOL, "grad": GRAD_TOL}, "within_tol": bool(e_tr <= TRACE_TOL and e_g <= GRAD_TOL),
+            "steps": K, "sample": f"GPU path vs the oracle on the cpu_baseline sample: {nx}x{nx} sub-mesh of the "
+                                  f"same recipe (p=4, N_r=32), 8 shots in one pass, {K} Newmark steps, set-up + "
+                                  "forward + misfit + adjoint + gradient"}
 
 
 # ---------------------------------------------------------------------------
@@ -374,13 +422,18 @@ def run_ours(args, rank, world):
 
     if rank != 0:
         return None
-    cpu = cpu_all = None
+    cpu = cpu_all = accuracy = None
     if not args.no_cpu_baseline:
-        rate, secs, sample = run_oracle_sample()
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs}
+        hc = host_cpu()
+        save = os.path.join(tempfile.mkdtemp(prefix="sbfwi_acc_"), "oracle_sample.npz")
+        rate, secs, sample = run_oracle_sample(save=save)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs,
+               "host_nproc": hc["nproc"], "cpu_model": hc["cpu_model"]}
         rate_all, wall_all, cores_all, sample_all = run_oracle_sample_all_cores()
         cpu_all = {"value": rate_all, "unit": UNIT, "cores": cores_all, "kind": "oracle", "sample": sample_all,
-                   "seconds": wall_all}
+                   "seconds": wall_all, "host_nproc": hc["nproc"], "cpu_model": hc["cpu_model"]}
+        if not diff:
+            accuracy = accuracy_check(lib, dev, save)
     lat = np.array(per_step)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -400,6 +453,7 @@ def run_ours(args, rank, world):
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "per_step": [float(x) for x in per_step]},
         "phases_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "accuracy": accuracy,
         "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e, "one_shot_path": one_shot, "gpu_launches": int(launches),
         "clocks": clk,
     }
@@ -659,11 +713,13 @@ def run_reference(args, rank, world):
         rates.append(r)
         secs.append(s)
     value = float(np.sum([r * s for r, s in zip(rates, secs)]) / np.sum(secs))
+    hc = host_cpu()
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "size recipe (p=4, N_r=32, 8 shots), bounded sample: " + sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host_nproc": hc["nproc"], "cpu_model": hc["cpu_model"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

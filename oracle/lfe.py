@@ -63,10 +63,12 @@ def lyapunov_mass(K, E0, E1, M0):
 # The low-frequency-expansion time loop (the paper's comparison method)
 # ----------------------------------------------------------------------------
 
-def element_matrices(mesh, c, rho_boundary_nodal, xi0=1e-3):
+def element_matrices(mesh, c, rho_boundary_nodal, xi0=1e-3, rho_mass=None):
     """K_e, M_e of every element with its density taken constant along xi (the values at
     its boundary nodes, Section 3.2): E0..M0 at xi = 1 (any xi: they do not depend on it
-    then) -> Riccati K, Lyapunov M."""
+    then) -> Riccati K, Lyapunov M.  ``rho_mass`` (tests only) gives M0 its own boundary
+    densities while E0, E1, E2 keep ``rho_boundary_nodal``: the density of the inertia
+    term alone."""
     from . import sbfem
     els = sbfem.elements_from_mesh(mesh)
     out = []
@@ -74,6 +76,9 @@ def element_matrices(mesh, c, rho_boundary_nodal, xi0=1e-3):
         rho = np.tile(np.asarray(rho_boundary_nodal, dtype=sbfem.XP)[el.dofs], (2, 1))
         E0, E1, E2, M0 = (np.asarray(q[-1], dtype=np.float64)
                           for q in sbfem.coefficient_matrices(el, mesh.node_xy, mesh.p, c, rho))
+        if rho_mass is not None:
+            rm = np.tile(np.asarray(rho_mass, dtype=sbfem.XP)[el.dofs], (2, 1))
+            M0 = np.asarray(sbfem.coefficient_matrices(el, mesh.node_xy, mesh.p, c, rm)[3][-1], dtype=np.float64)
         K, _ = riccati_stiffness(E0, E1, E2)
         out.append((el.dofs, K, lyapunov_mass(K, E0, E1, M0)))
     return out
@@ -111,14 +116,23 @@ def newmark(K, M, f, dt, beta=0.25, gamma=0.5, u0=None, v0=None):
 
 
 def forward_and_gradient(mesh, c, rho_boundary_nodal, dt, src_nodes, wavelets, rec_nodes, observed, beta=0.25,
-                         gamma=0.5):
+                         gamma=0.5, rho_mass=None, fields=False):
     """The comparison method's misfit pipeline on the boundary nodes: Newmark traces of
     every shot, E = 1/2 dt sum (d - u)^2, and the reversed-time adjoint (the same
     symmetric pencil driven by the residuals, last sample first) correlated with the
     forward velocities: g(node) = dt sum_m sum_shots u'_fwd[K-1-m] lambda'[m] (the
     conventions of ``oracle.fwi``; the expansion has nodal points on the boundary only).
-    Returns (traces (B, R, K), E, g (n_nodes,))."""
-    K_, M_ = assemble(mesh, element_matrices(mesh, c, rho_boundary_nodal))
+    ``rho_mass`` as in ``element_matrices``.  Returns (traces (B, R, K), E, g (n_nodes,)),
+    and with ``fields`` also the forward velocities (B, K, N) after every step and the
+    adjoint velocities (B, K, N) after every adjoint step.
+
+    The nodal product is the paper's convention (Section 4: the fields at the nodal points
+    used directly).  The exact derivative of E with respect to the density of the inertia
+    term is the consistent form dt sum_m u'_fwd[K-1-m]^T (dM/drho_j) lambda'[m] of the same
+    fields (pinned by finite differences in the tests); with only boundary nodes, whose
+    density sets the mass of a whole sector of the element, the nodal product is a coarse
+    stand-in for it."""
+    K_, M_ = assemble(mesh, element_matrices(mesh, c, rho_boundary_nodal, rho_mass=rho_mass))
     src_nodes, rec_nodes = np.asarray(src_nodes), np.asarray(rec_nodes)
     wavelets = np.atleast_2d(wavelets)
     B, K = wavelets.shape
@@ -134,11 +148,15 @@ def forward_and_gradient(mesh, c, rho_boundary_nodal, dt, src_nodes, wavelets, r
     res = np.asarray(observed, dtype=np.float64) - traces
     E = 0.5 * dt * float(np.sum(res * res))
     g = np.zeros(N)
+    lvel = np.zeros((B, K, N))
     for s in range(B):
         F = np.zeros((K, N))
         for m in range(K):
             np.add.at(F[m], rec_nodes, res[s, :, K - 1 - m])
         _, lv = newmark(K_, M_, F, dt, beta, gamma)
+        lvel[s] = lv
         for m in range(K):
             g += dt * vel[s, K - 1 - m] * lv[m]
+    if fields:
+        return traces, E, g, vel, lvel
     return traces, E, g

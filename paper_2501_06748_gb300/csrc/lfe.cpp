@@ -16,10 +16,20 @@
 // iteration X <- (c X + (c X)^-1) / 2 (Roberts' method); the shift sigma = 1/2 moves the
 // zero pair to the right half-plane while the stable eigenvalues, whose real parts are
 // at most -1 for these operators (the linear fields u ~ xi x, xi y give -1), stay left.
-// Lyapunov: one dense linear system in the n_b^2 entries of M.  Host code, FP64: this is
+// The projector's rank must be n_b - 1 (the stable eigenvalues, the constant mode's pair
+// being shifted to the right): its trace and the pivoted Gram-Schmidt basis are checked,
+// and an element whose spectrum does not split that way is refused (SBFWI_ESINGULAR)
+// rather than given a wrong subspace.
+// Lyapunov: with F = (K - E1) E0^-1 + I and G = E0^-1 (K - E1^T) + I the equation reads
+// F M + M G = M0.  G's eigenvalues are 1 + the exponents lambda >= 0 of the bounded modes
+// u ~ xi^lambda (G u = (1 + lambda) u, since xi u_xi = E0^-1 (K - E1^T) u on them), and F
+// shares them, so both spectra lie at or right of 1 and M = C_inf / 2 from the coupled
+// Newton sign iteration F <- (F + F^-1)/2, G <- (G + G^-1)/2, C <- (C + F^-1 C G^-1)/2
+// (Roberts' method for Sylvester equations), O(n_b^3) per step.  Host code, FP64: this is
 // per-model set-up of the comparison method, not part of the time loop.
 #include <algorithm>
 #include <cmath>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -142,12 +152,18 @@ int lfe_element(const double* E0, const double* E1, const double* E2, const doub
   std::vector<double> P((size_t)n2 * n2);
   for (int r = 0; r < n2; ++r)
     for (int c = 0; c < n2; ++c) P[(size_t)r * n2 + c] = 0.5 * ((r == c ? 1.0 : 0.0) - X[(size_t)r * n2 + c]);
+  double trace = 0.0;
+  for (int k = 0; k < n2; ++k) trace += P[(size_t)k * n2 + k];
+  if (std::fabs(trace - (n - 1)) > 0.25)
+    return fail(SBFWI_ESINGULAR, "an element's stable subspace has dimension " + std::to_string(trace) +
+                                     " instead of n_b - 1 = " + std::to_string(n - 1));
   std::vector<std::vector<double>> cols(n2, std::vector<double>(n2));
   for (int c = 0; c < n2; ++c)
     for (int r = 0; r < n2; ++r) cols[c][r] = P[(size_t)r * n2 + c];
   std::vector<std::vector<double>> basis;
   std::vector<bool> used(n2, false);
-  for (int k = 0; k < n - 1; ++k) {
+  double first = 0.0;
+  for (int k = 0; k < n; ++k) {
     int best = -1;
     double bn = 0.0;
     for (int c = 0; c < n2; ++c) {
@@ -156,7 +172,13 @@ int lfe_element(const double* E0, const double* E1, const double* E2, const doub
       for (int r = 0; r < n2; ++r) s += cols[c][r] * cols[c][r];
       if (s > bn) { bn = s; best = c; }
     }
-    if (best < 0 || !(bn > 0.0)) return fail(SBFWI_ESINGULAR, "an element's stable subspace is degenerate");
+    if (k == n - 1) {
+      // every column is now orthogonal to a basis of the whole range: what remains is rounding
+      if (bn > 1e-16 * first) return fail(SBFWI_ESINGULAR, "an element's stable subspace is not of rank n_b - 1");
+      break;
+    }
+    if (best < 0 || !(bn > 1e-16 * first)) return fail(SBFWI_ESINGULAR, "an element's stable subspace is degenerate");
+    if (k == 0) first = bn;
     used[best] = true;
     std::vector<double> q = cols[best];
     const double inv = 1.0 / std::sqrt(bn);
@@ -178,28 +200,34 @@ int lfe_element(const double* E0, const double* E1, const double* E2, const doub
   std::vector<double> Qui;
   if (!inverse(Qu, Qui, n)) return fail(SBFWI_ESINGULAR, "an element's Riccati basis is singular");
   const std::vector<double> K = matmul(Qq, Qui, n, n, n);
-  // Lyapunov: (A (x) I + I (x) B^T + 2 I) vec(M) = vec(M0), A = (K - E1) E0^-1, B = E0^-1 (K - E1^T)
+  // Lyapunov: F M + M G = M0 with F = (K - E1) E0^-1 + I, G = E0^-1 (K - E1^T) + I
   std::vector<double> kme1((size_t)n * n), kme1t((size_t)n * n);
   for (size_t t = 0; t < kme1.size(); ++t) { kme1[t] = K[t] - e1[t]; kme1t[t] = K[t] - e1t[t]; }
-  const std::vector<double> A = matmul(kme1, e0i, n, n, n);
-  const std::vector<double> Bm = matmul(e0i, kme1t, n, n, n);
-  const int nn = n * n;
-  std::vector<double> L((size_t)nn * nn, 0.0);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      const int row = i * n + j;
-      for (int k = 0; k < n; ++k) {
-        L[(size_t)row * nn + k * n + j] += A[(size_t)i * n + k];     // (A M)[i][j]
-        L[(size_t)row * nn + i * n + k] += Bm[(size_t)k * n + j];    // (M B)[i][j]
-      }
-      L[(size_t)row * nn + row] += 2.0;
+  std::vector<double> F = matmul(kme1, e0i, n, n, n);
+  std::vector<double> G = matmul(e0i, kme1t, n, n, n);
+  for (int k = 0; k < n; ++k) { F[(size_t)k * n + k] += 1.0; G[(size_t)k * n + k] += 1.0; }
+  std::vector<double> C(M0, M0 + (size_t)n * n), Fi, Gi;
+  converged = false;
+  for (int it = 0; it < 100; ++it) {
+    double logdet = 0.0;
+    if (!inverse(F, Fi, n, &logdet) || !inverse(G, Gi, n))
+      return fail(SBFWI_ESINGULAR, "the sign iteration of an element's Lyapunov equation met a singular matrix");
+    const double cs = it < 8 ? std::exp(-logdet / n) : 1.0;
+    const std::vector<double> FCG = matmul(matmul(Fi, C, n, n, n), Gi, n, n, n);
+    double diff = 0.0, norm = 0.0;
+    for (size_t t = 0; t < F.size(); ++t) {
+      const double nf = 0.5 * (cs * F[t] + Fi[t] / cs);
+      diff = std::max(diff, std::fabs(nf - F[t]));
+      norm = std::max(norm, std::fabs(nf));
+      F[t] = nf;
+      G[t] = 0.5 * (cs * G[t] + Gi[t] / cs);
+      C[t] = 0.5 * (cs * C[t] + FCG[t] / cs);
     }
-  std::vector<int> piv;
-  if (!lu_factor(L, piv, nn)) return fail(SBFWI_ESINGULAR, "an element's Lyapunov system is singular");
-  std::vector<double> m(M0, M0 + (size_t)nn);
-  lu_solve(L, piv, nn, m.data());
+    if (diff <= 1e-14 * norm) { converged = true; break; }
+  }
+  if (!converged) return fail(SBFWI_ESINGULAR, "the sign iteration of an element's Lyapunov equation did not converge");
   std::copy(K.begin(), K.end(), Kout);
-  std::copy(m.begin(), m.end(), Mout);
+  for (size_t t = 0; t < C.size(); ++t) Mout[t] = 0.5 * C[t];
   return SBFWI_OK;
 }
 

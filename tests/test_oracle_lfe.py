@@ -137,3 +137,44 @@ def test_fd_traces_approach_the_lfe_traces_at_low_frequency():
     assert err[(0.2, 5)] > err[(0.2, 9)] > err[(0.2, 17)]
     assert err[(0.2, 17)] < 0.05
     assert err[(0.4, 17)] > 3 * err[(0.2, 17)]
+
+
+def test_lfe_adjoint_fields_give_the_exact_inertia_derivative():
+    """The comparison method's gradient correlates forward and time-reversed adjoint
+    velocities.  Its consistent form, dt sum_m u'_fwd[K-1-m]^T (dM/drho) lambda'[m] with
+    dM/drho the Lyapunov mass's derivative along a direction of the inertia density (M is
+    linear in that density when K is held), must equal the central finite difference of the
+    misfit along that direction: this pins the adjoint's source, sign and time pairing.
+    The paper's nodal product (each boundary node's own velocities, weighted by the mass it
+    carries) is a lumped stand-in for that form: on this 4 x 4 order-2 plate it differs
+    from the exact derivative by 20-100 % along a direction (the boundary nodes' densities
+    each set the mass of a whole sector of an element), which is recorded, not asserted
+    beyond the sign of the smooth direction."""
+    from sbfwi_inputs import boundary_nodes, ricker
+    m = structured_mesh(4, 4, 2)
+    N = m.n_nodes
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * m.node_xy[:, 0]) * np.cos(np.pi * m.node_xy[:, 1])
+    top = boundary_nodes(m, "top")
+    src = [int(top[len(top) // 2])]
+    recs = np.unique(np.concatenate([boundary_nodes(m, s) for s in ("bottom", "left", "right")]))[::3]
+    dt, K = 0.0625, 96
+    wav = ricker(0.8, dt, K)[None]
+    obs = np.zeros((1, len(recs), K))
+    _, E, g, vel, lvel = lfe.forward_and_gradient(m, 1.0, rho, dt, src, wav, recs, obs, fields=True)
+    C = sum(dt * np.outer(vel[0, K - 1 - k], lvel[0, k]) for k in range(K))
+    _, M0 = lfe.assemble(m, lfe.element_matrices(m, 1.0, rho, rho_mass=rho))
+    one = np.ones(N)
+    mass = np.array([one @ (lfe.assemble(m, lfe.element_matrices(m, 1.0, rho, rho_mass=rho + e))[1] - M0) @ one
+                     for e in np.eye(N)])
+    assert mass.sum() == pytest.approx(1.0, rel=1e-12)          # the unit square's area
+    h = 1e-5
+    rng = np.random.default_rng(0)
+    for d in (np.cos(np.pi * m.node_xy[:, 0]), rng.standard_normal(N)):
+        dM = lfe.assemble(m, lfe.element_matrices(m, 1.0, rho, rho_mass=rho + d))[1] - M0
+        fd = (lfe.forward_and_gradient(m, 1.0, rho, dt, src, wav, recs, obs, rho_mass=rho + h * d)[1]
+              - lfe.forward_and_gradient(m, 1.0, rho, dt, src, wav, recs, obs, rho_mass=rho - h * d)[1]) / (2 * h)
+        assert np.sum(dM * C) == pytest.approx(fd, rel=1e-6)
+    smooth = np.cos(np.pi * m.node_xy[:, 0])
+    fd_s = (lfe.forward_and_gradient(m, 1.0, rho, dt, src, wav, recs, obs, rho_mass=rho + h * smooth)[1]
+            - lfe.forward_and_gradient(m, 1.0, rho, dt, src, wav, recs, obs, rho_mass=rho - h * smooth)[1]) / (2 * h)
+    assert np.sign((mass * g) @ smooth) == np.sign(fd_s)
