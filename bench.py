@@ -463,8 +463,10 @@ def run_ours(args, rank, world):
 
 
 def run_serving(args, rank, world):
-    """Forward-modelling requests with Poisson arrivals through the serving engine
-    (continuous batching of shots that share a model, step count and receivers)."""
+    """Shot requests with Poisson arrivals through the serving engine: continuous batching
+    of requests as the slots of library sessions (admitted between windows of 32 steps
+    while other slots run), a third of them gradient requests (forward, misfit, adjoint and
+    gradient), the rest trace requests."""
     import torch
     from paper_2501_06748_gb300 import build
     build.build()
@@ -499,30 +501,38 @@ def run_serving(args, rank, world):
         h = 1.0 / (spec[0] * spec[1])
         top = boundary_nodes(m, "top")
         wav = ricker(1.0 / (10 * h), dts[spec], K)
-        reqs.append(serving.Request(rid, key, int(rng.choice(top)), wav, recs[spec], arrival=0.0))
+        obs = np.zeros((recs[spec].size, K)) if rid % 3 == 0 else None
+        reqs.append(serving.Request(rid, key, int(rng.choice(top)), wav, recs[spec], arrival=0.0, observed=obs))
         units += m.n_elem * spec[2] * K
-    # arrival rate: 70 % of the rate one request at a time could sustain (service times
-    # of single-shot requests measured once per model, after its set-up)
-    eng0 = serving.Engine(build_model, max_batch=1, cache_capacity=len(keys))
-    probe = []
-    for k, key in enumerate(keys):
-        top = boundary_nodes(meshes[key[:3]][0], "top")
-        probe.append(serving.Request(-1 - k, key, int(top[len(top) // 2]),
-                                     ricker(1.0 / (10 / (key[0] * key[1])), dts[key[:3]], 500), recs[key[:3]], 0.0))
-    eng0.run(probe)                              # set-ups + warm-up
-    t_one = {}
-    for r in probe:
-        t0 = time.perf_counter()
-        lib.forward(eng0.cache.get(r.model_key), [r.src_node], r.wavelet[None], r.rec_nodes, keep=False)
+    for key in keys:
+        build_model(key)                          # warm-up of every mesh's device set-up
+    # arrival rate: 70 % of the rate one request at a time could sustain (single-shot service
+    # times per model: forward, and forward + misfit + adjoint for gradient requests)
+    t_fwd, t_grad = {}, {}
+    for key in keys:
+        md = build_model(key)
+        spec = key[:3]
+        top = boundary_nodes(meshes[spec][0], "top")
+        wav = ricker(1.0 / (10 / (key[0] * key[1])), dts[spec], 200)[None]
+        lib.forward(md, [int(top[len(top) // 2])], wav, recs[spec], keep=False)
         torch.cuda.synchronize()
-        t_one[r.model_key] = (time.perf_counter() - t0) / 500.0           # seconds per step, one shot
-    mean_service = float(np.mean([t_one[r.model_key] * r.K for r in reqs]))
+        t0 = time.perf_counter()
+        lib.forward(md, [int(top[len(top) // 2])], wav, recs[spec], keep=False)
+        torch.cuda.synchronize()
+        t_fwd[key] = (time.perf_counter() - t0) / 200.0
+        t0 = time.perf_counter()
+        tr, st = lib.forward(md, [int(top[len(top) // 2])], wav, recs[spec])
+        _, res = lib.misfit(tr, np.zeros_like(tr), md.dt)
+        lib.adjoint_gradient(md, st, res)
+        torch.cuda.synchronize()
+        t_grad[key] = (time.perf_counter() - t0) / 200.0
+    mean_service = float(np.mean([(t_grad if r.wants_gradient else t_fwd)[r.model_key] * r.K for r in reqs]))
     rate = 0.7 / mean_service
     t = 0.0
     for r in reqs:
         t += float(rng.exponential(1.0 / rate))
         r.arrival = t
-    eng = serving.Engine(build_model, max_batch=8, cache_capacity=len(keys))
+    eng = serving.Engine(build_model, max_batch=8, window=32, cache_capacity=len(keys))
     for key in keys:                             # models set up before the clock starts
         eng.cache.get(key)
     clocks = ClockSampler(os.path.join(args.clock_log, "clocks_serving.csv"))
@@ -533,17 +543,27 @@ def run_serving(args, rank, world):
     wall = time.perf_counter() - t0
     clk = clocks.stop(0)
     st = serving.latency_stats(reqs)
-    return {"metric": "serving: forward element-radial-node-steps/s; p50/p99 request latency",
+    st_g = serving.latency_stats([r for r in reqs if r.wants_gradient])
+    joined = sum(1 for r in reqs if r.admitted_at and r.admitted_at[1] > 0)
+    return {"metric": "serving: element-radial-node-steps/s of served requests; p50/p99 request latency",
             "value": units / wall, "unit": "element-radial-node-steps/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "serving: %d forward requests (one Ricker shot each, 16 receivers) on 8 seeded "
-                                   "flawed models over meshes %s (elements per side, p, N_r), K in {500, 1000}, Poisson "
-                                   "arrivals at 70%% of the one-request-at-a-time capacity; continuous batching of "
-                                   "up to 8 shots that share a model, K and receivers" % (n_req, specs),
-                       "requests": n_req, "arrival_rate_per_s": rate, "batches": len(eng.batches),
-                       "mean_batch": float(np.mean(eng.batches)), "l2": "models and traces stay on the device"},
-            "latency_ms": {"p50": st["p50_s"] * 1e3, "p99": st["p99_s"] * 1e3, "mean": st["mean_s"] * 1e3},
+            "config": {"workload": "serving: %d requests (one Ricker shot each, 16 receivers; every third also "
+                                   "misfit + adjoint + gradient) on 8 seeded flawed models over meshes %s (elements "
+                                   "per side, p, N_r), K in {500, 1000}, Poisson arrivals at 70%% of the "
+                                   "one-request-at-a-time capacity; continuous batching: requests are the slots "
+                                   "(shot columns, 8 per session) of library sessions, admitted between windows of "
+                                   "32 steps while the other slots run" % (n_req, specs),
+                       "requests": n_req, "gradient_requests": int(sum(r.wants_gradient for r in reqs)),
+                       "arrival_rate_per_s": rate, "windows": eng.windows,
+                       "mean_slots_busy": float(np.mean(eng.batches)) if eng.batches else 0.0,
+                       "admitted_while_others_in_flight": joined, "max_in_flight": eng.max_in_flight,
+                       "units": "one element-radial-node-step of a request's path (forward for trace requests, "
+                                "forward + adjoint + gradient for gradient requests)",
+                       "l2": "models, session state and forward fields stay on the device"},
+            "latency_ms": {"p50": st["p50_s"] * 1e3, "p99": st["p99_s"] * 1e3, "mean": st["mean_s"] * 1e3,
+                           "gradient_p50": st_g["p50_s"] * 1e3, "gradient_p99": st_g["p99_s"] * 1e3},
             "clocks": clk}
 
 
@@ -551,6 +571,8 @@ def run_serving(args, rank, world):
 # steps) on 12 CPU threads, Voronoi meshes; hole specimen, 5 and 7 radial intervals
 PAPER_EPOCH_S = {(1000, 5): 0.95, (2000, 5): 2.39, (4000, 5): 5.49, (8000, 5): 11.19,
                  (1000, 7): 1.32, (2000, 7): 3.21, (4000, 7): 6.82, (8000, 7): 13.92}
+# the same table's low-frequency-expansion column (the paper's comparison method)
+PAPER_LFE_EPOCH_S = {1000: 0.23, 2000: 0.46, 4000: 1.27, 8000: 2.70}
 
 
 def run_paper(args, rank, world):
@@ -596,12 +618,46 @@ def run_paper(args, rank, world):
         units_all += units
         secs_all += sec
         nb = getattr(w.mesh, "n_b", None)
-        rows.append({"elements": w.mesh.n_elem, "intervals": intervals, "N_r": w.n_r, "receivers": int(len(w.rec_nodes)),
+        rows.append({"method": "radial FD", "elements": w.mesh.n_elem, "intervals": intervals, "N_r": w.n_r,
+                     "receivers": int(len(w.rec_nodes)),
                      "n_b": [int(nb.min()), int(nb.max())] if nb is not None else 4 * w.mesh.p,
                      "s_per_epoch": sec, "units_per_s": units / sec,
                      "paper_s_per_epoch": PAPER_EPOCH_S[(n_elem, intervals)],
                      "paper_over_ours": PAPER_EPOCH_S[(n_elem, intervals)] / sec})
-    return {"metric": "paper-shaped plate: seconds per epoch (set-up + fwd + adj + grad, 2 sources, 200 steps)",
+        if intervals == 5:
+            # the comparison method on the same mesh and data (its set-up: the Riccati and
+            # Lyapunov solves of every element on the device)
+            def epoch_lfe():
+                md = lib.Model(M, w.c, w.rho_start, w.dt, lx=L, ly=L, lfe=True)
+                tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+                E, res = lib.misfit(tr, obs, w.dt)
+                return E, lib.adjoint_gradient(md, st, res)
+
+            for _ in range(max(1, args.warmup)):
+                epoch_lfe()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                epoch_lfe()
+            torch.cuda.synchronize()
+            sec_l = (time.perf_counter() - t0) / args.steps
+            lib.profile_read(reset=True)
+            lib.profile_enable(True)
+            lib.Model(M, w.c, w.rho_start, w.dt, lx=L, ly=L, lfe=True)
+            torch.cuda.synchronize()
+            lib.profile_enable(False)
+            setup_ms = lib.profile_read(reset=True)["setup"]["ms"]
+            lib.profile_enable(True)
+            lib.Model(M, w.c, w.rho_start, w.dt, lx=L, ly=L)
+            torch.cuda.synchronize()
+            lib.profile_enable(False)
+            setup_fd_ms = lib.profile_read(reset=True)["setup"]["ms"]
+            rows.append({"method": "low-frequency expansion", "elements": w.mesh.n_elem,
+                         "s_per_epoch": sec_l, "setup_ms": setup_ms, "fd_setup_ms": setup_fd_ms,
+                         "paper_s_per_epoch": PAPER_LFE_EPOCH_S[n_elem],
+                         "paper_over_ours": PAPER_LFE_EPOCH_S[n_elem] / sec_l})
+    return {"metric": "paper-shaped plate: seconds per epoch (set-up + fwd + adj + grad, 2 sources, 200 steps); "
+                      "radial FD rows and the comparison method's",
             "value": units_all / secs_all, "unit": "element-radial-node-steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs_all / len(rows), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -700,6 +756,85 @@ def run_batching(args, rank, world):
             "clocks": clk}
 
 
+def run_diffcheck(args, rank, world):
+    """The differentiation recipe's problem (128x128 elements, p = 4, N_r = 32, 16 shots, 64
+    receivers, 512x512 density grid) end to end at a stated step count: the exact gradient
+    (checkpointed forward, recomputed in the adjoint) against central differences of the
+    misfit along random directions of the grid, then projected L-BFGS iterations (memory 10)
+    with the paper's kernel from the homogeneous start towards the flawed model."""
+    import torch
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi as lib, inversion
+    from sbfwi_inputs import diff_workload
+    if rank != 0:
+        return None
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    K = args.time_steps or 500
+    w = diff_workload(K=K)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    wav = torch.tensor(w.wavelets, device=dev)
+    rho_start = torch.tensor(w.rho_start, device=dev)
+    m_true = lib.Model(M, w.c, torch.tensor(w.rho_true, device=dev), w.dt)
+    observed = torch.cat([lib.forward(m_true, w.src_nodes[lo:lo + 8], wav[lo:lo + 8], w.rec_nodes, keep=False)[0]
+                          for lo in range(0, w.n_shots, 8)])
+    del m_true
+    units = w.mesh.n_elem * w.n_r * K * w.n_shots
+    stats = {"evaluations": 0, "seconds": 0.0}
+
+    def timed(fg):
+        def run(x):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fg(x)
+            torch.cuda.synchronize()
+            stats["evaluations"] += 1
+            stats["seconds"] += time.perf_counter() - t0
+            return out
+        return run
+
+    clocks = ClockSampler(os.path.join(args.clock_log, "clocks_diffcheck.csv"))
+    clocks.start()
+    # the exact gradient against central differences
+    fg_exact = inversion.objective(M, w.c, w.dt, w.src_nodes, wav, w.rec_nodes, observed, ckpt_every=lib.CKPT_AUTO,
+                                   exact=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E0, g = fg_exact(rho_start)
+    torch.cuda.synchronize()
+    t_exact = time.perf_counter() - t0
+    f = inversion.misfit_only(M, w.c, w.dt, w.src_nodes, wav, w.rec_nodes, observed)
+    rng = np.random.default_rng(16)
+    h = 1e-5
+    errs = []
+    for _ in range(args.fd_directions):
+        d = torch.tensor(rng.standard_normal(w.rho_start.shape), device=dev)
+        fd = (f(rho_start + h * d) - f(rho_start - h * d)) / (2 * h)
+        errs.append(abs(float(torch.sum(g * d)) - fd) / abs(fd))
+    # L-BFGS with the paper's kernel (the box keeps the density where the radial scheme is stable)
+    fg = timed(inversion.objective(M, w.c, w.dt, w.src_nodes, wav, w.rec_nodes, observed, ckpt_every=lib.CKPT_AUTO))
+    _, hist = inversion.lbfgs(fg, rho_start, lo=0.2, hi=2.0, iters=args.lbfgs_iters, m=10)
+    clk = clocks.stop(0)
+    value = units * stats["evaluations"] / stats["seconds"]
+    return {"metric": "differentiation: exact gradient vs central differences, L-BFGS; "
+                      "element-radial-node-steps/s of the L-BFGS evaluations",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": stats["evaluations"], "warmup": 1,
+            "ms_per_step": 1e3 * stats["seconds"] / max(1, stats["evaluations"]), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"diff recipe at {K} of its 8000 steps: 128x128 square S-elements, p=4, N_r=32, "
+                                   "16 Ricker shots in passes of 8, 64 receivers, 512x512 density grid, checkpoints "
+                                   "at the memory-optimal interval (forward recomputed in the adjoint)",
+                       "time_steps": K, "fd_directions": args.fd_directions, "fd_step": h,
+                       "lbfgs_iterations": args.lbfgs_iters, "lbfgs_memory": 10, "box": [0.2, 2.0],
+                       "l2": "inputs larger than L2 (checkpoints and recompute windows of 16 shots)"},
+            "fd_check": {"gradient": "exact (SBFWI_GRAD_EXACT)", "max_rel_err": float(max(errs)) if errs else None,
+                         "rel_errs": [float(e) for e in errs], "exact_gradient_seconds": t_exact, "misfit": E0},
+            "lbfgs": {"misfit_history": [float(x) for x in hist], "evaluations": stats["evaluations"],
+                      "seconds": stats["seconds"], "reduction": float(hist[-1] / hist[0]) if hist[0] else None},
+            "clocks": clk}
+
+
 def run_reference(args, rank, world):
     """The oracle (the only reference this path has) on the host cores, rank 0 only."""
     if rank != 0:
@@ -730,12 +865,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=64, help="serving config: number of requests")
-    ap.add_argument("--config", choices=["size", "diff", "serving", "paper", "batching"], default="size",
+    ap.add_argument("--config", choices=["size", "diff", "serving", "paper", "batching", "diffcheck"], default="size",
                     help="size: 64x64 elements, 8 shots, 2000 steps, stored forward field (the default); "
                          "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint; "
                          "serving: forward-modelling requests with continuous batching; "
                          "paper: the paper's plate recipe at its Table 1 element counts; "
-                         "batching: 64 shots over 3 quadtree meshes with uneven elements")
+                         "batching: 64 shots over 3 quadtree meshes with uneven elements; "
+                         "diffcheck: the diff problem with an FD check of the exact gradient and L-BFGS")
+    ap.add_argument("--fd-directions", type=int, default=16, help="diffcheck config: random directions")
+    ap.add_argument("--lbfgs-iters", type=int, default=20, help="diffcheck config: L-BFGS iterations")
     ap.add_argument("--clock-log", default=tempfile.gettempdir(),
                     help="directory for the raw nvidia-smi clock samples of the timed region")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -760,6 +898,8 @@ def main():
         out = run_paper(args, rank, world)
     elif args.config == "batching":
         out = run_batching(args, rank, world)
+    elif args.config == "diffcheck":
+        out = run_diffcheck(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if out is not None:

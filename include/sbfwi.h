@@ -166,6 +166,11 @@ int sbfwi_set_model_lfe(sbfwi_model** out, const sbfwi_mesh* mesh, double c, con
  *            (padded n_b <= 32, <= 8 shots; SBFWI_EUNSUPPORTED at the time-loop
  *            call otherwise; its operator digits are prepared on first use);
  *            SBFWI_ELEMENT_FP64: the FP64 kernel.
+ *            SBFWI_ELEMENT_MIXED: on a mesh whose elements have different n_b (padded
+ *            beyond 16), the elements with n_b <= 16 on the one-tile tensor-core kernel
+ *            and the others on the FP64 kernel, two launches per step over element lists
+ *            (SBFWI_EUNSUPPORTED at the time-loop call unless both classes exist and at
+ *            most 8 shots run); AUTO picks it for a padded n_b of 17..20 or beyond 32.
  *   solve    SBFWI_SOLVE_AUTO: the dataflow solve (SBFWI_SOLVE=barrier|levels in
  *            the environment selects the others); SBFWI_SOLVE_DATAFLOW: one
  *            cooperative launch, tasks ordered by dependencies; SBFWI_SOLVE_BARRIER:
@@ -212,7 +217,28 @@ int sbfwi_lfe_element_matrices(const double* E0, const double* E1, const double*
 enum { SBFWI_TERMS_VELOCITY = 0, SBFWI_TERMS_FULL = 1 };
 int sbfwi_set_kernel_terms(sbfwi_model* model, int terms);
 
-enum { SBFWI_ELEMENT_AUTO = 0, SBFWI_ELEMENT_TENSOR = 1, SBFWI_ELEMENT_FP64 = 2 };
+/*
+ * sbfwi_set_gradient_mode -- which gradient later forward passes on `model` are kept for.
+ *   SBFWI_GRAD_KERNEL (default): the paper's gradient (Section 2 adjoint equation run in
+ *     reversed time, Section 4 velocity kernel); a stored forward field holds the nodal
+ *     velocities of every step.
+ *   SBFWI_GRAD_EXACT: the exact derivative of the discrete misfit E (Eq. (misfit)) with
+ *     respect to the nodal densities, i.e. the adjoint/stationarity conditions of Section 2
+ *     applied to the discrete system of Section 3.3 (Eq. (system) with its boundary-condition
+ *     rows, the condensation and Eq. (Newmark)) instead of the continuous equation.  The
+ *     radial finite-difference operator is not symmetric, so this differs from the paper's
+ *     kernel; it is what finite differences of E measure.  Forward passes then run the FP64
+ *     element kernel and a stored forward field holds the nodal displacements and
+ *     accelerations of every step (twice the velocity store); checkpointed forward states
+ *     serve both modes.  The first exact adjoint on a model prepares its extra operators
+ *     (the inverses of the modified pivot blocks, per element ~(N_r + 5) n_b^2 doubles, and
+ *     the transposed global factors).
+ * Errors: SBFWI_EINVAL for a NULL model or an unknown mode; SBFWI_EUNSUPPORTED for a
+ * comparison-method model (sbfwi_set_model_lfe), whose exact adjoint is not built.
+ */
+int sbfwi_set_gradient_mode(sbfwi_model* model, int mode);
+
+enum { SBFWI_ELEMENT_AUTO = 0, SBFWI_ELEMENT_TENSOR = 1, SBFWI_ELEMENT_FP64 = 2, SBFWI_ELEMENT_MIXED = 3 };
 enum { SBFWI_SOLVE_AUTO = 0, SBFWI_SOLVE_DATAFLOW = 1, SBFWI_SOLVE_BARRIER = 2, SBFWI_SOLVE_LEVELS = 3 };
 int sbfwi_set_schedule(sbfwi_model* model, int element, int solve);
 
@@ -291,15 +317,20 @@ int sbfwi_misfit_noalloc(const double* traces, const double* observed, int64_t n
  * directly).  Adjoint step m (0-based) injects residual[s][r][K-1-m] at
  * rec_node[r] (same sign slot as the forward source) and accumulates
  *     g(node) += dt * sum_s udot_fwd[K-1-m](node, s) * lambdadot^{m+1}(node, s).
+ * With SBFWI_GRAD_EXACT instead: g = dE/drho of the discrete path, E = 0.5 dt sum
+ * residual^2 (residual = d - u as from sbfwi_misfit), by the transposed condensation
+ * and global solve run backwards in time; summed over shots (see sbfwi_set_gradient_mode).
  *
  *   fwdstate  from sbfwi_forward(..., keep, ...) on the same model; not consumed.
  *             If it holds checkpoints, the forward field is recomputed window by
  *             window (last window first) with the element kernel that wrote them
  *             (SBFWI_ESTATE if SBFWI_ELEMENT now selects the other one).
  *   residual  [n_shots][n_rec][K] (d - u, as from sbfwi_misfit)
- *   mode      SBFWI_GRAD_KERNEL (the paper's kernel).  SBFWI_GRAD_EXACT returns
- *             SBFWI_EUNSUPPORTED in this build.  With SBFWI_GRAD_ACCUMULATE or-ed
- *             in, the result is added to grad (gradients of shot batches run one
+ *   mode      SBFWI_GRAD_KERNEL (the paper's kernel) or SBFWI_GRAD_EXACT (the exact
+ *             derivative; SBFWI_ESTATE unless the model was in SBFWI_GRAD_EXACT mode
+ *             when the forward state was made; SBFWI_GRAD_KERNEL on a stored field kept
+ *             for the exact adjoint is SBFWI_ESTATE too).  With SBFWI_GRAD_ACCUMULATE
+ *             or-ed in, the result is added to grad (gradients of shot batches run one
  *             after the other).
  *   grad      out: [gy][gx] (model set with SBFWI_RHO_GRID, the transpose of the
  *             bilinear map) or [n_nodal] (SBFWI_RHO_NODAL).
@@ -307,6 +338,49 @@ int sbfwi_misfit_noalloc(const double* traces, const double* observed, int64_t n
  */
 int sbfwi_adjoint_gradient(sbfwi_model* model, sbfwi_fwdstate* fwdstate, const double* residual,
                            int mode, double* grad, int mem, void* stream);
+
+/*
+ * Sessions: continuous batching of shot requests on one model (a service of the library
+ * for serving; the numerics are those of sbfwi_forward and sbfwi_adjoint_gradient with
+ * the paper's kernel, Section 2 and Section 4).  A session is a time loop whose B shot
+ * columns ("slots") carry independent requests.  It advances in windows of `window`
+ * Newmark steps; between windows a request can be admitted into a free slot (its state
+ * column is zeroed, so the slot starts its own step 0 at the next window) and a finished
+ * one collected, while the other slots keep running.  Every request's result is the same
+ * as that shot run alone through sbfwi_forward / sbfwi_adjoint_gradient (to rounding: the
+ * element kernels treat the shot columns independently).
+ *
+ *   kind      SBFWI_SESSION_FORWARD: a request is one point source (src_node, wavelet
+ *             values[K]); its result is the traces [n_rec][K] at the session's receivers;
+ *             with `field` (device, [K][n_nodal] doubles, caller-owned) its nodal
+ *             velocities of every step are written there for a later adjoint.
+ *             SBFWI_SESSION_ADJOINT: a request is a residual values[n_rec][K] (d - u, as
+ *             from sbfwi_misfit) with the forward velocities `field` of its shot (as
+ *             written by a forward session); its result is the gradient of the paper's
+ *             kernel for that shot on the model's parameter layout ([gy][gx] or [n_nodal]).
+ *   slots     1..16 shot columns; window 1..100000 steps per sbfwi_session_step.
+ *   rec_node  [n_rec] distinct receiver nodes (host), shared by the session's requests.
+ *
+ * sbfwi_session_step runs one window of every slot whose request is not finished and
+ * reports in finished[slots] (nullable) which slots hold a finished, uncollected request.
+ * sbfwi_session_collect copies a finished slot's result to `out` (mem) and frees the slot.
+ * Calls are synchronous on `stream` (given at creation).  Errors: SBFWI_EINVAL (bad
+ * argument), SBFWI_ESTATE (admission to a busy slot, collection of an unfinished one),
+ * SBFWI_EUNSUPPORTED (a model set for the full kernel or the exact adjoint).  The model
+ * must outlive the session; a session must not be used by two threads at once.
+ */
+enum { SBFWI_SESSION_FORWARD = 0, SBFWI_SESSION_ADJOINT = 1 };
+typedef struct sbfwi_session sbfwi_session;
+int sbfwi_session_create(sbfwi_session** out, sbfwi_model* model, int32_t kind, int32_t slots, int32_t n_rec,
+                         const int64_t* rec_node, int32_t window, void* stream);
+int sbfwi_session_admit(sbfwi_session* session, int32_t slot, int64_t src_node, const double* values, int64_t K,
+                        double* field, int mem);
+int sbfwi_session_step(sbfwi_session* session, int32_t* finished);
+int sbfwi_session_collect(sbfwi_session* session, int32_t slot, double* out, int mem);
+/* info[0..4] = doubles per step of a forward field (the rows of `field`), steps run so far,
+ * slots, window, slots holding a request. */
+int sbfwi_session_info(const sbfwi_session* session, int64_t* info);
+void sbfwi_session_destroy(sbfwi_session* session);
 
 /*
  * sbfwi_destroy_fwdstate -- frees a forward state.  Its velocity or checkpoint

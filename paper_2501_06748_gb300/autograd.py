@@ -3,11 +3,14 @@ around the library: the forward solve, the misfit and the adjoint all run in its
 kernels; this module only marshals arrays).
 
 ``misfit(rho, problem)`` returns E(rho) = 1/2 dt sum over shots, receivers and samples
-of (d - u)^2 (Eq. (misfit)) as a 0-d float64 tensor.  Its backward is the paper's
-gradient (Sections 2 and 4): the forward operator run in reversed time with the
-residuals as sources and the zero-lag correlation of forward and adjoint velocities,
-with the c^2 grad(lambda).grad(u) term dropped as the paper does, on the fine density
-grid (or on the nodal points for ``SBFWI_RHO_NODAL``).  The forward pass keeps, per
+of (d - u)^2 (Eq. (misfit)) as a 0-d float64 tensor.  Its backward is, with
+``problem.gradient == "kernel"``, the paper's gradient (Sections 2 and 4): the forward
+operator run in reversed time with the residuals as sources and the zero-lag correlation
+of forward and adjoint velocities, with the c^2 grad(lambda).grad(u) term dropped as the
+paper does; with ``"exact"`` the exact derivative of the discrete misfit (the library's
+transposed condensation run backwards in time), which is what finite differences of E
+measure.  Either lives on the fine density grid (or on the nodal points for
+``SBFWI_RHO_NODAL``).  The forward pass keeps, per
 pass of ``shots_per_pass`` shots, the forward field the adjoint needs: the velocities
 of every step, or with ``ckpt_every`` > 0 (or ``sbfwi.CKPT_AUTO``) only checkpoints,
 the forward being recomputed window by window during backward.
@@ -42,6 +45,7 @@ class Problem:
     ly: float = 1.0
     shots_per_pass: int = 8
     ckpt_every: int = 0
+    gradient: str = "kernel"       # "kernel" (the paper's) or "exact"
 
 
 def _host(x):
@@ -57,7 +61,11 @@ class _Misfit(torch.autograd.Function):
         r = rho.detach().contiguous() if dev else np.ascontiguousarray(_host(rho), dtype=np.float64)
         wav = prob.wavelets if dev else _host(prob.wavelets)
         obs = prob.observed if dev else _host(prob.observed)
+        if prob.gradient not in ("kernel", "exact"):
+            raise ValueError("gradient must be 'kernel' or 'exact'")
         model = sbfwi.Model(prob.mesh, prob.c, r, prob.dt, rho_kind=prob.rho_kind, lx=prob.lx, ly=prob.ly)
+        mode = sbfwi.GRAD_EXACT if prob.gradient == "exact" else sbfwi.GRAD_KERNEL
+        sbfwi.set_gradient_mode(model, mode)
         src = np.asarray(prob.src_nodes, dtype=np.int64)
         per = max(1, int(prob.shots_per_pass))
         E, passes = 0.0, []
@@ -67,7 +75,7 @@ class _Misfit(torch.autograd.Function):
             e, res = sbfwi.misfit(tr, obs[lo:hi], prob.dt)
             E += e
             passes.append((st, res))
-        ctx.model, ctx.passes = model, passes
+        ctx.model, ctx.passes, ctx.mode = model, passes, mode
         ctx.shape, ctx.device, ctx.cuda = tuple(rho.shape), rho.device, dev
         return torch.tensor(E, dtype=torch.float64, device=rho.device)
 
@@ -80,7 +88,7 @@ class _Misfit(torch.autograd.Function):
         else:
             g = np.zeros(ctx.shape)
         for st, res in ctx.passes:
-            sbfwi.adjoint_gradient(ctx.model, st, res, grad_out=g, accumulate=True)
+            sbfwi.adjoint_gradient(ctx.model, st, res, mode=ctx.mode, grad_out=g, accumulate=True)
         ctx.passes = None
         if not ctx.cuda:
             g = torch.from_numpy(g)
@@ -88,7 +96,7 @@ class _Misfit(torch.autograd.Function):
 
 
 def misfit(rho: torch.Tensor, problem: Problem) -> torch.Tensor:
-    """E(rho) with the paper's adjoint gradient as its backward."""
+    """E(rho) with the paper's adjoint gradient (or the exact one) as its backward."""
     return _Misfit.apply(rho, problem)
 
 

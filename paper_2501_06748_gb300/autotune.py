@@ -1,7 +1,7 @@
 """Schedule autotuner (a harness around the library; not part of the paper's method).
 
 For one model and one shot batch, ``tune`` times every element kernel (tensor-core,
-FP64) with every global-solve schedule (dataflow, barrier, per-level launches) on a
+FP64, and on meshes with uneven elements the per-class mix of the two) with every global-solve schedule (dataflow, barrier, per-level launches) on a
 few steps of the caller's own problem -- a forward pass that stores its velocities and
 the adjoint pass with the gradient, the two time loops of a misfit-and-gradient
 evaluation, whose element launches differ (store vs gradient) -- keeps the fastest on the model
@@ -18,12 +18,13 @@ import numpy as np
 
 from . import sbfwi
 
-ELEMENTS = {"tensor": sbfwi.ELEMENT_TENSOR, "fp64": sbfwi.ELEMENT_FP64}
+ELEMENTS = {"tensor": sbfwi.ELEMENT_TENSOR, "fp64": sbfwi.ELEMENT_FP64, "mixed": sbfwi.ELEMENT_MIXED}
 SOLVES = {"dataflow": sbfwi.SOLVE_DATAFLOW, "barrier": sbfwi.SOLVE_BARRIER, "levels": sbfwi.SOLVE_LEVELS}
 
 
 def tune(model, src_nodes, wavelets, rec_nodes, steps: int = 16, repeats: int = 3,
-         elements=("tensor", "fp64"), solves=("dataflow", "barrier", "levels"), shots_per_pass: int = 8) -> dict:
+         elements=("tensor", "fp64", "mixed"), solves=("dataflow", "barrier", "levels"),
+         shots_per_pass: int = 8) -> dict:
     """Time the candidates on ``steps`` steps of a misfit-and-gradient evaluation of these
     shots (passes of ``shots_per_pass``: forward with stored velocities + adjoint with the
     gradient) and set the fastest; returns {"element", "solve", "s_per_step" (the whole

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsbfwi.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["mesh.cpp", "lfe.cpp", "setup.cu", "step.cu", "tc.cu", "tc2.cu", "noalloc.cu"]
+SOURCES = ["mesh.cpp", "lfe.cpp", "lfe_setup.cu", "setup.cu", "step.cu", "exact.cu", "tc.cu", "tc2.cu", "noalloc.cu"]
 
 
 def nvcc_path() -> str:

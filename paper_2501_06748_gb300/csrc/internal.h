@@ -130,6 +130,9 @@ struct MeshDevice {
   // nodal gradient operator (CSR, rows 2q and 2q+1: x and y components at nodal point q)
   bool grad_ready = false;
   DevBuf grad_ptr, grad_col, grad_val;
+  // elements at each global node (CSR node -> e * nb + local dof), for the exact adjoint
+  bool inc_ready = false;
+  DevBuf inc_ptr, inc_list;
 };
 
 constexpr int kMaxBoundaryNodes = 40;   // largest n_b of an element
@@ -221,6 +224,15 @@ struct Model {
   // the same operators split into FP16 digits for the tensor-core element kernel
   DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
   bool tc_ready = false;
+  bool tc_one_tile = false;   // tc_frag holds one-tile digits although nb > 16 (mixed element kernels)
+  DevBuf rho_lo;           // [n_nodal] low part of the set-up's double-double density (re-runs of the set-up)
+  // exact discrete adjoint (sbfwi_set_gradient_mode(EXACT)): operators the set-up emits on request
+  int grad_mode = SBFWI_GRAD_KERNEL;
+  bool exact_ready = false;
+  DevBuf xops;             // [E][n][nb][nb] G_i = (modified phi_i)^{-1}
+  DevBuf xel;              // [E][6][nb][nb] rho_0, W, Gamma, Y_theta, Y_phi, Y_M
+  DevBuf kq;               // [E][L][ng][4] quadrature factors of the coefficient matrices
+  DevBuf factors_t;        // the global factors of the transposed matrix (X^T, C^T, G^T per tree node)
   bool lfe = false;        // the comparison method (low-frequency expansion, sbfwi_set_model_lfe)
   DevBuf lfe_M;            // its element masses [E][nb][nb]; S holds K + a0 M
   int kernel_terms = SBFWI_TERMS_VELOCITY;  // sbfwi_set_kernel_terms
@@ -230,15 +242,95 @@ struct Model {
   const MeshDevice& dev() const { return *mesh->dev; }
 };
 
-int build_level_tasks(Model& md, int shots, int grid);
+int build_level_tasks(const Model& md, LevelTasks& lt, int shots, int grid);
+int prepare_exact(Model& md, cudaStream_t st);   // setup.cu: Model::xops, xel, kq, factors_t
+// lfe_setup.cu: the comparison method's K + a0 M and M of every element from E0..M0 [E][4][nb][nb]
+int lfe_setup_device(Model& md, const double* Emat, double* S, double* M, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// exact discrete adjoint kernels (exact.cu)
+// ---------------------------------------------------------------------------
+struct ExactElemArgs {
+  int nb, n, B, epc;
+  int64_t E, N;
+  double a0, a1, a2;                       // Newmark predictor coefficients
+  double cu, cud, cudd, du, dud, dudd;     // u' and u'' of the Newmark update: c_u (u_new - u) + c_ud u' + c_udd u''
+  const double* mats;                      // [E][n][3][nb][nb] P, Q, H
+  const double* rt;                        // [E][2][nb][nb] R, T
+  const double* xops;                      // [E][n][nb][nb] G_i
+  const double* xel;                       // [E][6][nb][nb] rho_0, W, Gamma, Y_theta, Y_phi, Y_M
+  const int32_t* dofs;                     // [E][nb]
+  double* ua; double* uda; double* udda;   // adjoints of the interior u, u', u'' [E][n][nb][B]
+  double* s;                               // [E][n][nb][B] up-sweep values
+  const double* fbar;                      // [N][B] transposed solve (mu of the flux rows)
+  double* mu;                              // [E][n+2][nb][B] mu of rows -1..n
+  double* vbn;                             // [E][nb][B] T^T mu_{n+1}
+  double* fhat;                            // [E][nb][B] -H_{n-1}^T s_{n-1}
+  const double* fu_int;                    // forward u after the step: interior [E][n][nb][B]
+  const double* fu_b;                      // and boundary [N][B]
+  const double* fa_b;                      // forward u'' after the step, boundary [N][B]
+  double* ghost;                           // [E][2][nb][B] u_{-1}, u_{n+1} of the forward solution
+  int do_down, do_up;
+};
+
+struct ExactBoundaryArgs {
+  int64_t N;
+  int B;
+  double a0, a1, a2, cu, cud, cudd, du, dud, dudd;
+  double* ub; double* udb; double* uddb;   // adjoints of the boundary u, u', u'' [N][B]
+  double* ext;                             // pre: x_bar of the boundary nodes
+  const double* vbn;                       // post: per-element v_bar_n
+  const int64_t* inc_ptr;
+  const int64_t* inc_list;
+};
+
+struct ExactGradArgs {
+  int64_t E, N;
+  int nb, n, B, Bp, L, ng;
+  double h;
+  const double* xi;                        // [n+1]
+  const double* tab;                       // Gauss weights and Lagrange tables (double-double pairs)
+  const int64_t* lptr;                     // [E+1]
+  const int32_t* line_local;               // [lines][p+1]
+  const int32_t* dofs;
+  const double* mu;                        // [E][n+2][nb][B]
+  const double* fbar;                      // [N][B]
+  const double* fu_int; const double* fu_b;   // forward u after the step
+  const double* fa_int; const double* fa_b;   // forward u'' after the step
+  const double* ghost;                     // [E][2][nb][B]
+  double* gacc;                            // [E][n+1][4][L][ng]
+};
+
+struct ExactFinalArgs {
+  int64_t E;
+  int nb, n, pp, ng, L;
+  const int64_t* lptr;
+  const int32_t* line_local;
+  const double* tab;
+  const double* kq;                        // [E][L][ng][4]
+  const double* gacc;
+  double* g_nodal;                         // interior part of the library's nodal layout
+  double* g_bnd;                           // [E][nb] boundary station per element
+};
+
+size_t exact_element_smem(int nb, int n, int B, int epc);
+int exact_element_launch(const ExactElemArgs& a, cudaStream_t st);
+int exact_misfit_launch(double* ub, int B, int R, const int64_t* rec, const double* res, int64_t K, int64_t k, double dt,
+                        cudaStream_t st);
+int exact_boundary_launch(const ExactBoundaryArgs& a, bool post, cudaStream_t st);
+int exact_gradient_launch(const ExactGradArgs& a, int p, cudaStream_t st);
+int exact_finalize_launch(const ExactFinalArgs& a, const int64_t* inc_ptr, const int64_t* inc_list, int64_t N,
+                          double* g_nodal_b, cudaStream_t st);
 
 // tensor-core element operators (tc.cu)
 bool tc_supported(int nb, int B);   // the tensor-core kernel is the default for these shapes
 bool tc_available(int nb, int B);   // a tensor-core kernel exists for these shapes
 int tc_prepare(Model& md, cudaStream_t st);
+int tc_prepare_one_tile(Model& md, cudaStream_t st);   // one-tile digits even when n_b is padded beyond 16
 int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
                       const double* ub, const double* udb, const double* uddb, double* q, double* fhat,
-                      double* store_int, const double* fwd_int, double* grad_int, double* u_out, cudaStream_t st);
+                      double* store_int, const double* fwd_int, double* grad_int, double* u_out, cudaStream_t st,
+                      const int32_t* elems = nullptr, int64_t n_elems = 0, int* status = nullptr);
 
 struct FwdState {
   Model* model = nullptr;
@@ -251,9 +343,15 @@ struct FwdState {
   // ckpt_every == 0: [K][n_nodal][B] nodal velocities after every step;
   // ckpt_every == c > 0: [ceil(K/c) - 1][state_doubles] Newmark states before steps c, 2c, ...
   DevBuf store;
-  DevBuf store_u;               // full kernel: [K][n_nodal][B] nodal displacements after every step
+  DevBuf store_u;               // full kernel and exact adjoint: [K][n_nodal][B] nodal displacements after every step
+  DevBuf store_a;               // exact adjoint: [K][n_nodal][B] nodal accelerations after every step
+  bool exact = false;           // written for the exact adjoint (FP64 element kernel, u and u'' kept)
   DevBuf values, nodes;         // wavelets and source nodes, for the recompute (c > 0)
-  ~FwdState() { store_release(store); }
+  // the largest store goes to the one-slot cache (the velocities, or the exact adjoint's displacements)
+  ~FwdState() {
+    if (store.p) store_release(store);
+    else store_release(store_u);
+  }
 };
 
 }  // namespace sbfwi

@@ -14,8 +14,8 @@
 //     pivoting inside each separator block).
 #include <algorithm>
 #include <cmath>
-#include <memory>
 #include <cstdio>
+#include <memory>
 #include <vector>
 
 #include "dd.cuh"
@@ -244,6 +244,11 @@ struct ElemArgs {
   double* mats;               // [E][n][3][nb][nb], zero beyond n_b(e)
   double* rt;                 // [E][2][nb][nb]
   double* S;                  // [E][nb][nb]
+  // exact discrete adjoint (nullable; see ExactOps in internal.h)
+  double* xops;               // [E][n][nb][nb] G_i, the inverse of the modified pivot block phi_i
+  double* xel;                // [E][6][nb][nb] rho_0, W, Gamma, Y_theta, Y_phi, Y_M
+  double* kq;                 // [E][L][ng][4] quadrature factors of Eq. (Es): c^2 w det (b1.b1),
+                              // c^2 w det (b2.b1), c^2 w det (b2.b2), w det
   int* status;
 };
 
@@ -476,6 +481,8 @@ __global__ void element_setup_kernel(ElemArgs a) {
     K[1] = dd_mul(wdc, dd_add(dd_mul(b2x, b1x), dd_mul(b2y, b1y)));
     K[2] = dd_mul(wdc, dd_add(dd_mul(b2x, b2x), dd_mul(b2y, b2y)));
     K[3] = wd;
+    if (a.kq)
+      for (int k = 0; k < 4; ++k) a.kq[((e * a.L + l) * ng + g) * 4 + k] = K[k].hi;
   }
   __syncthreads();
 
@@ -544,6 +551,19 @@ __global__ void element_setup_kernel(ElemArgs a) {
         __syncthreads();
         gj_inverse<Op>(nb, T1, Gm, sm.col, sm.piv, a.status);
         mm<Op>(nb, th, Gm, Hp);                                   // Hp <- rho_0
+        if (a.xel) {
+          // rho_0, and the ghost u_{-1} = u_1 + Gamma u_0 from row -1: Gamma = -theta_{-1}^{-1} E1_0^T
+          double* X = a.xel + e * 6 * nns;
+          for (int t = tid; t < nn; t += nt) {
+            const int r = t / nb, cc = t - r * nb;
+            dd g = Op::make(0.0);
+            for (int k = 0; k < nb; ++k) g = Op::fma(g, Gm[r * nb + k], E1w[s_cur][cc * nb + k]);
+            const int64_t to = (int64_t)r * nbs + cc;
+            X[to] = Hp[t].hi;
+            X[2 * nns + to] = -g.hi;
+          }
+          __syncthreads();
+        }
         // phi_0 -= rho_0 phi_{-1}; psi_0 -= rho_0 psi_{-1}
         for (int t = tid; t < nn; t += nt) {
           const int r = t / nb, cc = t - r * nb;
@@ -563,6 +583,11 @@ __global__ void element_setup_kernel(ElemArgs a) {
         }
         __syncthreads();
       } else {
+        if (i == n && a.xel) {
+          // the unmodified phi_n, for the ghost u_{n+1} (the next-point window slot is free at i = n)
+          for (int t = tid; t < nn; t += nt) E0w[s_next][t] = ph[t];
+          __syncthreads();
+        }
         // Thomas sweep: phi_i -= theta_i phi_{i-1}^{-1} psi_{i-1} = theta_i H_{i-1}
         mm<Op>(nb, th, Hp, T1);
         for (int t = tid; t < nn; t += nt) ph[t] = Op::sub(ph[t], T1[t]);
@@ -570,6 +595,10 @@ __global__ void element_setup_kernel(ElemArgs a) {
       }
       if (i < n) {
         gj_inverse<Op>(nb, ph, Gm, sm.col, sm.piv, a.status);     // G_i, destroys ph
+        if (a.xops) {
+          double* Gi = a.xops + (e * (int64_t)n + i) * nns;
+          for (int t = tid; t < nn; t += nt) Gi[(int64_t)(t / nb) * nbs + (t % nb)] = Gm[t].hi;
+        }
         double* Pi = mats_e + (int64_t)i * matstride;
         for (int t = tid; t < nn; t += nt) {
           const int r = t / nb, cc = t - r * nb;
@@ -604,6 +633,29 @@ __global__ void element_setup_kernel(ElemArgs a) {
           T1[t] = s;
         }
         __syncthreads();
+        if (a.xel) {
+          // W, and the ghost u_{n+1} from the unmodified row n:
+          // u_{n+1} = -(Y_theta u_{n-1} + Y_phi u_n - Y_M u''_n), Y_X = psi_n^{-1} X with
+          // X = theta_n, the stiffness part of phi_n (phi_n + xi_n^2 M0_n / (beta dt^2)), xi_n^2 M0_n
+          double* X = a.xel + e * 6 * nns;
+          for (int t = tid; t < nn; t += nt) {
+            const int r = t / nb, cc = t - r * nb;
+            dd yt = Op::make(0.0), yp = Op::make(0.0), ym = Op::make(0.0);
+            for (int k = 0; k < nb; ++k) {
+              const dd gk = Gm[r * nb + k];
+              const dd mk = Op::mul(x2, M0w[w_cur][k * nb + cc]);
+              yt = Op::fma(yt, gk, th[k * nb + cc]);
+              yp = Op::fma(yp, gk, Op::add(E0w[s_next][k * nb + cc], Op::mul(a.mass, mk)));
+              ym = Op::fma(ym, gk, mk);
+            }
+            const int64_t to = (int64_t)r * nbs + cc;
+            X[nns + to] = T1[t].hi;
+            X[3 * nns + to] = yt.hi;
+            X[4 * nns + to] = yp.hi;
+            X[5 * nns + to] = ym.hi;
+          }
+          __syncthreads();
+        }
         // phi_{n+1} modified = E1_n^T - theta_{n+1} H_{n-1}, theta_{n+1} = -xi_n E0_n/(2h)
         for (int t = tid; t < nn; t += nt) {
           const int r = t / nb, cc = t - r * nb;
@@ -791,6 +843,35 @@ __global__ void front_factor_kernel(FactorArgs a) {
     double acc = F[(int64_t)(s + r) * f + s + c];
     for (int k = 0; k < s; ++k) acc = fma(-C[(int64_t)r * s + k], F[(int64_t)k * f + s + c], acc);
     U[t] = acc;
+  }
+}
+
+// Factors of the transposed global matrix from those of the matrix: the front of a tree node
+// for A^T is the transpose of its front for A, so X' = F11^{-T} = X^T, G' = X' F21^T = C^T and
+// C' = F12^T X' = G^T (same storage layout: X' s x s, G' s x b, C' b x s).  One block per node.
+__global__ void transpose_factors_kernel(const TreeNodeDev* nodes, int n_nodes, const double* f, double* ft) {
+  for (int v = blockIdx.x; v < n_nodes; v += gridDim.x) {
+    const TreeNodeDev nd = nodes[v];
+    const int s = nd.s, b = nd.b;
+    if (s == 0) continue;
+    const double* X = f + nd.X_off;
+    const double* G = X + (int64_t)s * s;
+    const double* C = G + (int64_t)s * b;
+    double* Xt = ft + nd.X_off;
+    double* Gt = Xt + (int64_t)s * s;
+    double* Ct = Gt + (int64_t)s * b;
+    for (int64_t t = threadIdx.x; t < (int64_t)s * s; t += blockDim.x) {
+      const int r = (int)(t / s), c = (int)(t - (int64_t)r * s);
+      Xt[t] = X[(int64_t)c * s + r];
+    }
+    for (int64_t t = threadIdx.x; t < (int64_t)s * b; t += blockDim.x) {     // G'[r][c] = C[c][r], r < s, c < b
+      const int r = (int)(t / b), c = (int)(t - (int64_t)r * b);
+      Gt[t] = C[(int64_t)c * s + r];
+    }
+    for (int64_t t = threadIdx.x; t < (int64_t)b * s; t += blockDim.x) {     // C'[r][c] = G[c][r], r < b, c < s
+      const int r = (int)(t / s), c = (int)(t - (int64_t)r * s);
+      Ct[t] = G[(int64_t)c * b + r];
+    }
   }
 }
 
@@ -1037,6 +1118,56 @@ int ensure_gradient_operator(const Mesh& m, cudaStream_t st) {
   return SBFWI_OK;
 }
 
+// One launch sequence of the element set-up kernel (chunked when the working matrices
+// live in global memory).  E_out: the comparison method's coefficient matrices only;
+// xops/xel/kq: the exact adjoint's extra operators (nullable).
+static int launch_element_setup(Model& md, const Mesh& m, const double* rho_hi, const double* rho_lo, double* E_out,
+                                double* xops, double* xel, double* kq, int* status, cudaStream_t st) {
+  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
+  const int ng = (3 * p + 2) / 2;
+  const int64_t E = m.n_elem, nn = (int64_t)nb * nb;
+  const MeshDevice& d = *m.dev;
+  Profiler& prof = profiler();
+  ElemArgs a;
+  a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
+  a.nbe = d.nbe.as<int32_t>(); a.lptr = d.lptr.as<int64_t>(); a.mat_ws = nullptr; a.e0 = 0;
+  a.E_out = E_out;
+  a.xops = xops; a.xel = xel; a.kq = kq;
+  a.c = md.c;
+  a.mass = dd_div(dd_make(1.0), dd_mul(dd_make(md.beta), two_prod(md.dt, md.dt)));
+  a.h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
+  a.node_xy = d.xy.as<double>(); a.centre_xy = d.ctr.as<double>();
+  a.line_nodes = d.lines.as<int64_t>(); a.line_local = d.lloc.as<int32_t>(); a.dofs = d.dofs.as<int32_t>();
+  a.rho_hi = rho_hi; a.rho_lo = rho_lo;
+  a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>(); a.tab = d.tab.as<double>();
+  a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>(); a.S = md.S.as<double>(); a.status = status;
+  // the 16 working matrices live in shared memory up to n_b = 24; beyond, in a global
+  // workspace, with the elements set up in chunks that bound its size
+  const size_t small = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb) + 16;
+  const size_t mat_bytes = sizeof(dd) * 16 * (size_t)nn;
+  const bool in_smem = small + mat_bytes <= 160 * 1024;
+  const size_t smem = in_smem ? small + mat_bytes : small;
+  SBFWI_CUDA(cudaFuncSetAttribute(element_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaFuncAttributes fattr;
+  SBFWI_CUDA(cudaFuncGetAttributes(&fattr, element_setup_kernel));
+  int threads = (int)std::min<int64_t>((nn + 31) / 32 * 32, fattr.maxThreadsPerBlock / 32 * 32);
+  if (threads < 64) threads = 64;
+  const int64_t chunk = in_smem ? E : std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)((256u << 20) / mat_bytes)));
+  DevBuf ws;
+  if (!in_smem) {
+    SBFWI_CUDA(ws.alloc(mat_bytes * chunk));
+    a.mat_ws = ws.as<dd>();
+  }
+  for (int64_t e0 = 0; e0 < E; e0 += chunk) {
+    a.e0 = e0;
+    element_setup_kernel<<<(unsigned)std::min(chunk, E - e0), threads, smem, st>>>(a);
+    prof.count(kPhaseSetup);
+    SBFWI_CUDA(cudaGetLastError());
+  }
+  if (!in_smem) SBFWI_CUDA(cudaStreamSynchronize(st));   // the workspace is freed on return
+  return SBFWI_OK;
+}
+
 int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st) {
   const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
   const int ng = (3 * p + 2) / 2;
@@ -1095,6 +1226,10 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   }
   SBFWI_CUDA(md.rho_nodal.alloc(sizeof(double) * np));
   SBFWI_CUDA(cudaMemcpyAsync(md.rho_nodal.p, rho_hi.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+  if (!md.lfe) {
+    SBFWI_CUDA(md.rho_lo.alloc(sizeof(double) * np));
+    SBFWI_CUDA(cudaMemcpyAsync(md.rho_lo.p, rho_lo.p, sizeof(double) * np, cudaMemcpyDeviceToDevice, st));
+  }
 
   if (md.lfe) {
     const unsigned blocks = (unsigned)std::min<int64_t>((m.n_int + 255) / 256, 152 * 8);
@@ -1106,8 +1241,9 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
 
   // element set-up
   const int64_t nn = (int64_t)nb * nb;
-  SBFWI_CUDA(md.mats.alloc(sizeof(double) * E * n * 3 * nn));
-  SBFWI_CUDA(md.rt.alloc(sizeof(double) * E * 2 * nn));
+  // the comparison method has no radial interior: no per-point operators
+  SBFWI_CUDA(md.mats.alloc(md.lfe ? 16 : sizeof(double) * E * n * 3 * nn));
+  SBFWI_CUDA(md.rt.alloc(md.lfe ? 16 : sizeof(double) * E * 2 * nn));
   SBFWI_CUDA(md.S.alloc(sizeof(double) * E * nn));
   if (m.uneven) {   // rows and columns beyond an element's n_b stay zero
     SBFWI_CUDA(cudaMemsetAsync(md.mats.p, 0, md.mats.bytes, st));
@@ -1115,74 +1251,20 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     SBFWI_CUDA(cudaMemsetAsync(md.S.p, 0, md.S.bytes, st));
   }
   {
-    ElemArgs a;
-    a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
-    a.nbe = d.nbe.as<int32_t>(); a.lptr = d.lptr.as<int64_t>(); a.mat_ws = nullptr; a.e0 = 0;
     DevBuf E_dev;
-    a.E_out = nullptr;
     if (md.lfe) {
       SBFWI_CUDA(E_dev.alloc(sizeof(double) * E * 4 * nn));
       SBFWI_CUDA(cudaMemsetAsync(E_dev.p, 0, E_dev.bytes, st));
-      a.E_out = E_dev.as<double>();
     }
-    a.c = md.c;
-    a.mass = dd_div(dd_make(1.0), dd_mul(dd_make(md.beta), two_prod(md.dt, md.dt)));
-    a.h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
-    a.node_xy = d.xy.as<double>(); a.centre_xy = d.ctr.as<double>();
-    a.line_nodes = d.lines.as<int64_t>(); a.line_local = d.lloc.as<int32_t>(); a.dofs = d.dofs.as<int32_t>();
-    a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>();
-    a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>(); a.tab = d.tab.as<double>();
-    a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>(); a.S = md.S.as<double>(); a.status = status.as<int>();
-    // the 16 working matrices live in shared memory up to n_b = 24; beyond, in a global
-    // workspace, with the elements set up in chunks that bound its size
-    const size_t small = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb) + 16;
-    const size_t mat_bytes = sizeof(dd) * 16 * (size_t)nn;
-    const bool in_smem = small + mat_bytes <= 160 * 1024;
-    const size_t smem = in_smem ? small + mat_bytes : small;
-    SBFWI_CUDA(cudaFuncSetAttribute(element_setup_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cudaFuncAttributes fattr;
-    SBFWI_CUDA(cudaFuncGetAttributes(&fattr, element_setup_kernel));
-    int threads = (int)std::min<int64_t>((nn + 31) / 32 * 32, fattr.maxThreadsPerBlock / 32 * 32);
-    if (threads < 64) threads = 64;
-    const int64_t chunk = in_smem ? E : std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)((256u << 20) / mat_bytes)));
-    DevBuf ws;
-    if (!in_smem) {
-      SBFWI_CUDA(ws.alloc(mat_bytes * chunk));
-      a.mat_ws = ws.as<dd>();
-    }
-    for (int64_t e0 = 0; e0 < E; e0 += chunk) {
-      a.e0 = e0;
-      element_setup_kernel<<<(unsigned)std::min(chunk, E - e0), threads, smem, st>>>(a);
-      prof.count(kPhaseSetup);
-      SBFWI_CUDA(cudaGetLastError());
-    }
-    if (!in_smem) SBFWI_CUDA(cudaStreamSynchronize(st));   // the workspace is freed on return
+    if ((rc = launch_element_setup(md, m, rho_hi.as<double>(), rho_lo.as<double>(), md.lfe ? E_dev.as<double>() : nullptr,
+                                   nullptr, nullptr, nullptr, status.as<int>(), st)))
+      return rc;
     if (md.lfe) {
-      // the comparison method's K and M per element on the host; S = K + a0 M for the global
-      // system, M for the per-step effective sources
-      std::vector<double> Eh((size_t)E * 4 * nn), Sh((size_t)E * nn, 0.0), Mh((size_t)E * nn, 0.0);
-      SBFWI_CUDA(cudaMemcpyAsync(Eh.data(), E_dev.p, sizeof(double) * Eh.size(), cudaMemcpyDeviceToHost, st));
-      SBFWI_CUDA(cudaStreamSynchronize(st));
-      for (int64_t e = 0; e < E; ++e) {
-        const int ne = m.nbe[e];
-        std::vector<double> blk(4 * (size_t)ne * ne), K((size_t)ne * ne), M((size_t)ne * ne);
-        for (int k = 0; k < 4; ++k)
-          for (int r = 0; r < ne; ++r)
-            for (int c = 0; c < ne; ++c)
-              blk[(size_t)k * ne * ne + r * ne + c] = Eh[(size_t)(e * 4 + k) * nn + (size_t)r * nb + c];
-        int rc_l = lfe_element(blk.data(), blk.data() + ne * ne, blk.data() + 2 * ne * ne, blk.data() + 3 * ne * ne,
-                               ne, K.data(), M.data());
-        if (rc_l) return rc_l;
-        for (int r = 0; r < ne; ++r)
-          for (int c = 0; c < ne; ++c) {
-            Sh[(size_t)e * nn + (size_t)r * nb + c] = K[(size_t)r * ne + c] + md.a0 * M[(size_t)r * ne + c];
-            Mh[(size_t)e * nn + (size_t)r * nb + c] = M[(size_t)r * ne + c];
-          }
-      }
-      int rc_u;
-      if ((rc_u = upload(md.lfe_M, Mh, st))) return rc_u;
-      SBFWI_CUDA(cudaMemcpyAsync(md.S.p, Sh.data(), sizeof(double) * Sh.size(), cudaMemcpyHostToDevice, st));
-      SBFWI_CUDA(cudaStreamSynchronize(st));
+      // the comparison method's K and M of every element on the device (lfe_setup.cu); S = K + a0 M
+      // for the global system, M for the per-step effective sources
+      SBFWI_CUDA(md.lfe_M.alloc(sizeof(double) * E * nn));
+      SBFWI_CUDA(cudaMemsetAsync(md.lfe_M.p, 0, md.lfe_M.bytes, st));
+      if ((rc = lfe_setup_device(md, E_dev.as<double>(), md.S.as<double>(), md.lfe_M.as<double>(), st))) return rc;
     }
   }
 
@@ -1229,6 +1311,61 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   if ((rc = read_status(status, st, &code))) return rc;
   if (code == SBFWI_EINVAL) return fail(SBFWI_EINVAL, "density must be positive at every nodal point");
   if (code) return fail(SBFWI_ESINGULAR, "a pivot block of the radial condensation or a separator block of the global matrix is singular");
+  return SBFWI_OK;
+}
+
+// The exact discrete adjoint's operators for a model set up with the radial finite
+// differences: the element set-up runs once more (same density, so mats, rt and S are
+// rewritten with the same values) and also emits G_i, rho_0, W, the ghost operators and
+// the quadrature factors; the global factors are transposed.
+int prepare_exact(Model& md, cudaStream_t st) {
+  if (md.exact_ready) return SBFWI_OK;
+  if (md.lfe) return fail(SBFWI_EUNSUPPORTED, "the exact adjoint is built for the radial finite differences, not the comparison method");
+  const Mesh& m = *md.mesh;
+  const int nb = m.nb, n = m.n, L = m.L, ng = (3 * m.p + 2) / 2;
+  const int64_t E = m.n_elem, nn = (int64_t)nb * nb;
+  SBFWI_CUDA(md.xops.alloc(sizeof(double) * E * n * nn));
+  SBFWI_CUDA(md.xel.alloc(sizeof(double) * E * 6 * nn));
+  SBFWI_CUDA(md.kq.alloc(sizeof(double) * E * L * ng * 4));
+  SBFWI_CUDA(cudaMemsetAsync(md.xops.p, 0, md.xops.bytes, st));
+  SBFWI_CUDA(cudaMemsetAsync(md.xel.p, 0, md.xel.bytes, st));
+  SBFWI_CUDA(cudaMemsetAsync(md.kq.p, 0, md.kq.bytes, st));
+  DevBuf status;
+  SBFWI_CUDA(status.alloc(sizeof(int)));
+  SBFWI_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+  Profiler& prof = profiler();
+  prof.begin(kPhaseSetup, st);
+  int rc = launch_element_setup(md, m, md.rho_nodal.as<double>(), md.rho_lo.as<double>(), nullptr, md.xops.as<double>(),
+                                md.xel.as<double>(), md.kq.as<double>(), status.as<int>(), st);
+  if (rc) return rc;
+  const Tree& t = m.tree;
+  SBFWI_CUDA(md.factors_t.alloc(sizeof(double) * (size_t)std::max<int64_t>(t.X_total, 1)));
+  const int tn = (int)t.nodes.size();
+  transpose_factors_kernel<<<(unsigned)std::min(tn, 152 * 8), 256, 0, st>>>(m.dev->tree_nodes.as<TreeNodeDev>(), tn,
+                                                                           md.factors.as<double>(),
+                                                                           md.factors_t.as<double>());
+  prof.count(kPhaseSetup);
+  SBFWI_CUDA(cudaGetLastError());
+  prof.end(kPhaseSetup, st);
+  int code = 0;
+  if ((rc = read_status(status, st, &code))) return rc;
+  if (code) return fail(SBFWI_ESINGULAR, "a pivot block of the radial condensation is singular");
+  if (!m.dev->inc_ready) {
+    // the elements at each global node (padding dofs, which point at node N, left out)
+    std::vector<int64_t> ptr(m.n_nodes + 1, 0), list;
+    for (int64_t e = 0; e < E; ++e)
+      for (int j = 0; j < m.nbe[e]; ++j) ++ptr[m.dofs[e * nb + j] + 1];
+    for (int64_t g = 0; g < m.n_nodes; ++g) ptr[g + 1] += ptr[g];
+    list.resize(ptr[m.n_nodes]);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+      for (int j = 0; j < m.nbe[e]; ++j) list[fill[m.dofs[e * nb + j]]++] = e * nb + j;
+    if ((rc = upload(m.dev->inc_ptr, ptr, st))) return rc;
+    if ((rc = upload(m.dev->inc_list, list, st))) return rc;
+    SBFWI_CUDA(cudaStreamSynchronize(st));
+    m.dev->inc_ready = true;
+  }
+  md.exact_ready = true;
   return SBFWI_OK;
 }
 

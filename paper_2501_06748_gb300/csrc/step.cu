@@ -51,7 +51,10 @@ struct ElemStepArgs {
   double* store_int;    // forward: velocities of this step, interior part [E][n][nb][B]
   const double* fwd_int;// adjoint: paired forward velocities, interior part
   double* grad_int;     // adjoint: accumulators [E][n][nb][B]
-  double* u_out;        // full Frechet kernel: the new interior displacements [E][n][nb][B]
+  double* u_out;        // full Frechet kernel, exact adjoint: the new interior displacements [E][n][nb][B]
+  double* a_out;        // exact adjoint: the new interior accelerations [E][n][nb][B]
+  const int32_t* elems; // the elements of this launch (an element class), or NULL for all
+  int64_t n_elems;
 };
 
 __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
@@ -60,8 +63,9 @@ __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
   const int per = nb * B;
   const int tid = threadIdx.x;
   const int le = tid / per, rem = tid - le * per, r = rem / B, s = rem - r * B;
-  const int64_t e = (int64_t)blockIdx.x * a.epc + le;
-  const bool act = (le < a.epc) && (e < a.E);
+  const int64_t idx = (int64_t)blockIdx.x * a.epc + le;
+  const bool act = (le < a.epc) && (idx < a.n_elems);
+  const int64_t e = act ? (a.elems ? (int64_t)a.elems[idx] : idx) : 0;
   double* vbuf = sh + (size_t)le * n * per;                 // [n][nb][B] predictors of the new state
   double* xb = sh + (size_t)a.epc * n * per + (size_t)le * per;   // [nb][B] exchange
   double* vn = sh + (size_t)a.epc * (n + 1) * per + (size_t)le * per;
@@ -88,6 +92,7 @@ __global__ void __launch_bounds__(512) element_step_kernel(ElemStepArgs a) {
         if (a.store_int) a.store_int[o] = udn;
         if (a.grad_int) a.grad_int[o] = fma(a.fwd_int[o], udn, a.grad_int[o]);   // dt applied at the end
         if (a.u_out) a.u_out[o] = un;
+        if (a.a_out) a.a_out[o] = uddn;
         if (a.do_up) vbuf[i * per + r * B + s] = fma(a.a0, un, fma(a.a1, udn, a.a2 * uddn));
       }
       __syncthreads();
@@ -621,7 +626,8 @@ struct BoundaryArgs {
   const int64_t* rec;
   double* traces;         // [B][R][K]
   double* store_b;        // forward: velocities of this step at the boundary nodes [N][B]
-  double* store_ub;       // forward, full kernel: displacements of this step at the boundary nodes [N][B]
+  double* store_ub;       // forward, full kernel / exact adjoint: displacements of this step at the boundary nodes [N][B]
+  double* store_ab;       // forward, exact adjoint: accelerations of this step at the boundary nodes [N][B]
   const double* fwd_b;    // adjoint: paired forward velocities [N][B]
   double* grad_b;         // adjoint accumulators [N][B]
 };
@@ -637,6 +643,7 @@ __global__ void boundary_update_kernel(BoundaryArgs a) {
     a.ub[t] = un; a.udb[t] = udn; a.uddb[t] = uddn;
     if (a.store_b) a.store_b[t] = udn;
     if (a.store_ub) a.store_ub[t] = un;
+    if (a.store_ab) a.store_ab[t] = uddn;
     if (a.grad_b) a.grad_b[t] = fma(a.fwd_b[t], udn, a.grad_b[t]);          // dt applied at the end
   }
   if (a.traces) {
@@ -811,12 +818,11 @@ static size_t block_task_doubles(const Task& t, int B, bool fwd) {
 // lanes per output fill the block's 256 threads.  Leaves that eliminate nothing get
 // no task (their parents read f_hat directly).  Warp tasks are grouped so that a
 // level's items about fill the grid.
-int build_level_tasks(Model& md, int B, int grid) {
+int build_level_tasks(const Model& md, LevelTasks& lt, int B, int grid) {
   const int rows_max = std::max(1, 256 / B);
   const Tree& t = md.mesh->tree;
   const int L = t.levels;
   std::vector<Task> fwd, bwd;
-  LevelTasks& lt = md.tasks;
   lt.fwd_start.assign(L + 1, 0); lt.bwd_start.assign(L + 1, 0);
   lt.fwd_wstart.assign(L, 0); lt.bwd_wstart.assign(L, 0);
   lt.fwd_group.assign(L, 1); lt.bwd_group.assign(L, 1);
@@ -938,9 +944,15 @@ struct RunBuffers {
   DevBuf u, ud, udd, v, ub, udb, uddb, q, fhat, ext, ysep, ybnd, x;
   DevBuf lam;                       // full kernel, adjoint: interior displacements of the current step
   DevBuf grad_int;                  // grad accumulators [n_nodal][B] (adjoint)
+  // exact adjoint: mu of rows -1..n, v_bar_n per element, ghosts of the forward solution,
+  // Gauss-point products, boundary station of the gradient per element
+  DevBuf mu, vbn, ghost, gacc, gbnd;
 };
 
-enum class Mode { Forward, Adjoint };
+// Forward: the forward solve; Adjoint: the paper's time-reversed adjoint with the velocity
+// kernel; Exact: the exact discrete adjoint (transposed condensation, transposed global
+// solve, Gauss-point products of the derivative of every block)
+enum class Mode { Forward, Adjoint, Exact };
 
 // The time loop of B shots over K Newmark steps, resumable over windows of steps.
 // Forward: values = wavelets [B][K] at nodes[0..B-1], receivers nodes[B..B+R-1];
@@ -967,10 +979,12 @@ struct Stepper {
   // forward: velocities of step k go to store + (k - store_k0) * n_nodal * B
   double* store = nullptr;
   double* store_u = nullptr;        // full kernel: displacements of step k at store_u + (k - store_k0) * n_nodal * B
+  double* store_a = nullptr;        // exact adjoint: accelerations of step k, paired like store_u
   int64_t store_k0 = 0;
   // adjoint: forward velocities of step j are read at fwd + (j - fwd_k0) * n_nodal * B
   const double* fwd = nullptr;
-  const double* fwd_u = nullptr;    // full kernel: forward displacements, paired like fwd
+  const double* fwd_u = nullptr;    // full kernel and exact adjoint: forward displacements, paired like fwd
+  const double* fwd_a = nullptr;    // exact adjoint: forward accelerations of step j at fwd_a + (j - fwd_k0) * n_nodal * B
   int64_t fwd_k0 = 0;
   // source values and nodes (forward: wavelets [B][K], nodes = B sources then R
   // receivers; adjoint: residuals [B][R][K], nodes = R receivers) and the device
@@ -979,23 +993,44 @@ struct Stepper {
   const int64_t* nodes = nullptr;
   double* traces = nullptr;
 
+  // the solve's task lists: the model's (shared by the steppers of one call), or the
+  // caller's own when this stepper outlives a call (a session: a later call with another
+  // shot count rebuilds the model's)
+  LevelTasks* tasks_own = nullptr;
+  // resume: the window that run(0, k1) starts continues a nonzero state (the forward sweep
+  // of its first step is computed from it)
+  bool resume = false;
+
   Stepper(Model& m, Mode mo, int b, int64_t k, int r, RunBuffers& buffers, cudaStream_t s)
       : md(m), mode(mo), B(b), R(r), K(k), rb(buffers), st(s) {}
 
   int init();
   int zero_state();
   int run(int64_t k0, int64_t k1);
+  // exact adjoint: forward steps k1-1 down to k0 (fwd_u, fwd_a hold those steps), and the
+  // gradient on the nodal points once every step has run
+  int run_exact(int64_t k0, int64_t k1);
+  int finalize_exact();
   int check_status();
   bool tensor_core_path() const { return use_tc; }
+  // doubles per step and shot in a forward-field store, and where its boundary part starts:
+  // every nodal point, or the boundary nodes alone for the comparison method (no radial interior)
+  int64_t store_stride() const { return md.lfe ? N : np; }
+  int64_t store_bnd_off() const { return md.lfe ? 0 : nint; }
   // the Newmark state between windows, as one flat array of state_doubles() values
   int64_t state_doubles() const;
   int save_state(double* dst);
   int restore_state(const double* src);
+  // zero one shot column of the Newmark state (and of the gradient accumulators)
+  int zero_column(int s);
 
  private:
   int nb = 0, n = 0;
   int64_t E = 0, N = 0, np = 0, nint = 0;
   bool use_tc = false, persistent = false;
+  bool use_mixed = false;            // per-class kernels (one-tile tensor-core + FP64) on an uneven mesh
+  DevBuf elems_tc, elems_fp;         // the element classes of the mixed kernels
+  int64_t n_tc = 0, n_fp = 0;
   ElemStepArgs ea;
   SolveArgs sa;
   PersistentSolveArgs pa;
@@ -1006,10 +1041,14 @@ struct Stepper {
   int e_threads = 0, p_grid = 0;
   unsigned e_blocks = 0, b_blocks = 0;
   DevBuf bar, pstatus;
+  LevelTasks* lt = nullptr;
   bool flow = false;                 // dataflow solve (default) instead of level barriers
   DevBuf flow_counters;              // done_f [nodes] | done_b [nodes] | item counter (u64)
   FlowArgs fa;
   unsigned flow_gen = 0;
+  ExactElemArgs xa;
+  ExactBoundaryArgs xba;
+  ExactGradArgs xga;
   bool use_window = false;
   cudaAccessPolicyWindow window = {};
   int setup_l2_window(int device);
@@ -1029,27 +1068,63 @@ int Stepper::init() {
   // element kernel: FP16 tensor cores with error-free splitting when the shapes allow,
   // else FP64 (SBFWI_ELEMENT=fp64 forces the FP64 kernel)
   const char* elem_env = std::getenv("SBFWI_ELEMENT");
+  const bool exact = md.grad_mode == SBFWI_GRAD_EXACT || mode == Mode::Exact;
   if (md.lfe) {
     use_tc = false;                  // the comparison method has no radial interior
+    if (mode == Mode::Exact) return fail(SBFWI_EUNSUPPORTED, "the exact adjoint is not built for the comparison method");
+  } else if (exact) {
+    // the exact adjoint keeps u and u'' of every step, which the FP64 kernel writes
+    if (md.elem_pref == SBFWI_ELEMENT_TENSOR)
+      return fail(SBFWI_EUNSUPPORTED, "the exact adjoint runs the FP64 element kernel, not the tensor-core one");
+    use_tc = false;
   } else if (md.elem_pref == SBFWI_ELEMENT_TENSOR) {
     if (!tc_available(nb, B))
       return fail(SBFWI_EUNSUPPORTED, "no tensor-core element kernel for this n_b and shot count");
     use_tc = true;
   } else if (md.elem_pref == SBFWI_ELEMENT_FP64) {
     use_tc = false;
+  } else if (md.elem_pref == SBFWI_ELEMENT_MIXED) {
+    use_tc = false;
+    use_mixed = true;
   } else {
     use_tc = tc_supported(nb, B) && !(elem_env && std::strcmp(elem_env, "fp64") == 0);
   }
-  if (use_tc && !md.tc_ready) {
+  // elements of one mesh with different n_b: those with n_b <= 16 on the one-tile tensor-core
+  // kernel, the others on the FP64 kernel, each element keeping its own kernel's state
+  int64_t n_small = 0;
+  for (int32_t v : m.nbe) n_small += v <= 16 ? 1 : 0;
+  const bool mixed_ok = !md.lfe && !exact && B <= 8 && nb > 16 && n_small > 0 && n_small < E;
+  if (use_mixed && !mixed_ok)
+    return fail(SBFWI_EUNSUPPORTED, "mixed element kernels need elements on both sides of n_b = 16 and at most 8 shots");
+  if (md.elem_pref == SBFWI_ELEMENT_AUTO && mixed_ok && !tc_supported(nb, B) &&
+      !(elem_env && std::strcmp(elem_env, "fp64") == 0))
+    use_mixed = true;                // padded n_b 17..20 or beyond 32
+  if (use_tc && (!md.tc_ready || md.tc_one_tile)) {
     const int rc_tc = tc_prepare(md, st);
     if (rc_tc) return rc_tc;
   }
+  if (use_mixed) {
+    if (!md.tc_ready || !md.tc_one_tile) {
+      const int rc_tc = tc_prepare_one_tile(md, st);
+      if (rc_tc) return rc_tc;
+    }
+    std::vector<int32_t> small, large;
+    for (int64_t e = 0; e < E; ++e) (m.nbe[e] <= 16 ? small : large).push_back((int32_t)e);
+    SBFWI_CUDA(elems_tc.alloc(sizeof(int32_t) * small.size()));
+    SBFWI_CUDA(elems_fp.alloc(sizeof(int32_t) * large.size()));
+    SBFWI_CUDA(cudaMemcpy(elems_tc.p, small.data(), sizeof(int32_t) * small.size(), cudaMemcpyHostToDevice));
+    SBFWI_CUDA(cudaMemcpy(elems_fp.p, large.data(), sizeof(int32_t) * large.size(), cudaMemcpyHostToDevice));
+    n_tc = (int64_t)small.size();
+    n_fp = (int64_t)large.size();
+  }
   // the tensor-core path carries the predictor v and z = u' + dt (1 - gamma) u'' (in ud), not u, u''
-  SBFWI_CUDA(rb.u.alloc(sizeof(double) * (use_tc ? 1 : si)));
-  SBFWI_CUDA(rb.ud.alloc(sizeof(double) * si));
-  SBFWI_CUDA(rb.udd.alloc(sizeof(double) * (use_tc ? 1 : si)));
-  SBFWI_CUDA(rb.q.alloc(sizeof(double) * si));
-  if (use_tc) SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
+  // the comparison method keeps no interior state
+  const int64_t si_state = md.lfe ? 1 : si;
+  SBFWI_CUDA(rb.u.alloc(sizeof(double) * (use_tc ? 1 : si_state)));
+  SBFWI_CUDA(rb.ud.alloc(sizeof(double) * si_state));
+  SBFWI_CUDA(rb.udd.alloc(sizeof(double) * (use_tc ? 1 : si_state)));
+  SBFWI_CUDA(rb.q.alloc(sizeof(double) * si_state));
+  if (use_tc || use_mixed) SBFWI_CUDA(rb.v.alloc(sizeof(double) * si));
   SBFWI_CUDA(rb.ub.alloc(sizeof(double) * sb1));
   SBFWI_CUDA(rb.udb.alloc(sizeof(double) * sb1));
   SBFWI_CUDA(rb.uddb.alloc(sizeof(double) * sb1));
@@ -1062,6 +1137,19 @@ int Stepper::init() {
     SBFWI_CUDA(rb.grad_int.alloc(sizeof(double) * np * B));
     SBFWI_CUDA(cudaMemsetAsync(rb.grad_int.p, 0, rb.grad_int.bytes, st));
   }
+  if (mode == Mode::Exact) {
+    int rc_x = prepare_exact(md, st);
+    if (rc_x) return rc_x;
+    const int ng = (3 * m.p + 2) / 2;
+    SBFWI_CUDA(rb.mu.alloc(sizeof(double) * E * (n + 2) * nb * B));
+    SBFWI_CUDA(rb.vbn.alloc(sizeof(double) * E * nb * B));
+    SBFWI_CUDA(rb.ghost.alloc(sizeof(double) * E * 2 * nb * B));
+    SBFWI_CUDA(rb.gacc.alloc(sizeof(double) * E * (n + 1) * 4 * m.L * ng));
+    SBFWI_CUDA(rb.gbnd.alloc(sizeof(double) * E * nb));
+    SBFWI_CUDA(rb.grad_int.alloc(sizeof(double) * np));
+    for (DevBuf* b : {&rb.mu, &rb.vbn, &rb.ghost, &rb.gacc, &rb.gbnd, &rb.grad_int})
+      SBFWI_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
+  }
   int rc = zero_state();
   if (rc) return rc;
   // the solve's tasks are built for 4 blocks per SM; a block task stages its front's
@@ -1072,11 +1160,12 @@ int Stepper::init() {
   SBFWI_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device));
   SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
   const int grid = 4 * sms;
-  if (md.tasks.shots != B || md.tasks.grid != grid) {
-    rc = build_level_tasks(md, B, grid);
+  lt = tasks_own ? tasks_own : &md.tasks;
+  if (lt->shots != B || lt->grid != grid) {
+    rc = build_level_tasks(md, *lt, B, grid);
     if (rc) return rc;
   }
-  s_smem = sizeof(double) * std::max(md.tasks.block_doubles, 8 * solve_warp_doubles(B));
+  s_smem = sizeof(double) * std::max(lt->block_doubles, 8 * solve_warp_doubles(B));
   if (s_smem > 200 * 1024) return fail(SBFWI_EUNSUPPORTED, "solve staging area exceeds shared memory");
   for (const void* f : {(const void*)solve_forward_kernel, (const void*)solve_backward_kernel,
                         (const void*)solve_persistent_kernel, (const void*)solve_flow_kernel})
@@ -1089,7 +1178,7 @@ int Stepper::init() {
   ea.u = rb.u.as<double>(); ea.ud = rb.ud.as<double>(); ea.udd = rb.udd.as<double>();
   ea.ub = rb.ub.as<double>(); ea.udb = rb.udb.as<double>(); ea.uddb = rb.uddb.as<double>();
   ea.q = rb.q.as<double>(); ea.fhat = rb.fhat.as<double>();
-  ea.u_out = nullptr;
+  ea.u_out = nullptr; ea.a_out = nullptr;
   if (mode == Mode::Adjoint && md.kernel_terms == SBFWI_TERMS_FULL) {
     SBFWI_CUDA(rb.lam.alloc(sizeof(double) * std::max<int64_t>(si, 1)));
     SBFWI_CUDA(cudaMemsetAsync(rb.lam.p, 0, rb.lam.bytes, st));
@@ -1097,7 +1186,9 @@ int Stepper::init() {
     if (rc_g) return rc_g;
   }
   e_threads = ea.epc * nb * B;
-  e_blocks = (unsigned)((E + ea.epc - 1) / ea.epc);
+  ea.elems = use_mixed ? elems_fp.as<int32_t>() : nullptr;
+  ea.n_elems = use_mixed ? n_fp : E;
+  e_blocks = (unsigned)std::max<int64_t>(1, (ea.n_elems + ea.epc - 1) / ea.epc);
   e_smem = sizeof(double) * (size_t)ea.epc * (n + 2) * nb * B;
   cudaFuncAttributes eattr;
   SBFWI_CUDA(cudaFuncGetAttributes(&eattr, element_step_kernel));
@@ -1108,7 +1199,9 @@ int Stepper::init() {
 
   const MeshDevice& mdev = md.dev();
   sa.sep_nodes = md.solve_sep; sa.bnd_nodes = md.solve_bnd;
-  sa.src0 = md.solve_src0; sa.src1 = md.solve_src1; sa.factors = md.factors.as<double>();
+  sa.src0 = md.solve_src0; sa.src1 = md.solve_src1;
+  // the exact adjoint solves with the transposed matrix: same tree, transposed factors
+  sa.factors = mode == Mode::Exact ? md.factors_t.as<double>() : md.factors.as<double>();
   sa.fhat = rb.fhat.as<double>(); sa.ext = rb.ext.as<double>();
   sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
   sa.nb = nb; sa.B = B;
@@ -1130,36 +1223,38 @@ int Stepper::init() {
     persistent = md.solve_pref != SBFWI_SOLVE_LEVELS;
     flow = md.solve_pref == SBFWI_SOLVE_DATAFLOW;
   }
-  ftasks = md.tasks.fwd.as<Task>();
-  btasks = md.tasks.bwd.as<Task>();
-  rc = setup_l2_window(device);
+  ftasks = lt->fwd.as<Task>();
+  btasks = lt->bwd.as<Task>();
+  rc = mode == Mode::Exact ? SBFWI_OK : setup_l2_window(device);   // the window covers the forward factors
   if (rc) return rc;
+  // status word of the bounded device waits (the solve's barriers and counters, the element
+  // kernels' copy barriers)
+  SBFWI_CUDA(pstatus.alloc(sizeof(int)));
+  SBFWI_CUDA(cudaMemsetAsync(pstatus.p, 0, pstatus.bytes, st));
   if (persistent) {
     SBFWI_CUDA(bar.alloc(2 * sizeof(unsigned)));
-    SBFWI_CUDA(pstatus.alloc(sizeof(int)));
     SBFWI_CUDA(cudaMemsetAsync(bar.p, 0, bar.bytes, st));
-    SBFWI_CUDA(cudaMemsetAsync(pstatus.p, 0, pstatus.bytes, st));
     pa.s = sa;
     pa.fwd = ftasks; pa.bwd = btasks;
-    pa.fwd_meta = md.tasks.fwd_meta.as<int32_t>(); pa.bwd_meta = md.tasks.bwd_meta.as<int32_t>();
+    pa.fwd_meta = lt->fwd_meta.as<int32_t>(); pa.bwd_meta = lt->bwd_meta.as<int32_t>();
     pa.levels = t.levels;
     pa.bar = bar.as<unsigned>(); pa.status = pstatus.as<int>();
     pa.budget = 4000000000LL;            // ~2 s at 2 GHz
     pa.trace = nullptr;
-    p_grid = std::max(1, std::min(std::min(per_sm, 4) * sms, md.tasks.max_level_items));
+    p_grid = std::max(1, std::min(std::min(per_sm, 4) * sms, lt->max_level_items));
   }
   if (flow) {
     int per_sm_flow = 0;
     SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, solve_flow_kernel, 256, s_smem));
     if (per_sm_flow < 1) return fail(SBFWI_EUNSUPPORTED, "the dataflow solve does not fit on an SM");
-    const int T = md.tasks.nodes;
+    const int T = lt->nodes;
     const size_t cb = ((sizeof(unsigned) * 2 * (size_t)T + 15) / 16) * 16;
     SBFWI_CUDA(flow_counters.alloc(cb + sizeof(unsigned long long)));
     SBFWI_CUDA(cudaMemsetAsync(flow_counters.p, 0, flow_counters.bytes, st));
     fa.s = sa;
     fa.fwd = ftasks; fa.bwd = btasks;
-    fa.items = md.tasks.flow_items.as<int4>(); fa.n_items = md.tasks.n_items;
-    fa.node_info = md.tasks.node_info.as<int32_t>(); fa.nodes = T;
+    fa.items = lt->flow_items.as<int4>(); fa.n_items = lt->n_items;
+    fa.node_info = lt->node_info.as<int32_t>(); fa.nodes = T;
     fa.done_f = flow_counters.as<unsigned>(); fa.done_b = fa.done_f + T;
     fa.claim = reinterpret_cast<unsigned long long*>(flow_counters.as<char>() + cb);
     fa.status = pstatus.as<int>();
@@ -1172,8 +1267,41 @@ int Stepper::init() {
   ba.K = K;
   ba.a0 = md.a0; ba.a1 = md.a1; ba.a2 = md.a2; ba.c1 = md.c1; ba.c2 = md.c2; ba.dt = md.dt;
   ba.x = rb.x.as<double>(); ba.ub = rb.ub.as<double>(); ba.udb = rb.udb.as<double>(); ba.uddb = rb.uddb.as<double>();
-  ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.store_ub = nullptr; ba.fwd_b = nullptr; ba.grad_b = nullptr;
+  ba.rec = nullptr; ba.traces = nullptr; ba.store_b = nullptr; ba.store_ub = nullptr; ba.store_ab = nullptr;
+  ba.fwd_b = nullptr; ba.grad_b = nullptr;
   b_blocks = (unsigned)std::min<int64_t>((sb + 255) / 256, 152 * 8);
+
+  if (mode == Mode::Exact) {
+    const double beta = md.beta, gamma = md.gamma, dt = md.dt;
+    xa.nb = nb; xa.n = n; xa.B = B; xa.E = E; xa.N = N;
+    xa.epc = std::max(1, 128 / (nb * B));
+    xa.a0 = md.a0; xa.a1 = md.a1; xa.a2 = md.a2;
+    xa.cu = gamma / (beta * dt); xa.cud = 1.0 - gamma / beta; xa.cudd = dt * (1.0 - gamma / (2.0 * beta));
+    xa.du = 1.0 / (beta * dt * dt); xa.dud = -1.0 / (beta * dt); xa.dudd = 1.0 - 1.0 / (2.0 * beta);
+    xa.mats = md.mats.as<double>(); xa.rt = md.rt.as<double>();
+    xa.xops = md.xops.as<double>(); xa.xel = md.xel.as<double>(); xa.dofs = md.dev().dofs.as<int32_t>();
+    xa.ua = rb.u.as<double>(); xa.uda = rb.ud.as<double>(); xa.udda = rb.udd.as<double>();
+    xa.s = rb.q.as<double>(); xa.fbar = rb.x.as<double>(); xa.mu = rb.mu.as<double>(); xa.vbn = rb.vbn.as<double>();
+    xa.fhat = rb.fhat.as<double>(); xa.ghost = rb.ghost.as<double>();
+    xa.fu_int = xa.fu_b = xa.fa_b = nullptr;
+    if (xa.epc * nb * B > 512 || exact_element_smem(nb, n, B, xa.epc) > 227 * 1024)
+      return fail(SBFWI_EUNSUPPORTED, "n_b x shots x radial points too large for one element block of the exact adjoint");
+    xba.N = N; xba.B = B;
+    xba.a0 = md.a0; xba.a1 = md.a1; xba.a2 = md.a2;
+    xba.cu = xa.cu; xba.cud = xa.cud; xba.cudd = xa.cudd; xba.du = xa.du; xba.dud = xa.dud; xba.dudd = xa.dudd;
+    xba.ub = rb.ub.as<double>(); xba.udb = rb.udb.as<double>(); xba.uddb = rb.uddb.as<double>();
+    xba.ext = rb.ext.as<double>(); xba.vbn = rb.vbn.as<double>();
+    xba.inc_ptr = md.dev().inc_ptr.as<int64_t>(); xba.inc_list = md.dev().inc_list.as<int64_t>();
+    int Bp = 1;
+    while (Bp < B) Bp <<= 1;
+    xga.E = E; xga.N = N; xga.nb = nb; xga.n = n; xga.B = B; xga.Bp = Bp; xga.L = m.L; xga.ng = (3 * m.p + 2) / 2;
+    xga.h = (1.0 - m.xi0) / n;
+    xga.xi = md.dev().xih.as<double>(); xga.tab = md.dev().tab.as<double>();
+    xga.lptr = md.dev().lptr.as<int64_t>(); xga.line_local = md.dev().lloc.as<int32_t>();
+    xga.dofs = md.dev().dofs.as<int32_t>();
+    xga.mu = rb.mu.as<double>(); xga.fbar = rb.x.as<double>(); xga.ghost = rb.ghost.as<double>();
+    xga.gacc = rb.gacc.as<double>();
+  }
   return SBFWI_OK;
 }
 
@@ -1242,6 +1370,7 @@ int Stepper::zero_state() {
 
 std::vector<DevBuf*> Stepper::state_bufs() const {
   if (use_tc) return {&rb.v, &rb.ud, &rb.ub, &rb.udb, &rb.uddb};
+  if (use_mixed) return {&rb.u, &rb.ud, &rb.udd, &rb.v, &rb.ub, &rb.udb, &rb.uddb};
   return {&rb.u, &rb.ud, &rb.udd, &rb.ub, &rb.udb, &rb.uddb};
 }
 
@@ -1289,6 +1418,7 @@ int Stepper::element_launch(int down, int up, int64_t done_step) {
   ea.store_int = nullptr; ea.fwd_int = nullptr; ea.grad_int = nullptr; ea.u_out = nullptr;
   if (down && mode == Mode::Forward && store) ea.store_int = store + (done_step - store_k0) * np * B;
   if (down && mode == Mode::Forward && store_u) ea.u_out = store_u + (done_step - store_k0) * np * B;
+  ea.a_out = (down && mode == Mode::Forward && store_a) ? store_a + (done_step - store_k0) * np * B : nullptr;
   const bool grad_term = down && mode == Mode::Adjoint && fwd_u != nullptr;
   if (grad_term) ea.u_out = rb.lam.as<double>();
   if (down && mode == Mode::Adjoint) {
@@ -1296,13 +1426,13 @@ int Stepper::element_launch(int down, int up, int64_t done_step) {
     ea.grad_int = rb.grad_int.as<double>();
   }
   prof.begin(kPhaseElement, st);
-  if (use_tc)
+  if (use_tc || use_mixed)
     tc_element_launch(md, B, down, up, ea.u, ea.ud, ea.udd, rb.v.as<double>(), ea.ub, ea.udb, ea.uddb, ea.q, ea.fhat,
-                      ea.store_int, ea.fwd_int, ea.grad_int, ea.u_out, st);
-  else
-    element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
+                      ea.store_int, ea.fwd_int, ea.grad_int, ea.u_out, st, use_mixed ? elems_tc.as<int32_t>() : nullptr,
+                      n_tc, pstatus.as<int>());
+  if (!use_tc && (!use_mixed || n_fp > 0)) element_step_kernel<<<e_blocks, e_threads, e_smem, st>>>(ea);
   prof.end(kPhaseElement, st);
-  prof.count(kPhaseElement);
+  prof.count(kPhaseElement, use_mixed ? 2 : 1);
   if (grad_term) {
     // the full kernel's gradient term of this step: the interior adjoint field was just
     // written to lam, its boundary part is the current boundary state
@@ -1341,18 +1471,18 @@ int Stepper::solve() {
     LevelKernelArgs la;
     la.s = sa; la.levels = t.levels;
     for (int l = 0; l < t.levels; ++l) {
-      const int cnt = md.tasks.items(true, l);
+      const int cnt = lt->items(true, l);
       if (cnt == 0) continue;
-      la.tasks = ftasks; la.meta = md.tasks.fwd_meta.as<int32_t>(); la.level = l;
+      la.tasks = ftasks; la.meta = lt->fwd_meta.as<int32_t>(); la.level = l;
       void* kargs[] = {&la};
       int rc = launch_solve((const void*)solve_forward_kernel, (unsigned)cnt, kargs, false);
       if (rc) return rc;
       prof.count(kPhaseSolve);
     }
     for (int l = t.levels - 1; l >= 0; --l) {
-      const int cnt = md.tasks.items(false, l);
+      const int cnt = lt->items(false, l);
       if (cnt == 0) continue;
-      la.tasks = btasks; la.meta = md.tasks.bwd_meta.as<int32_t>(); la.level = l;
+      la.tasks = btasks; la.meta = lt->bwd_meta.as<int32_t>(); la.level = l;
       void* kargs[] = {&la};
       int rc = launch_solve((const void*)solve_backward_kernel, (unsigned)cnt, kargs, false);
       if (rc) return rc;
@@ -1366,8 +1496,8 @@ int Stepper::solve() {
 int Stepper::run(int64_t k0, int64_t k1) {
   Profiler& prof = profiler();
   if (k0 < 0 || k1 > K || k0 >= k1) return fail(SBFWI_EINVAL, "bad step window");
-  // the forward sweep of step k0 (at k0 = 0 the zero state gives f_hat = 0)
-  if (k0 > 0) element_launch(0, 1, k0 - 1);
+  // the forward sweep of step k0 (at k0 = 0 the zero state gives f_hat = 0, unless resuming)
+  if (k0 > 0 || resume) element_launch(0, 1, k0 - 1);
   for (int64_t k = k0; k < k1; ++k) {
     if (k > k0) element_launch(1, 1, k - 1);
     // sources of step k
@@ -1385,10 +1515,11 @@ int Stepper::run(int64_t k0, int64_t k1) {
       ba.R = R;
       ba.rec = nodes + B;
       ba.traces = R > 0 ? traces : nullptr;
-      ba.store_b = store ? store + (k - store_k0) * np * B + nint * B : nullptr;
+      ba.store_b = store ? store + ((k - store_k0) * store_stride() + store_bnd_off()) * B : nullptr;
       ba.store_ub = store_u ? store_u + (k - store_k0) * np * B + nint * B : nullptr;
+      ba.store_ab = store_a ? store_a + (k - store_k0) * np * B + nint * B : nullptr;
     } else {
-      ba.fwd_b = fwd + (K - 1 - k - fwd_k0) * np * B + nint * B;
+      ba.fwd_b = fwd + ((K - 1 - k - fwd_k0) * store_stride() + store_bnd_off()) * B;
       ba.grad_b = rb.grad_int.as<double>() + nint * B;
     }
     boundary_update_kernel<<<b_blocks, 256, 0, st>>>(ba);
@@ -1399,12 +1530,54 @@ int Stepper::run(int64_t k0, int64_t k1) {
   return SBFWI_OK;
 }
 
+int Stepper::run_exact(int64_t k0, int64_t k1) {
+  Profiler& prof = profiler();
+  if (mode != Mode::Exact) return fail(SBFWI_ESTATE, "not an exact-adjoint stepper");
+  if (k0 < 0 || k1 > K || k0 >= k1) return fail(SBFWI_EINVAL, "bad step window");
+  int rc;
+  for (int64_t k = k1 - 1; k >= k0; --k) {
+    // the misfit's share at the receivers, then x_bar of the boundary nodes
+    if ((rc = exact_misfit_launch(rb.ub.as<double>(), B, R, nodes, values, K, k, md.dt, st))) return rc;
+    if ((rc = exact_boundary_launch(xba, false, st))) return rc;
+    prof.count(kPhaseOther, R > 0 ? 2 : 1);
+    if ((rc = solve())) return rc;
+    // the forward solution after step k
+    const double* fu = fwd_u + (k - fwd_k0) * np * B;
+    const double* fa_ = fwd_a + (k - fwd_k0) * np * B;
+    xa.fu_int = fu; xa.fu_b = fu + nint * B; xa.fa_b = fa_ + nint * B;
+    xa.do_down = 1; xa.do_up = k > 0 ? 1 : 0;
+    prof.begin(kPhaseElement, st);
+    rc = exact_element_launch(xa, st);
+    prof.end(kPhaseElement, st);
+    prof.count(kPhaseElement);
+    if (rc) return rc;
+    if ((rc = exact_boundary_launch(xba, true, st))) return rc;
+    xga.fu_int = fu; xga.fu_b = fu + nint * B; xga.fa_int = fa_; xga.fa_b = fa_ + nint * B;
+    if ((rc = exact_gradient_launch(xga, md.mesh->p, st))) return rc;
+    prof.count(kPhaseOther, 2);
+  }
+  SBFWI_CUDA(cudaGetLastError());
+  return SBFWI_OK;
+}
+
+int Stepper::finalize_exact() {
+  const Mesh& m = *md.mesh;
+  ExactFinalArgs f;
+  f.E = E; f.nb = nb; f.n = n; f.pp = m.p + 1; f.ng = (3 * m.p + 2) / 2; f.L = m.L;
+  f.lptr = md.dev().lptr.as<int64_t>(); f.line_local = md.dev().lloc.as<int32_t>(); f.tab = md.dev().tab.as<double>();
+  f.kq = md.kq.as<double>(); f.gacc = rb.gacc.as<double>();
+  f.g_nodal = rb.grad_int.as<double>(); f.g_bnd = rb.gbnd.as<double>();
+  int rc = exact_finalize_launch(f, md.dev().inc_ptr.as<int64_t>(), md.dev().inc_list.as<int64_t>(), N,
+                                 rb.grad_int.as<double>() + nint, st);
+  profiler().count(kPhaseOther, 2);
+  return rc;
+}
+
 int Stepper::check_status() {
-  if (!persistent) return SBFWI_OK;
   int code = 0;
   SBFWI_CUDA(cudaMemcpyAsync(&code, pstatus.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   SBFWI_CUDA(cudaStreamSynchronize(st));
-  if (code) return fail(SBFWI_ETIMEOUT, "a grid barrier of the global solve timed out");
+  if (code) return fail(SBFWI_ETIMEOUT, "a bounded device wait (global solve or element-kernel copy) timed out");
   return SBFWI_OK;
 }
 
@@ -1413,7 +1586,183 @@ bool have_device() {
   return cudaGetDeviceCount(&count) == cudaSuccess && count > 0;
 }
 
+// ---------------------------------------------------------------------------
+// sessions: continuous batching.  The shots of a session are the columns ("slots") of
+// one resumable stepper; each slot carries its own request, admitted at a window boundary
+// with a zero state and its own step offset, and retired when its steps are done.  A
+// window runs W steps of every slot; the sources, traces and forward fields of the
+// window pass through window buffers that kernels fill from, and empty into, each
+// slot's own arrays at its own local step.
+// ---------------------------------------------------------------------------
+struct SlotDev {
+  const double* values;   // forward: wavelet [K]; adjoint: residual [R][K]
+  double* traces;         // forward: [R][K]
+  double* field;          // forward: velocities [K][stride] out (nullable); adjoint: the forward ones in
+  int64_t start, K;       // global step of the slot's first step, its step count
+  int32_t active, pad;
+};
+
+__global__ void session_sources_kernel(const SlotDev* slots, int B, int R, int64_t k0, int W, int adjoint,
+                                       double* out) {
+  const int64_t tot = adjoint ? (int64_t)B * R * W : (int64_t)B * W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % W);
+    const int64_t sr = t / W;                       // forward: slot; adjoint: slot * R + receiver
+    const int s = (int)(adjoint ? sr / R : sr);
+    const SlotDev sl = slots[s];
+    const int64_t m = k0 + j - sl.start;            // the slot's own step
+    const bool in = sl.active && m >= 0 && m < sl.K;
+    if (!adjoint) {
+      out[t] = in ? sl.values[m] : 0.0;
+    } else {
+      // the window's adjoint step j injects the residual sample K - 1 - m, stored reversed as
+      // the stepper reads it (column W - 1 - j of a window of W steps)
+      const int r = (int)(sr - (int64_t)s * R);
+      out[sr * W + (W - 1 - j)] = in ? sl.values[(int64_t)r * sl.K + (sl.K - 1 - m)] : 0.0;
+    }
+  }
+}
+
+__global__ void session_traces_kernel(const SlotDev* slots, int B, int R, int64_t k0, int W, const double* win) {
+  const int64_t tot = (int64_t)B * R * W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % W);
+    const int64_t sr = t / W;
+    const int s = (int)(sr / R), r = (int)(sr - (int64_t)s * R);
+    const SlotDev sl = slots[s];
+    const int64_t m = k0 + j - sl.start;
+    if (sl.active && m >= 0 && m < sl.K) sl.traces[(int64_t)r * sl.K + m] = win[t];
+  }
+}
+
+// forward: the window's nodal velocities [W][stride][B] go to each slot's field at its own
+// step; adjoint: each slot's forward velocities are gathered into the window, reversed in
+// time as the adjoint stepper pairs them
+__global__ void session_field_kernel(const SlotDev* slots, int B, int64_t stride, int64_t k0, int W, int adjoint,
+                                     double* win) {
+  const int64_t tot = (int64_t)W * stride * B;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(t % B);
+    const int64_t jq = t / B;
+    const int j = (int)(jq / stride);
+    const int64_t q = jq - (int64_t)j * stride;
+    const SlotDev sl = slots[s];
+    const int64_t m = k0 + j - sl.start;
+    const bool in = sl.active && sl.field && m >= 0 && m < sl.K;
+    if (!adjoint) {
+      if (in) sl.field[m * stride + q] = win[t];
+    } else {
+      win[((int64_t)(W - 1 - j) * stride + q) * B + s] = in ? sl.field[(sl.K - 1 - m) * stride + q] : 0.0;
+    }
+  }
+}
+
+__global__ void column_zero_kernel(double* buf, int64_t rows, int B, int s) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows; q += (int64_t)gridDim.x * blockDim.x)
+    buf[q * B + s] = 0.0;
+}
+
+__global__ void column_copy_kernel(const double* acc, int64_t rows, int B, int s, double scale, double* out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < rows; q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = scale * acc[q * B + s];
+}
+
+int Stepper::zero_column(int s) {
+  std::vector<DevBuf*> bufs = state_bufs();
+  // the sources kernel writes only the column's current source node: the previous
+  // request's last sample at its node must not act on the next one
+  bufs.push_back(&rb.ext);
+  if (mode == Mode::Adjoint) bufs.push_back(&rb.grad_int);
+  for (DevBuf* b : bufs) {
+    const int64_t rows = (int64_t)(b->bytes / sizeof(double)) / B;
+    if (rows == 0) continue;
+    column_zero_kernel<<<(unsigned)std::min<int64_t>((rows + 255) / 256, 152 * 8), 256, 0, st>>>(b->as<double>(), rows,
+                                                                                                 B, s);
+    profiler().count(kPhaseOther);
+  }
+  SBFWI_CUDA(cudaGetLastError());
+  return SBFWI_OK;
+}
+
+struct SlotHost {
+  bool active = false, finished = false;
+  int64_t start = 0, K = 0;
+  DevBuf values, traces;
+  double* field = nullptr;
+};
+
 }  // namespace
+
+// the gradient on the model's parameter layout from nodal values in the library's layout
+static int emit_gradient(Model& md, const double* g_lib, double* grad, int mem, bool accumulate, cudaStream_t st);
+
+struct Session {
+  Model* md = nullptr;
+  int kind = 0, B = 0, R = 0, W = 0;
+  cudaStream_t st = nullptr;
+  std::vector<int64_t> rec;
+  RunBuffers rb;
+  LevelTasks tasks;
+  std::unique_ptr<Stepper> sp;
+  DevBuf nodes, win_values, win_traces, win_field, slots_dev;
+  std::vector<SlotHost> slots;
+  std::vector<SlotDev> slots_h;
+  int64_t kglob = 0;
+  bool field_used = false;
+
+  int upload_slots() {
+    for (int s = 0; s < B; ++s) {
+      const SlotHost& h = slots[s];
+      SlotDev& d = slots_h[s];
+      d.values = h.values.as<double>(); d.traces = h.traces.as<double>(); d.field = h.field;
+      d.start = h.start; d.K = h.K; d.active = h.active ? 1 : 0; d.pad = 0;
+    }
+    SBFWI_CUDA(cudaMemcpyAsync(slots_dev.p, slots_h.data(), sizeof(SlotDev) * B, cudaMemcpyHostToDevice, st));
+    // the host array must stay unchanged until the copy has run
+    SBFWI_CUDA(cudaStreamSynchronize(st));
+    return SBFWI_OK;
+  }
+};
+
+}  // namespace sbfwi
+
+struct sbfwi_session : public sbfwi::Session {};
+
+namespace sbfwi {
+
+static int emit_gradient(Model& md, const double* g_lib, double* grad, int mem, bool accumulate, cudaStream_t st) {
+  const Mesh& msh = *md.mesh;
+  const bool grid = md.rho_kind == SBFWI_RHO_GRID;
+  const int64_t nout = grid ? md.gx * md.gy : msh.n_nodal_api;
+  DevBuf gout;
+  double* dst = nullptr;
+  if (mem == SBFWI_MEM_DEVICE) dst = grad;
+  else {
+    SBFWI_CUDA(gout.alloc(sizeof(double) * nout));
+    dst = gout.as<double>();
+    if (accumulate) SBFWI_CUDA(cudaMemcpyAsync(dst, grad, sizeof(double) * nout, cudaMemcpyHostToDevice, st));
+  }
+  const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
+  if (grid) {
+    // the transpose of the bilinear map of the fine grid
+    const MeshDevice& mdev = md.dev();
+    grid_transpose_kernel<<<gb, 256, 0, st>>>(g_lib, md.pts_hi.as<double>(), mdev.cell.as<int32_t>(),
+                                              mdev.clamp.as<int8_t>(), mdev.cell_ptr.as<int64_t>(),
+                                              mdev.cell_list.as<int64_t>(), md.gx, md.gy, md.lx, md.ly, dst,
+                                              accumulate ? 1 : 0);
+  } else if (msh.uneven) {
+    // the padded layout gathered to the caller's
+    gather_nodal_kernel<<<gb, 256, 0, st>>>(g_lib, md.dev().api_map.as<int64_t>(), nout, dst, accumulate ? 1 : 0);
+  } else {
+    sum_shots_kernel<<<gb, 256, 0, st>>>(g_lib, nout, 1, 1.0, dst, accumulate ? 1 : 0);
+  }
+  profiler().count(kPhaseOther);
+  SBFWI_CUDA(cudaGetLastError());
+  if (mem == SBFWI_MEM_HOST) SBFWI_CUDA(cudaMemcpyAsync(grad, dst, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
+  SBFWI_CUDA(cudaStreamSynchronize(st));
+  return SBFWI_OK;
+}
+
 }  // namespace sbfwi
 
 using namespace sbfwi;
@@ -1479,9 +1828,18 @@ int sbfwi_set_kernel_terms(sbfwi_model* m, int terms) {
   return SBFWI_OK;
 }
 
+int sbfwi_set_gradient_mode(sbfwi_model* m, int mode) {
+  if (!m) return fail(SBFWI_EINVAL, "model is NULL");
+  if (mode != SBFWI_GRAD_KERNEL && mode != SBFWI_GRAD_EXACT) return fail(SBFWI_EINVAL, "unknown gradient mode");
+  if (mode == SBFWI_GRAD_EXACT && m->lfe)
+    return fail(SBFWI_EUNSUPPORTED, "the exact adjoint is not built for the comparison method");
+  m->grad_mode = mode;
+  return SBFWI_OK;
+}
+
 int sbfwi_set_schedule(sbfwi_model* m, int element, int solve) {
   if (!m) return fail(SBFWI_EINVAL, "model is NULL");
-  if (element < SBFWI_ELEMENT_AUTO || element > SBFWI_ELEMENT_FP64) return fail(SBFWI_EINVAL, "unknown element kernel");
+  if (element < SBFWI_ELEMENT_AUTO || element > SBFWI_ELEMENT_MIXED) return fail(SBFWI_EINVAL, "unknown element kernel");
   if (solve < SBFWI_SOLVE_AUTO || solve > SBFWI_SOLVE_LEVELS) return fail(SBFWI_EINVAL, "unknown solve schedule");
   m->elem_pref = element;
   m->solve_pref = solve;
@@ -1541,24 +1899,31 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     fs->model = md; fs->B = B; fs->R = n_rec; fs->K = K;
     fs->rec.assign(rec_node, rec_node + n_rec);
     const int64_t sd = f.state_doubles();
+    const int64_t ss = f.store_stride();
     c = ckpt_every;
     if (c == SBFWI_CKPT_AUTO) {
-      // memory (K/c) * sd + c * np * B is least at c = sqrt(K sd / (np B))
-      c = (int64_t)std::ceil(std::sqrt((double)K * (double)sd / ((double)np * B)));
+      // memory (K/c) * sd + c * ss * B is least at c = sqrt(K sd / (ss B))
+      c = (int64_t)std::ceil(std::sqrt((double)K * (double)sd / ((double)ss * B)));
     }
     c = std::min<int64_t>(c, K);
     if (md->kernel_terms == SBFWI_TERMS_FULL && md->lfe)
       return fail(SBFWI_EUNSUPPORTED, "the comparison method has no radial field for the full kernel's gradient term");
-    if (md->kernel_terms == SBFWI_TERMS_FULL && c != 0)
+    if (md->kernel_terms == SBFWI_TERMS_FULL && c != 0 && md->grad_mode != SBFWI_GRAD_EXACT)
       return fail(SBFWI_EUNSUPPORTED, "the full Frechet kernel needs the stored forward field (ckpt_every = 0)");
     fs->ckpt_every = c;
     fs->state_doubles = sd;
     fs->tensor_core_path = f.tensor_core_path();
+    fs->exact = md->grad_mode == SBFWI_GRAD_EXACT;
     cudaError_t e = cudaSuccess;
     double gb = 0;
-    if (c == 0) {
-      gb = (double)K * np * B * 8 / 1e9;
-      e = store_alloc(fs->store, sizeof(double) * (size_t)K * np * B);
+    if (c == 0 && fs->exact) {
+      // the exact adjoint reads u and u'' of every step (no velocities)
+      gb = 2.0 * K * np * B * 8 / 1e9;
+      e = store_alloc(fs->store_u, sizeof(double) * (size_t)K * np * B);
+      if (e == cudaSuccess) e = fs->store_a.alloc(sizeof(double) * (size_t)K * np * B);
+    } else if (c == 0) {
+      gb = (double)K * ss * B * 8 / 1e9;
+      e = store_alloc(fs->store, sizeof(double) * (size_t)K * ss * B);
       if (e == cudaSuccess && md->kernel_terms == SBFWI_TERMS_FULL) {
         gb *= 2;
         e = fs->store_u.alloc(sizeof(double) * (size_t)K * np * B);
@@ -1574,8 +1939,9 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     }
   }
   if (!keep || c == 0) {
-    f.store = fs ? fs->store.as<double>() : nullptr;
+    f.store = (fs && fs->store.p) ? fs->store.as<double>() : nullptr;
     f.store_u = (fs && fs->store_u.p) ? fs->store_u.as<double>() : nullptr;
+    f.store_a = (fs && fs->store_a.p) ? fs->store_a.as<double>() : nullptr;
     rc = f.run(0, K);
   } else {
     // checkpoints: the Newmark state before steps c, 2c, ... (before step 0 it is zero)
@@ -1608,9 +1974,16 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   if (fs->model != md) return fail(SBFWI_ESTATE, "forward state belongs to another model");
   const bool accumulate = (mode & SBFWI_GRAD_ACCUMULATE) != 0;
   mode &= ~SBFWI_GRAD_ACCUMULATE;
-  if (mode == SBFWI_GRAD_EXACT) return fail(SBFWI_EUNSUPPORTED, "the exact discrete adjoint is not in this build");
-  if (mode != SBFWI_GRAD_KERNEL) return fail(SBFWI_EINVAL, "unknown gradient mode");
+  if (mode != SBFWI_GRAD_KERNEL && mode != SBFWI_GRAD_EXACT) return fail(SBFWI_EINVAL, "unknown gradient mode");
   if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  const bool exact = mode == SBFWI_GRAD_EXACT;
+  const int64_t c = fs->ckpt_every;
+  if (exact && !fs->exact)
+    return fail(SBFWI_ESTATE, "the forward pass was not kept for the exact adjoint: "
+                              "call sbfwi_set_gradient_mode(model, SBFWI_GRAD_EXACT) before it");
+  if (!exact && c == 0 && !fs->store.p)
+    return fail(SBFWI_ESTATE, "the forward pass kept displacements and accelerations for the exact adjoint, "
+                              "not the velocities of the paper's kernel");
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int B = fs->B, R = fs->R;
   const int64_t K = fs->K, np = md->mesh->n_nodal;
@@ -1623,22 +1996,27 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   SBFWI_CUDA(nodes.alloc(sizeof(int64_t) * std::max<size_t>(fs->rec.size(), 1)));
   if (R > 0) SBFWI_CUDA(cudaMemcpyAsync(nodes.p, fs->rec.data(), sizeof(int64_t) * R, cudaMemcpyHostToDevice, st));
   RunBuffers rb;
-  Stepper adj(*md, Mode::Adjoint, B, K, R, rb, st);
+  Stepper adj(*md, exact ? Mode::Exact : Mode::Adjoint, B, K, R, rb, st);
   adj.values = values.as<double>(); adj.nodes = nodes.as<int64_t>();
   int rc = adj.init();
   if (rc) return rc;
-  const int64_t c = fs->ckpt_every;
-  if (md->kernel_terms == SBFWI_TERMS_FULL) {
+  if (!exact && md->kernel_terms == SBFWI_TERMS_FULL) {
     if (!fs->store_u.p)
       return fail(SBFWI_ESTATE, "the forward pass kept no displacements: set the full kernel before the forward pass");
     adj.fwd_u = fs->store_u.as<double>();
   }
   if (c == 0) {
-    adj.fwd = fs->store.as<double>();
-    rc = adj.run(0, K);
+    if (exact) {
+      adj.fwd_u = fs->store_u.as<double>();
+      adj.fwd_a = fs->store_a.as<double>();
+      rc = adj.run_exact(0, K);
+    } else {
+      adj.fwd = fs->store.as<double>();
+      rc = adj.run(0, K);
+    }
   } else {
-    // recompute the forward velocities one window of c steps at a time from the
-    // checkpoints, last window first, and run the adjoint steps that pair with them
+    // recompute the forward field one window of c steps at a time from the checkpoints,
+    // last window first, and run the adjoint steps that pair with it
     RunBuffers rf;
     Stepper fwd(*md, Mode::Forward, B, K, 0, rf, st);
     fwd.values = fs->values.as<double>(); fwd.nodes = fs->nodes.as<int64_t>();
@@ -1646,65 +2024,53 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
     if (rc) return rc;
     if (fwd.tensor_core_path() != fs->tensor_core_path || fwd.state_doubles() != fs->state_doubles)
       return fail(SBFWI_ESTATE, "the element kernel differs from the one that wrote the checkpoints");
-    DevBuf window;
-    cudaError_t e = window.alloc(sizeof(double) * (size_t)c * np * B);
+    DevBuf window, window_a;
+    const int64_t ss = exact ? np : fwd.store_stride();
+    cudaError_t e = window.alloc(sizeof(double) * (size_t)c * ss * B);
+    if (e == cudaSuccess && exact) e = window_a.alloc(sizeof(double) * (size_t)c * ss * B);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(SBFWI_ENOMEM, "not enough device memory for one recompute window (" +
-                                    std::to_string((double)c * np * B * 8 / 1e9) + " GB)");
+                                    std::to_string((exact ? 2.0 : 1.0) * c * ss * B * 8 / 1e9) + " GB)");
     }
     const int64_t nseg = (K + c - 1) / c;
     for (int64_t seg = nseg - 1; seg >= 0 && rc == SBFWI_OK; --seg) {
       const int64_t a = seg * c, b = std::min(K, a + c);
       rc = seg == 0 ? fwd.zero_state() : fwd.restore_state(fs->store.as<double>() + (seg - 1) * fs->state_doubles);
-      fwd.store = window.as<double>(); fwd.store_k0 = a;
+      fwd.store_k0 = a;
+      if (exact) {
+        fwd.store = nullptr;
+        fwd.store_u = window.as<double>();
+        fwd.store_a = window_a.as<double>();
+      } else {
+        fwd.store = window.as<double>();
+      }
       if (rc == SBFWI_OK) rc = fwd.run(a, b);
-      adj.fwd = window.as<double>(); adj.fwd_k0 = a;
-      if (rc == SBFWI_OK) rc = adj.run(K - b, K - a);
+      if (exact) {
+        adj.fwd_u = window.as<double>(); adj.fwd_a = window_a.as<double>(); adj.fwd_k0 = a;
+        if (rc == SBFWI_OK) rc = adj.run_exact(a, b);
+      } else {
+        adj.fwd = window.as<double>(); adj.fwd_k0 = a;
+        if (rc == SBFWI_OK) rc = adj.run(K - b, K - a);
+      }
     }
     if (rc == SBFWI_OK) rc = fwd.check_status();
   }
+  if (rc == SBFWI_OK && exact) rc = adj.finalize_exact();
   if (rc == SBFWI_OK) rc = adj.check_status();
   if (rc) return rc;
-  DevBuf gn, gout;
-  const Mesh& msh = *md->mesh;
-  const int64_t nout = (md->rho_kind == SBFWI_RHO_GRID) ? md->gx * md->gy : msh.n_nodal_api;
-  double* dst = nullptr;
-  if (mem == SBFWI_MEM_DEVICE) dst = grad;
-  else {
-    SBFWI_CUDA(gout.alloc(sizeof(double) * nout));
-    dst = gout.as<double>();
-    if (accumulate) SBFWI_CUDA(cudaMemcpyAsync(dst, grad, sizeof(double) * nout, cudaMemcpyHostToDevice, st));
-  }
+  // the paper's kernel accumulates per shot and applies dt at the end; the exact gradient is
+  // already summed over shots (dt is in its misfit adjoint)
+  const int Bsum = exact ? 1 : B;
+  const double scale = exact ? 1.0 : md->dt;
+  DevBuf gn;
   SBFWI_CUDA(gn.alloc(sizeof(double) * np));
   const unsigned blocks = (unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8);
-  const bool grid = md->rho_kind == SBFWI_RHO_GRID;
-  // nodal output: shots summed straight into the output (accumulating if asked); on
-  // uneven meshes into the padded layout first, then gathered to the caller's
-  const bool direct = !grid && !msh.uneven;
-  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, B, md->dt, direct ? dst : gn.as<double>(),
-                                           (direct && accumulate) ? 1 : 0);
+  sum_shots_kernel<<<blocks, 256, 0, st>>>(rb.grad_int.as<double>(), np, Bsum, scale, gn.as<double>(), 0);
   profiler().count(kPhaseOther);
-  if (!grid && msh.uneven) {
-    const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
-    gather_nodal_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->dev().api_map.as<int64_t>(), nout, dst,
-                                            accumulate ? 1 : 0);
-    profiler().count(kPhaseOther);
-  }
-  if (grid) {
-    const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
-    const MeshDevice& mdev = md->dev();
-    grid_transpose_kernel<<<gb, 256, 0, st>>>(gn.as<double>(), md->pts_hi.as<double>(), mdev.cell.as<int32_t>(),
-                                              mdev.clamp.as<int8_t>(), mdev.cell_ptr.as<int64_t>(),
-                                              mdev.cell_list.as<int64_t>(), md->gx, md->gy, md->lx, md->ly, dst,
-                                              accumulate ? 1 : 0);
-    profiler().count(kPhaseOther);
-  }
-  SBFWI_CUDA(cudaGetLastError());
-  if (mem == SBFWI_MEM_HOST) SBFWI_CUDA(cudaMemcpyAsync(grad, dst, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
-  SBFWI_CUDA(cudaStreamSynchronize(st));
+  rc = emit_gradient(*md, gn.as<double>(), grad, mem, accumulate, st);
   profiler().resolve();
-  return SBFWI_OK;
+  return rc;
 }
 
 int sbfwi_misfit(const double* traces, const double* observed, int64_t n, double dt, double* E_out, double* residual_out,
@@ -1773,6 +2139,200 @@ int sbfwi_selftest_barrier(int32_t n_blocks, int32_t n_absent, int64_t budget_cy
   SBFWI_CUDA(cudaStreamSynchronize(st));
   if (code) return fail(SBFWI_ETIMEOUT, "grid barrier self-test: a block did not arrive within the budget");
   return SBFWI_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// sessions (continuous batching)
+// ---------------------------------------------------------------------------
+int sbfwi_session_create(sbfwi_session** out, sbfwi_model* md, int32_t kind, int32_t slots, int32_t n_rec,
+                         const int64_t* rec_node, int32_t window, void* stream) {
+  if (!out) return fail(SBFWI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!md) return fail(SBFWI_EINVAL, "model is NULL");
+  if (kind != SBFWI_SESSION_FORWARD && kind != SBFWI_SESSION_ADJOINT) return fail(SBFWI_EINVAL, "unknown session kind");
+  if (slots < 1 || slots > kMaxShots) return fail(SBFWI_EINVAL, "slots must be in 1..16");
+  if (window < 1 || window > 100000) return fail(SBFWI_EINVAL, "window must be in 1..100000");
+  if (n_rec < 0 || (n_rec > 0 && !rec_node)) return fail(SBFWI_EINVAL, "receivers need rec_node");
+  if (kind == SBFWI_SESSION_ADJOINT && md->kernel_terms == SBFWI_TERMS_FULL)
+    return fail(SBFWI_EUNSUPPORTED, "sessions accumulate the velocity kernel only");
+  if (md->grad_mode == SBFWI_GRAD_EXACT)
+    return fail(SBFWI_EUNSUPPORTED, "sessions run the paper's kernel, not the exact adjoint");
+  for (int r = 0; r < n_rec; ++r) {
+    if (rec_node[r] < 0 || rec_node[r] >= md->N) return fail(SBFWI_EINVAL, "receiver node out of range");
+    for (int r2 = 0; r2 < r; ++r2)
+      if (rec_node[r2] == rec_node[r]) return fail(SBFWI_EINVAL, "receiver nodes must be distinct");
+  }
+  if (!have_device()) return fail(SBFWI_ECUDA, "no CUDA device");
+  std::unique_ptr<sbfwi_session> S(new sbfwi_session());
+  S->md = md; S->kind = kind; S->B = slots; S->R = n_rec; S->W = window;
+  S->st = static_cast<cudaStream_t>(stream);
+  S->rec.assign(rec_node, rec_node + n_rec);
+  const bool fwd = kind == SBFWI_SESSION_FORWARD;
+  S->sp.reset(new Stepper(*md, fwd ? Mode::Forward : Mode::Adjoint, slots, window, n_rec, S->rb, S->st));
+  Stepper& sp = *S->sp;
+  sp.tasks_own = &S->tasks;
+  sp.resume = true;
+  // node list: forward B sources (set on admission) then the receivers; adjoint the receivers
+  std::vector<int64_t> nv;
+  if (fwd) nv.assign(slots, S->rec.empty() ? 0 : S->rec[0]);
+  nv.insert(nv.end(), S->rec.begin(), S->rec.end());
+  SBFWI_CUDA(S->nodes.alloc(sizeof(int64_t) * std::max<size_t>(nv.size(), 1)));
+  if (!nv.empty()) SBFWI_CUDA(cudaMemcpy(S->nodes.p, nv.data(), sizeof(int64_t) * nv.size(), cudaMemcpyHostToDevice));
+  int rc = sp.init();
+  if (rc) return rc;
+  const int64_t nval = fwd ? (int64_t)slots * window : (int64_t)slots * n_rec * window;
+  SBFWI_CUDA(S->win_values.alloc(sizeof(double) * std::max<int64_t>(nval, 1)));
+  SBFWI_CUDA(cudaMemsetAsync(S->win_values.p, 0, S->win_values.bytes, S->st));
+  if (fwd && n_rec > 0) SBFWI_CUDA(S->win_traces.alloc(sizeof(double) * (size_t)slots * n_rec * window));
+  if (!fwd) {
+    SBFWI_CUDA(S->win_field.alloc(sizeof(double) * (size_t)window * sp.store_stride() * slots));
+    sp.fwd = S->win_field.as<double>();
+    sp.fwd_k0 = 0;
+  }
+  sp.values = S->win_values.as<double>();
+  sp.nodes = S->nodes.as<int64_t>();
+  sp.traces = S->win_traces.as<double>();
+  SBFWI_CUDA(S->slots_dev.alloc(sizeof(SlotDev) * slots));
+  S->slots.resize(slots);
+  S->slots_h.resize(slots);
+  if ((rc = S->upload_slots())) return rc;
+  *out = S.release();
+  return SBFWI_OK;
+}
+
+int sbfwi_session_info(const sbfwi_session* S, int64_t* info) {
+  if (!S || !info) return fail(SBFWI_EINVAL, "NULL argument");
+  info[0] = S->sp->store_stride();
+  info[1] = S->kglob;
+  info[2] = S->B;
+  info[3] = S->W;
+  int64_t busy = 0;
+  for (const SlotHost& h : S->slots) busy += h.active ? 1 : 0;
+  info[4] = busy;
+  return SBFWI_OK;
+}
+
+void sbfwi_session_destroy(sbfwi_session* S) {
+  if (S && S->st) cudaStreamSynchronize(S->st);
+  delete S;
+}
+
+int sbfwi_session_admit(sbfwi_session* S, int32_t slot, int64_t src_node, const double* values, int64_t K,
+                        double* field, int mem) {
+  if (!S) return fail(SBFWI_EINVAL, "session is NULL");
+  if (slot < 0 || slot >= S->B) return fail(SBFWI_EINVAL, "slot out of range");
+  if (S->slots[slot].active) return fail(SBFWI_ESTATE, "slot is busy");
+  if (K < 1 || !values) return fail(SBFWI_EINVAL, "need K >= 1 values");
+  if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  const bool fwd = S->kind == SBFWI_SESSION_FORWARD;
+  if (fwd && (src_node < 0 || src_node >= S->md->N)) return fail(SBFWI_EINVAL, "source node out of range");
+  if (!fwd && !field) return fail(SBFWI_EINVAL, "an adjoint slot needs the forward velocities");
+  SlotHost& h = S->slots[slot];
+  const int64_t nv = fwd ? K : (int64_t)S->R * K;
+  SBFWI_CUDA(h.values.alloc(sizeof(double) * std::max<int64_t>(nv, 1)));
+  if (nv > 0)
+    SBFWI_CUDA(cudaMemcpyAsync(h.values.p, values, sizeof(double) * nv,
+                               mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->st));
+  h.traces.release();
+  if (fwd && S->R > 0) {
+    SBFWI_CUDA(h.traces.alloc(sizeof(double) * (size_t)S->R * K));
+    SBFWI_CUDA(cudaMemsetAsync(h.traces.p, 0, h.traces.bytes, S->st));
+  }
+  h.field = field;
+  h.start = S->kglob; h.K = K; h.active = true; h.finished = false;
+  int rc = S->sp->zero_column(slot);
+  if (rc) return rc;
+  if (fwd) {
+    SBFWI_CUDA(cudaMemcpyAsync(S->nodes.as<int64_t>() + slot, &src_node, sizeof(int64_t), cudaMemcpyHostToDevice, S->st));
+    if (field && !S->field_used) {
+      SBFWI_CUDA(S->win_field.alloc(sizeof(double) * (size_t)S->W * S->sp->store_stride() * S->B));
+      S->sp->store = S->win_field.as<double>();
+      S->sp->store_k0 = 0;
+      S->field_used = true;
+    }
+  }
+  return S->upload_slots();        // synchronises: src_node is read before returning
+}
+
+int sbfwi_session_step(sbfwi_session* S, int32_t* finished) {
+  if (!S) return fail(SBFWI_EINVAL, "session is NULL");
+  const int B = S->B, R = S->R, W = S->W;
+  const bool fwd = S->kind == SBFWI_SESSION_FORWARD;
+  bool any = false;
+  for (const SlotHost& h : S->slots) any = any || (h.active && !h.finished);
+  if (any) {
+    Profiler& prof = profiler();
+    const cudaStream_t st = S->st;
+    const SlotDev* sd = S->slots_dev.as<SlotDev>();
+    const int64_t nval = fwd ? (int64_t)B * W : (int64_t)B * R * W;
+    if (nval > 0) {
+      session_sources_kernel<<<(unsigned)std::min<int64_t>((nval + 255) / 256, 152 * 8), 256, 0, st>>>(
+          sd, B, R, S->kglob, W, fwd ? 0 : 1, S->win_values.as<double>());
+      prof.count(kPhaseOther);
+    }
+    const int64_t stride = S->sp->store_stride();
+    const int64_t nf = (int64_t)W * stride * B;
+    if (!fwd) {
+      session_field_kernel<<<(unsigned)std::min<int64_t>((nf + 255) / 256, 152 * 16), 256, 0, st>>>(
+          sd, B, stride, S->kglob, W, 1, S->win_field.as<double>());
+      prof.count(kPhaseOther);
+    }
+    SBFWI_CUDA(cudaGetLastError());
+    int rc = S->sp->run(0, W);
+    if (rc == SBFWI_OK) rc = S->sp->check_status();
+    if (rc) return rc;
+    if (fwd && R > 0) {
+      const int64_t nt = (int64_t)B * R * W;
+      session_traces_kernel<<<(unsigned)std::min<int64_t>((nt + 255) / 256, 152 * 8), 256, 0, st>>>(
+          sd, B, R, S->kglob, W, S->win_traces.as<double>());
+      prof.count(kPhaseOther);
+    }
+    if (fwd && S->field_used) {
+      session_field_kernel<<<(unsigned)std::min<int64_t>((nf + 255) / 256, 152 * 16), 256, 0, st>>>(
+          sd, B, stride, S->kglob, W, 0, S->win_field.as<double>());
+      prof.count(kPhaseOther);
+    }
+    SBFWI_CUDA(cudaGetLastError());
+    SBFWI_CUDA(cudaStreamSynchronize(st));
+    profiler().resolve();
+    S->kglob += W;
+  }
+  for (int s = 0; s < B; ++s) {
+    SlotHost& h = S->slots[s];
+    if (h.active && !h.finished && S->kglob >= h.start + h.K) h.finished = true;
+    if (finished) finished[s] = (h.active && h.finished) ? 1 : 0;
+  }
+  return SBFWI_OK;
+}
+
+int sbfwi_session_collect(sbfwi_session* S, int32_t slot, double* out, int mem) {
+  if (!S || !out) return fail(SBFWI_EINVAL, "NULL argument");
+  if (slot < 0 || slot >= S->B) return fail(SBFWI_EINVAL, "slot out of range");
+  if (mem != SBFWI_MEM_HOST && mem != SBFWI_MEM_DEVICE) return fail(SBFWI_EINVAL, "unknown mem");
+  SlotHost& h = S->slots[slot];
+  if (!h.active || !h.finished) return fail(SBFWI_ESTATE, "slot has no finished request");
+  const cudaStream_t st = S->st;
+  int rc = SBFWI_OK;
+  if (S->kind == SBFWI_SESSION_FORWARD) {
+    if (S->R > 0)
+      SBFWI_CUDA(cudaMemcpyAsync(out, h.traces.p, sizeof(double) * S->R * h.K,
+                                 mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    SBFWI_CUDA(cudaStreamSynchronize(st));
+  } else {
+    Model& md = *S->md;
+    const int64_t np = md.mesh->n_nodal;
+    DevBuf g;
+    SBFWI_CUDA(g.alloc(sizeof(double) * np));
+    column_copy_kernel<<<(unsigned)std::min<int64_t>((np + 255) / 256, 152 * 8), 256, 0, st>>>(
+        S->rb.grad_int.as<double>(), np, S->B, slot, md.dt, g.as<double>());
+    profiler().count(kPhaseOther);
+    rc = emit_gradient(md, g.as<double>(), out, mem, false, st);
+  }
+  h.active = false; h.finished = false;
+  h.values.release(); h.traces.release(); h.field = nullptr;
+  if (rc == SBFWI_OK) rc = S->upload_slots();
+  return rc;
 }
 
 }  // extern "C"

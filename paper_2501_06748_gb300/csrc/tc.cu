@@ -128,34 +128,54 @@ __global__ void slice_operators_kernel(SliceArgs a) {
 namespace tc {
 
 // One pipeline stage: the digit fragments of one or two operators and their row
-// exponents.  Each lane copies its own fragments; lanes 0..16*nops-1 the exponents.
+// exponents, brought in by two bulk copies (fragments, exponents) that complete on the
+// stage's mbarrier; lane 0 issues them.
 constexpr int kStageFrags = 2 * kSlices * 32;     // uint4
 struct WarpSmem {
   uint4 frag[2][kStageFrags];
   int exps[2][32];
   double xch[kTile * kCols];
+  uint64_t bar[2];
 };
 constexpr int kWarpsPerBlock = 4;
 
-__device__ __forceinline__ void stage_ops(uint4* dst, int* dexp, const uint4* src, const int* sexp, int nops, int lane) {
-  for (int k = 0; k < nops * kSlices; ++k) cp_async16(dst + k * 32 + lane, src + k * 32 + lane);
-  if (lane < 16 * nops) cp_async4(dexp + lane, sexp + lane);
+__device__ __forceinline__ void stage_ops(WarpSmem& W, int buf, const uint4* src, const int* sexp, int nops,
+                                          int lane) {
+  if (lane == 0) {
+    const unsigned fb = (unsigned)(nops * kSlices * 32 * sizeof(uint4)), eb = (unsigned)(nops * 16 * sizeof(int));
+    fence_proxy_async();                  // the warp's earlier reads of this stage come first
+    mbar_expect_tx(&W.bar[buf], fb + eb);
+    bulk_g2s(W.frag[buf], src, fb, &W.bar[buf]);
+    bulk_g2s(W.exps[buf], sexp, eb, &W.bar[buf]);
+  }
 }
 
 }  // namespace tc
 
 // One warp per element.  The operator digits of the next radial point are copied to
-// shared memory (cp.async, two stages) while the current point computes, and each
-// point's state is loaded before its products, so the memory latency overlaps the
-// tensor-core and integer work instead of stalling every radial point.
+// shared memory (bulk copies on mbarriers, two stages) while the current point computes,
+// and each point's state is loaded before its products, so the memory latency overlaps
+// the tensor-core and integer work instead of stalling every radial point.
 template <bool kAvgAccel>
 __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
   using namespace tc;
   extern __shared__ __align__(16) unsigned char tc_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpSmem& W = reinterpret_cast<WarpSmem*>(tc_smem)[warp];
-  const int64_t e = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
-  if (e >= a.E) return;                       // whole warp leaves together
+  const int64_t idx = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+  if (idx >= a.n_elems) return;               // whole warp leaves together
+  const int64_t e = a.elems ? (int64_t)a.elems[idx] : idx;
+  if (lane == 0) {
+    mbar_init(&W.bar[0], 1);
+    mbar_init(&W.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  unsigned phase = 0;                         // bit b: parity of stage b's next completion
+  auto wait_stage = [&](int b) {
+    mbar_wait(&W.bar[b], (phase >> b) & 1u, a.status);
+    phase ^= 1u << b;
+  };
   const int nb = a.nb, n = a.n, B = a.B;
   const int per = nb * B;
   double* X = W.xch;
@@ -230,15 +250,12 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
     const int64_t hop = (int64_t)3 * kSlices * 32;       // uint4 between radial points
     const uint4* Hsrc = a.frag + ((e * n + (n - 1)) * 3 + 2) * kSlices * 32;
     const int* Hexp = a.exps + ((e * n + (n - 1)) * 3 + 2) * 16;
-    stage_ops(W.frag[(n - 1) & 1], W.exps[(n - 1) & 1], Hsrc, Hexp, 1, lane);
-    cp_async_commit();
+    stage_ops(W, (n - 1) & 1, Hsrc, Hexp, 1, lane);
 #pragma unroll
     for (int j = 0; j < 4; ++j) xb[j] = bok[j] ? a.ub[(int64_t)a.dofs[e * nb + br[j]] * B + g] : 0.0;
     for (int i = n - 1; i >= 0; --i) {
       const int buf = i & 1;
-      if (i > 0) stage_ops(W.frag[buf ^ 1], W.exps[buf ^ 1], Hsrc - (int64_t)(n - i) * hop,
-                           Hexp - (int64_t)(n - i) * 48, 1, lane);
-      cp_async_commit();
+      if (i > 0) stage_ops(W, buf ^ 1, Hsrc - (int64_t)(n - i) * hop, Hexp - (int64_t)(n - i) * 48, 1, lane);
       // the state of this radial point, loaded ahead of the product
       double zo[4], vo[4], qo[4], fw[4], gr[4];
 #pragma unroll
@@ -250,8 +267,7 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
         fw[j] = (cok[j] && a.grad_int) ? a.fwd_int[o] : 0.0;
         gr[j] = (cok[j] && a.grad_int) ? a.grad_int[o] : 0.0;
       }
-      cp_async_wait<1>();
-      __syncwarp();
+      wait_stage(buf);
       double hu[4];
       apply(W.frag[buf], W.exps[buf], xb, hu);
       double un[4];
@@ -285,18 +301,15 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
       }
       c_to_b(un, xb);     // ends with __syncwarp: the stage just read may be refilled
     }
-    cp_async_wait<0>();
   }
   if (!a.do_up) return;
   __syncwarp();
   // forward sweep: q_i = -(P_i v_i + Q_i q_{i-1}); stage i holds P_i and Q_i, stage n R and T
   auto stage_up = [&](int i, int buf) {
-    if (i < n) stage_ops(W.frag[buf], W.exps[buf], a.frag + (e * n + i) * 3 * kSlices * 32, a.exps + (e * n + i) * 3 * 16,
-                         2, lane);
-    else stage_ops(W.frag[buf], W.exps[buf], a.frag_rt + e * 2 * kSlices * 32, a.exps_rt + e * 32, 2, lane);
+    if (i < n) stage_ops(W, buf, a.frag + (e * n + i) * 3 * kSlices * 32, a.exps + (e * n + i) * 3 * 16, 2, lane);
+    else stage_ops(W, buf, a.frag_rt + e * 2 * kSlices * 32, a.exps_rt + e * 32, 2, lane);
   };
   stage_up(0, 0);
-  cp_async_commit();
   double vnext[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) vnext[j] = bok[j] ? a.v[base + br[j] * B + g] : 0.0;
@@ -304,15 +317,13 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
   for (int i = 0; i < n; ++i) {
     const int buf = i & 1;
     stage_up(i + 1, buf ^ 1);
-    cp_async_commit();
     double vb[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       vb[j] = vnext[j];
       vnext[j] = (i + 1 < n && bok[j]) ? a.v[base + (int64_t)(i + 1) * per + br[j] * B + g] : 0.0;
     }
-    cp_async_wait<1>();
-    __syncwarp();
+    wait_stage(buf);
     double qc[4];
     apply_pq(W.frag[buf], W.frag[buf] + kSlices * 32, W.exps[buf], W.exps[buf] + 16, vb, qb, qc);
 #pragma unroll
@@ -332,10 +343,9 @@ __global__ void __launch_bounds__(128, 4) element_step_tc_kernel(ElemTcArgs a) {
       vb[j] = fma(a.a0, a.ub[gi], fma(a.a1, a.udb[gi], a.a2 * a.uddb[gi]));
     }
   }
-  cp_async_wait<0>();
-  __syncwarp();
-  double rq[4], tv[4];
   const int bn = n & 1;
+  wait_stage(bn);
+  double rq[4], tv[4];
   apply(W.frag[bn], W.exps[bn], qb, rq);
   apply(W.frag[bn] + kSlices * 32, W.exps[bn] + 16, vb, tv);
 #pragma unroll
@@ -358,6 +368,14 @@ bool tc_available(int nb, int B) { return nb <= 2 * tc::kTile && B <= tc::kCols;
 int tc_prepare(Model& md, cudaStream_t st) {
   using namespace tc;
   if (md.nb > kTile) return tc2_prepare(md, st);
+  return tc_prepare_one_tile(md, st);
+}
+
+// One-tile digits of every element's operators (their top-left 16 x 16 block; for a mesh
+// padded beyond 16 this is the whole operator of its elements with n_b <= 16, whose padded
+// rows and columns are zero)
+int tc_prepare_one_tile(Model& md, cudaStream_t st) {
+  using namespace tc;
   const int nb = md.nb, n = md.n;
   const int64_t E = md.E;
   SBFWI_CUDA(md.tc_frag.alloc(sizeof(uint4) * (size_t)E * n * 3 * kSlices * 32));
@@ -377,12 +395,14 @@ int tc_prepare(Model& md, cudaStream_t st) {
   for (const void* f : {(const void*)element_step_tc_kernel<true>, (const void*)element_step_tc_kernel<false>})
     SBFWI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(WarpSmem) * kWarpsPerBlock)));
   md.tc_ready = true;
+  md.tc_one_tile = nb > kTile;
   return SBFWI_OK;
 }
 
 int tc_element_launch(const Model& md, int B, int down, int up, double* u, double* ud, double* udd, double* v,
                       const double* ub, const double* udb, const double* uddb, double* q, double* fhat,
-                      double* store_int, const double* fwd_int, double* grad_int, double* u_out, cudaStream_t st) {
+                      double* store_int, const double* fwd_int, double* grad_int, double* u_out, cudaStream_t st,
+                      const int32_t* elems, int64_t n_elems, int* status) {
   ElemTcArgs a;
   a.nb = md.nb; a.n = md.n; a.B = B; a.E = md.E;
   a.a0 = md.a0; a.a1 = md.a1; a.a2 = md.a2; a.c1 = md.c1; a.c2 = md.c2; a.dt = md.dt;
@@ -392,9 +412,14 @@ int tc_element_launch(const Model& md, int B, int down, int up, double* u, doubl
   a.u = u; a.ud = ud; a.udd = udd; a.v = v; a.ub = ub; a.udb = udb; a.uddb = uddb; a.q = q; a.fhat = fhat;
   a.do_down = down; a.do_up = up;
   a.store_int = store_int; a.fwd_int = fwd_int; a.grad_int = grad_int; a.u_out = u_out;
-  if (md.nb > tc::kTile) return tc2_element_launch(a, md.a2 == 1.0 && md.c1 == md.c2, st);
+  a.elems = elems; a.n_elems = elems ? n_elems : md.E;
+  a.status = status;
+  if (a.n_elems == 0) return SBFWI_OK;
+  // one 16-row tile: n_b <= 16, or the elements of n_b <= 16 of a mesh padded beyond (the
+  // one-tile digits of its operators, prepared by tc_prepare_one_tile)
+  if (md.nb > tc::kTile && !md.tc_one_tile) return tc2_element_launch(a, md.a2 == 1.0 && md.c1 == md.c2, st);
   const int smem = (int)(sizeof(tc::WarpSmem) * tc::kWarpsPerBlock);   // attribute set by tc_prepare
-  const unsigned blocks = (unsigned)((md.E + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock);
+  const unsigned blocks = (unsigned)((a.n_elems + tc::kWarpsPerBlock - 1) / tc::kWarpsPerBlock);
   // average acceleration (beta = 1/4, gamma = 1/2): the shorter predictor update
   if (md.a2 == 1.0 && md.c1 == md.c2) element_step_tc_kernel<true><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);
   else element_step_tc_kernel<false><<<blocks, 32 * tc::kWarpsPerBlock, smem, st>>>(a);

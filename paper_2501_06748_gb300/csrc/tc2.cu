@@ -25,15 +25,22 @@ struct WarpSmem {
   uint4 frag[2][2 * kOpFrags];               // two stages of one or two operators
   int exps[2][2 * kR];
   double xch[kR * kCols];
+  uint64_t bar[2];                           // the stages' mbarriers
 };
 
 __device__ __forceinline__ const uint4* tile(const uint4* op, int rt, int kt) {
   return op + (rt * kRT + kt) * kSlices * 32;
 }
 
-__device__ __forceinline__ void stage_ops(uint4* dst, int* dexp, const uint4* src, const int* sexp, int nops, int lane) {
-  for (int k = 0; k < nops * kRT * kRT * kSlices; ++k) cp_async16(dst + k * 32 + lane, src + k * 32 + lane);
-  for (int q = lane; q < nops * kR; q += 32) cp_async4(dexp + q, sexp + q);
+// one stage: two bulk copies (fragments, exponents) completing on the stage's mbarrier
+__device__ __forceinline__ void stage_ops(WarpSmem& W, int buf, const uint4* src, const int* sexp, int nops, int lane) {
+  if (lane == 0) {
+    const unsigned fb = (unsigned)(nops * kOpFrags * sizeof(uint4)), eb = (unsigned)(nops * kR * sizeof(int));
+    fence_proxy_async();
+    mbar_expect_tx(&W.bar[buf], fb + eb);
+    bulk_g2s(W.frag[buf], src, fb, &W.bar[buf]);
+    bulk_g2s(W.exps[buf], sexp, eb, &W.bar[buf]);
+  }
 }
 
 }  // namespace tc2
@@ -117,8 +124,20 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
   extern __shared__ __align__(16) unsigned char tc2_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   WarpSmem& W = reinterpret_cast<WarpSmem*>(tc2_smem)[warp];
-  const int64_t e = (int64_t)blockIdx.x * kWarps + warp;
-  if (e >= a.E) return;
+  const int64_t idx = (int64_t)blockIdx.x * kWarps + warp;
+  if (idx >= a.n_elems) return;
+  const int64_t e = a.elems ? (int64_t)a.elems[idx] : idx;
+  if (lane == 0) {
+    mbar_init(&W.bar[0], 1);
+    mbar_init(&W.bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  unsigned phase = 0;                         // bit b: parity of stage b's next completion
+  auto wait_stage = [&](int b) {
+    mbar_wait(&W.bar[b], (phase >> b) & 1u, a.status);
+    phase ^= 1u << b;
+  };
   const int nb = a.nb, n = a.n, B = a.B;
   const int per = nb * B;
   double* X = W.xch;
@@ -215,8 +234,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
     const int64_t hop = (int64_t)3 * kOpFrags;
     const uint4* Hsrc = a.frag + ((e * n + (n - 1)) * 3 + 2) * kOpFrags;
     const int* Hexp = a.exps + ((e * n + (n - 1)) * 3 + 2) * kR;
-    stage_ops(W.frag[(n - 1) & 1], W.exps[(n - 1) & 1], Hsrc, Hexp, 1, lane);
-    cp_async_commit();
+    stage_ops(W, (n - 1) & 1, Hsrc, Hexp, 1, lane);
 #pragma unroll
     for (int k = 0; k < kRT; ++k)
 #pragma unroll
@@ -224,9 +242,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
         xb[k][j] = bok[k][j] ? a.ub[(int64_t)a.dofs[e * nb + k * kTile + br[j]] * B + g] : 0.0;
     for (int i = n - 1; i >= 0; --i) {
       const int buf = i & 1;
-      if (i > 0) stage_ops(W.frag[buf ^ 1], W.exps[buf ^ 1], Hsrc - (int64_t)(n - i) * hop,
-                           Hexp - (int64_t)(n - i) * 3 * kR, 1, lane);
-      cp_async_commit();
+      if (i > 0) stage_ops(W, buf ^ 1, Hsrc - (int64_t)(n - i) * hop, Hexp - (int64_t)(n - i) * 3 * kR, 1, lane);
       double qo[kRT][4], zo[kRT][4], vo[kRT][4], fw[kRT][4], gr[kRT][4];
 #pragma unroll
       for (int r = 0; r < kRT; ++r)
@@ -239,8 +255,7 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
           fw[r][j] = (cok[r][j] && a.grad_int) ? a.fwd_int[o] : 0.0;
           gr[r][j] = (cok[r][j] && a.grad_int) ? a.grad_int[o] : 0.0;
         }
-      cp_async_wait<1>();
-      __syncwarp();
+      wait_stage(buf);
       double hu[kRT][4];
       apply(W.frag[buf], W.exps[buf], xb, hu);
       double un[kRT][4];
@@ -270,17 +285,14 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
         }
       c_to_b(un, xb);
     }
-    cp_async_wait<0>();
   }
   if (!a.do_up) return;
   __syncwarp();
   auto stage_up = [&](int i, int buf) {
-    if (i < n) stage_ops(W.frag[buf], W.exps[buf], a.frag + (e * n + i) * 3 * kOpFrags, a.exps + (e * n + i) * 3 * kR,
-                         2, lane);
-    else stage_ops(W.frag[buf], W.exps[buf], a.frag_rt + e * 2 * kOpFrags, a.exps_rt + e * 2 * kR, 2, lane);
+    if (i < n) stage_ops(W, buf, a.frag + (e * n + i) * 3 * kOpFrags, a.exps + (e * n + i) * 3 * kR, 2, lane);
+    else stage_ops(W, buf, a.frag_rt + e * 2 * kOpFrags, a.exps_rt + e * 2 * kR, 2, lane);
   };
   stage_up(0, 0);
-  cp_async_commit();
   double qb[kRT][4];
 #pragma unroll
   for (int k = 0; k < kRT; ++k)
@@ -289,15 +301,13 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
   for (int i = 0; i < n; ++i) {
     const int buf = i & 1;
     stage_up(i + 1, buf ^ 1);
-    cp_async_commit();
     double vb[kRT][4];
 #pragma unroll
     for (int k = 0; k < kRT; ++k)
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         vb[k][j] = bok[k][j] ? a.v[base + (int64_t)i * per + (k * kTile + br[j]) * B + g] : 0.0;
-    cp_async_wait<1>();
-    __syncwarp();
+    wait_stage(buf);
     double qc[kRT][4];
     apply_pq(W.frag[buf], W.frag[buf] + kOpFrags, W.exps[buf], W.exps[buf] + kR, vb, qb, qc);
 #pragma unroll
@@ -321,10 +331,9 @@ __global__ void __launch_bounds__(64, 2) element_step_tc2_kernel(ElemTcArgs a) {
         vb[k][j] = fma(a.a0, a.ub[gi], fma(a.a1, a.udb[gi], a.a2 * a.uddb[gi]));
       }
     }
-  cp_async_wait<0>();
-  __syncwarp();
-  double rq[kRT][4], tv[kRT][4];
   const int bn = n & 1;
+  wait_stage(bn);
+  double rq[kRT][4], tv[kRT][4];
   apply(W.frag[bn], W.exps[bn], qb, rq);
   apply(W.frag[bn] + kOpFrags, W.exps[bn] + kR, vb, tv);
 #pragma unroll
@@ -355,13 +364,14 @@ int tc2_prepare(Model& md, cudaStream_t st) {
   for (const void* f : {(const void*)element_step_tc2_kernel<true>, (const void*)element_step_tc2_kernel<false>})
     SBFWI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(WarpSmem) * kWarps)));
   md.tc_ready = true;
+  md.tc_one_tile = false;
   return SBFWI_OK;
 }
 
 int tc2_element_launch(const ElemTcArgs& a, bool avg_accel, cudaStream_t st) {
   using namespace tc2;
   const int smem = (int)(sizeof(WarpSmem) * kWarps);
-  const unsigned blocks = (unsigned)((a.E + kWarps - 1) / kWarps);
+  const unsigned blocks = (unsigned)((a.n_elems + kWarps - 1) / kWarps);
   if (avg_accel) element_step_tc2_kernel<true><<<blocks, 32 * kWarps, smem, st>>>(a);
   else element_step_tc2_kernel<false><<<blocks, 32 * kWarps, smem, st>>>(a);
   return SBFWI_OK;

@@ -165,18 +165,43 @@ __device__ __forceinline__ void zero(float (&acc)[kLevels][4]) {
 }
 
 
-// asynchronous global -> shared copies (Ampere-style cp.async; completion per thread)
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+// Bulk global -> shared copies by the TMA engine (cp.async.bulk), completing on an mbarrier
+// in shared memory: one thread arms the barrier with the byte count and issues the copies;
+// every consumer waits on the barrier's phase.  Addresses and sizes are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+// the barrier initialisation visible to the TMA engine before its first use
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+// shared memory that the warp read through ordinary loads may now be overwritten by the TMA engine
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n}\n"
+               ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_addr(smem)), "l"(gmem), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// wait until the barrier has completed the phase with this parity; bounded: after about
+// 2^24 polls (tens of ms) it records SBFWI_ETIMEOUT in *status and gives up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int* status) {
+  const unsigned a = smem_addr(bar);
+  for (int it = 0; it < (1 << 24); ++it) {
+    unsigned done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  if (status) atomicCAS(status, 0, -4 /* SBFWI_ETIMEOUT */);
+  return false;
+}
 
 }  // namespace tc
 
@@ -212,6 +237,11 @@ struct ElemTcArgs {
   const double* fwd_int;
   double* grad_int;
   double* u_out;          // full Frechet kernel: the new interior displacements (store or adjoint field)
+  // the elements this launch steps: elems[0..n_elems) (an element class of a mesh with
+  // uneven elements), or all E elements when elems is NULL
+  const int32_t* elems;
+  int64_t n_elems;
+  int* status;            // a bounded wait that gives up records SBFWI_ETIMEOUT here (nullable)
 };
 
 // elements padded to 21..32 boundary nodes (tc2.cu)

@@ -20,16 +20,34 @@ from . import shots
 
 
 def objective(mesh, c, dt, src_nodes, wavelets, rec_nodes, observed, lx=1.0, ly=1.0, shots_per_pass=8,
-              ckpt_every=0, group=None):
+              ckpt_every=0, group=None, exact=False):
     """fg(rho_grid) -> (misfit, gradient on the grid): one model set-up and every shot's
-    forward, misfit and adjoint through the library."""
+    forward, misfit and adjoint through the library (the paper's kernel, or with ``exact``
+    the exact derivative of the discrete misfit)."""
     from . import sbfwi
 
     def fg(rho):
         model = sbfwi.Model(mesh, c, rho, dt, lx=lx, ly=ly)
         return shots.misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed,
-                                         shots_per_pass=shots_per_pass, group=group, ckpt_every=ckpt_every)
+                                         shots_per_pass=shots_per_pass, group=group, ckpt_every=ckpt_every,
+                                         exact=exact)
     return fg
+
+
+def misfit_only(mesh, c, dt, src_nodes, wavelets, rec_nodes, observed, lx=1.0, ly=1.0, shots_per_pass=8):
+    """f(rho_grid) -> misfit: forward passes and the misfit only (finite-difference checks)."""
+    from . import sbfwi
+
+    def f(rho):
+        model = sbfwi.Model(mesh, c, rho, dt, lx=lx, ly=ly)
+        src = np.asarray(src_nodes, dtype=np.int64)
+        E = 0.0
+        for lo in range(0, src.size, max(1, shots_per_pass)):
+            hi = min(src.size, lo + max(1, shots_per_pass))
+            tr, _ = sbfwi.forward(model, src[lo:hi], wavelets[lo:hi], rec_nodes, keep=False)
+            E += sbfwi.misfit(tr, observed[lo:hi], dt, want_residual=False)[0]
+        return E
+    return f
 
 
 def _ops(x):

@@ -21,9 +21,10 @@ RHO_GRID, RHO_NODAL = 0, 1
 GRAD_KERNEL, GRAD_EXACT = 0, 1
 GRAD_ACCUMULATE = 0x100
 CKPT_AUTO = -1
-ELEMENT_AUTO, ELEMENT_TENSOR, ELEMENT_FP64 = 0, 1, 2
+ELEMENT_AUTO, ELEMENT_TENSOR, ELEMENT_FP64, ELEMENT_MIXED = 0, 1, 2, 3
 SOLVE_AUTO, SOLVE_DATAFLOW, SOLVE_BARRIER, SOLVE_LEVELS = 0, 1, 2, 3
 TERMS_VELOCITY, TERMS_FULL = 0, 1
+SESSION_FORWARD, SESSION_ADJOINT = 0, 1
 PHASES = ("setup", "element", "solve", "other")
 
 _NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", ESTATE: "ESTATE",
@@ -71,8 +72,20 @@ def _load():
     lib.sbfwi_lfe_element_matrices.restype = ctypes.c_int
     lib.sbfwi_set_kernel_terms.argtypes = [VP, ctypes.c_int]
     lib.sbfwi_set_kernel_terms.restype = ctypes.c_int
+    lib.sbfwi_set_gradient_mode.argtypes = [VP, ctypes.c_int]
+    lib.sbfwi_set_gradient_mode.restype = ctypes.c_int
     lib.sbfwi_set_schedule.argtypes = [VP, ctypes.c_int, ctypes.c_int]
     lib.sbfwi_set_schedule.restype = ctypes.c_int
+    lib.sbfwi_session_create.argtypes = [P(VP), VP, I32, I32, I32, pi64, I32, VP]
+    lib.sbfwi_session_admit.argtypes = [VP, I32, I64, VP, I64, VP, ctypes.c_int]
+    lib.sbfwi_session_step.argtypes = [VP, P(I32)]
+    lib.sbfwi_session_collect.argtypes = [VP, I32, VP, ctypes.c_int]
+    lib.sbfwi_session_info.argtypes = [VP, pi64]
+    lib.sbfwi_session_destroy.argtypes = [VP]
+    lib.sbfwi_session_destroy.restype = None
+    for name in ("sbfwi_session_create", "sbfwi_session_admit", "sbfwi_session_step", "sbfwi_session_collect",
+                 "sbfwi_session_info"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.sbfwi_selftest_barrier.argtypes = [I32, I32, I64, I32, VP]
     lib.sbfwi_selftest_barrier.restype = ctypes.c_int
     for name in ("sbfwi_build_mesh", "sbfwi_mesh_info", "sbfwi_set_model", "sbfwi_forward", "sbfwi_misfit",
@@ -209,12 +222,80 @@ class Model:
                                     float(lx), float(ly), float(dt), float(beta), float(gamma), r.mem, r.stream))
         self._h = h
         self.mesh = mesh                 # keeps the mesh alive for the model's lifetime
-        self.rho_kind, self.gx, self.gy, self.dt = rho_kind, int(gx), int(gy), float(dt)
+        self.rho_kind, self.gx, self.gy, self.dt, self.lfe = rho_kind, int(gx), int(gy), float(dt), bool(lfe)
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             _lib.sbfwi_destroy_model(h)
+            self._h = None
+
+
+class Session:
+    """Continuous batching on one model (sbfwi_session_*): ``slots`` shot columns advanced in
+    windows of ``window`` steps; requests are admitted into free slots between windows and
+    collected when finished.  Forward requests give traces [R][K] (and, with ``field``, the
+    nodal velocities for a later adjoint request); adjoint requests give the gradient of one
+    shot.  Runs on torch's current stream of ``device``."""
+
+    def __init__(self, model: "Model", kind, slots, rec_nodes, window=32, device=None):
+        import torch
+        self.model, self.kind = model, int(kind)
+        self.rec = _i64_host(rec_nodes)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._stream = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        h = ctypes.c_void_p()
+        _check(_lib.sbfwi_session_create(ctypes.byref(h), model._h, self.kind, int(slots), int(self.rec.size),
+                                         _iptr(self.rec), int(window), self._stream))
+        self._h = h
+        info = self.info()
+        self.field_stride, self.slots, self.window = info["field_stride"], info["slots"], info["window"]
+        self._keep = {}                  # per slot: the arrays the library reads or writes asynchronously
+
+    def info(self):
+        v = np.zeros(5, dtype=np.int64)
+        _check(_lib.sbfwi_session_info(self._h, _iptr(v)))
+        return {"field_stride": int(v[0]), "steps": int(v[1]), "slots": int(v[2]), "window": int(v[3]),
+                "busy": int(v[4])}
+
+    def admit(self, slot, values, src_node=0, field=None):
+        """Forward: values = wavelet [K] at ``src_node``; adjoint: values = residual [R][K].
+        ``field``: a CUDA float64 tensor [K][field_stride] (forward: filled; adjoint: read)."""
+        v = _Arr(values)
+        K = int(v.obj.shape[-1])
+        fptr = None
+        if field is not None:
+            if not _is_torch_cuda(field):
+                raise ValueError("field must be a CUDA tensor")
+            if tuple(field.shape) != (K, self.field_stride) or not field.is_contiguous():
+                raise ValueError(f"field must be a contiguous [{K}][{self.field_stride}] tensor")
+            fptr = ctypes.c_void_p(field.data_ptr())
+        _check(_lib.sbfwi_session_admit(self._h, int(slot), int(src_node), v.ptr, K, fptr, v.mem))
+        self._keep[int(slot)] = (v, field, K)
+
+    def step(self):
+        """One window; returns the slots holding a finished request."""
+        fin = np.zeros(self.slots, dtype=np.int32)
+        _check(_lib.sbfwi_session_step(self._h, fin.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return [int(s) for s in np.nonzero(fin)[0]]
+
+    def collect(self, slot):
+        """The finished request's result as a CUDA tensor (traces [R][K] or the gradient)."""
+        import torch
+        _, _, K = self._keep.pop(int(slot))
+        if self.kind == SESSION_FORWARD:
+            out = torch.empty((self.rec.size, K), dtype=torch.float64, device=self.device)
+        else:
+            m = self.model
+            shape = (m.gy, m.gx) if m.rho_kind == RHO_GRID else (m.mesh.n_nodal,)
+            out = torch.zeros(shape, dtype=torch.float64, device=self.device)
+        _check(_lib.sbfwi_session_collect(self._h, int(slot), ctypes.c_void_p(out.data_ptr()), MEM_DEVICE))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.sbfwi_session_destroy(h)
             self._h = None
 
 
@@ -258,6 +339,10 @@ def misfit(traces, observed, dt, residual_out=None, want_residual=True):
     """E = 0.5 dt sum (observed - traces)^2 and the residual observed - traces."""
     t, o = _Arr(traces), _Arr(observed)
     n = int(np.prod(t.obj.shape))
+    if int(np.prod(o.obj.shape)) != n:
+        raise ValueError("observed and traces must have the same number of samples")
+    if residual_out is not None and int(np.prod(residual_out.shape)) != n:
+        raise ValueError("residual_out must have as many samples as traces")
     if want_residual and residual_out is None:
         if t.mem == MEM_DEVICE:
             import torch
@@ -273,9 +358,10 @@ def misfit(traces, observed, dt, residual_out=None, want_residual=True):
 
 
 def adjoint_gradient(model: Model, state: FwdState, residual, mode=GRAD_KERNEL, grad_out=None, accumulate=False):
-    """Time-reversed adjoint and velocity Frechet kernel; returns the gradient on the
-    model's parameter layout ([gy][gx] grid or [n_nodal]).  ``accumulate`` adds into
-    ``grad_out``."""
+    """Time-reversed adjoint and velocity Frechet kernel (``mode=GRAD_KERNEL``) or the exact
+    derivative of the discrete misfit (``mode=GRAD_EXACT``, forward state made in that
+    gradient mode); returns the gradient on the model's parameter layout ([gy][gx] grid or
+    [n_nodal]).  ``accumulate`` adds into ``grad_out``."""
     if accumulate:
         if grad_out is None:
             raise ValueError("accumulate needs grad_out")
@@ -309,6 +395,13 @@ def misfit_noalloc(traces, observed, dt, E_out, residual_out=None):
     if any(a.mem != MEM_DEVICE for a in arrs):
         raise ValueError("misfit_noalloc takes CUDA tensors only")
     n = int(np.prod(arrs[0].obj.shape))
+    # the C entry point cannot see the lengths of device arrays: check them here
+    if int(np.prod(arrs[1].obj.shape)) != n:
+        raise ValueError("observed and traces must have the same number of samples")
+    if residual_out is not None and int(np.prod(arrs[3].obj.shape)) != n:
+        raise ValueError("residual_out must have as many samples as traces")
+    if int(np.prod(arrs[2].obj.shape)) < 1:
+        raise ValueError("E_out needs at least one element")
     _check(_lib.sbfwi_misfit_noalloc(arrs[0].ptr, arrs[1].ptr, n, float(dt), arrs[2].ptr,
                                      arrs[3].ptr if residual_out is not None else None, arrs[0].stream))
     return E_out, residual_out
@@ -327,6 +420,12 @@ def set_kernel_terms(model: Model, terms: int = TERMS_VELOCITY) -> None:
     """Velocity term only (the paper's kernel) or the full Frechet kernel for later
     forward/adjoint pairs on the model."""
     _check(_lib.sbfwi_set_kernel_terms(model._h, int(terms)))
+
+
+def set_gradient_mode(model: Model, mode: int = GRAD_KERNEL) -> None:
+    """GRAD_KERNEL (the paper's velocity kernel) or GRAD_EXACT (the exact derivative of the
+    discrete misfit) for the forward states of later forward passes on the model."""
+    _check(_lib.sbfwi_set_gradient_mode(model._h, int(mode)))
 
 
 def set_schedule(model: Model, element: int = ELEMENT_AUTO, solve: int = SOLVE_AUTO) -> None:

@@ -55,15 +55,18 @@ def allreduce_misfit_gradient(E: float, grad, group=None):
 
 
 def misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed, shots_per_pass: int = 8, group=None,
-                        ckpt_every: int = 0):
+                        ckpt_every: int = 0, exact: bool = False):
     """Misfit and density gradient of all shots, sharded over the ranks of `group`.
 
     `src_nodes` [S], `wavelets` [S][K] and `observed` [S][R][K] hold every shot; each
     rank takes its `shard`, runs it through the library in passes of at most
     `shots_per_pass` shots (forward with the velocity store, or with checkpoints every
     `ckpt_every` steps, misfit, adjoint with the gradient accumulated), then joins the
-    one all-reduce.  Host arrays in, host arrays out; CUDA tensors in, CUDA tensors out."""
+    one all-reduce.  Host arrays in, host arrays out; CUDA tensors in, CUDA tensors out.
+    ``exact`` gives the exact derivative of the discrete misfit instead of the paper's kernel."""
     from . import sbfwi
+    mode = sbfwi.GRAD_EXACT if exact else sbfwi.GRAD_KERNEL
+    sbfwi.set_gradient_mode(model, mode)
     dist = _dist()
     rank = dist.get_rank(group) if dist else 0
     world = dist.get_world_size(group) if dist else 1
@@ -80,7 +83,7 @@ def misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed, shots_p
         hi = min(mine.stop, lo + max(1, shots_per_pass))
         tr, st = sbfwi.forward(model, src[lo:hi], wavelets[lo:hi], rec_nodes, ckpt_every=ckpt_every)
         Ec, res = sbfwi.misfit(tr, observed[lo:hi], model.dt)
-        sbfwi.adjoint_gradient(model, st, res, grad_out=grad, accumulate=True)
+        sbfwi.adjoint_gradient(model, st, res, mode=mode, grad_out=grad, accumulate=True)
         E += Ec
         del st
     return allreduce_misfit_gradient(E, grad, group)

@@ -143,9 +143,12 @@ def test_errors_are_reported(lib, tiny):
     with pytest.raises(lib.SbfwiError):
         lib.forward(md, w.src_nodes, w.wavelets, [w.rec_nodes[0], w.rec_nodes[0]])
     tr, st = lib.forward(md, w.src_nodes, w.wavelets[:, :5], w.rec_nodes)
-    with pytest.raises(lib.SbfwiError) as ei:
+    with pytest.raises(lib.SbfwiError) as ei:       # the forward state was not kept for the exact adjoint
         lib.adjoint_gradient(md, st, tr, mode=lib.GRAD_EXACT)
-    assert ei.value.code == lib.EUNSUPPORTED
+    assert ei.value.code == lib.ESTATE
+    with pytest.raises(lib.SbfwiError) as ei:
+        lib.adjoint_gradient(md, st, tr, mode=5)
+    assert ei.value.code == lib.EINVAL
 
 
 @pytest.mark.slow

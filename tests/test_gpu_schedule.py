@@ -5,7 +5,7 @@ the choice is checked against the shapes, and the autotuner keeps a valid fastes
 import numpy as np
 import pytest
 
-from oracle import uneven
+from oracle import fwi, uneven
 from sbfwi_inputs import boundary_nodes, min_spacing, nearest_node, quadtree_mesh, ricker
 
 pytestmark = pytest.mark.gpu
@@ -45,9 +45,10 @@ def test_every_schedule_gives_the_same_traces(lib):
     assert rel(out[(lib.ELEMENT_TENSOR, 1)], out[(lib.ELEMENT_FP64, 1)]) <= 1e-12
 
 
-def test_tensor_kernel_on_request_where_the_default_is_fp64(lib):
-    """Padded n_b = 18 runs the FP64 kernel by default; asking for the tensor-core kernel
-    prepares its operator digits on first use, and both match the oracle."""
+def test_tensor_kernel_on_request_where_the_default_is_mixed(lib):
+    """Padded n_b = 18 runs the mixed kernels by default (n_b <= 16 on the one-tile
+    tensor-core kernel, the n_b = 18 elements on FP64); asking for the two-tile tensor-core
+    kernel prepares its operator digits on first use, and both match the oracle."""
     m = quadtree_mesh(4, 1, lambda x0, y0, x1, y1, lvl: x0 < 0.25 or y0 < 0.25, 3)    # corner cell: n_b 18
     assert m.n_b.max() == 18
     _, rho, dt, src, wav, rec = _problem()
@@ -94,8 +95,43 @@ def test_autotuner_keeps_a_valid_fastest_schedule(lib):
     md = lib.Model(M, 1.0, rho, dt)
     ref, _ = lib.forward(md, src, wav, rec, keep=False)
     choice = autotune.tune(md, src, wav, rec, steps=8, repeats=2)
-    assert len(choice["candidates"]) == 6
+    assert len(choice["candidates"]) == 9
     times = [c["s_per_step"] for c in choice["candidates"] if c["s_per_step"] is not None]
+    # padded n_b 15: every element fits one tile, so the mixed kernels do not apply
     assert len(times) == 6 and choice["s_per_step"] == min(times)
+    assert all(c["s_per_step"] is None for c in choice["candidates"] if c["element"] == "mixed")
     tr, _ = lib.forward(md, src, wav, rec, keep=False)
     assert rel(tr, ref) <= 1e-12
+
+
+def test_mixed_element_kernels_on_uneven_elements(lib):
+    """A quadtree whose corner cells have n_b = 18 (the rest 12 and 15): the elements of
+    n_b <= 16 run the one-tile tensor-core kernel and the others the FP64 kernel, two
+    launches per step over element lists.  Traces and gradient match the oracle (1e-10 /
+    1e-8) and the all-FP64 run (1e-12); checkpointed = stored field bit for bit."""
+    m = quadtree_mesh(4, 1, lambda x0, y0, x1, y1, lvl: x0 < 0.25 or y0 < 0.25, 3)
+    nbs = m.n_b
+    assert nbs.max() == 18 and (nbs <= 16).sum() > 0
+    _, rho, dt, src, wav, rec = _problem()
+    om = uneven.build_model(m, 5, 1.0, rho, dt)
+    to, store, _ = uneven.forward(om, src, wav, rec)
+    obs = 0.01 * np.random.default_rng(3).standard_normal(to.shape)
+    Eo, reso = fwi.misfit(to, obs, dt)
+    go = uneven.gradient_to_grid(om, uneven.adjoint_gradient(om, store, reso, rec), 17, 17)
+    M = lib.Mesh.from_inputs(m, 5)
+    md = lib.Model(M, 1.0, rho, dt)
+    out = {}
+    for e in (lib.ELEMENT_MIXED, lib.ELEMENT_FP64):
+        lib.set_schedule(md, e)
+        for c in (0, 7):
+            tr, st = lib.forward(md, src, wav, rec, ckpt_every=c)
+            _, res = lib.misfit(tr, obs, dt)
+            out[(e, c)] = (tr, lib.adjoint_gradient(md, st, res))
+    tr, g = out[(lib.ELEMENT_MIXED, 0)]
+    assert rel(tr, to) <= 1e-10 and rel(g, go) <= 1e-8
+    assert rel(tr, out[(lib.ELEMENT_FP64, 0)][0]) <= 1e-12
+    assert not np.array_equal(tr, out[(lib.ELEMENT_FP64, 0)][0])          # the tensor cores ran
+    assert np.array_equal(g, out[(lib.ELEMENT_MIXED, 7)][1])
+    lib.set_schedule(md, lib.ELEMENT_AUTO)
+    tr_auto, _ = lib.forward(md, src, wav, rec, keep=False)
+    assert np.array_equal(tr_auto, tr)                                      # the default for padded n_b 18

@@ -148,3 +148,31 @@ def test_compute_calls_fail_loudly_without_a_device(binding):
     with pytest.raises(binding.SbfwiError) as ei:
         binding.selftest_barrier(4, 1)
     assert ei.value.code == binding.ECUDA
+
+
+def test_misfit_wrappers_check_lengths_before_the_call(binding):
+    """The C entry points take one sample count n for every array; the binding refuses
+    arrays of different lengths before calling them (a short device array would be read
+    or written beyond its end)."""
+    with pytest.raises(ValueError):
+        binding.misfit(np.zeros(5), np.ones(4), 0.1)
+    with pytest.raises(ValueError):
+        binding.misfit(np.zeros(5), np.ones(5), 0.1, residual_out=np.zeros(3))
+
+
+def test_lfe_refuses_an_element_whose_stable_subspace_has_the_wrong_rank(binding):
+    """K is built from the n_b - 1 stable eigen-solutions plus the constant mode; that split
+    exists because E1^T 1 = E2 1 = 0 gives the constant mode an exact zero pair.  Coefficient
+    matrices that break it (E2 + 0.1 max|E2| I: the pair splits into +-0.73, one of them joins
+    the stable side, 8 = n_b stable solutions) must be refused, not given a wrong subspace;
+    a tiny perturbation that keeps the split is still accepted."""
+    from oracle import sbfem
+    m = structured_mesh(2, 2, 2)
+    el = sbfem.elements_from_mesh(m)[0]
+    nb = el.dofs.size
+    E0, E1, E2, M0 = (np.asarray(q[0], dtype=np.float64)
+                      for q in sbfem.coefficient_matrices(el, m.node_xy, m.p, 1.0, np.ones((1, nb), dtype=sbfem.XP)))
+    binding.lfe_element_matrices(E0, E1, E2 + 1e-3 * np.abs(E2).max() * np.eye(nb), M0)
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.lfe_element_matrices(E0, E1, E2 + 0.1 * np.abs(E2).max() * np.eye(nb), M0)
+    assert ei.value.code == binding.ESINGULAR and "n_b - 1" in str(ei.value)
