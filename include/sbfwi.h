@@ -210,8 +210,8 @@ int sbfwi_lfe_element_matrices(const double* E0, const double* E1, const double*
  *     coordinate map of each element line through it (second-order differences along
  *     the radial grid, the line's Lagrange derivative along it; the mean over the
  *     element lines that meet at the point).  Forward passes then also keep the
- *     nodal displacements of every step (twice the stored field); checkpointed
- *     forward passes (ckpt_every != 0) return SBFWI_EUNSUPPORTED.
+ *     nodal displacements of every step (twice the stored field); with checkpoints
+ *     (ckpt_every != 0) the adjoint's recompute windows keep them (twice the window).
  * Errors: SBFWI_EINVAL for a NULL model or an unknown value.
  */
 enum { SBFWI_TERMS_VELOCITY = 0, SBFWI_TERMS_FULL = 1 };

@@ -189,12 +189,17 @@ __device__ __forceinline__ double lane_group_sum(double v, int ks) {
 //
 // Forward: [c_sep (s B values, + external sources at the separator nodes) | the
 // task's rows of C (rows x s)]; c_sep also goes to ysep if asked.
+// part: kStageAll, or kStageConst (the factor rows: they do not depend on other tasks, so
+// the dataflow schedule stages them before waiting for its dependencies) or kStageData.
+enum { kStageAll = 0, kStageConst = 1, kStageData = 2 };
+
 template <int U>
 __device__ __forceinline__ void stage_forward(const SolveArgs& a, const Task& tk, double* sm, bool write_ysep, int tid,
-                                              int nthr) {
+                                              int nthr, int part = kStageAll) {
   const int B = a.B, S = tk.s, n1 = S * B, n2 = (tk.r1 - tk.r0) * S;
   const double* C = a.factors + tk.X_off + (int64_t)S * S + (int64_t)S * tk.b + (int64_t)tk.r0 * S;
-  for (int base = 0; base < n1 + n2; base += U * nthr) {
+  const int lo = part == kStageConst ? n1 : 0, hi = part == kStageData ? n1 : n1 + n2;
+  for (int base = lo; base < hi; base += U * nthr) {
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -203,14 +208,14 @@ __device__ __forceinline__ void stage_forward(const SolveArgs& a, const Task& tk
       if (t < n1) {
         const int k = t / B, s = t - k * B;
         v[u] = front_value(a, tk, k, s) + a.ext[(int64_t)a.sep_nodes[tk.sep_off + k] * B + s];
-      } else if (t < n1 + n2) {
+      } else if (t < hi) {
         v[u] = C[t - n1];
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int t = base + u * nthr + tid;
-      if (t < n1 + n2) sm[t] = v[u];
+      if (t < hi) sm[t] = v[u];
       if (write_ysep && t < n1) a.ysep[tk.sep_off * B + t] = v[u];
     }
   }
@@ -219,12 +224,14 @@ __device__ __forceinline__ void stage_forward(const SolveArgs& a, const Task& tk
 // Backward: [y_sep (s B) | x at the front's boundary nodes (b B) | the task's rows of
 // X (rows x s) | the task's rows of G (rows x b)]
 template <int U>
-__device__ __forceinline__ void stage_backward(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+__device__ __forceinline__ void stage_backward(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr,
+                                               int part = kStageAll) {
   const int B = a.B, S = tk.s, Bn = tk.b, rows = tk.r1 - tk.r0;
   const int n1 = S * B, n2 = n1 + Bn * B, n3 = n2 + rows * S, n4 = n3 + rows * Bn;
   const double* X = a.factors + tk.X_off + (int64_t)tk.r0 * S;
   const double* G = a.factors + tk.X_off + (int64_t)S * S + (int64_t)tk.r0 * Bn;
-  for (int base = 0; base < n4; base += U * nthr) {
+  const int lo = part == kStageConst ? n2 : 0, hi = part == kStageData ? n2 : n4;
+  for (int base = lo; base < hi; base += U * nthr) {
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -244,15 +251,16 @@ __device__ __forceinline__ void stage_backward(const SolveArgs& a, const Task& t
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int t = base + u * nthr + tid;
-      if (t < n4) sm[t] = v[u];
+      if (t < hi) sm[t] = v[u];
     }
   }
 }
 
-// forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element)
-__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* sm) {
+// forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element);
+// part: what is left to stage (kStageData when the constants were staged before the wait)
+__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* sm, int part = kStageAll) {
   const int B = a.B, S = tk.s;
-  stage_forward<8>(a, tk, sm, tk.r0 == 0, threadIdx.x, blockDim.x);
+  stage_forward<8>(a, tk, sm, tk.r0 == 0, threadIdx.x, blockDim.x, part);
   __syncthreads();
   const double* csep = sm;
   const double* Cs = sm + S * B;          // rows r0.. of C, s each
@@ -279,9 +287,9 @@ __device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* sm
 }
 
 // backward pass: x_sep = X y_sep - G x_bnd
-__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* sm) {
+__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* sm, int part = kStageAll) {
   const int B = a.B, S = tk.s, Bn = tk.b, rows = tk.r1 - tk.r0;
-  stage_backward<8>(a, tk, sm, threadIdx.x, blockDim.x);
+  stage_backward<8>(a, tk, sm, threadIdx.x, blockDim.x, part);
   __syncthreads();
   const double* ys = sm;
   const double* xbn = ys + S * B;
@@ -311,9 +319,9 @@ __device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* s
 }
 
 // the same for a small front done by one warp (all rows; no block synchronisation)
-__device__ void solve_forward_warp(const SolveArgs& a, const Task tk, double* sm, int lane) {
+__device__ void solve_forward_warp(const SolveArgs& a, const Task tk, double* sm, int lane, int part = kStageAll) {
   const int B = a.B, S = tk.s, Bn = tk.b;
-  stage_forward<8>(a, tk, sm, true, lane, 32);
+  stage_forward<8>(a, tk, sm, true, lane, 32, part);
   __syncwarp();
   const double* csep = sm;
   const double* Cs = sm + S * B;           // all b rows of C, s each
@@ -340,9 +348,9 @@ __device__ void solve_forward_warp(const SolveArgs& a, const Task tk, double* sm
   __syncwarp();
 }
 
-__device__ void solve_backward_warp(const SolveArgs& a, const Task tk, double* sm, int lane) {
+__device__ void solve_backward_warp(const SolveArgs& a, const Task tk, double* sm, int lane, int part = kStageAll) {
   const int B = a.B, S = tk.s, Bn = tk.b;
-  stage_backward<8>(a, tk, sm, lane, 32);
+  stage_backward<8>(a, tk, sm, lane, 32, part);
   __syncwarp();
   const double* ys = sm;
   const double* xbn = ys + S * B;
@@ -577,24 +585,29 @@ __global__ void __launch_bounds__(256, 4) solve_flow_kernel(FlowArgs a) {
     const Task* tasks = im.w ? a.bwd : a.fwd;
     if (im.z) {                                            // block task
       const Task tk = tasks[im.x];
+      // the factor rows first: they hide their latency behind the wait for the inputs
+      if (im.w) stage_backward<8>(a.s, tk, sm_f, threadIdx.x, blockDim.x, kStageConst);
+      else stage_forward<8>(a.s, tk, sm_f, false, threadIdx.x, blockDim.x, kStageConst);
       if (threadIdx.x == 0) s_ok = wait_deps(a, tk, im.w) ? 1 : 0;
       __syncthreads();
       if (!s_ok) return;
-      if (im.w) solve_backward_task(a.s, tk, sm_f);
-      else solve_forward_task(a.s, tk, sm_f);          // both end with __syncthreads
+      if (im.w) solve_backward_task(a.s, tk, sm_f, kStageData);
+      else solve_forward_task(a.s, tk, sm_f, kStageData);   // both end with __syncthreads
       if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd((im.w ? a.done_b : a.done_f) + tk.node, 1u);
       }
     } else if (warp < im.y) {                              // warp task
       const Task tk = tasks[im.x + warp];
+      double* wsm = sm_f + (size_t)warp * a.s.warp_doubles;
+      if (im.w) stage_backward<8>(a.s, tk, wsm, lane, 32, kStageConst);
+      else stage_forward<8>(a.s, tk, wsm, false, lane, 32, kStageConst);
       int ok = 1;
       if (lane == 0) ok = wait_deps(a, tk, im.w) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (ok) {                                            // else: the status stops the block at its next claim
-        double* wsm = sm_f + (size_t)warp * a.s.warp_doubles;
-        if (im.w) solve_backward_warp(a.s, tk, wsm, lane);
-        else solve_forward_warp(a.s, tk, wsm, lane);    // both end with __syncwarp
+        if (im.w) solve_backward_warp(a.s, tk, wsm, lane, kStageData);
+        else solve_forward_warp(a.s, tk, wsm, lane, kStageData);   // both end with __syncwarp
         if (lane == 0) {
           __threadfence();
           atomicAdd((im.w ? a.done_b : a.done_f) + tk.node, 1u);
@@ -1908,8 +1921,6 @@ int sbfwi_forward(sbfwi_model* md, int32_t n_shots, const int64_t* src_node, con
     c = std::min<int64_t>(c, K);
     if (md->kernel_terms == SBFWI_TERMS_FULL && md->lfe)
       return fail(SBFWI_EUNSUPPORTED, "the comparison method has no radial field for the full kernel's gradient term");
-    if (md->kernel_terms == SBFWI_TERMS_FULL && c != 0 && md->grad_mode != SBFWI_GRAD_EXACT)
-      return fail(SBFWI_EUNSUPPORTED, "the full Frechet kernel needs the stored forward field (ckpt_every = 0)");
     fs->ckpt_every = c;
     fs->state_doubles = sd;
     fs->tensor_core_path = f.tensor_core_path();
@@ -2000,7 +2011,8 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
   adj.values = values.as<double>(); adj.nodes = nodes.as<int64_t>();
   int rc = adj.init();
   if (rc) return rc;
-  if (!exact && md->kernel_terms == SBFWI_TERMS_FULL) {
+  const bool full = !exact && md->kernel_terms == SBFWI_TERMS_FULL;
+  if (full && c == 0) {
     if (!fs->store_u.p)
       return fail(SBFWI_ESTATE, "the forward pass kept no displacements: set the full kernel before the forward pass");
     adj.fwd_u = fs->store_u.as<double>();
@@ -2024,10 +2036,12 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
     if (rc) return rc;
     if (fwd.tensor_core_path() != fs->tensor_core_path || fwd.state_doubles() != fs->state_doubles)
       return fail(SBFWI_ESTATE, "the element kernel differs from the one that wrote the checkpoints");
+    // the window holds the recomputed velocities (the paper's kernel), plus the displacements
+    // for the full kernel's gradient term; the exact adjoint's displacements and accelerations
     DevBuf window, window_a;
-    const int64_t ss = exact ? np : fwd.store_stride();
+    const int64_t ss = (exact || full) ? np : fwd.store_stride();
     cudaError_t e = window.alloc(sizeof(double) * (size_t)c * ss * B);
-    if (e == cudaSuccess && exact) e = window_a.alloc(sizeof(double) * (size_t)c * ss * B);
+    if (e == cudaSuccess && (exact || full)) e = window_a.alloc(sizeof(double) * (size_t)c * ss * B);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(SBFWI_ENOMEM, "not enough device memory for one recompute window (" +
@@ -2044,6 +2058,7 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
         fwd.store_a = window_a.as<double>();
       } else {
         fwd.store = window.as<double>();
+        if (full) fwd.store_u = window_a.as<double>();
       }
       if (rc == SBFWI_OK) rc = fwd.run(a, b);
       if (exact) {
@@ -2051,6 +2066,7 @@ int sbfwi_adjoint_gradient(sbfwi_model* md, sbfwi_fwdstate* fs, const double* re
         if (rc == SBFWI_OK) rc = adj.run_exact(a, b);
       } else {
         adj.fwd = window.as<double>(); adj.fwd_k0 = a;
+        if (full) adj.fwd_u = window_a.as<double>();
         if (rc == SBFWI_OK) rc = adj.run(K - b, K - a);
       }
     }

@@ -61,9 +61,6 @@ def test_full_kernel_state_errors(lib):
         lib.adjoint_gradient(md, st, -tr)
     assert ei.value.code == lib.ESTATE
     with pytest.raises(lib.SbfwiError) as ei:
-        lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes, ckpt_every=5)
-    assert ei.value.code == lib.EUNSUPPORTED
-    with pytest.raises(lib.SbfwiError) as ei:
         lib.set_kernel_terms(md, 5)
     assert ei.value.code == lib.EINVAL
     lib.set_kernel_terms(md, lib.TERMS_VELOCITY)
@@ -97,3 +94,20 @@ def test_full_kernel_on_uneven_meshes(lib, p):
     tr, st = lib.forward(md, src, wav, rec)
     g = lib.adjoint_gradient(md, st, -tr)
     assert rel(g, go) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("element", ["tensor", "fp64"])
+def test_full_kernel_with_checkpoints_is_the_stored_field_kernel(lib, element):
+    """Checkpointed forward passes: the adjoint recomputes velocities and displacements window
+    by window; the full kernel's gradient equals the stored-field one bit for bit."""
+    w = tiny_workload(K=60)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    md = lib.Model(M, w.c, w.rho_true, w.dt)
+    lib.set_schedule(md, lib.ELEMENT_TENSOR if element == "tensor" else lib.ELEMENT_FP64)
+    lib.set_kernel_terms(md, lib.TERMS_FULL)
+    tr, st = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes)
+    g0 = lib.adjoint_gradient(md, st, -tr)
+    for c in (1, 7, 60, lib.CKPT_AUTO):
+        tr_c, st_c = lib.forward(md, w.src_nodes, w.wavelets, w.rec_nodes, ckpt_every=c)
+        assert np.array_equal(tr_c, tr)
+        assert np.array_equal(lib.adjoint_gradient(md, st_c, -tr), g0), c

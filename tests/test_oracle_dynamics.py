@@ -262,3 +262,24 @@ def test_sharp_high_contrast_is_unstable_for_the_radial_fd_scheme(tiny):
         mins.append(w2.real.min())
     assert mins[0] < -1e3
     assert mins[1] > -1e-6
+
+
+def test_a_tapered_edge_does_not_stabilise_the_1e3_contrast(tiny):
+    """Grading the flaw's edge does not rescue the configs' 1e-3 contrast: with the density
+    falling log-linearly from 1 to 1e-3 over one radius outside the flaw the pencil still
+    has negative omega^2, while 1e-2 with the same taper has none (sharp 1e-2 does)."""
+    import scipy.linalg as sla
+    w = tiny
+    X, Y = np.meshgrid((np.arange(64) + 0.5) / 64, (np.arange(64) + 0.5) / 64)
+    cx, cy = w.info["flaw"]["centre"]
+    r = np.hypot(X - cx, Y - cy)
+    s = np.clip((0.2 - r) / 0.1, 0.0, 1.0)            # 1 inside r <= 0.1, 0 beyond 0.2
+    mins = {}
+    for f in (1e-3, 1e-2):
+        rho = np.exp(np.log(f) * s)
+        m = fwi.build_model(w.mesh, w.n_r, 1.0, rho, w.dt, static=True)
+        fs = bruteforce.FullSystem(w.mesh, w.n_r, 1.0, m.rho_nodal, w.dt, static=True)
+        vals = sla.eigvals(fs.matrix.toarray(), fs.mass.toarray())
+        mins[f] = (-vals[np.isfinite(vals)]).real.min()
+    assert mins[1e-3] < -1e3
+    assert mins[1e-2] > -1e-6
