@@ -30,12 +30,22 @@ class FullSystem:
     def __init__(self, mesh, n_r, c, rho_nodal, dt, beta=0.25, gamma=0.5, xi0=1e-3, static=False):
         self.mesh = mesh
         self.n = n = n_r - 1
-        self.elements = sbfem.elements_from_mesh(mesh)
+        dim = getattr(mesh, "dim", 2)        # 3: hexahedral S-elements (oracle.sbfem3d)
+        if dim == 3:
+            from . import sbfem3d
+            self.elements = sbfem3d.elements_from_mesh3d(mesh)
+            coefficients = lambda el, r: sbfem3d.coefficient_matrices3d(el, mesh.node_xyz, mesh.p, c, r)
+        else:
+            self.elements = sbfem.elements_from_mesh(mesh)
+            coefficients = lambda el, r: sbfem.coefficient_matrices(el, mesh.node_xy, mesh.p, c, r)
         self.nb = nb = self.elements[0].dofs.size
         xi = sbfem.radial_grid(n, xi0, sbfem.XP)
         self.xi = np.asarray(xi, dtype=np.float64)
         self.dt, self.beta, self.gamma = dt, beta, gamma
-        pts, int_ptr = fwi.nodal_points(mesh, self.elements, xi)
+        if dim == 3:
+            pts, int_ptr = sbfem3d.nodal_points3d(mesh, self.elements, xi)
+        else:
+            pts, int_ptr = fwi.nodal_points(mesh, self.elements, xi)
         self.int_ptr = int_ptr
         n_int = int(int_ptr[-1])
         E = len(self.elements)
@@ -51,10 +61,10 @@ class FullSystem:
             r = np.empty((n + 1, nb), dtype=sbfem.XP)
             r[:n] = rho_nodal[int_ptr[e]:int_ptr[e + 1]].reshape(n, nb)
             r[n] = rho_nodal[n_int + el.dofs]
-            mats = sbfem.coefficient_matrices(el, mesh.node_xy, mesh.p, c, r)
+            mats = coefficients(el, r)
             for k in range(4):
                 Es[k][e] = mats[k]
-        sysall = sbfem.element_system(*Es, xi, dt, beta, static=static)
+        sysall = sbfem.element_system(*Es, xi, dt, beta, static=static, dim=dim)
         # blocks are kept in extended precision; float64 copies feed the factorisation
         self.theta, self.phi, self.psi, self.M0 = sysall.theta, sysall.phi, sysall.psi, sysall.M0
         self.M0_64 = np.asarray(sysall.M0, dtype=np.float64)

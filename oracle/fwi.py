@@ -408,3 +408,104 @@ def gradient_to_grid(model: Model, g_nodal, gx, gy, lx=None, ly=None):
     lx = model.mesh.lx if lx is None else lx
     ly = model.mesh.ly if ly is None else ly
     return points_to_grid(g_nodal, model.points, gx, gy, lx, ly)
+
+
+# ----------------------------------------------------------------------------
+# Three-dimensional meshes (``oracle.sbfem3d``)
+# ----------------------------------------------------------------------------
+
+def trilinear_weights(points, gx, gy, gz, lx, ly, lz):
+    """Cells and weights of trilinear interpolation of a cell-centred grid rho[gz, gy, gx]
+    (value (ix, iy, iz) at ((ix+1/2) lx/gx, (iy+1/2) ly/gy, (iz+1/2) lz/gz)), clamped at
+    the edges like ``bilinear_weights``.  Returns (idx (m, 8), w (m, 8)), flat indices
+    (iz gy + iy) gx + ix, corner c = cx + 2 cy + 4 cz."""
+    points = np.asarray(points)
+    points = points.astype(np.result_type(points.dtype, np.float64))
+    ft = points.dtype.type
+    ii, tt = [], []
+    for d, (g, L) in enumerate(((gx, lx), (gy, ly), (gz, lz))):
+        f = points[:, d] * ft(g) / ft(L) - ft(0.5)
+        i = np.floor(f).astype(np.int64)
+        t = f - i
+        lo = i < 0
+        i[lo], t[lo] = 0, 0.0
+        hi = i > g - 2
+        i[hi], t[hi] = g - 2, 1.0
+        ii.append(i)
+        tt.append(t)
+    idx, w = [], []
+    for cz in range(2):
+        for cy in range(2):
+            for cx in range(2):
+                idx.append(((ii[2] + cz) * gy + ii[1] + cy) * gx + ii[0] + cx)
+                w.append((tt[0] if cx else 1 - tt[0]) * (tt[1] if cy else 1 - tt[1]) * (tt[2] if cz else 1 - tt[2]))
+    return np.stack(idx, axis=1), np.stack(w, axis=1)
+
+
+def grid_to_points3d(rho_grid, points, lx, ly, lz):
+    gz, gy, gx = rho_grid.shape
+    idx, w = trilinear_weights(points, gx, gy, gz, lx, ly, lz)
+    return np.sum(rho_grid.ravel()[idx].astype(w.dtype) * w, axis=1)
+
+
+def points_to_grid3d(g_points, points, gx, gy, gz, lx, ly, lz):
+    """Adjoint (transpose) of ``grid_to_points3d``, in float64."""
+    idx, w = trilinear_weights(points, gx, gy, gz, lx, ly, lz)
+    out = np.zeros(gx * gy * gz)
+    np.add.at(out, idx.ravel(), (w.astype(np.float64) * np.asarray(g_points, dtype=np.float64)[:, None]).ravel())
+    return out.reshape(gz, gy, gx)
+
+
+def build_model3d(mesh, n_r, c, rho, dt, beta=0.25, gamma=0.5, xi0=1e-3, rho_kind="grid", static=False) -> Model:
+    """``build_model`` for a mesh of 3-D S-elements (``sbfwi_inputs.mesh3d``): nodal
+    densities (trilinear map of a rho[gz, gy, gx] grid, or nodal), the 3-D coefficient
+    matrices, the blocks of the 3-D radial equation, condensation and the global matrix.
+    The time loop, misfit and velocity-kernel adjoint of this module apply unchanged."""
+    from . import sbfem3d
+    XP = sbfem.XP
+    n = n_r - 1
+    if n < 2:
+        raise ValueError("need at least 3 radial points")
+    elements = sbfem3d.elements_from_mesh3d(mesh)
+    nb = elements[0].dofs.size
+    if any(el.dofs.size != nb for el in elements):
+        raise ValueError("this oracle expects one boundary-node count for all elements")
+    xi = sbfem.radial_grid(n, xi0, XP)
+    points, int_ptr = sbfem3d.nodal_points3d(mesh, elements, xi)
+    if rho_kind == "grid":
+        rho_nodal = grid_to_points3d(np.asarray(rho, dtype=np.float64), points, mesh.lx, mesh.ly, mesh.lz)
+    elif rho_kind == "nodal":
+        rho_nodal = np.asarray(rho).astype(XP)
+        if rho_nodal.shape != (points.shape[0],):
+            raise ValueError("nodal density has the wrong length")
+    else:
+        raise ValueError(rho_kind)
+    if np.any(rho_nodal <= 0):
+        raise ValueError("density must be positive")
+    n_int = int(int_ptr[-1])
+    E = len(elements)
+    Es = [np.zeros((E, n + 1, nb, nb), dtype=XP) for _ in range(4)]
+    for e, el in enumerate(elements):
+        r = np.empty((n + 1, nb), dtype=XP)
+        r[:n] = rho_nodal[int_ptr[e]:int_ptr[e + 1]].reshape(n, nb)
+        r[n] = rho_nodal[n_int + el.dofs]
+        mats = sbfem3d.coefficient_matrices3d(el, mesh.node_xyz, mesh.p, c, r)
+        for k in range(4):
+            Es[k][e] = mats[k]
+    sys_ = sbfem.element_system(*Es, xi, dt, beta, static=static, dim=3)
+    cd = sbfem.condense(sys_)
+    f64 = lambda a: np.asarray(a, dtype=np.float64)
+    dofs = np.stack([el.dofs for el in elements])
+    S = f64(cd.S)
+    rr = np.repeat(dofs, nb, axis=1).ravel()
+    cc = np.tile(dofs, (1, nb)).ravel()
+    N = mesh.n_nodes
+    A = sp.coo_matrix((S.ravel(), (rr, cc)), shape=(N, N)).tocsc()
+    lu = spla.splu(A)
+    return Model(mesh, elements, n, f64(xi), c, dt, beta, gamma, int_ptr, f64(points), f64(rho_nodal),
+                 dofs, f64(sys_.M0), f64(cd.rho), f64(cd.psi_t), f64(cd.phi_t_inv), f64(cd.W), S, A, lu)
+
+
+def gradient_to_grid3d(model: Model, g_nodal, gx, gy, gz):
+    m = model.mesh
+    return points_to_grid3d(g_nodal, model.points, gx, gy, gz, m.lx, m.ly, m.lz)

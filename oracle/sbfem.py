@@ -271,7 +271,7 @@ class ElementSystem:
     M0: np.ndarray          # (E, n+1, n_b, n_b) at the radial points
 
 
-def element_system(E0, E1, E2, M0, xi, dt, beta, static=False) -> ElementSystem:
+def element_system(E0, E1, E2, M0, xi, dt, beta, static=False, dim=2) -> ElementSystem:
     """Blocks theta_i, phi_i, psi_i of the discretised radial ODE (Section 3.3).
 
     ``E0..M0`` have shape (E, n+1, n_b, n_b).  For i = 0..n (Eq. (discretized) with
@@ -280,6 +280,8 @@ def element_system(E0, E1, E2, M0, xi, dt, beta, static=False) -> ElementSystem:
       theta_i = xi_i^2 E0 / h^2 - xi_i D_i / (2h)
       phi_i   = -2 xi_i^2 E0 / h^2 - E2 + xi_i (dE1/dxi)^T - xi_i^2 M0 / (beta dt^2)
       psi_i   = xi_i^2 E0 / h^2 + xi_i D_i / (2h)
+    ``dim=3``: the radial equation of a 3-D element (``oracle.sbfem3d``), D_i with 2 E0
+    instead of E0 and phi_i with + E1^T; the boundary-condition rows are unchanged.
     Boundary-condition rows (internal source vector q = xi E0 u' + E1^T u, Eq. (internal)):
       row -1 at xi_0: theta = -xi_0 E0(xi_0)/(2h), phi = E1(xi_0)^T, psi = xi_0 E0(xi_0)/(2h)
       row n+1 at xi_n: theta = -xi_n E0(xi_n)/(2h), phi = E1(xi_n)^T, psi = xi_n E0(xi_n)/(2h)
@@ -296,9 +298,13 @@ def element_system(E0, E1, E2, M0, xi, dt, beta, static=False) -> ElementSystem:
     psi = np.zeros_like(theta)
     mass = dtype(0) if static else 1 / (dtype(beta) * dtype(dt) * dtype(dt))
     x = xi[None, :, None, None]
-    D = E0 + _T(E1) - E1 + x * dE0
+    if dim not in (2, 3):
+        raise ValueError("dim must be 2 or 3")
+    D = (dim - 1) * E0 + _T(E1) - E1 + x * dE0
     theta[:, 1:n + 2] = x * x * E0 / (h * h) - x * D / (2 * h)
     phi[:, 1:n + 2] = -2 * x * x * E0 / (h * h) - E2 + x * _T(dE1) - mass * x * x * M0
+    if dim == 3:
+        phi[:, 1:n + 2] += _T(E1)
     psi[:, 1:n + 2] = x * x * E0 / (h * h) + x * D / (2 * h)
     theta[:, 0] = -xi[0] * E0[:, 0] / (2 * h)
     phi[:, 0] = _T(E1[:, 0])
