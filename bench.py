@@ -669,6 +669,66 @@ def run_paper(args, rank, world):
                        "rows": rows, "l2": "small workloads: latency-bound, inputs fit L2"}}
 
 
+def run_solid(args, rank, world):
+    """3-D hexahedral S-elements (the paper's Section 3 preamble: 3-D needs only minor
+    changes): per step, set-up + forward + misfit + adjoint + gradient of all shots on the
+    3-D recipe, observed data from the flawed model."""
+    import torch
+    from paper_2501_06748_gb300 import build
+    build.build()
+    from paper_2501_06748_gb300 import sbfwi as lib
+    from sbfwi_inputs import solid_workload
+    if rank != 0:
+        return None
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = solid_workload(K=args.time_steps or 500, p=args.solid_p)
+    M = lib.Mesh.from_inputs(w.mesh, w.n_r)
+    wav = torch.tensor(w.wavelets, device=dev)
+    mt = lib.Model(M, w.c, torch.tensor(w.rho_true, device=dev), w.dt)
+    obs, _ = lib.forward(mt, w.src_nodes, wav, w.rec_nodes, keep=False)
+    del mt
+    rho0 = torch.tensor(w.rho_start, device=dev)
+
+    def step():
+        md = lib.Model(M, w.c, rho0, w.dt)
+        tr, st = lib.forward(md, w.src_nodes, wav, w.rec_nodes)
+        E, res = lib.misfit(tr, obs, w.dt)
+        return E, lib.adjoint_gradient(md, st, res)
+
+    for _ in range(max(3, args.warmup)):
+        E, g = step()
+    clocks = ClockSampler(os.path.join(args.clock_log, "clocks_solid.csv"))
+    clocks.start()
+    lib.profile_read(reset=True)
+    lib.profile_enable(True)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        E, g = step()
+    t1.record()
+    torch.cuda.synchronize()
+    lib.profile_enable(False)
+    prof = lib.profile_read(reset=True)
+    clk = clocks.stop(0)
+    ms = t0.elapsed_time(t1) / args.steps
+    units = w.mesh.n_elem * w.n_r * w.K * w.n_shots
+    phases = {k: v["ms"] / args.steps for k, v in prof.items()}
+    return {"metric": "3-D S-elements: element-radial-node-steps/s fwd+adj+grad", "value": units / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"solid: unit cube in {w.mesh.nx}^3 hexahedral S-elements, faces of order "
+                                   f"{w.mesh.p} (n_b = {M.n_b}), N_r = {w.n_r}, {w.n_shots} Ricker shots on the top face, "
+                                   f"{len(w.rec_nodes)} receivers, {w.K} Newmark steps, {w.gx}^3 density grid with one "
+                                   "spherical flaw; per step: set-up + forward + misfit + adjoint + gradient",
+                       "elements": w.mesh.n_elem, "global_nodes": w.mesh.n_nodes, "n_b": M.n_b, "N_r": w.n_r,
+                       "shots": w.n_shots, "time_steps": w.K, "tree_levels": M.tree_levels,
+                       "factor_entries": M.factor_entries, "misfit": E,
+                       "l2": "inputs larger than L2 (forward velocity store per pass)"},
+            "phases_ms_per_step": phases, "clocks": clk}
+
+
 def run_batching(args, rank, world):
     """The batching recipe: 64 shots over three seeded quadtree meshes (p = 2, 3, 5 with
     N_r = 16, 32, 48; elements with 4 to 8 line elements, so n_b varies inside each mesh
@@ -865,13 +925,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--requests", type=int, default=64, help="serving config: number of requests")
-    ap.add_argument("--config", choices=["size", "diff", "serving", "paper", "batching", "diffcheck"], default="size",
+    ap.add_argument("--config", choices=["size", "diff", "serving", "paper", "batching", "diffcheck", "solid"],
+                    default="size",
                     help="size: 64x64 elements, 8 shots, 2000 steps, stored forward field (the default); "
                          "diff: 128x128 elements, 16 shots, 8000 steps, checkpointed adjoint; "
                          "serving: forward-modelling requests with continuous batching; "
                          "paper: the paper's plate recipe at its Table 1 element counts; "
                          "batching: 64 shots over 3 quadtree meshes with uneven elements; "
-                         "diffcheck: the diff problem with an FD check of the exact gradient and L-BFGS")
+                         "diffcheck: the diff problem with an FD check of the exact gradient and L-BFGS; "
+                         "solid: 3-D hexahedral S-elements")
+    ap.add_argument("--solid-p", type=int, default=2, help="solid config: face order (1 or 2)")
     ap.add_argument("--fd-directions", type=int, default=16, help="diffcheck config: random directions")
     ap.add_argument("--lbfgs-iters", type=int, default=20, help="diffcheck config: L-BFGS iterations")
     ap.add_argument("--clock-log", default=tempfile.gettempdir(),
@@ -900,6 +963,8 @@ def main():
         out = run_batching(args, rank, world)
     elif args.config == "diffcheck":
         out = run_diffcheck(args, rank, world)
+    elif args.config == "solid":
+        out = run_solid(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if out is not None:

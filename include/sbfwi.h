@@ -103,6 +103,45 @@ int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes,
                      const int64_t* elem_ptr, const int64_t* line_nodes, int64_t n_lines,
                      const double* centre_xy, int64_t n_elem, int32_t p, int32_t n_r, double xi0);
 
+/*
+ * sbfwi_build_mesh3d -- a mesh of 3-D scaled-boundary elements: the paper's Section 3
+ * preamble says a three-dimensional formulation needs only minor changes; this build
+ * carries it out for a boundary surface.  Each element is a star-convex polyhedron
+ * whose boundary is a set of quadrilateral faces of Lagrange order p, with scaling
+ * centre x0 and the map x = x0 + xi (x_b(eta, zeta) - x0).  The coefficient matrices
+ * are the surface integrals E0 = int rho c^2 N^T (b1.b1) N det J_b, E1 = int rho c^2
+ * B2^T b1 N det J_b, E2 = int rho c^2 B2^T B2 det J_b, M0 = int rho N^T N det J_b with
+ * B2 = b2 N_eta + b3 N_zeta and b1, b2, b3 the columns of the inverse boundary Jacobian
+ * (rows x_b - x0, x_b,eta, x_b,zeta); the radial equation is
+ *   xi^2 E0 u'' + xi (2 E0 + E1^T - E1 + xi E0') u' + (E1^T - E2 + xi E1^T') u - xi^2 M0 u_tt = 0
+ * (the 2-D equation with 2 E0 for E0 in the u' coefficient and + E1^T in the u
+ * coefficient), discretised, condensed and stepped exactly as in 2-D.
+ *
+ *   node_xyz    [n_nodes][3]         node coordinates
+ *   elem_ptr    [n_elem+1]           element e owns faces elem_ptr[e]..elem_ptr[e+1]-1
+ *   face_nodes  [n_faces][(p+1)^2]   global node ids of each face in tensor order: node
+ *                                    (a, b) at a + (p+1) b, a along the face's first
+ *                                    direction eta, b along zeta, with eta x zeta
+ *                                    pointing out of the element
+ *   centre_xyz  [n_elem][3]          scaling centres
+ *   p           face order, 1..4 (nodes equally spaced on the bilinear patch of the
+ *               face's corners; planar faces give exact quadrature)
+ *   n_r, xi0    as sbfwi_build_mesh
+ *
+ * Checks: ids in range, at least four faces per element, nodes on the bilinear patch of
+ * the corners, det J_b > 0 at the corners and middle of every face, every face edge
+ * shared by exactly two faces of the element (a closed surface).  Returns
+ * SBFWI_EINVAL with the offending element in the message, SBFWI_EUNSUPPORTED beyond 40
+ * boundary nodes per element (a hexahedron has 8 at p = 1 and 26 at p = 2).  The nodal
+ * points and their order are those of the 2-D meshes.  A 3-D mesh takes its model from
+ * sbfwi_set_model3d; the comparison method, the full kernel's gradient term and the
+ * exact adjoint are not built for it (SBFWI_EINVAL / SBFWI_EUNSUPPORTED).  All arrays
+ * are host memory, copied.
+ */
+int sbfwi_build_mesh3d(sbfwi_mesh** out, const double* node_xyz, int64_t n_nodes,
+                       const int64_t* elem_ptr, const int64_t* face_nodes, int64_t n_faces,
+                       const double* centre_xyz, int64_t n_elem, int32_t p, int32_t n_r, double xi0);
+
 /* info[0..7] = n_elem, n_nodes, n_b (the largest), N_r, n_nodal (= n_int + n_nodes),
  * n_int (= (N_r - 1) x the sum of n_b(e)), levels of the global elimination tree,
  * nonzeros kept by the global factors. */
@@ -135,6 +174,18 @@ int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const d
                     int rho_kind, int64_t gx, int64_t gy, double lx, double ly,
                     double dt, double beta, double gamma, int mem, void* stream);
 void sbfwi_destroy_model(sbfwi_model* model);
+
+/*
+ * sbfwi_set_model3d -- sbfwi_set_model for a mesh from sbfwi_build_mesh3d.
+ *   rho  SBFWI_RHO_GRID:  [gz][gy][gx] cell-centred values on [0,lx]x[0,ly]x[0,lz],
+ *                         mapped to nodal points by trilinear interpolation (clamped at
+ *                         the edges); the gradient comes back on the same grid;
+ *        SBFWI_RHO_NODAL: [n_nodal] values on the nodal points.
+ * Other arguments and errors as sbfwi_set_model; SBFWI_EINVAL for a 2-D mesh.
+ */
+int sbfwi_set_model3d(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho,
+                      int rho_kind, int64_t gx, int64_t gy, int64_t gz, double lx, double ly, double lz,
+                      double dt, double beta, double gamma, int mem, void* stream);
 
 /*
  * sbfwi_set_model_lfe -- the same set-up for the paper's comparison method, the
@@ -427,6 +478,23 @@ int sbfwi_profile_read(double* ms, int64_t* intervals, int64_t* launches, int re
  * device.
  */
 int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_t* steps, int reset);
+
+/*
+ * Per-phase tracing of the dataflow global solve (the default schedule; a diagnostic
+ * of this implementation, the paper does not specify the solver).  While profiling is
+ * on, every such launch stamps the global timer when a block starts, when it claims an
+ * item, when the item's inputs are ready and when the item has finished (the last 64
+ * solves are kept).  A phase is one tree level of one pass: phases 0..L-1 are the
+ * forward levels (leaves -> root), L..2L-1 the backward levels (root -> leaves).  Fills
+ * us[min(cap, 8L)] with, per phase: [0, 2L) the time from the launch's first block
+ * start to the phase's last item finishing (the phase's completion time), [2L, 4L)
+ * the mean execution time of an item (inputs ready -> finished), [4L, 6L) the mean
+ * time an item waited for its inputs after being claimed, [6L, 8L) items per solve;
+ * microseconds, averaged over the recorded solves.  *n_slots = 8L (0 if nothing was
+ * recorded), *steps = solves recorded; reset != 0 starts a new record.  Synchronises
+ * the current device.  SBFWI_ESTATE if the trace lives on another device.
+ */
+int sbfwi_profile_solve_flow(double* us, int32_t cap, int32_t* n_slots, int64_t* steps, int reset);
 
 /*
  * Failure-detection self-test (no counterpart in the paper; a guard of this

@@ -89,7 +89,7 @@ struct Task {               // a row range of one tree node, with the node's fie
   int32_t ksplit;           // lanes that share one output's dot product (1, 2, 4 or 8)
   int32_t s, b;             // separator and boundary sizes of the node
   int32_t leaf;             // 1 if the node is an element (front values come from f_hat)
-  int32_t pad;
+  int32_t pad;              // the node's height (the dataflow trace's phase)
   int64_t sep_off, bnd_off, map_off, X_off;
 };
 
@@ -122,9 +122,10 @@ struct MeshDevice {
   DevBuf F, U;                       // factorisation workspaces
   // bilinear map of one fine grid: base cell and clamping of every nodal point, and
   // the transpose as CSR grid cell -> (point*4 + corner) sorted by point
+  // (3-D meshes: trilinear, point*8 + corner)
   bool grid_ready = false;
-  int64_t gx = 0, gy = 0;
-  double lx = 0, ly = 0;
+  int64_t gx = 0, gy = 0, gz = 1;
+  double lx = 0, ly = 0, lz = 0;
   DevBuf cell, clamp, cell_ptr, cell_list;
   DevBuf nbe, lptr, api_map;         // n_b per element, first line per element, Mesh::api_to_lib
   // nodal gradient operator (CSR, rows 2q and 2q+1: x and y components at nodal point q)
@@ -142,15 +143,20 @@ constexpr int kMaxBoundaryNodes = 40;   // largest n_b of an element
 // padding, mapped to the extra global node n_nodes, whose state stays zero, and their
 // rows and columns of every element operator are zero, so they stay zero through the
 // time loop and never reach the global system.
+// A 3-D mesh (dim = 3) has the same arrays with surface elements in place of line
+// elements: node_xy and centre_xy hold three coordinates per point, line_nodes and
+// line_local hold (p+1)^2 nodes per quadrilateral face in tensor order (fpp = nodes per
+// boundary element: p+1 in 2-D, (p+1)^2 in 3-D), L counts faces.
 struct Mesh {
   int64_t n_elem = 0, n_nodes = 0, n_lines = 0;
   int p = 0, n_r = 0, nb = 0, n = 0, L = 0;   // n = N_r - 1 intervals; nb, L: largest n_b, lines per element
+  int dim = 2, fpp = 0;
   double xi0 = 1e-3;
   std::vector<double> node_xy, centre_xy;
   std::vector<int64_t> elem_ptr, line_nodes;
   std::vector<int32_t> nbe;         // [n_elem] n_b of each element
   std::vector<int32_t> dofs;        // [n_elem][nb] global node of each local dof (n_nodes for padding)
-  std::vector<int32_t> line_local;  // [n_lines][p+1] local dof of each line position
+  std::vector<int32_t> line_local;  // [n_lines][fpp] local dof of each line (face) position
   bool uneven = false;              // some element has fewer than nb boundary nodes
   Tree tree;
   // nodal points in the library's layout: interior (e, i, j) at (e n + i) nb + j for
@@ -204,8 +210,8 @@ struct Model {
   double c = 1, dt = 0, beta = 0.25, gamma = 0.5;
   double a0 = 0, a1 = 0, a2 = 0, c1 = 0, c2 = 0;  // Newmark constants
   int rho_kind = SBFWI_RHO_GRID;
-  int64_t gx = 0, gy = 0;
-  double lx = 1, ly = 1;
+  int64_t gx = 0, gy = 0, gz = 1;
+  double lx = 1, ly = 1, lz = 1;
   // element operators, FP64: per element and radial point i = 0..n-1: P_i, Q_i, H_i; then R, T
   DevBuf mats;      // [E][n][3][nb][nb]
   DevBuf rt;        // [E][2][nb][nb]
@@ -220,7 +226,7 @@ struct Model {
   const int32_t* solve_sep = nullptr;
   const int32_t* solve_bnd = nullptr;
   size_t solve_bytes = 0;
-  DevBuf pts_hi, pts_lo; // [n_nodal][2] dd location of every nodal point
+  DevBuf pts_hi, pts_lo; // [n_nodal][dim] dd location of every nodal point
   // the same operators split into FP16 digits for the tensor-core element kernel
   DevBuf tc_frag, tc_frag_rt, tc_exps, tc_exps_rt;
   bool tc_ready = false;

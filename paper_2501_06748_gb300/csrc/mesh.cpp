@@ -50,18 +50,23 @@ struct Builder {
   int make(int32_t a, int32_t b) {
     int32_t left = -1, right = -1;
     if (b - a > 1) {
-      double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-      for (int32_t k = a; k < b; ++k) {
-        double x = m.centre_xy[2 * order[k]], y = m.centre_xy[2 * order[k] + 1];
-        xmin = std::min(xmin, x); xmax = std::max(xmax, x);
-        ymin = std::min(ymin, y); ymax = std::max(ymax, y);
-      }
-      int ax = (xmax - xmin >= ymax - ymin) ? 0 : 1;
+      const int D = m.dim;
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int32_t k = a; k < b; ++k)
+        for (int d = 0; d < D; ++d) {
+          const double x = m.centre_xy[(size_t)D * order[k] + d];
+          lo[d] = std::min(lo[d], x);
+          hi[d] = std::max(hi[d], x);
+        }
+      int ax = 0;                        // the longest extent (the first of equal ones)
+      for (int d = 1; d < D; ++d)
+        if (hi[d] - lo[d] > hi[ax] - lo[ax]) ax = d;
       std::stable_sort(order.begin() + a, order.begin() + b, [&](int32_t e1, int32_t e2) {
-        double p1 = m.centre_xy[2 * e1 + ax], p2 = m.centre_xy[2 * e2 + ax];
-        if (p1 != p2) return p1 < p2;
-        double q1 = m.centre_xy[2 * e1 + 1 - ax], q2 = m.centre_xy[2 * e2 + 1 - ax];
-        if (q1 != q2) return q1 < q2;
+        for (int k = 0; k < D; ++k) {    // the split axis first, then the others in order
+          const int d = k == 0 ? ax : (k <= ax ? k - 1 : k);
+          const double p1 = m.centre_xy[(size_t)D * e1 + d], p2 = m.centre_xy[(size_t)D * e2 + d];
+          if (p1 != p2) return p1 < p2;
+        }
         return e1 < e2;
       });
       int32_t mid = a + (b - a) / 2;
@@ -273,6 +278,37 @@ Profiler& profiler() {
 }
 }  // namespace sbfwi
 
+// the padded dof table, nodal-point layouts and the elimination tree of a validated mesh
+static int finish_mesh(Mesh& mm) {
+  Mesh* m = &mm;
+  const int64_t n_elem = m->n_elem, n_nodes = m->n_nodes;
+  const int nb_max = m->nb;
+  // padded dof table: padding points at the extra zero node n_nodes
+  {
+    std::vector<int32_t> padded((size_t)n_elem * nb_max, (int32_t)n_nodes);
+    int64_t k = 0;
+    for (int64_t e = 0; e < n_elem; ++e)
+      for (int j = 0; j < m->nbe[e]; ++j) padded[(size_t)e * nb_max + j] = m->dofs[k++];
+    m->dofs.swap(padded);
+  }
+  m->n_int = m->n_elem * (int64_t)m->n * m->nb;
+  m->n_nodal = m->n_int + m->n_nodes;
+  m->n_int_api = 0;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    m->n_int_api += (int64_t)m->n * m->nbe[e];
+    if (m->nbe[e] != m->nb) m->uneven = true;
+  }
+  m->n_nodal_api = m->n_int_api + m->n_nodes;
+  if (m->uneven) {
+    m->api_to_lib.reserve(m->n_nodal_api);
+    for (int64_t e = 0; e < n_elem; ++e)
+      for (int i = 0; i < m->n; ++i)
+        for (int j = 0; j < m->nbe[e]; ++j) m->api_to_lib.push_back((e * m->n + i) * m->nb + j);
+    for (int64_t g = 0; g < n_nodes; ++g) m->api_to_lib.push_back(m->n_int + g);
+  }
+  return build_tree(*m);
+}
+
 extern "C" {
 
 int sbfwi_profile_enable(int on) {
@@ -320,6 +356,54 @@ int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_
   return SBFWI_OK;
 }
 
+int sbfwi_profile_solve_flow(double* us, int32_t cap, int32_t* n_slots, int64_t* steps, int reset) {
+  Profiler& p = profiler();
+  const int phases = p.flow_acc ? (p.flow_stride - 1) / 4 : 0;
+  if (n_slots) *n_slots = 4 * phases;
+  if (steps) *steps = p.flow_steps;
+  if (!p.flow_acc) return SBFWI_OK;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != p.flow_device) return fail(SBFWI_ESTATE, "the solve trace was recorded on another device");
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  const int rows = (int)std::min<int64_t>(p.flow_steps, Profiler::kFlowRows);
+  std::vector<unsigned long long> acc((size_t)p.flow_stride * std::max(rows, 1));
+  if (rows > 0) {
+    e = cudaMemcpy(acc.data(), p.flow_acc, sizeof(unsigned long long) * p.flow_stride * rows, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read solve trace");
+  }
+  // device phase index: forward level l -> l, backward level l -> L + l; reported in the
+  // order the phases run: forward 0..L-1, then backward L-1..0
+  const int L = phases / 2;
+  std::vector<double> out(4 * (size_t)phases, 0.0);
+  for (int q = 0; q < phases; ++q) {
+    const int ph = q < L ? q : L + (phases - 1 - q);
+    double done = 0, exec = 0, wait = 0, items = 0;
+    int solves = 0;
+    for (int r = 0; r < rows; ++r) {
+      const unsigned long long* row = acc.data() + (size_t)r * p.flow_stride;
+      const unsigned long long* f = row + 1 + 4 * ph;
+      if (f[3] == 0) continue;
+      done += (double)(f[0] - row[0]);
+      exec += (double)f[1];
+      wait += (double)f[2];
+      items += (double)f[3];
+      ++solves;
+    }
+    if (solves == 0) continue;
+    out[q] = done / solves / 1e3;
+    out[phases + q] = exec / items / 1e3;
+    out[2 * phases + q] = wait / items / 1e3;
+    out[3 * phases + q] = items / solves;
+  }
+  if (us)
+    for (int k = 0; k < std::min<int>(cap, 4 * phases); ++k) us[k] = out[k];
+  if (reset) p.flow_steps = 0;
+  return SBFWI_OK;
+}
+
 int sbfwi_release_cache(void) {
   store_cache_clear();
   return SBFWI_OK;
@@ -343,6 +427,7 @@ int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes, c
   auto m = new sbfwi_mesh();
   m->n_elem = n_elem; m->n_nodes = n_nodes; m->n_lines = n_lines;
   m->p = p; m->n_r = n_r; m->n = n_r - 1; m->xi0 = xi0;
+  m->dim = 2; m->fpp = p + 1;
   m->node_xy.assign(node_xy, node_xy + 2 * n_nodes);
   m->centre_xy.assign(centre_xy, centre_xy + 2 * n_elem);
   m->elem_ptr.assign(elem_ptr, elem_ptr + n_elem + 1);
@@ -392,30 +477,104 @@ int sbfwi_build_mesh(sbfwi_mesh** out, const double* node_xy, int64_t n_nodes, c
   }
   m->nb = nb_max;
   m->L = L_max;
-  // padded dof table: padding points at the extra zero node n_nodes
-  {
-    std::vector<int32_t> padded((size_t)n_elem * nb_max, (int32_t)n_nodes);
-    int64_t k = 0;
-    for (int64_t e = 0; e < n_elem; ++e)
-      for (int j = 0; j < m->nbe[e]; ++j) padded[(size_t)e * nb_max + j] = m->dofs[k++];
-    m->dofs.swap(padded);
-  }
-  m->n_int = m->n_elem * (int64_t)m->n * m->nb;
-  m->n_nodal = m->n_int + m->n_nodes;
-  m->n_int_api = 0;
+  int rc = finish_mesh(*m);
+  if (rc != SBFWI_OK) { delete m; return rc; }
+  *out = m;
+  return SBFWI_OK;
+}
+
+int sbfwi_build_mesh3d(sbfwi_mesh** out, const double* node_xyz, int64_t n_nodes, const int64_t* elem_ptr,
+                       const int64_t* face_nodes, int64_t n_faces, const double* centre_xyz, int64_t n_elem,
+                       int32_t p, int32_t n_r, double xi0) {
+  if (!out) return fail(SBFWI_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!node_xyz || !elem_ptr || !face_nodes || !centre_xyz) return fail(SBFWI_EINVAL, "NULL array");
+  if (n_nodes < 1 || n_elem < 1 || n_faces < 1) return fail(SBFWI_EINVAL, "empty mesh");
+  if (n_nodes > INT32_MAX / 2 || n_elem > INT32_MAX / 2) return fail(SBFWI_EINVAL, "mesh too large");
+  if (p < 1 || p > 4) return fail(SBFWI_EINVAL, "face order p must be in 1..4");
+  if (n_r < 3) return fail(SBFWI_EINVAL, "need at least 3 radial points");
+  if (!(xi0 > 0.0 && xi0 < 1.0)) return fail(SBFWI_EINVAL, "xi0 must be in (0, 1)");
+  if (elem_ptr[0] != 0 || elem_ptr[n_elem] != n_faces) return fail(SBFWI_EINVAL, "elem_ptr must start at 0 and end at n_faces");
+  const int pp = p + 1, fpp = pp * pp;
+  auto m = new sbfwi_mesh();
+  m->n_elem = n_elem; m->n_nodes = n_nodes; m->n_lines = n_faces;
+  m->p = p; m->n_r = n_r; m->n = n_r - 1; m->xi0 = xi0;
+  m->dim = 3; m->fpp = fpp;
+  m->node_xy.assign(node_xyz, node_xyz + 3 * n_nodes);
+  m->centre_xy.assign(centre_xyz, centre_xyz + 3 * n_elem);
+  m->elem_ptr.assign(elem_ptr, elem_ptr + n_elem + 1);
+  m->line_nodes.assign(face_nodes, face_nodes + n_faces * fpp);
+  auto bad = [&](int code, const std::string& msg) { delete m; return fail(code, msg); };
+  for (int64_t k = 0; k < n_faces * fpp; ++k)
+    if (face_nodes[k] < 0 || face_nodes[k] >= n_nodes) return bad(SBFWI_EINVAL, "face node id out of range");
+  auto X = [&](int64_t g, int d) { return node_xyz[3 * g + d]; };
+  int nb_max = 0, L_max = 0;
   for (int64_t e = 0; e < n_elem; ++e) {
-    m->n_int_api += (int64_t)m->n * m->nbe[e];
-    if (m->nbe[e] != m->nb) m->uneven = true;
+    const int64_t f0 = elem_ptr[e], f1 = elem_ptr[e + 1];
+    const std::string tag = "element " + std::to_string(e) + ": ";
+    if (f1 - f0 < 4) return bad(SBFWI_EINVAL, tag + "needs at least four faces");
+    const double* c = centre_xyz + 3 * e;
+    std::vector<int32_t> order;
+    std::map<std::pair<int64_t, int64_t>, int> edges;
+    for (int64_t f = f0; f < f1; ++f) {
+      const int64_t* fn = face_nodes + f * fpp;
+      // corners (a, b) = (0,0), (p,0), (p,p), (0,p); the face must be the bilinear patch
+      // of its corners with equally spaced nodes
+      const int64_t cn[4] = {fn[0], fn[p], fn[p + pp * p], fn[pp * p]};
+      double diam = 0;
+      for (int k = 0; k < 4; ++k)
+        for (int d = 0; d < 3; ++d) diam = std::max(diam, std::fabs(X(cn[k], d) - X(cn[(k + 1) % 4], d)));
+      if (!(diam > 0)) return bad(SBFWI_EINVAL, tag + "degenerate face");
+      for (int b = 0; b <= p; ++b)
+        for (int a = 0; a <= p; ++a) {
+          const double u = (double)a / p, v = (double)b / p;
+          for (int d = 0; d < 3; ++d) {
+            const double want = (1 - u) * (1 - v) * X(cn[0], d) + u * (1 - v) * X(cn[1], d) + u * v * X(cn[2], d) +
+                                (1 - u) * v * X(cn[3], d);
+            if (std::fabs(X(fn[a + pp * b], d) - want) > 1e-9 * diam)
+              return bad(SBFWI_EINVAL, tag + "face nodes must be equally spaced on the bilinear patch of its corners");
+          }
+        }
+      // det J_b = (x_b - x0) . (x_eta x x_zeta) > 0 at the corners and the middle
+      for (int k = 0; k < 5; ++k) {
+        const double u = k == 4 ? 0.5 : (k == 1 || k == 2 ? 1.0 : 0.0), v = k == 4 ? 0.5 : (k >= 2 ? 1.0 : 0.0);
+        double r[3], xe[3], xz[3];
+        for (int d = 0; d < 3; ++d) {
+          r[d] = (1 - u) * (1 - v) * X(cn[0], d) + u * (1 - v) * X(cn[1], d) + u * v * X(cn[2], d) +
+                 (1 - u) * v * X(cn[3], d) - c[d];
+          xe[d] = (1 - v) * (X(cn[1], d) - X(cn[0], d)) + v * (X(cn[2], d) - X(cn[3], d));
+          xz[d] = (1 - u) * (X(cn[3], d) - X(cn[0], d)) + u * (X(cn[2], d) - X(cn[1], d));
+        }
+        const double det = r[0] * (xe[1] * xz[2] - xe[2] * xz[1]) + r[1] * (xe[2] * xz[0] - xe[0] * xz[2]) +
+                           r[2] * (xe[0] * xz[1] - xe[1] * xz[0]);
+        if (!(det > 1e-14 * diam * diam * diam))
+          return bad(SBFWI_EINVAL, tag + "det J_b <= 0 (centre not strictly inside, or a face not oriented outward)");
+      }
+      for (int k = 0; k < 4; ++k) {
+        const int64_t u = cn[k], v = cn[(k + 1) % 4];
+        edges[{std::min(u, v), std::max(u, v)}] += 1;
+      }
+      for (int k = 0; k < fpp; ++k)
+        if (std::find(order.begin(), order.end(), (int32_t)fn[k]) == order.end()) order.push_back((int32_t)fn[k]);
+    }
+    for (const auto& ed : edges)
+      if (ed.second != 2) return bad(SBFWI_EINVAL, tag + "faces do not close the element (an edge not shared by two faces)");
+    const int L = (int)(f1 - f0);
+    if ((int)order.size() > kMaxBoundaryNodes)
+      return bad(SBFWI_EUNSUPPORTED, tag + "more than " + std::to_string(kMaxBoundaryNodes) + " boundary nodes");
+    nb_max = std::max(nb_max, (int)order.size());
+    L_max = std::max(L_max, L);
+    m->nbe.push_back((int32_t)order.size());
+    m->dofs.insert(m->dofs.end(), order.begin(), order.end());
+    for (int64_t f = f0; f < f1; ++f)
+      for (int k = 0; k < fpp; ++k) {
+        const int32_t g = (int32_t)face_nodes[f * fpp + k];
+        m->line_local.push_back((int32_t)(std::find(order.begin(), order.end(), g) - order.begin()));
+      }
   }
-  m->n_nodal_api = m->n_int_api + m->n_nodes;
-  if (m->uneven) {
-    m->api_to_lib.reserve(m->n_nodal_api);
-    for (int64_t e = 0; e < n_elem; ++e)
-      for (int i = 0; i < m->n; ++i)
-        for (int j = 0; j < m->nbe[e]; ++j) m->api_to_lib.push_back((e * m->n + i) * m->nb + j);
-    for (int64_t g = 0; g < n_nodes; ++g) m->api_to_lib.push_back(m->n_int + g);
-  }
-  int rc = build_tree(*m);
+  m->nb = nb_max;
+  m->L = L_max;
+  int rc = finish_mesh(*m);
   if (rc != SBFWI_OK) { delete m; return rc; }
   *out = m;
   return SBFWI_OK;

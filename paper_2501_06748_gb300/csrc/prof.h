@@ -84,6 +84,42 @@ struct Profiler {
     }
     return level_acc;
   }
+
+  // Per-phase timing of the dataflow global solve: one row per solve (the last kFlowRows
+  // solves kept), row = [earliest block start | per phase p (forward levels, then backward
+  // levels): latest item finish, sum of item execution times (inputs ready -> finished),
+  // sum of item waits (claimed -> inputs ready), items], global timer ns.
+  static constexpr int kFlowRows = 64;
+  unsigned long long* flow_acc = nullptr;
+  int flow_stride = 0;
+  int flow_device = -1;
+  int64_t flow_steps = 0;
+  // the zeroed row of the next solve on the current device, or nullptr
+  unsigned long long* flow_trace(int phases, cudaStream_t st) {
+    if (!on) return nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    const int stride = 1 + 4 * phases;
+    if (flow_acc && (flow_device != dev || flow_stride != stride)) {
+      cudaFree(flow_acc);
+      flow_acc = nullptr;
+    }
+    if (!flow_acc) {
+      if (cudaMalloc(&flow_acc, sizeof(unsigned long long) * stride * kFlowRows) != cudaSuccess) {
+        cudaGetLastError();
+        flow_acc = nullptr;
+        return nullptr;
+      }
+      flow_stride = stride;
+      flow_device = dev;
+      flow_steps = 0;
+    }
+    unsigned long long* row = flow_acc + (size_t)(flow_steps % kFlowRows) * stride;
+    cudaMemsetAsync(row, 0xFF, sizeof(unsigned long long), st);          // start: a minimum
+    cudaMemsetAsync(row + 1, 0, sizeof(unsigned long long) * (stride - 1), st);
+    ++flow_steps;
+    return row;
+  }
 };
 
 Profiler& profiler();

@@ -117,13 +117,14 @@ struct DensityArgs {
   const int32_t* dofs;
   const double* xi_hi;
   const double* xi_lo;
-  const double* grid;        // [gy][gx] or nodal values
+  const double* grid;        // [gy][gx] ([gz][gy][gx] in 3-D) or nodal values
   int rho_kind;
-  int64_t gx, gy;
-  double lx, ly;
+  int dim;
+  int64_t gx, gy, gz;
+  double lx, ly, lz;
   const int32_t* cell_of_point;
   const int8_t* clamp_of_point;
-  double* pts_hi;            // [n_nodal][2]
+  double* pts_hi;            // [n_nodal][dim]
   double* pts_lo;
   double* rho_hi;            // [n_nodal]
   double* rho_lo;
@@ -193,6 +194,61 @@ __global__ void density_kernel(DensityArgs a) {
   }
 }
 
+// The same for a 3-D mesh: nodal points x0 + xi_i (x_j - x0) in three coordinates and
+// trilinear interpolation of the cell-centred [gz][gy][gx] grid, clamped at the edges
+__global__ void density3d_kernel(DensityArgs a) {
+  const int64_t np = a.n_int + a.n_nodes;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
+    dd px[3];
+    if (q < a.n_int) {
+      const int64_t e = q / ((int64_t)a.n * a.nb);
+      const int64_t rem = q - e * (int64_t)a.n * a.nb;
+      const int i = (int)(rem / a.nb), j = (int)(rem - (int64_t)i * a.nb);
+      const double* c0 = a.centre_xy + 3 * e;
+      if (j >= a.nbe[e]) {                 // padding: never used by the method
+        for (int d = 0; d < 3; ++d) { a.pts_hi[3 * q + d] = c0[d]; a.pts_lo[3 * q + d] = 0.0; }
+        a.rho_hi[q] = 1.0; a.rho_lo[q] = 0.0;
+        continue;
+      }
+      const int32_t g = a.dofs[e * a.nb + j];
+      const dd xi{a.xi_hi[i], a.xi_lo[i]};
+      for (int d = 0; d < 3; ++d) px[d] = dd_add(dd_make(c0[d]), dd_mul(xi, two_sum(a.node_xy[3 * g + d], -c0[d])));
+    } else {
+      const int64_t g = q - a.n_int;
+      for (int d = 0; d < 3; ++d) px[d] = dd_make(a.node_xy[3 * g + d]);
+    }
+    for (int d = 0; d < 3; ++d) { a.pts_hi[3 * q + d] = px[d].hi; a.pts_lo[3 * q + d] = px[d].lo; }
+    dd rho;
+    if (a.rho_kind == SBFWI_RHO_NODAL) {
+      rho = dd_make(a.grid[q]);
+    } else {
+      const int64_t cell = a.cell_of_point[q];
+      const int8_t cl = a.clamp_of_point[q];
+      const int64_t ix = cell % a.gx, iy = (cell / a.gx) % a.gy, iz = cell / (a.gx * a.gy);
+      const int64_t gdim[3] = {a.gx, a.gy, a.gz}, base[3] = {ix, iy, iz};
+      const double len[3] = {a.lx, a.ly, a.lz};
+      dd t[3];
+      for (int d = 0; d < 3; ++d) {
+        if (cl & (1 << (2 * d))) t[d] = dd_make(0.0);
+        else if (cl & (2 << (2 * d))) t[d] = dd_make(1.0);
+        else t[d] = dd_sub(dd_div(dd_mul_d(px[d], (double)gdim[d]), dd_make(len[d])), dd_make(0.5 + (double)base[d]));
+      }
+      const dd one = dd_make(1.0);
+      dd v = dd_make(0.0);
+      for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        const dd w = dd_mul(dd_mul(cx ? t[0] : dd_sub(one, t[0]), cy ? t[1] : dd_sub(one, t[1])),
+                            cz ? t[2] : dd_sub(one, t[2]));
+        v = dd_add(v, dd_mul(w, dd_make(a.grid[((iz + cz) * a.gy + iy + cy) * a.gx + ix + cx])));
+      }
+      rho = v;
+    }
+    if (!(rho.hi > 0.0)) atomic_flag(a.status, SBFWI_EINVAL);
+    a.rho_hi[q] = rho.hi;
+    a.rho_lo[q] = rho.lo;
+  }
+}
+
 __global__ void fill_kernel(double* x, int64_t n, double v) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) x[q] = v;
 }
@@ -222,6 +278,7 @@ __global__ void scatter_nodal_kernel(const double* api, const int64_t* map, int6
 // ---------------------------------------------------------------------------
 struct ElemArgs {
   int nb, n, L, p, ng;        // nb, L: largest n_b and line count (strides of the outputs and smem)
+  int dim, fpp, nk;           // 2 or 3; nodes per line (face); geometry factors per Gauss point (4 or 7)
   int64_t e0;                 // first element of this launch
   const int32_t* nbe;         // [E] n_b of each element
   const int64_t* lptr;        // [E+1] first line of each element
@@ -240,7 +297,8 @@ struct ElemArgs {
   const double* rho_lo;
   const double* xi_hi;        // [n+1]
   const double* xi_lo;
-  const double* tab;          // dd tables (hi,lo pairs): w[ng], phi[ng][p+1], dphi[ng][p+1]
+  const double* tab;          // dd tables (hi,lo pairs): w[ng], phi[ng][fpp], dphi[ng][fpp], (3-D) dphi_zeta[ng][fpp]
+                              // (3-D: ng points of the tensor face rule, phi = N, dphi = N_eta)
   double* mats;               // [E][n][3][nb][nb], zero beyond n_b(e)
   double* rt;                 // [E][2][nb][nb]
   double* S;                  // [E][nb][nb]
@@ -253,11 +311,14 @@ struct ElemArgs {
 };
 
 struct ElemSmem {
-  dd* K;      // [L][ng][4] geometry factors: c^2 w det (b1.b1), c^2 w det (b2.b1), c^2 w det (b2.b2), w det
-  dd* KR;     // [L][ng][4] the same times rho at the Gauss point
-  dd* Eline;  // [L][p+1][p+1][4] per-line contributions
-  dd* phi;    // [ng][p+1]
-  dd* dphi;   // [ng][p+1]
+  dd* K;      // [L][ng][nk] geometry factors.  2-D: c^2 w det (b1.b1), c^2 w det (b2.b1),
+              // c^2 w det (b2.b2), w det.  3-D: c^2 w det times b1.b1, b2.b1, b3.b1, b2.b2,
+              // b2.b3, b3.b3, then w det
+  dd* KR;     // [L][ng][nk] the same times rho at the Gauss point
+  dd* Eline;  // [L][fpp][fpp][4] per-line (face) contributions
+  dd* phi;    // [ng][fpp]
+  dd* dphi;   // [ng][fpp]
+  dd* dphz;   // [ng][fpp] (3-D)
   dd* mat;    // 16 matrices of n_b(e)^2 (placed nb*nb apart)
   dd* col;    // [nb] Gauss-Jordan factor column
   int* piv;
@@ -302,8 +363,8 @@ template <class Op>
 __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int64_t e, int i,
                                      dd* E0, dd* E1, dd* E2, dd* M0) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int nb = sm.nb, L = sm.L, p = a.p, ng = a.ng, pp = p + 1, nbs = a.nb;
-  // density at the Gauss points of every line, times the geometry factors
+  const int nb = sm.nb, L = sm.L, ng = a.ng, pp = a.fpp, nk = a.nk, nbs = a.nb;
+  // density at the Gauss points of every line (face), times the geometry factors
   for (int t = tid; t < L * ng; t += nt) {
     const int l = t / ng, g = t - l * ng;
     dd r = Op::make(0.0);
@@ -312,28 +373,40 @@ __device__ void coefficient_matrices(const ElemArgs& a, const ElemSmem& sm, int6
       const int64_t idx = (i < a.n) ? e * (int64_t)a.n * nbs + (int64_t)i * nbs + j : a.n_int + a.dofs[e * nbs + j];
       r = Op::fma(r, sm.phi[g * pp + q], ldd(a.rho_hi, a.rho_lo, idx));
     }
-    for (int k = 0; k < 4; ++k) sm.KR[(l * ng + g) * 4 + k] = Op::mul(sm.K[(l * ng + g) * 4 + k], r);
+    for (int k = 0; k < nk; ++k) sm.KR[(l * ng + g) * nk + k] = Op::mul(sm.K[(l * ng + g) * nk + k], r);
   }
   __syncthreads();
-  // per-line matrices: sum over Gauss points
+  // per-line (face) matrices: sum over Gauss points
   for (int t = tid; t < L * pp * pp; t += nt) {
     const int l = t / (pp * pp), ab = t - l * pp * pp, aa = ab / pp, bb = ab - aa * pp;
     dd s0 = Op::make(0.0), s1 = s0, s2 = s0, sm0 = s0;
     for (int g = 0; g < ng; ++g) {
-      const dd* kr = sm.KR + (l * ng + g) * 4;
+      const dd* kr = sm.KR + (l * ng + g) * nk;
       const dd pa = sm.phi[g * pp + aa], pb = sm.phi[g * pp + bb];
       const dd da = sm.dphi[g * pp + aa], db = sm.dphi[g * pp + bb];
       const dd papb = Op::mul(pa, pb);
       s0 = Op::fma(s0, kr[0], papb);
-      s1 = Op::fma(s1, kr[1], Op::mul(da, pb));
-      s2 = Op::fma(s2, kr[2], Op::mul(da, db));
-      sm0 = Op::fma(sm0, kr[3], papb);
+      if (a.dim == 2) {
+        s1 = Op::fma(s1, kr[1], Op::mul(da, pb));
+        s2 = Op::fma(s2, kr[2], Op::mul(da, db));
+        sm0 = Op::fma(sm0, kr[3], papb);
+      } else {
+        // B2 = b2 N_eta + b3 N_zeta: E1 += (b2.b1 N_eta,a + b3.b1 N_zeta,a) N_b,
+        // E2 += b2.b2 N_eta,a N_eta,b + b2.b3 (N_eta,a N_zeta,b + N_zeta,a N_eta,b) + b3.b3 N_zeta,a N_zeta,b
+        const dd za = sm.dphz[g * pp + aa], zb = sm.dphz[g * pp + bb];
+        s1 = Op::fma(s1, Op::add(Op::mul(kr[1], da), Op::mul(kr[2], za)), pb);
+        dd q2 = Op::mul(kr[3], Op::mul(da, db));
+        q2 = Op::fma(q2, kr[4], Op::add(Op::mul(da, zb), Op::mul(za, db)));
+        q2 = Op::fma(q2, kr[5], Op::mul(za, zb));
+        s2 = Op::add(s2, q2);
+        sm0 = Op::fma(sm0, kr[6], papb);
+      }
     }
     dd* out = sm.Eline + (size_t)t * 4;
     out[0] = s0; out[1] = s1; out[2] = s2; out[3] = sm0;
   }
   __syncthreads();
-  // assemble the element matrices from the lines
+  // assemble the element matrices from the lines (faces)
   for (int t = tid; t < nb * nb; t += nt) {
     const int A = t / nb, B = t - A * nb;
     dd s0 = Op::make(0.0), s1 = s0, s2 = s0, s3 = s0;
@@ -416,7 +489,7 @@ __device__ void mm(int nb, const dd* A, const dd* B, dd* C) {
 __global__ void element_setup_kernel(ElemArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int64_t e = a.e0 + blockIdx.x;
-  const int p = a.p, ng = a.ng, pp = p + 1, n = a.n, nbs = a.nb;
+  const int ng = a.ng, pp = a.fpp, nk = a.nk, n = a.n, nbs = a.nb;
   const int nb = a.nbe[e], L = (int)(a.lptr[e + 1] - a.lptr[e]);
   const int nn = nb * nb;                 // this element's matrices are dense nb x nb
   const int64_t nns = (int64_t)nbs * nbs; // stride of the padded outputs
@@ -424,11 +497,12 @@ __global__ void element_setup_kernel(ElemArgs a) {
   ElemSmem sm;
   sm.nb = nb; sm.L = L; sm.l0 = a.lptr[e];
   dd* base = reinterpret_cast<dd*>(smem_raw);
-  sm.K = base;                     base += a.L * ng * 4;
-  sm.KR = base;                    base += a.L * ng * 4;
+  sm.K = base;                     base += a.L * ng * nk;
+  sm.KR = base;                    base += a.L * ng * nk;
   sm.Eline = base;                 base += a.L * pp * pp * 4;
   sm.phi = base;                   base += ng * pp;
   sm.dphi = base;                  base += ng * pp;
+  sm.dphz = base;                  base += a.dim == 3 ? ng * pp : 0;
   sm.col = base;                   base += nbs;
   if (a.mat_ws) {
     sm.mat = a.mat_ws + (int64_t)blockIdx.x * 16 * nns;
@@ -453,11 +527,57 @@ __global__ void element_setup_kernel(ElemArgs a) {
     const int g = t / pp, q = t - g * pp;
     sm.phi[t] = dd{a.tab[2 * (ng + g * pp + q)], a.tab[2 * (ng + g * pp + q) + 1]};
     sm.dphi[t] = dd{a.tab[2 * (ng + ng * pp + g * pp + q)], a.tab[2 * (ng + ng * pp + g * pp + q) + 1]};
+    if (a.dim == 3)
+      sm.dphz[t] = dd{a.tab[2 * (ng + 2 * ng * pp + g * pp + q)], a.tab[2 * (ng + 2 * ng * pp + g * pp + q) + 1]};
   }
   __syncthreads();
-  const double x0 = a.centre_xy[2 * e], y0 = a.centre_xy[2 * e + 1];
   const dd c2 = two_prod(a.c, a.c);
-  for (int t = tid; t < L * ng; t += nt) {
+  if (a.dim == 3) {
+    // face geometry: J_b rows r_b = x_b - x0, x_b,eta, x_b,zeta; b1, b2, b3 the columns of
+    // J_b^{-1}: (x_eta x x_zeta, x_zeta x r_b, r_b x x_eta) / det J_b
+    const double* c0 = a.centre_xy + 3 * e;
+    for (int t = tid; t < L * ng; t += nt) {
+      const int l = t / ng, g = t - l * ng;
+      const int64_t* fn = a.line_nodes + (sm.l0 + l) * pp;
+      dd r[3], xe[3], xz[3];
+      for (int d = 0; d < 3; ++d) { r[d] = dd_make(0.0); xe[d] = r[d]; xz[d] = r[d]; }
+      for (int q = 0; q < pp; ++q)
+        for (int d = 0; d < 3; ++d) {
+          const double X = a.node_xy[3 * fn[q] + d];
+          r[d] = dd_add(r[d], dd_mul_d(sm.phi[g * pp + q], X));
+          xe[d] = dd_add(xe[d], dd_mul_d(sm.dphi[g * pp + q], X));
+          xz[d] = dd_add(xz[d], dd_mul_d(sm.dphz[g * pp + q], X));
+        }
+      for (int d = 0; d < 3; ++d) r[d] = dd_sub(r[d], dd_make(c0[d]));
+      auto cross = [](const dd* u, const dd* v, dd* out) {
+        out[0] = dd_sub(dd_mul(u[1], v[2]), dd_mul(u[2], v[1]));
+        out[1] = dd_sub(dd_mul(u[2], v[0]), dd_mul(u[0], v[2]));
+        out[2] = dd_sub(dd_mul(u[0], v[1]), dd_mul(u[1], v[0]));
+      };
+      auto dot = [](const dd* u, const dd* v) { return dd_add(dd_add(dd_mul(u[0], v[0]), dd_mul(u[1], v[1])), dd_mul(u[2], v[2])); };
+      dd n1[3], n2[3], n3[3];
+      cross(xe, xz, n1);
+      cross(xz, r, n2);
+      cross(r, xe, n3);
+      const dd det = dot(r, n1);
+      const dd inv = dd_div(dd_make(1.0), det);
+      dd b1[3], b2[3], b3[3];
+      for (int d = 0; d < 3; ++d) { b1[d] = dd_mul(n1[d], inv); b2[d] = dd_mul(n2[d], inv); b3[d] = dd_mul(n3[d], inv); }
+      const dd w = dd{a.tab[2 * g], a.tab[2 * g + 1]};
+      const dd wd = dd_mul(w, det);
+      const dd wdc = dd_mul(wd, c2);
+      dd* K = sm.K + (l * ng + g) * 7;
+      K[0] = dd_mul(wdc, dot(b1, b1));
+      K[1] = dd_mul(wdc, dot(b2, b1));
+      K[2] = dd_mul(wdc, dot(b3, b1));
+      K[3] = dd_mul(wdc, dot(b2, b2));
+      K[4] = dd_mul(wdc, dot(b2, b3));
+      K[5] = dd_mul(wdc, dot(b3, b3));
+      K[6] = wd;
+    }
+  }
+  const double x0 = a.centre_xy[(size_t)a.dim * e], y0 = a.centre_xy[(size_t)a.dim * e + 1];
+  for (int t = tid; a.dim == 2 && t < L * ng; t += nt) {
     const int l = t / ng, g = t - l * ng;
     const int64_t* ln = a.line_nodes + (sm.l0 + l) * pp;
     dd xb = dd_make(0.0), yb = xb, xe = xb, ye = xb;
@@ -533,7 +653,8 @@ __global__ void element_setup_kernel(ElemArgs a) {
           dE0 = Op::mul(Op::sub(E0w[s_next][t], E0w[s_prev][t]), inv_2h);
           dE1T = Op::mul(Op::sub(E1w[s_next][tt], E1w[s_prev][tt]), inv_2h);
         }
-        const dd D = Op::add(Op::sub(Op::add(E0, E1T), E1), Op::mul(xi, dE0));
+        dd D = Op::add(Op::sub(Op::add(E0, E1T), E1), Op::mul(xi, dE0));
+        if (a.dim == 3) D = Op::add(D, E0);                   // 3-D: 2 E0 + E1^T - E1 + xi dE0
         const dd a2 = Op::mul(Op::mul(x2, E0), inv_h2);
         const dd a1 = Op::mul(Op::mul(xi, D), inv_2h);
         th[t] = Op::sub(a2, a1);
@@ -541,6 +662,7 @@ __global__ void element_setup_kernel(ElemArgs a) {
         dd f = Op::neg(Op::add(a2, a2));
         f = Op::sub(f, E2w[w_cur][t]);
         f = Op::add(f, Op::mul(xi, dE1T));
+        if (a.dim == 3) f = Op::add(f, E1T);                  // 3-D: + E1^T in the u coefficient
         f = Op::sub(f, Op::mul(a.mass, Op::mul(x2, M0w[w_cur][t])));
         ph[t] = f;
       }
@@ -900,6 +1022,7 @@ static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
   d->device = device;
   const int n = m.n, p = m.p, pp = p + 1;
   const int ng = (3 * p + 2) / 2;
+  const int ng1 = (3 * p + 4) / 2;          // 3-D: points per direction of the tensor face rule
   // radial grid xi_i = xi0 + i h (xi_n = 1), double-double
   std::vector<double> xi_hi(n + 1), xi_lo(n + 1);
   const dd h = dd_div(dd_sub(dd_make(1.0), dd_make(m.xi0)), dd_make((double)n));
@@ -907,17 +1030,42 @@ static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
     dd x = (i == n) ? dd_make(1.0) : dd_add(dd_make(m.xi0), dd_mul_d(h, (double)i));
     xi_hi[i] = x.hi; xi_lo[i] = x.lo;
   }
-  // Gauss rule and Lagrange tables
-  std::vector<dd> gx_, gw_;
-  gauss_legendre_dd(ng, gx_, gw_);
-  std::vector<double> tab(2 * (ng + 2 * ng * pp));
-  for (int g = 0; g < ng; ++g) {
-    tab[2 * g] = gw_[g].hi; tab[2 * g + 1] = gw_[g].lo;
-    std::vector<dd> ph(pp), dph(pp);
-    lagrange_dd(p, gx_[g], ph.data(), dph.data());
-    for (int q = 0; q < pp; ++q) {
-      tab[2 * (ng + g * pp + q)] = ph[q].hi; tab[2 * (ng + g * pp + q) + 1] = ph[q].lo;
-      tab[2 * (ng + ng * pp + g * pp + q)] = dph[q].hi; tab[2 * (ng + ng * pp + g * pp + q) + 1] = dph[q].lo;
+  // Gauss rule and Lagrange tables.  2-D lines: ng points, phi and dphi of the p+1 line
+  // nodes.  3-D faces: the tensor rule of ng1^2 points (point ga + ng1 gb at (eta_ga,
+  // zeta_gb)), N, N_eta and N_zeta of the (p+1)^2 face nodes (node a + (p+1) b)
+  std::vector<double> tab;
+  if (m.dim == 3) {
+    std::vector<dd> gx_, gw_;
+    gauss_legendre_dd(ng1, gx_, gw_);
+    const int G = ng1 * ng1, F = pp * pp;
+    tab.assign(2 * (G + 3 * G * F), 0.0);
+    std::vector<dd> ph(pp * ng1), dph(pp * ng1);
+    for (int g = 0; g < ng1; ++g) lagrange_dd(p, gx_[g], ph.data() + g * pp, dph.data() + g * pp);
+    auto put = [&](size_t k, dd v) { tab[2 * k] = v.hi; tab[2 * k + 1] = v.lo; };
+    for (int gb = 0; gb < ng1; ++gb)
+      for (int ga = 0; ga < ng1; ++ga) {
+        const int g = ga + ng1 * gb;
+        put(g, dd_mul(gw_[ga], gw_[gb]));
+        for (int b = 0; b < pp; ++b)
+          for (int a2 = 0; a2 < pp; ++a2) {
+            const int q = a2 + pp * b;
+            put(G + (size_t)g * F + q, dd_mul(ph[ga * pp + a2], ph[gb * pp + b]));
+            put(G + (size_t)G * F + (size_t)g * F + q, dd_mul(dph[ga * pp + a2], ph[gb * pp + b]));
+            put(G + 2 * (size_t)G * F + (size_t)g * F + q, dd_mul(ph[ga * pp + a2], dph[gb * pp + b]));
+          }
+      }
+  } else {
+    std::vector<dd> gx_, gw_;
+    gauss_legendre_dd(ng, gx_, gw_);
+    tab.assign(2 * (ng + 2 * ng * pp), 0.0);
+    for (int g = 0; g < ng; ++g) {
+      tab[2 * g] = gw_[g].hi; tab[2 * g + 1] = gw_[g].lo;
+      std::vector<dd> ph(pp), dph(pp);
+      lagrange_dd(p, gx_[g], ph.data(), dph.data());
+      for (int q = 0; q < pp; ++q) {
+        tab[2 * (ng + g * pp + q)] = ph[q].hi; tab[2 * (ng + g * pp + q) + 1] = ph[q].lo;
+        tab[2 * (ng + ng * pp + g * pp + q)] = dph[q].hi; tab[2 * (ng + ng * pp + g * pp + q) + 1] = dph[q].lo;
+      }
     }
   }
   int rc;
@@ -953,12 +1101,14 @@ static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
   return SBFWI_OK;
 }
 
-// base cell, clamping and transpose CSR of the bilinear map for one fine grid
-static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, double lx, double ly, cudaStream_t st) {
+// base cell, clamping and transpose CSR of the bilinear (3-D: trilinear) map for one
+// fine grid
+static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, int64_t gz, double lx, double ly, double lz,
+                           cudaStream_t st) {
   MeshDevice& d = *m.dev;
-  if (d.grid_ready && d.gx == gx && d.gy == gy && d.lx == lx && d.ly == ly) return SBFWI_OK;
+  if (d.grid_ready && d.gx == gx && d.gy == gy && d.gz == gz && d.lx == lx && d.ly == ly && d.lz == lz) return SBFWI_OK;
   d.grid_ready = false;
-  const int n = m.n, nb = m.nb;
+  const int n = m.n, nb = m.nb, D = m.dim, corners = 1 << D;
   const int64_t np = m.n_nodal;
   std::vector<int32_t> cell(np, 0);
   std::vector<int8_t> clamp(np, 0);
@@ -970,55 +1120,58 @@ static int ensure_grid_map(const Mesh& m, int64_t gx, int64_t gy, double lx, dou
     const int64_t e = q / ((int64_t)n * nb);
     return (int)(q % nb) >= m.nbe[e];
   };
+  const int64_t gdim[3] = {gx, gy, gz};
+  const long double len[3] = {lx, ly, lz};
   for (int64_t q = 0; q < np; ++q) {
-    long double x, y;
-    if (padding(q)) {
-      const int64_t e = q / ((int64_t)n * nb);
-      x = m.centre_xy[2 * e];
-      y = m.centre_xy[2 * e + 1];
-    } else if (q < m.n_int) {
-      const int64_t e = q / ((int64_t)n * nb), rem = q - e * (int64_t)n * nb;
-      const int i = (int)(rem / nb), j = (int)(rem - (int64_t)i * nb);
-      const int32_t g = m.dofs[e * nb + j];
-      const long double xi = (long double)m.xi0 + (long double)i * h;
-      x = m.centre_xy[2 * e] + xi * ((long double)m.node_xy[2 * g] - m.centre_xy[2 * e]);
-      y = m.centre_xy[2 * e + 1] + xi * ((long double)m.node_xy[2 * g + 1] - m.centre_xy[2 * e + 1]);
-    } else {
-      x = m.node_xy[2 * (q - m.n_int)];
-      y = m.node_xy[2 * (q - m.n_int) + 1];
+    long double x[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) {
+      if (padding(q)) {
+        const int64_t e = q / ((int64_t)n * nb);
+        x[k] = m.centre_xy[(size_t)D * e + k];
+      } else if (q < m.n_int) {
+        const int64_t e = q / ((int64_t)n * nb), rem = q - e * (int64_t)n * nb;
+        const int i = (int)(rem / nb), j = (int)(rem - (int64_t)i * nb);
+        const int32_t g = m.dofs[e * nb + j];
+        const long double xi = (long double)m.xi0 + (long double)i * h;
+        const long double c0 = m.centre_xy[(size_t)D * e + k];
+        x[k] = c0 + xi * ((long double)m.node_xy[(size_t)D * g + k] - c0);
+      } else {
+        x[k] = m.node_xy[(size_t)D * (q - m.n_int) + k];
+      }
     }
-    const long double fx = x * gx / lx - 0.5L, fy = y * gy / ly - 0.5L;
-    int64_t ix = (int64_t)std::floor(fx), iy = (int64_t)std::floor(fy);
+    int64_t ix[3] = {0, 0, 0};
     int8_t cl = 0;
-    if (ix < 0) { ix = 0; cl |= 1; }
-    if (ix > gx - 2) { ix = gx - 2; cl |= 2; }
-    if (iy < 0) { iy = 0; cl |= 4; }
-    if (iy > gy - 2) { iy = gy - 2; cl |= 8; }
-    cell[q] = (int32_t)(iy * gx + ix);
+    for (int k = 0; k < D; ++k) {
+      const long double f = x[k] * gdim[k] / len[k] - 0.5L;
+      ix[k] = (int64_t)std::floor(f);
+      if (ix[k] < 0) { ix[k] = 0; cl |= (int8_t)(1 << (2 * k)); }
+      if (ix[k] > gdim[k] - 2) { ix[k] = gdim[k] - 2; cl |= (int8_t)(2 << (2 * k)); }
+    }
+    cell[q] = (int32_t)((D == 3 ? ix[2] * gy : 0) * gx + ix[1] * gx + ix[0]);
     clamp[q] = cl;
   }
   // the transpose map gathers, per grid cell, the points touching it in point order
-  std::vector<int64_t> cnt(gx * gy + 1, 0);
+  const int64_t ncell = gx * gy * (D == 3 ? gz : 1);
+  std::vector<int64_t> cnt(ncell + 1, 0);
   auto corner_cell = [&](int64_t q, int k) {
-    const int64_t ix = cell[q] % gx, iy = cell[q] / gx;
-    return (iy + (k >> 1)) * gx + ix + (k & 1);
+    return (int64_t)cell[q] + (k & 1) + ((k >> 1) & 1) * gx + (k >> 2) * gx * gy;
   };
   for (int64_t q = 0; q < np; ++q)
     if (!padding(q))
-      for (int k = 0; k < 4; ++k) cnt[corner_cell(q, k) + 1]++;
-  for (int64_t c = 0; c < gx * gy; ++c) cnt[c + 1] += cnt[c];
+      for (int k = 0; k < corners; ++k) cnt[corner_cell(q, k) + 1]++;
+  for (int64_t c = 0; c < ncell; ++c) cnt[c + 1] += cnt[c];
   std::vector<int64_t> list(cnt.back());
   std::vector<int64_t> fillp(cnt.begin(), cnt.end() - 1);
   for (int64_t q = 0; q < np; ++q)
     if (!padding(q))
-      for (int k = 0; k < 4; ++k) list[fillp[corner_cell(q, k)]++] = q * 4 + k;
+      for (int k = 0; k < corners; ++k) list[fillp[corner_cell(q, k)]++] = q * corners + k;
   int rc;
   if ((rc = upload(d.cell, cell, st))) return rc;
   if ((rc = upload(d.clamp, clamp, st))) return rc;
   if ((rc = upload(d.cell_ptr, cnt, st))) return rc;
   if ((rc = upload(d.cell_list, list, st))) return rc;
   SBFWI_CUDA(cudaStreamSynchronize(st));
-  d.gx = gx; d.gy = gy; d.lx = lx; d.ly = ly;
+  d.gx = gx; d.gy = gy; d.gz = gz; d.lx = lx; d.ly = ly; d.lz = lz;
   d.grid_ready = true;
   return SBFWI_OK;
 }
@@ -1123,13 +1276,15 @@ int ensure_gradient_operator(const Mesh& m, cudaStream_t st) {
 // xops/xel/kq: the exact adjoint's extra operators (nullable).
 static int launch_element_setup(Model& md, const Mesh& m, const double* rho_hi, const double* rho_lo, double* E_out,
                                 double* xops, double* xel, double* kq, int* status, cudaStream_t st) {
-  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
-  const int ng = (3 * p + 2) / 2;
+  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = m.fpp;
+  const int ng = m.dim == 3 ? ((3 * p + 4) / 2) * ((3 * p + 4) / 2) : (3 * p + 2) / 2;
+  const int nk = m.dim == 3 ? 7 : 4;
   const int64_t E = m.n_elem, nn = (int64_t)nb * nb;
   const MeshDevice& d = *m.dev;
   Profiler& prof = profiler();
   ElemArgs a;
   a.nb = nb; a.n = n; a.L = L; a.p = p; a.ng = ng; a.n_elem = E; a.n_int = m.n_int;
+  a.dim = m.dim; a.fpp = pp; a.nk = nk;
   a.nbe = d.nbe.as<int32_t>(); a.lptr = d.lptr.as<int64_t>(); a.mat_ws = nullptr; a.e0 = 0;
   a.E_out = E_out;
   a.xops = xops; a.xel = xel; a.kq = kq;
@@ -1143,7 +1298,8 @@ static int launch_element_setup(Model& md, const Mesh& m, const double* rho_hi, 
   a.mats = md.mats.as<double>(); a.rt = md.rt.as<double>(); a.S = md.S.as<double>(); a.status = status;
   // the 16 working matrices live in shared memory up to n_b = 24; beyond, in a global
   // workspace, with the elements set up in chunks that bound its size
-  const size_t small = sizeof(dd) * ((size_t)L * ng * 8 + (size_t)L * pp * pp * 4 + 2 * (size_t)ng * pp + nb) + 16;
+  const size_t small =
+      sizeof(dd) * ((size_t)L * ng * 2 * nk + (size_t)L * pp * pp * 4 + (m.dim == 3 ? 3 : 2) * (size_t)ng * pp + nb) + 16;
   const size_t mat_bytes = sizeof(dd) * 16 * (size_t)nn;
   const bool in_smem = small + mat_bytes <= 160 * 1024;
   const size_t smem = in_smem ? small + mat_bytes : small;
@@ -1175,7 +1331,8 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   md.nb = nb; md.n = n; md.E = E; md.N = N;
   int rc;
   if ((rc = ensure_mesh_device(m, st))) return rc;
-  if (md.rho_kind == SBFWI_RHO_GRID && (rc = ensure_grid_map(m, md.gx, md.gy, md.lx, md.ly, st))) return rc;
+  if (md.rho_kind == SBFWI_RHO_GRID && (rc = ensure_grid_map(m, md.gx, md.gy, md.gz, md.lx, md.ly, md.lz, st)))
+    return rc;
   const MeshDevice& d = *m.dev;
   DevBuf status;
   SBFWI_CUDA(status.alloc(sizeof(int)));
@@ -1187,7 +1344,7 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   // them to the library's padded layout, padding points get 1)
   DevBuf d_rho_in, d_rho_api;
   const bool nodal = md.rho_kind == SBFWI_RHO_NODAL;
-  const int64_t nrho = nodal ? m.n_nodal_api : md.gx * md.gy;
+  const int64_t nrho = nodal ? m.n_nodal_api : md.gx * md.gy * (m.dim == 3 ? md.gz : 1);
   const cudaMemcpyKind kind = mem == SBFWI_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   if (nodal && m.uneven) {
     SBFWI_CUDA(d_rho_api.alloc(sizeof(double) * nrho));
@@ -1206,21 +1363,23 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
   DevBuf rho_hi, rho_lo;
   SBFWI_CUDA(rho_hi.alloc(sizeof(double) * np));
   SBFWI_CUDA(rho_lo.alloc(sizeof(double) * np));
-  SBFWI_CUDA(md.pts_hi.alloc(sizeof(double) * 2 * np));
-  SBFWI_CUDA(md.pts_lo.alloc(sizeof(double) * 2 * np));
+  SBFWI_CUDA(md.pts_hi.alloc(sizeof(double) * m.dim * np));
+  SBFWI_CUDA(md.pts_lo.alloc(sizeof(double) * m.dim * np));
   {
     DensityArgs a;
     a.n_elem = E; a.n_nodes = N; a.n_int = m.n_int; a.nb = nb; a.n = n; a.nbe = d.nbe.as<int32_t>();
     a.node_xy = d.xy.as<double>(); a.centre_xy = d.ctr.as<double>(); a.dofs = d.dofs.as<int32_t>();
     a.xi_hi = d.xih.as<double>(); a.xi_lo = d.xil.as<double>();
-    a.grid = d_rho_in.as<double>(); a.rho_kind = md.rho_kind; a.gx = md.gx; a.gy = md.gy; a.lx = md.lx; a.ly = md.ly;
+    a.grid = d_rho_in.as<double>(); a.rho_kind = md.rho_kind; a.dim = m.dim;
+    a.gx = md.gx; a.gy = md.gy; a.gz = md.gz; a.lx = md.lx; a.ly = md.ly; a.lz = md.lz;
     a.cell_of_point = md.rho_kind == SBFWI_RHO_GRID ? d.cell.as<int32_t>() : nullptr;
     a.clamp_of_point = md.rho_kind == SBFWI_RHO_GRID ? d.clamp.as<int8_t>() : nullptr;
     a.pts_hi = md.pts_hi.as<double>(); a.pts_lo = md.pts_lo.as<double>();
     a.rho_hi = rho_hi.as<double>(); a.rho_lo = rho_lo.as<double>(); a.status = status.as<int>();
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((np + threads - 1) / threads, 152 * 32);
-    density_kernel<<<blocks, threads, 0, st>>>(a);
+    if (m.dim == 3) density3d_kernel<<<blocks, threads, 0, st>>>(a);
+    else density_kernel<<<blocks, threads, 0, st>>>(a);
     prof.count(kPhaseSetup);
     SBFWI_CUDA(cudaGetLastError());
   }

@@ -155,26 +155,26 @@ struct SolveArgs {
   double* ybnd;          // [bnd_rows][B]
   double* x;             // [N][B] solution
   int nb, B;
+  unsigned bdiv;         // floor(2^32 / B) + 1 (B >= 2): see div_shots
   int warp_doubles;      // shared memory of one warp task (doubles)
 };
 
-// One source term of a front position: a row of ybnd (r >= 0, a child's boundary),
-// an f_hat row (r <= -2: the leaf's own element or a pass-through child leaf) or
-// nothing (r = -1).  Branch-free (the absent case reads f_hat row 0 and drops it).
-// ybnd is written by other blocks earlier in the same persistent launch: read through L2.
-__device__ __forceinline__ double src_value(const SolveArgs& a, int32_t r, int s) {
-  const bool in_y = r >= 0;
-  const int64_t row = in_y ? (int64_t)r : (r <= -2 ? (int64_t)(-2 - r) : 0);
-  const double v = __ldcg((in_y ? a.ybnd : a.fhat) + row * a.B + s);
-  return r == -1 ? 0.0 : v;
+// Sources of a front position: rows of f_hat (r <= -2: the leaf's own element, or a
+// pass-through child leaf) and the external sources are written before the solve
+// starts; rows of ybnd (r >= 0, a child's boundary) are written by other tasks of the
+// same solve (read through L2).  r = -1: absent.  Staging reads the first kind before
+// a task waits for its inputs and only the second kind after the wait.
+__device__ __forceinline__ double fhat_part(const SolveArgs& a, int32_t r, int s) {
+  return r <= -2 ? __ldcg(a.fhat + (int64_t)(-2 - r) * a.B + s) : 0.0;
+}
+__device__ __forceinline__ double ybnd_part(const SolveArgs& a, int32_t r, int s) {
+  return r >= 0 ? __ldcg(a.ybnd + (int64_t)r * a.B + s) : 0.0;
 }
 
-__device__ __forceinline__ double front_value(const SolveArgs& a, const Task& tk, int pos, int s) {
-  const int32_t r0 = a.src0[tk.map_off + pos], r1 = a.src1[tk.map_off + pos];
-  double v = 0.0;
-  v += src_value(a, r0, s);
-  v += src_value(a, r1, s);
-  return v;
+// t / B for 0 <= t < 2^20: a multiply by floor(2^32 / B) + 1 and the high word (exact in
+// that range for B < 4096), instead of an integer division
+__device__ __forceinline__ int div_shots(const SolveArgs& a, int t) {
+  return a.B == 1 ? t : (int)__umulhi((unsigned)t, a.bdiv);
 }
 
 // sum over the ks consecutive lanes that share one output (ks in {1, 2, ..., 32})
@@ -183,55 +183,268 @@ __device__ __forceinline__ double lane_group_sum(double v, int ks) {
   return v;
 }
 
-// Shared-memory staging of a task, U values per thread at a time: all loads of a
-// batch are issued before any of its stores, so the loads of different positions
-// overlap instead of running one after another.
+// Shared-memory staging of a task, U values per thread at a time: all loads of a batch
+// are issued before any of its stores, so the loads of different positions overlap.
+// Every task stages in parts: the constant part (factor rows, index arrays, and the
+// front values that do not come from other tasks) can be loaded before the task waits
+// for its inputs; the data part after.  The data part reads index arrays that the
+// constant part wrote, so the two are separated by a block (or warp) barrier.
 //
-// Forward: [c_sep (s B values, + external sources at the separator nodes) | the
-// task's rows of C (rows x s)]; c_sep also goes to ysep if asked.
-// part: kStageAll, or kStageConst (the factor rows: they do not depend on other tasks, so
-// the dataflow schedule stages them before waiting for its dependencies) or kStageData.
-enum { kStageAll = 0, kStageConst = 1, kStageData = 2 };
+// Forward task (rows r0..r1 of the node's boundary):
+//   [front values: c_sep (s B), then c_bnd of the task's rows (rows B) | the task's rows
+//    of C (rows x s) | ybnd source rows of those s + rows positions (2 (s + rows) int32)]
+// c = ext + f_hat parts + ybnd parts, in this order for every schedule.
+struct FwdStage {
+  double* vals;
+  double* C;
+  int32_t* i0;
+  int32_t* i1;
+  int P, rows;
+};
+__device__ __forceinline__ FwdStage fwd_layout(const Task& tk, double* sm, int B) {
+  FwdStage f;
+  f.rows = tk.r1 - tk.r0;
+  f.P = tk.s + f.rows;
+  f.vals = sm;
+  f.C = sm + (size_t)f.P * B;
+  f.i0 = reinterpret_cast<int32_t*>(f.C + (size_t)f.rows * tk.s);
+  f.i1 = f.i0 + f.P;
+  return f;
+}
 
 template <int U>
-__device__ __forceinline__ void stage_forward(const SolveArgs& a, const Task& tk, double* sm, bool write_ysep, int tid,
-                                              int nthr, int part = kStageAll) {
-  const int B = a.B, S = tk.s, n1 = S * B, n2 = (tk.r1 - tk.r0) * S;
+__device__ __forceinline__ void fwd_stage_const(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+  const int B = a.B, S = tk.s;
+  const FwdStage f = fwd_layout(tk, sm, B);
   const double* C = a.factors + tk.X_off + (int64_t)S * S + (int64_t)S * tk.b + (int64_t)tk.r0 * S;
-  const int lo = part == kStageConst ? n1 : 0, hi = part == kStageData ? n1 : n1 + n2;
-  for (int base = lo; base < hi; base += U * nthr) {
+  const int nv = f.P * B, n = nv + f.rows * S;
+  for (int base = 0; base < n; base += U * nthr) {
     double v[U];
+    int32_t q0[U], q1[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int t = base + u * nthr + tid;
       v[u] = 0.0;
-      if (t < n1) {
-        const int k = t / B, s = t - k * B;
-        v[u] = front_value(a, tk, k, s) + a.ext[(int64_t)a.sep_nodes[tk.sep_off + k] * B + s];
-      } else if (t < hi) {
-        v[u] = C[t - n1];
+      q0[u] = -1;
+      q1[u] = -1;
+      if (t < nv) {
+        const int p = div_shots(a, t), sh = t - p * B;
+        const int pos = p < S ? p : S + tk.r0 + (p - S);
+        q0[u] = a.src0[tk.map_off + pos];
+        q1[u] = a.src1[tk.map_off + pos];
+        if (p < S) v[u] = __ldcg(a.ext + (int64_t)a.sep_nodes[tk.sep_off + p] * B + sh);
+      } else if (t < n) {
+        v[u] = C[t - nv];
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int t = base + u * nthr + tid;
-      if (t < hi) sm[t] = v[u];
-      if (write_ysep && t < n1) a.ysep[tk.sep_off * B + t] = v[u];
+      if (t < nv) {
+        const int p = div_shots(a, t), sh = t - p * B;
+        v[u] += fhat_part(a, q0[u], sh);
+        v[u] += fhat_part(a, q1[u], sh);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < nv) {
+        const int p = div_shots(a, t), sh = t - p * B;
+        f.vals[t] = v[u];
+        if (sh == 0) {
+          f.i0[p] = q0[u];
+          f.i1[p] = q1[u];
+        }
+      } else if (t < n) {
+        f.C[t - nv] = v[u];
+      }
     }
   }
 }
 
-// Backward: [y_sep (s B) | x at the front's boundary nodes (b B) | the task's rows of
-// X (rows x s) | the task's rows of G (rows x b)]
+// the ybnd parts (children's boundaries); c_sep also goes to ysep if asked
 template <int U>
-__device__ __forceinline__ void stage_backward(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr,
-                                               int part = kStageAll) {
-  const int B = a.B, S = tk.s, Bn = tk.b, rows = tk.r1 - tk.r0;
-  const int n1 = S * B, n2 = n1 + Bn * B, n3 = n2 + rows * S, n4 = n3 + rows * Bn;
+__device__ __forceinline__ void fwd_stage_data(const SolveArgs& a, const Task& tk, double* sm, bool write_ysep, int tid,
+                                               int nthr) {
+  const int B = a.B, S = tk.s;
+  const FwdStage f = fwd_layout(tk, sm, B);
+  const int nv = f.P * B;
+  for (int base = 0; base < nv; base += U * nthr) {
+    double y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      y[u] = 0.0;
+      if (t < nv) {
+        const int p = div_shots(a, t), sh = t - p * B;
+        y[u] = ybnd_part(a, f.i0[p], sh);
+        y[u] += ybnd_part(a, f.i1[p], sh);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < nv) {
+        const double c = f.vals[t] + y[u];
+        f.vals[t] = c;
+        if (write_ysep && t < S * B) a.ysep[tk.sep_off * B + t] = c;
+      }
+    }
+  }
+}
+
+// Backward task (rows r0..r1 of the node's separator):
+//   [y_sep (s B) | x at the node's boundary nodes (b B) | the task's rows of X (rows x s) |
+//    the task's rows of G (rows x b) | boundary node ids (b int32) | separator node ids of
+//    the task's rows (rows int32)]
+// Parts: constant (factor rows, node ids), own (y_sep: this node's forward tasks) and data
+// (x at the boundary: the nearest ancestor's backward tasks).
+struct BwdStage {
+  double* ys;
+  double* xb;
+  double* X;
+  double* G;
+  int32_t* bnd;
+  int32_t* sep;
+  int rows;
+};
+__device__ __forceinline__ BwdStage bwd_layout(const Task& tk, double* sm, int B) {
+  BwdStage g;
+  g.rows = tk.r1 - tk.r0;
+  g.ys = sm;
+  g.xb = sm + (size_t)tk.s * B;
+  g.X = g.xb + (size_t)tk.b * B;
+  g.G = g.X + (size_t)g.rows * tk.s;
+  g.bnd = reinterpret_cast<int32_t*>(g.G + (size_t)g.rows * tk.b);
+  g.sep = g.bnd + tk.b;
+  return g;
+}
+
+template <int U>
+__device__ __forceinline__ void bwd_stage_const(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+  const int S = tk.s, Bn = tk.b;
+  const BwdStage g = bwd_layout(tk, sm, a.B);
   const double* X = a.factors + tk.X_off + (int64_t)tk.r0 * S;
   const double* G = a.factors + tk.X_off + (int64_t)S * S + (int64_t)tk.r0 * Bn;
-  const int lo = part == kStageConst ? n2 : 0, hi = part == kStageData ? n2 : n4;
-  for (int base = lo; base < hi; base += U * nthr) {
+  const int n1 = g.rows * S, n2 = n1 + g.rows * Bn, n3 = n2 + Bn, n4 = n3 + g.rows;
+  for (int base = 0; base < n4; base += U * nthr) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      v[u] = 0.0;
+      if (t < n1) v[u] = X[t];
+      else if (t < n2) v[u] = G[t - n1];
+      else if (t < n3) v[u] = __hiloint2double(0, a.bnd_nodes[tk.bnd_off + (t - n2)]);
+      else if (t < n4) v[u] = __hiloint2double(0, a.sep_nodes[tk.sep_off + tk.r0 + (t - n3)]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < n1) g.X[t] = v[u];
+      else if (t < n2) g.G[t - n1] = v[u];
+      else if (t < n3) g.bnd[t - n2] = __double2loint(v[u]);
+      else if (t < n4) g.sep[t - n3] = __double2loint(v[u]);
+    }
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void bwd_stage_own(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+  const BwdStage g = bwd_layout(tk, sm, a.B);
+  const int n = tk.s * a.B;
+  for (int base = 0; base < n; base += U * nthr) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      v[u] = t < n ? __ldcg(a.ysep + tk.sep_off * a.B + t) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < n) g.ys[t] = v[u];
+    }
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void bwd_stage_data(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+  const int B = a.B;
+  const BwdStage g = bwd_layout(tk, sm, B);
+  const int n = tk.b * B;
+  for (int base = 0; base < n; base += U * nthr) {
+    double v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      v[u] = 0.0;
+      if (t < n) {
+        const int j = div_shots(a, t), sh = t - j * B;
+        v[u] = __ldcg(a.x + (int64_t)g.bnd[j] * B + sh);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < n) g.xb[t] = v[u];
+    }
+  }
+}
+
+// Everything at once, for the schedules that have nothing to wait for (barrier, per
+// level): the same values in the same order of summation as the parts, so every schedule
+// gives the same bits, in one pass of dependent loads (index, then value).
+template <int U>
+__device__ __forceinline__ void fwd_stage_all(const SolveArgs& a, const Task& tk, double* sm, bool write_ysep, int tid,
+                                              int nthr) {
+  const int B = a.B, S = tk.s;
+  const FwdStage f = fwd_layout(tk, sm, B);
+  const double* C = a.factors + tk.X_off + (int64_t)S * S + (int64_t)S * tk.b + (int64_t)tk.r0 * S;
+  const int nv = f.P * B, n = nv + f.rows * S;
+  for (int base = 0; base < n; base += U * nthr) {
+    double v[U], y[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      v[u] = 0.0;
+      y[u] = 0.0;
+      if (t < nv) {
+        const int p = div_shots(a, t), sh = t - p * B;
+        const int pos = p < S ? p : S + tk.r0 + (p - S);
+        const int32_t q0 = a.src0[tk.map_off + pos], q1 = a.src1[tk.map_off + pos];
+        if (p < S) v[u] = __ldcg(a.ext + (int64_t)a.sep_nodes[tk.sep_off + p] * B + sh);
+        v[u] += fhat_part(a, q0, sh);
+        v[u] += fhat_part(a, q1, sh);
+        y[u] = ybnd_part(a, q0, sh);
+        y[u] += ybnd_part(a, q1, sh);
+      } else if (t < n) {
+        v[u] = C[t - nv];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = base + u * nthr + tid;
+      if (t < nv) {
+        const double c = v[u] + y[u];
+        f.vals[t] = c;
+        if (write_ysep && t < S * B) a.ysep[tk.sep_off * B + t] = c;
+      } else if (t < n) {
+        f.C[t - nv] = v[u];
+      }
+    }
+  }
+}
+
+template <int U>
+__device__ __forceinline__ void bwd_stage_all(const SolveArgs& a, const Task& tk, double* sm, int tid, int nthr) {
+  const int B = a.B, S = tk.s, Bn = tk.b;
+  const BwdStage g = bwd_layout(tk, sm, B);
+  const double* X = a.factors + tk.X_off + (int64_t)tk.r0 * S;
+  const double* G = a.factors + tk.X_off + (int64_t)S * S + (int64_t)tk.r0 * Bn;
+  const int n1 = S * B, n2 = n1 + Bn * B, n3 = n2 + g.rows * S, n4 = n3 + g.rows * Bn, n5 = n4 + g.rows;
+  for (int base = 0; base < n5; base += U * nthr) {
     double v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -240,129 +453,135 @@ __device__ __forceinline__ void stage_backward(const SolveArgs& a, const Task& t
       if (t < n1) {
         v[u] = __ldcg(a.ysep + tk.sep_off * B + t);
       } else if (t < n2) {
-        const int q = t - n1, j = q / B, s = q - j * B;
-        v[u] = __ldcg(a.x + (int64_t)a.bnd_nodes[tk.bnd_off + j] * B + s);
+        const int q = t - n1, j = div_shots(a, q), sh = q - j * B;
+        v[u] = __ldcg(a.x + (int64_t)a.bnd_nodes[tk.bnd_off + j] * B + sh);
       } else if (t < n3) {
         v[u] = X[t - n2];
       } else if (t < n4) {
         v[u] = G[t - n3];
+      } else if (t < n5) {
+        v[u] = __hiloint2double(0, a.sep_nodes[tk.sep_off + tk.r0 + (t - n4)]);
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int t = base + u * nthr + tid;
-      if (t < hi) sm[t] = v[u];
+      if (t < n1) g.ys[t] = v[u];
+      else if (t < n2) g.xb[t - n1] = v[u];
+      else if (t < n3) g.X[t - n2] = v[u];
+      else if (t < n4) g.G[t - n3] = v[u];
+      else if (t < n5) g.sep[t - n4] = __double2loint(v[u]);
     }
   }
 }
 
-// forward pass: y_bnd = c_bnd - C c_sep, c assembled from the children (or the element);
-// part: what is left to stage (kStageData when the constants were staged before the wait)
-__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* sm, int part = kStageAll) {
+// forward products of a block task: y_bnd = c_bnd - C c_sep for the task's rows
+__device__ void fwd_compute_block(const SolveArgs& a, const Task& tk, const double* sm) {
   const int B = a.B, S = tk.s;
-  stage_forward<8>(a, tk, sm, tk.r0 == 0, threadIdx.x, blockDim.x, part);
-  __syncthreads();
-  const double* csep = sm;
-  const double* Cs = sm + S * B;          // rows r0.. of C, s each
-  const int ks = tk.ksplit;
-  const int outputs = (tk.r1 - tk.r0) * B;
+  const FwdStage f = fwd_layout(tk, const_cast<double*>(sm), B);
+  const double* csep = f.vals;
+  const double* cb = f.vals + (size_t)S * B;
+  const int ks = tk.ksplit, kl = __ffs(ks) - 1;     // ks: a power of two
+  const int outputs = f.rows * B;
   // every lane walks the same number of rounds so that the lane-group shuffles see full warps
   const int rounds = (outputs * ks + blockDim.x - 1) / blockDim.x;
   for (int rd = 0; rd < rounds; ++rd) {
     const int t = rd * blockDim.x + threadIdx.x;
-    const int o = t / ks, kk = t - o * ks;
+    const int o = t >> kl, kk = t & (ks - 1);
     const bool live = o < outputs;
-    const int ro = live ? o / B : 0, s = live ? o % B : 0;
-    double acc = 0.0, cb = 0.0;
+    const int ro = live ? div_shots(a, o) : 0, sh = live ? o - ro * B : 0;
+    double acc = 0.0;
     if (live) {
-      if (kk == 0) cb = front_value(a, tk, S + tk.r0 + ro, s);
-      const double* Cr = Cs + ro * S;
+      const double* Cr = f.C + ro * S;
 #pragma unroll 4
-      for (int k = kk; k < S; k += ks) acc = fma(Cr[k], csep[k * B + s], acc);
+      for (int k = kk; k < S; k += ks) acc = fma(Cr[k], csep[k * B + sh], acc);
     }
     acc = lane_group_sum(acc, ks);
-    if (live && kk == 0) a.ybnd[(tk.bnd_off + tk.r0 + ro) * B + s] = cb - acc;
+    if (live && kk == 0) a.ybnd[(tk.bnd_off + tk.r0 + ro) * B + sh] = cb[ro * B + sh] - acc;
   }
-  __syncthreads();     // the staging area is reused by the next task of this block
 }
 
-// backward pass: x_sep = X y_sep - G x_bnd
-__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* sm, int part = kStageAll) {
-  const int B = a.B, S = tk.s, Bn = tk.b, rows = tk.r1 - tk.r0;
-  stage_backward<8>(a, tk, sm, threadIdx.x, blockDim.x, part);
-  __syncthreads();
-  const double* ys = sm;
-  const double* xbn = ys + S * B;
-  const double* Xs = xbn + Bn * B;
-  const double* Gs = Xs + rows * S;
-  const int ks = tk.ksplit;
-  const int outputs = rows * B;
+// backward products of a block task: x_sep = X y_sep - G x_bnd for the task's rows
+__device__ void bwd_compute_block(const SolveArgs& a, const Task& tk, const double* sm) {
+  const int B = a.B, S = tk.s, Bn = tk.b;
+  const BwdStage g = bwd_layout(tk, const_cast<double*>(sm), B);
+  const int ks = tk.ksplit, kl = __ffs(ks) - 1;     // ks: a power of two
+  const int outputs = g.rows * B;
   const int rounds = (outputs * ks + blockDim.x - 1) / blockDim.x;
   for (int rd = 0; rd < rounds; ++rd) {
     const int t = rd * blockDim.x + threadIdx.x;
-    const int o = t / ks, kk = t - o * ks;
+    const int o = t >> kl, kk = t & (ks - 1);
     const bool live = o < outputs;
-    const int ro = live ? o / B : 0, s = live ? o % B : 0;
+    const int ro = live ? div_shots(a, o) : 0, sh = live ? o - ro * B : 0;
     double acc = 0.0;
     if (live) {
-      const double* Xr = Xs + ro * S;
+      const double* Xr = g.X + ro * S;
 #pragma unroll 4
-      for (int k = kk; k < S; k += ks) acc = fma(Xr[k], ys[k * B + s], acc);
-      const double* Gr = Gs + ro * Bn;
+      for (int k = kk; k < S; k += ks) acc = fma(Xr[k], g.ys[k * B + sh], acc);
+      const double* Gr = g.G + ro * Bn;
 #pragma unroll 4
-      for (int j = kk; j < Bn; j += ks) acc = fma(-Gr[j], xbn[j * B + s], acc);
+      for (int j = kk; j < Bn; j += ks) acc = fma(-Gr[j], g.xb[j * B + sh], acc);
     }
     acc = lane_group_sum(acc, ks);
-    if (live && kk == 0) a.x[(int64_t)a.sep_nodes[tk.sep_off + tk.r0 + ro] * B + s] = acc;
+    if (live && kk == 0) a.x[(int64_t)g.sep[ro] * B + sh] = acc;
   }
-  __syncthreads();
 }
 
 // the same for a small front done by one warp (all rows; no block synchronisation)
-__device__ void solve_forward_warp(const SolveArgs& a, const Task tk, double* sm, int lane, int part = kStageAll) {
-  const int B = a.B, S = tk.s, Bn = tk.b;
-  stage_forward<8>(a, tk, sm, true, lane, 32, part);
-  __syncwarp();
-  const double* csep = sm;
-  const double* Cs = sm + S * B;           // all b rows of C, s each
-  constexpr int U = 8;
-  for (int base = 0; base < Bn * B; base += U * 32) {
-    double y[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int o = base + u * 32 + lane;
-      y[u] = 0.0;
-      if (o < Bn * B) y[u] = front_value(a, tk, S + o / B, o % B);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int o = base + u * 32 + lane;
-      if (o < Bn * B) {
-        const int r = o / B, s = o - r * B;
-        double acc = 0.0;
-        for (int k = 0; k < S; ++k) acc = fma(Cs[r * S + k], csep[k * B + s], acc);
-        a.ybnd[tk.bnd_off * B + o] = y[u] - acc;
-      }
-    }
+__device__ void fwd_compute_warp(const SolveArgs& a, const Task& tk, const double* sm, int lane) {
+  const int B = a.B, S = tk.s;
+  const FwdStage f = fwd_layout(tk, const_cast<double*>(sm), B);
+  const double* csep = f.vals;
+  const double* cb = f.vals + (size_t)S * B;
+  const int n = f.rows * B;
+  for (int o = lane; o < n; o += 32) {
+    const int r = div_shots(a, o), sh = o - r * B;
+    double acc = 0.0;
+    for (int k = 0; k < S; ++k) acc = fma(f.C[r * S + k], csep[k * B + sh], acc);
+    a.ybnd[tk.bnd_off * B + o] = cb[o] - acc;
   }
+}
+
+__device__ void bwd_compute_warp(const SolveArgs& a, const Task& tk, const double* sm, int lane) {
+  const int B = a.B, S = tk.s, Bn = tk.b;
+  const BwdStage g = bwd_layout(tk, const_cast<double*>(sm), B);
+  for (int o = lane; o < g.rows * B; o += 32) {
+    const int r = div_shots(a, o), sh = o - r * B;
+    double acc = 0.0;
+    for (int k = 0; k < S; ++k) acc = fma(g.X[r * S + k], g.ys[k * B + sh], acc);
+    for (int j = 0; j < Bn; ++j) acc = fma(-g.G[r * Bn + j], g.xb[j * B + sh], acc);
+    a.x[(int64_t)g.sep[r] * B + sh] = acc;
+  }
+}
+
+// A whole task with nothing to wait for (the barrier and per-level schedules).  Block
+// tasks end with __syncthreads (the staging area is reused by the block's next task),
+// warp tasks with __syncwarp.
+__device__ void solve_forward_task(const SolveArgs& a, const Task tk, double* sm) {
+  fwd_stage_all<8>(a, tk, sm, tk.r0 == 0, threadIdx.x, blockDim.x);
+  __syncthreads();
+  fwd_compute_block(a, tk, sm);
+  __syncthreads();
+}
+
+__device__ void solve_backward_task(const SolveArgs& a, const Task tk, double* sm) {
+  bwd_stage_all<8>(a, tk, sm, threadIdx.x, blockDim.x);
+  __syncthreads();
+  bwd_compute_block(a, tk, sm);
+  __syncthreads();
+}
+
+__device__ void solve_forward_warp(const SolveArgs& a, const Task tk, double* sm, int lane) {
+  fwd_stage_all<8>(a, tk, sm, true, lane, 32);
+  __syncwarp();
+  fwd_compute_warp(a, tk, sm, lane);
   __syncwarp();
 }
 
-__device__ void solve_backward_warp(const SolveArgs& a, const Task tk, double* sm, int lane, int part = kStageAll) {
-  const int B = a.B, S = tk.s, Bn = tk.b;
-  stage_backward<8>(a, tk, sm, lane, 32, part);
+__device__ void solve_backward_warp(const SolveArgs& a, const Task tk, double* sm, int lane) {
+  bwd_stage_all<8>(a, tk, sm, lane, 32);
   __syncwarp();
-  const double* ys = sm;
-  const double* xbn = ys + S * B;
-  const double* Xs = xbn + Bn * B;
-  const double* Gs = Xs + S * S;
-  for (int o = lane; o < S * B; o += 32) {
-    const int r = o / B, s = o - r * B;
-    double acc = 0.0;
-    for (int k = 0; k < S; ++k) acc = fma(Xs[r * S + k], ys[k * B + s], acc);
-    for (int j = 0; j < Bn; ++j) acc = fma(-Gs[r * Bn + j], xbn[j * B + s], acc);
-    a.x[(int64_t)a.sep_nodes[tk.sep_off + r] * B + s] = acc;
-  }
+  bwd_compute_warp(a, tk, sm, lane);
   __syncwarp();
 }
 
@@ -462,7 +681,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-__global__ void __launch_bounds__(256) solve_persistent_kernel(PersistentSolveArgs a) {
+__global__ void __launch_bounds__(256, 4) solve_persistent_kernel(PersistentSolveArgs a) {
   extern __shared__ double sm_p[];
   // trace (profiling only): [0, 2L) wall time per phase seen by block 0, [2L, 4L) the
   // longest time any block spent in its tasks of the phase, [4L, 6L) the sum over
@@ -527,16 +746,41 @@ struct FlowArgs {
   unsigned gen;               // this launch's number in the time loop, from 1
   int* status;
   long long budget;
+  int levels;
+  unsigned long long* trace;  // nullable: this solve's row of the per-phase trace (profiling)
 };
 
-__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(volatile const unsigned*)p; }
+// profiling: one item of phase `ph` finished (timer values of its claim and of its inputs
+// being ready)
+__device__ __forceinline__ void flow_record(const FlowArgs& a, int ph, unsigned long long t_claim,
+                                            unsigned long long t_ready) {
+  const unsigned long long t = global_ns();
+  unsigned long long* f = a.trace + 1 + 4 * ph;
+  atomicMax(f, t);
+  atomicAdd(f + 1, t - t_ready);
+  atomicAdd(f + 2, t_ready - t_claim);
+  atomicAdd(f + 3, 1ULL);
+}
 
-// one thread: wait until counter >= target; false if the budget ran out or another
+// completion counter update: a release, so every write of the task (ordered before it by
+// the block or warp barrier) is visible to a thread whose acquire load sees the new count
+__device__ __forceinline__ void add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// one thread: wait until counter >= target (an acquire: the producers' writes before
+// their counter update are visible after it); false if the budget ran out or another
 // wait gave up
 __device__ bool wait_count(const unsigned* counter, unsigned target, int* status, long long budget) {
-  if (ld_volatile(counter) >= target) return true;
+  if (ld_acquire(counter) >= target) return true;
   const long long t0 = clock64();
-  while (ld_volatile(counter) < target) {
+  while (ld_acquire(counter) < target) {
     if (clock64() - t0 > budget || *(volatile int*)status != 0) {
       atomicCAS(status, 0, SBFWI_ETIMEOUT);
       return false;
@@ -546,72 +790,120 @@ __device__ bool wait_count(const unsigned* counter, unsigned target, int* status
   return true;
 }
 
-__device__ bool wait_deps(const FlowArgs& a, const Task& tk, int dir) {
+// A forward task reads its children's boundaries: every forward task of both children.
+__device__ bool wait_children(const FlowArgs& a, int node) {
   const int T = a.nodes;
   const int32_t* nf = a.node_info;
-  const int32_t* nbk = a.node_info + T;
-  const int32_t* c0 = a.node_info + 2 * T;
-  const int32_t* c1 = a.node_info + 3 * T;
-  const int32_t* dep = a.node_info + 4 * T;
+  const int ch[2] = {a.node_info[2 * T + node], a.node_info[3 * T + node]};
   bool ok = true;
-  if (dir == 0) {
-    const int ch[2] = {c0[tk.node], c1[tk.node]};
-    for (int k = 0; k < 2 && ok; ++k)
-      if (ch[k] >= 0) ok = wait_count(a.done_f + ch[k], a.gen * (unsigned)nf[ch[k]], a.status, a.budget);
-  } else {
-    ok = wait_count(a.done_f + tk.node, a.gen * (unsigned)nf[tk.node], a.status, a.budget);
-    const int d = dep[tk.node];
-    if (ok && d >= 0) ok = wait_count(a.done_b + d, a.gen * (unsigned)nbk[d], a.status, a.budget);
-  }
-  __threadfence();
+  for (int k = 0; k < 2 && ok; ++k)
+    if (ch[k] >= 0) ok = wait_count(a.done_f + ch[k], a.gen * (unsigned)nf[ch[k]], a.status, a.budget);
   return ok;
 }
 
+// A backward task reads y_sep of its own node (that node's forward tasks) ...
+__device__ bool wait_own(const FlowArgs& a, int node) {
+  return wait_count(a.done_f + node, a.gen * (unsigned)a.node_info[node], a.status, a.budget);
+}
+
+// ... and x at its boundary: the backward tasks of its nearest ancestor that has any.
+__device__ bool wait_ancestor(const FlowArgs& a, int node) {
+  const int T = a.nodes;
+  const int d = a.node_info[4 * T + node];
+  return d < 0 || wait_count(a.done_b + d, a.gen * (unsigned)a.node_info[T + d], a.status, a.budget);
+}
+
+// kTrace: the profiling variant that stamps the timer (a.trace set); the other ignores a.trace
+template <bool kTrace>
 __global__ void __launch_bounds__(256, 4) solve_flow_kernel(FlowArgs a) {
   extern __shared__ double sm_f[];
   __shared__ long long s_item;
-  __shared__ int s_ok;
+  __shared__ int s_ok[2];
+  __shared__ unsigned long long s_tclaim;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr bool tr = kTrace;
+  if (tr && threadIdx.x == 0) atomicMin(a.trace, global_ns());
   for (;;) {
     // a wait that gave up anywhere stops every block at its next claim
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
       s_item = *(volatile int*)a.status != 0 ? (long long)a.n_items
                                             : (long long)(atomicAdd(a.claim, 1ULL) - a.base);
+      if (tr) s_tclaim = global_ns();
+    }
     __syncthreads();
     const long long it = s_item;
     __syncthreads();
     if (it >= a.n_items) return;
     const int4 im = a.items[it];
     const Task* tasks = im.w ? a.bwd : a.fwd;
-    if (im.z) {                                            // block task
+    unsigned long long t_ready = tr ? s_tclaim : 0ULL;     // profiling: when the inputs were ready
+    if (im.z == 1) {                                       // block task
       const Task tk = tasks[im.x];
-      // the factor rows first: they hide their latency behind the wait for the inputs
-      if (im.w) stage_backward<8>(a.s, tk, sm_f, threadIdx.x, blockDim.x, kStageConst);
-      else stage_forward<8>(a.s, tk, sm_f, false, threadIdx.x, blockDim.x, kStageConst);
-      if (threadIdx.x == 0) s_ok = wait_deps(a, tk, im.w) ? 1 : 0;
-      __syncthreads();
-      if (!s_ok) return;
-      if (im.w) solve_backward_task(a.s, tk, sm_f, kStageData);
-      else solve_forward_task(a.s, tk, sm_f, kStageData);   // both end with __syncthreads
+      // what does not depend on other tasks first: it hides its latency behind the waits
+      if (im.w) {
+        bwd_stage_const<8>(a.s, tk, sm_f, threadIdx.x, blockDim.x);
+        if (threadIdx.x == 0) s_ok[0] = wait_own(a, tk.node) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok[0]) return;
+        bwd_stage_own<8>(a.s, tk, sm_f, threadIdx.x, blockDim.x);
+        if (threadIdx.x == 0) s_ok[1] = wait_ancestor(a, tk.node) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok[1]) return;
+        if (tr && threadIdx.x == 0) t_ready = global_ns();
+        bwd_stage_data<8>(a.s, tk, sm_f, threadIdx.x, blockDim.x);
+        __syncthreads();
+        bwd_compute_block(a.s, tk, sm_f);
+      } else {
+        fwd_stage_const<8>(a.s, tk, sm_f, threadIdx.x, blockDim.x);
+        if (threadIdx.x == 0) s_ok[0] = wait_children(a, tk.node) ? 1 : 0;
+        __syncthreads();
+        if (!s_ok[0]) return;
+        if (tr && threadIdx.x == 0) t_ready = global_ns();
+        fwd_stage_data<8>(a.s, tk, sm_f, tk.r0 == 0, threadIdx.x, blockDim.x);
+        __syncthreads();
+        fwd_compute_block(a.s, tk, sm_f);
+      }
+      __syncthreads();     // every output stored; the staging area is free for the next item
       if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd((im.w ? a.done_b : a.done_f) + tk.node, 1u);
+        add_release((im.w ? a.done_b : a.done_f) + tk.node, 1u);
+        if (tr) flow_record(a, im.w * a.levels + (tk.pad & 0xff), s_tclaim, t_ready);
       }
     } else if (warp < im.y) {                              // warp task
       const Task tk = tasks[im.x + warp];
       double* wsm = sm_f + (size_t)warp * a.s.warp_doubles;
-      if (im.w) stage_backward<8>(a.s, tk, wsm, lane, 32, kStageConst);
-      else stage_forward<8>(a.s, tk, wsm, false, lane, 32, kStageConst);
       int ok = 1;
-      if (lane == 0) ok = wait_deps(a, tk, im.w) ? 1 : 0;
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (ok) {                                            // else: the status stops the block at its next claim
-        if (im.w) solve_backward_warp(a.s, tk, wsm, lane, kStageData);
-        else solve_forward_warp(a.s, tk, wsm, lane, kStageData);   // both end with __syncwarp
-        if (lane == 0) {
-          __threadfence();
-          atomicAdd((im.w ? a.done_b : a.done_f) + tk.node, 1u);
+      if (im.w) {
+        bwd_stage_const<8>(a.s, tk, wsm, lane, 32);
+        if (lane == 0) ok = wait_own(a, tk.node) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+          bwd_stage_own<8>(a.s, tk, wsm, lane, 32);
+          if (lane == 0) ok = wait_ancestor(a, tk.node) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
         }
+        if (ok) {
+          if (tr && lane == 0) t_ready = global_ns();
+          __syncwarp();
+          bwd_stage_data<8>(a.s, tk, wsm, lane, 32);
+          __syncwarp();
+          bwd_compute_warp(a.s, tk, wsm, lane);
+        }
+      } else {
+        fwd_stage_const<8>(a.s, tk, wsm, lane, 32);
+        if (lane == 0) ok = wait_children(a, tk.node) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+          if (tr && lane == 0) t_ready = global_ns();
+          __syncwarp();
+          fwd_stage_data<8>(a.s, tk, wsm, true, lane, 32);
+          __syncwarp();
+          fwd_compute_warp(a.s, tk, wsm, lane);
+        }
+      }
+      __syncwarp();
+      if (ok && lane == 0) {                               // else: the status stops the block at its next claim
+        add_release((im.w ? a.done_b : a.done_f) + tk.node, 1u);
+        if (tr) flow_record(a, im.w * a.levels + (tk.pad & 0xff), s_tclaim, t_ready);
       }
     }
   }
@@ -767,6 +1059,34 @@ __global__ void grid_transpose_kernel(const double* g_nodal, const double* pts, 
   }
 }
 
+// the same for a 3-D grid (trilinear weights, cell_list entries point * 8 + corner)
+__global__ void grid_transpose3d_kernel(const double* g_nodal, const double* pts, const int32_t* cell_of_point,
+                                        const int8_t* clamp, const int64_t* cell_ptr, const int64_t* cell_list,
+                                        int64_t gx, int64_t gy, int64_t gz, double lx, double ly, double lz,
+                                        double* out, int accumulate) {
+  const int64_t ncell = gx * gy * gz;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t l = cell_ptr[c]; l < cell_ptr[c + 1]; ++l) {
+      const int64_t q = cell_list[l] >> 3;
+      const int k = (int)(cell_list[l] & 7);
+      const int64_t base = cell_of_point[q];
+      const int64_t b3[3] = {base % gx, (base / gx) % gy, base / (gx * gy)};
+      const int64_t g3[3] = {gx, gy, gz};
+      const double l3[3] = {lx, ly, lz};
+      const int8_t cl = clamp[q];
+      double w = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        const double t = (cl & (1 << (2 * d))) ? 0.0 : (cl & (2 << (2 * d))) ? 1.0
+                                                     : pts[3 * q + d] * g3[d] / l3[d] - 0.5 - (double)b3[d];
+        w *= ((k >> d) & 1) ? t : 1.0 - t;
+      }
+      acc = fma(w, g_nodal[q], acc);
+    }
+    out[c] = accumulate ? out[c] + acc : acc;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // misfit (deterministic two-pass reduction)
 // ---------------------------------------------------------------------------
@@ -817,12 +1137,16 @@ static int pow2_floor(int v) {
 // Small fronts (s <= kWarpS, b <= kWarpB) are warp tasks: one warp does every row.
 static constexpr int kWarpS = 8, kWarpB = 32;
 static bool warp_front(const TreeNodeDev& r) { return r.s <= kWarpS && r.b <= kWarpB; }
-// staging area of one warp task: vectors (s + b) B plus the factors s (s + b)
-size_t solve_warp_doubles(int B) { return (size_t)(kWarpS + kWarpB) * B + (size_t)kWarpS * (kWarpS + kWarpB); }
-// staging area of a block task (see stage_forward / stage_backward)
+// staging area of one warp task: vectors (s + b) B, the factors s (s + b) and the node
+// ids or source rows (at most 2 (s + b) int32)
+size_t solve_warp_doubles(int B) {
+  return (size_t)(kWarpS + kWarpB) * (B + 1) + (size_t)kWarpS * (kWarpS + kWarpB);
+}
+// staging area of a block task (the layouts of fwd_layout / bwd_layout)
 static size_t block_task_doubles(const Task& t, int B, bool fwd) {
   const size_t rows = (size_t)(t.r1 - t.r0);
-  return fwd ? (size_t)t.s * B + rows * t.s : (size_t)(t.s + t.b) * B + rows * (t.s + t.b);
+  return fwd ? (t.s + rows) * B + rows * t.s + (t.s + rows)
+             : (size_t)(t.s + t.b) * B + rows * (t.s + t.b) + (t.b + rows + 1) / 2;
 }
 
 // B shots, `grid` blocks.  Block tasks of a level take a power-of-two number of rows
@@ -843,7 +1167,7 @@ int build_level_tasks(const Model& md, LevelTasks& lt, int B, int grid) {
     const TreeNodeDev& r = t.nodes[nd];
     Task tk;
     tk.node = nd; tk.r0 = r0; tk.r1 = r1; tk.ksplit = ks;
-    tk.s = r.s; tk.b = r.b; tk.leaf = r.elem >= 0 ? 1 : 0; tk.pad = 0;
+    tk.s = r.s; tk.b = r.b; tk.leaf = r.elem >= 0 ? 1 : 0; tk.pad = t.level_of[nd];   // height: the trace's phase
     tk.sep_off = r.sep_off; tk.bnd_off = r.bnd_off; tk.map_off = r.map_off; tk.X_off = r.X_off;
     return tk;
   };
@@ -1181,7 +1505,8 @@ int Stepper::init() {
   s_smem = sizeof(double) * std::max(lt->block_doubles, 8 * solve_warp_doubles(B));
   if (s_smem > 200 * 1024) return fail(SBFWI_EUNSUPPORTED, "solve staging area exceeds shared memory");
   for (const void* f : {(const void*)solve_forward_kernel, (const void*)solve_backward_kernel,
-                        (const void*)solve_persistent_kernel, (const void*)solve_flow_kernel})
+                        (const void*)solve_persistent_kernel, (const void*)solve_flow_kernel<false>,
+                        (const void*)solve_flow_kernel<true>})
     if (s_smem > 48 * 1024) SBFWI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_smem));
 
   ea.nb = nb; ea.n = n; ea.B = B; ea.E = E;
@@ -1219,6 +1544,7 @@ int Stepper::init() {
   sa.ysep = rb.ysep.as<double>(); sa.ybnd = rb.ybnd.as<double>(); sa.x = rb.x.as<double>();
   sa.nb = nb; sa.B = B;
   sa.warp_doubles = (int)solve_warp_doubles(B);
+  sa.bdiv = B >= 2 ? (unsigned)((1ULL << 32) / (unsigned long long)B + 1ULL) : 0u;
 
   // one cooperative persistent launch per time step for the whole tree, unless the
   // device cannot launch cooperatively or SBFWI_SOLVE=levels asks for one launch per level
@@ -1258,7 +1584,7 @@ int Stepper::init() {
   }
   if (flow) {
     int per_sm_flow = 0;
-    SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, solve_flow_kernel, 256, s_smem));
+    SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, solve_flow_kernel<true>, 256, s_smem));
     if (per_sm_flow < 1) return fail(SBFWI_EUNSUPPORTED, "the dataflow solve does not fit on an SM");
     const int T = lt->nodes;
     const size_t cb = ((sizeof(unsigned) * 2 * (size_t)T + 15) / 16) * 16;
@@ -1272,6 +1598,8 @@ int Stepper::init() {
     fa.claim = reinterpret_cast<unsigned long long*>(flow_counters.as<char>() + cb);
     fa.status = pstatus.as<int>();
     fa.budget = 4000000000LL;
+    fa.levels = md.mesh->tree.levels;
+    fa.trace = nullptr;
     p_grid = std::max(1, std::min(per_sm_flow, 4) * sms);    // every block co-resident (cooperative launch)
     flow_gen = 0;
   }
@@ -1468,9 +1796,11 @@ int Stepper::solve() {
   if (flow) {
     ++flow_gen;
     fa.gen = flow_gen;
+    fa.trace = prof.flow_trace(2 * t.levels, st);
     fa.base = (unsigned long long)(flow_gen - 1) * (unsigned long long)(fa.n_items + p_grid);
     void* kargs[] = {&fa};
-    int rc = launch_solve((const void*)solve_flow_kernel, (unsigned)p_grid, kargs, true);
+    int rc = launch_solve(fa.trace ? (const void*)solve_flow_kernel<true> : (const void*)solve_flow_kernel<false>,
+                          (unsigned)p_grid, kargs, true);
     if (rc) return rc;
     prof.count(kPhaseSolve);
   } else if (persistent) {
@@ -1746,7 +2076,7 @@ namespace sbfwi {
 static int emit_gradient(Model& md, const double* g_lib, double* grad, int mem, bool accumulate, cudaStream_t st) {
   const Mesh& msh = *md.mesh;
   const bool grid = md.rho_kind == SBFWI_RHO_GRID;
-  const int64_t nout = grid ? md.gx * md.gy : msh.n_nodal_api;
+  const int64_t nout = grid ? md.gx * md.gy * (msh.dim == 3 ? md.gz : 1) : msh.n_nodal_api;
   DevBuf gout;
   double* dst = nullptr;
   if (mem == SBFWI_MEM_DEVICE) dst = grad;
@@ -1756,7 +2086,14 @@ static int emit_gradient(Model& md, const double* g_lib, double* grad, int mem, 
     if (accumulate) SBFWI_CUDA(cudaMemcpyAsync(dst, grad, sizeof(double) * nout, cudaMemcpyHostToDevice, st));
   }
   const unsigned gb = (unsigned)std::min<int64_t>((nout + 255) / 256, 152 * 8);
-  if (grid) {
+  if (grid && msh.dim == 3) {
+    // the transpose of the trilinear map of the fine grid
+    const MeshDevice& mdev = md.dev();
+    grid_transpose3d_kernel<<<gb, 256, 0, st>>>(g_lib, md.pts_hi.as<double>(), mdev.cell.as<int32_t>(),
+                                                mdev.clamp.as<int8_t>(), mdev.cell_ptr.as<int64_t>(),
+                                                mdev.cell_list.as<int64_t>(), md.gx, md.gy, md.gz, md.lx, md.ly,
+                                                md.lz, dst, accumulate ? 1 : 0);
+  } else if (grid) {
     // the transpose of the bilinear map of the fine grid
     const MeshDevice& mdev = md.dev();
     grid_transpose_kernel<<<gb, 256, 0, st>>>(g_lib, md.pts_hi.as<double>(), mdev.cell.as<int32_t>(),
@@ -1783,27 +2120,37 @@ using namespace sbfwi;
 extern "C" {
 
 static int set_model_impl(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
-                          int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
-                          void* stream, bool lfe);
+                          int64_t gx, int64_t gy, int64_t gz, double lx, double ly, double lz, double dt, double beta,
+                          double gamma, int mem, void* stream, bool lfe, int dim);
 
 int sbfwi_set_model(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
                     int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
                     void* stream) {
-  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, lx, ly, dt, beta, gamma, mem, stream, false);
+  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, 1, lx, ly, 1.0, dt, beta, gamma, mem, stream, false, 2);
 }
 
 int sbfwi_set_model_lfe(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
                         int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
                         void* stream) {
-  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, lx, ly, dt, beta, gamma, mem, stream, true);
+  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, 1, lx, ly, 1.0, dt, beta, gamma, mem, stream, true, 2);
+}
+
+int sbfwi_set_model3d(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
+                      int64_t gx, int64_t gy, int64_t gz, double lx, double ly, double lz, double dt, double beta,
+                      double gamma, int mem, void* stream) {
+  if (rho_kind == SBFWI_RHO_GRID && (gz < 2 || !(lz > 0))) return fail(SBFWI_EINVAL, "grid density needs gz >= 2 and lz > 0");
+  return set_model_impl(out, mesh, c, rho, rho_kind, gx, gy, gz, lx, ly, lz, dt, beta, gamma, mem, stream, false, 3);
 }
 
 static int set_model_impl(sbfwi_model** out, const sbfwi_mesh* mesh, double c, const double* rho, int rho_kind,
-                          int64_t gx, int64_t gy, double lx, double ly, double dt, double beta, double gamma, int mem,
-                          void* stream, bool lfe) {
+                          int64_t gx, int64_t gy, int64_t gz, double lx, double ly, double lz, double dt, double beta,
+                          double gamma, int mem, void* stream, bool lfe, int dim) {
   if (!out) return fail(SBFWI_EINVAL, "out is NULL");
   *out = nullptr;
   if (!mesh || !rho) return fail(SBFWI_EINVAL, "NULL argument");
+  if (mesh->dim != dim)
+    return fail(SBFWI_EINVAL, dim == 3 ? "sbfwi_set_model3d needs a mesh from sbfwi_build_mesh3d"
+                                       : "a mesh from sbfwi_build_mesh3d needs sbfwi_set_model3d");
   if (!(c > 0) || !(dt > 0) || !(beta > 0) || !(gamma >= 0)) return fail(SBFWI_EINVAL, "need c > 0, dt > 0, beta > 0, gamma >= 0");
   if (rho_kind != SBFWI_RHO_GRID && rho_kind != SBFWI_RHO_NODAL) return fail(SBFWI_EINVAL, "unknown rho_kind");
   if (rho_kind == SBFWI_RHO_GRID && (gx < 2 || gy < 2 || !(lx > 0) || !(ly > 0)))
@@ -1818,7 +2165,7 @@ static int set_model_impl(sbfwi_model** out, const sbfwi_mesh* mesh, double c, c
   md->a2 = 1.0 / (2.0 * beta) - 1.0;
   md->c1 = dt * (1.0 - gamma);
   md->c2 = dt * gamma;
-  md->rho_kind = rho_kind; md->gx = gx; md->gy = gy; md->lx = lx; md->ly = ly;
+  md->rho_kind = rho_kind; md->gx = gx; md->gy = gy; md->gz = gz; md->lx = lx; md->ly = ly; md->lz = lz;
   md->lfe = lfe;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc = setup_model(*md, *mesh, rho, mem, st);
@@ -1837,6 +2184,8 @@ void sbfwi_destroy_model(sbfwi_model* m) { delete m; }
 int sbfwi_set_kernel_terms(sbfwi_model* m, int terms) {
   if (!m) return fail(SBFWI_EINVAL, "model is NULL");
   if (terms != SBFWI_TERMS_VELOCITY && terms != SBFWI_TERMS_FULL) return fail(SBFWI_EINVAL, "unknown kernel terms");
+  if (terms == SBFWI_TERMS_FULL && m->mesh->dim == 3)
+    return fail(SBFWI_EUNSUPPORTED, "the full kernel's gradient term is not built for 3-D meshes");
   m->kernel_terms = terms;
   return SBFWI_OK;
 }
@@ -1846,6 +2195,8 @@ int sbfwi_set_gradient_mode(sbfwi_model* m, int mode) {
   if (mode != SBFWI_GRAD_KERNEL && mode != SBFWI_GRAD_EXACT) return fail(SBFWI_EINVAL, "unknown gradient mode");
   if (mode == SBFWI_GRAD_EXACT && m->lfe)
     return fail(SBFWI_EUNSUPPORTED, "the exact adjoint is not built for the comparison method");
+  if (mode == SBFWI_GRAD_EXACT && m->mesh->dim == 3)
+    return fail(SBFWI_EUNSUPPORTED, "the exact adjoint is not built for 3-D meshes");
   m->grad_mode = mode;
   return SBFWI_OK;
 }

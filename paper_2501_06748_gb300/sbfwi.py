@@ -48,6 +48,13 @@ def _load():
     lib.sbfwi_version.restype = ctypes.c_int
     lib.sbfwi_build_mesh.argtypes = [P(VP), pd, I64, pi64, pi64, I64, pd, I64, I32, I32, D]
     lib.sbfwi_mesh_info.argtypes = [VP, pi64]
+    lib.sbfwi_build_mesh3d.argtypes = [P(VP), pd, ctypes.c_int64, pi64, pi64, ctypes.c_int64, pd, ctypes.c_int64,
+                                       I32, I32, ctypes.c_double]
+    lib.sbfwi_build_mesh3d.restype = ctypes.c_int
+    lib.sbfwi_set_model3d.argtypes = [P(VP), VP, ctypes.c_double, VP, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, VP]
+    lib.sbfwi_set_model3d.restype = ctypes.c_int
     lib.sbfwi_destroy_mesh.argtypes = [VP]
     lib.sbfwi_destroy_mesh.restype = None
     lib.sbfwi_set_model.argtypes = [P(VP), VP, D, VP, ctypes.c_int, I64, I64, D, D, D, D, D, ctypes.c_int, VP]
@@ -66,6 +73,8 @@ def _load():
     lib.sbfwi_profile_read.argtypes = [pd, pi64, pi64, ctypes.c_int]
     lib.sbfwi_profile_solve_levels.argtypes = [pd, I32, P(I32), pi64, ctypes.c_int]
     lib.sbfwi_profile_solve_levels.restype = ctypes.c_int
+    lib.sbfwi_profile_solve_flow.argtypes = [pd, I32, P(I32), pi64, ctypes.c_int]
+    lib.sbfwi_profile_solve_flow.restype = ctypes.c_int
     lib.sbfwi_release_cache.argtypes = []
     lib.sbfwi_release_cache.restype = ctypes.c_int
     lib.sbfwi_lfe_element_matrices.argtypes = [pd, pd, pd, pd, I32, pd, pd]
@@ -135,6 +144,22 @@ def profile_solve_levels(reset: bool = False):
     return {"wall": us[:k].copy(), "busy_max": us[k:2 * k].copy(), "busy_sum": us[2 * k:3 * k].copy()}, int(steps.value)
 
 
+def profile_solve_flow(reset: bool = False):
+    """Per-phase timing (us) of the dataflow global solve while profiling was on (phases:
+    forward levels leaves -> root, then backward levels root -> leaves).  Returns (dict with
+    'done' [2L] time from the launch's start to the phase's last item finishing, 'exec' [2L]
+    mean item execution time after its inputs were ready, 'wait' [2L] mean time an item
+    waited for its inputs, 'items' [2L] items per solve), solves recorded)."""
+    cap = 512
+    us = np.zeros(cap)
+    n = ctypes.c_int32(0)
+    steps = ctypes.c_int64(0)
+    _check(_lib.sbfwi_profile_solve_flow(_dptr(us), cap, ctypes.byref(n), ctypes.byref(steps), 1 if reset else 0))
+    k = n.value // 4
+    return ({"done": us[:k].copy(), "exec": us[k:2 * k].copy(), "wait": us[2 * k:3 * k].copy(),
+             "items": us[3 * k:4 * k].copy()}, int(steps.value))
+
+
 def _is_torch_cuda(x) -> bool:
     return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and bool(x.is_cuda)
 
@@ -188,10 +213,16 @@ def _same_mem(*args):
 
 class Mesh:
     def __init__(self, node_xy, elem_ptr, line_nodes, centre_xy, p, n_r, xi0=1e-3):
+        """2-D: node_xy [N][2], line elements [L][p+1]; 3-D: node_xy [N][3] and faces
+        [F][(p+1)^2] (sbfwi_build_mesh3d), told apart by the coordinate count."""
         xy, ep, ln, ct = _f64_host(node_xy), _i64_host(elem_ptr), _i64_host(line_nodes), _f64_host(centre_xy)
+        self.dim = int(xy.shape[1])
+        if self.dim not in (2, 3) or ct.shape[1] != self.dim:
+            raise ValueError("node and centre coordinates must both be 2-D or both 3-D")
         h = ctypes.c_void_p()
-        _check(_lib.sbfwi_build_mesh(ctypes.byref(h), _dptr(xy), xy.shape[0], _iptr(ep), _iptr(ln), ln.shape[0],
-                                     _dptr(ct), ct.shape[0], int(p), int(n_r), float(xi0)))
+        build = _lib.sbfwi_build_mesh3d if self.dim == 3 else _lib.sbfwi_build_mesh
+        _check(build(ctypes.byref(h), _dptr(xy), xy.shape[0], _iptr(ep), _iptr(ln), ln.shape[0],
+                     _dptr(ct), ct.shape[0], int(p), int(n_r), float(xi0)))
         self._h = h
         info = np.zeros(8, dtype=np.int64)
         _check(_lib.sbfwi_mesh_info(h, _iptr(info)))
@@ -200,7 +231,9 @@ class Mesh:
 
     @classmethod
     def from_inputs(cls, mesh, n_r, xi0=1e-3):
-        """From an ``sbfwi_inputs`` mesh object."""
+        """From an ``sbfwi_inputs`` mesh object (2-D, or 3-D from ``sbfwi_inputs.mesh3d``)."""
+        if getattr(mesh, "dim", 2) == 3:
+            return cls(mesh.node_xyz, mesh.elem_ptr, mesh.face_nodes, mesh.centre_xyz, mesh.p, n_r, xi0)
         return cls(mesh.node_xy, mesh.elem_ptr, mesh.line_nodes, mesh.centre_xy, mesh.p, n_r, xi0)
 
     def __del__(self):
@@ -211,18 +244,38 @@ class Mesh:
 
 
 class Model:
-    def __init__(self, mesh: Mesh, c, rho, dt, beta=0.25, gamma=0.5, rho_kind=RHO_GRID, lx=1.0, ly=1.0, lfe=False):
+    def __init__(self, mesh: Mesh, c, rho, dt, beta=0.25, gamma=0.5, rho_kind=RHO_GRID, lx=1.0, ly=1.0, lfe=False,
+                 lz=1.0):
         """``lfe=True``: the paper's comparison method (low-frequency expansion) instead of
-        the radial finite differences."""
+        the radial finite differences.  On a 3-D mesh a grid density is [gz][gy][gx] on
+        [0,lx]x[0,ly]x[0,lz] (sbfwi_set_model3d)."""
         r = _Arr(rho)
-        gy, gx = (r.obj.shape if rho_kind == RHO_GRID else (0, 0))
         h = ctypes.c_void_p()
-        setup = _lib.sbfwi_set_model_lfe if lfe else _lib.sbfwi_set_model
-        _check(setup(ctypes.byref(h), mesh._h, float(c), r.ptr, int(rho_kind), int(gx), int(gy),
-                                    float(lx), float(ly), float(dt), float(beta), float(gamma), r.mem, r.stream))
+        dim = getattr(mesh, "dim", 2)
+        if dim == 3:
+            if lfe:
+                raise ValueError("the comparison method is built for 2-D meshes only")
+            gz, gy, gx = (r.obj.shape if rho_kind == RHO_GRID else (0, 0, 0))
+            _check(_lib.sbfwi_set_model3d(ctypes.byref(h), mesh._h, float(c), r.ptr, int(rho_kind), int(gx), int(gy),
+                                          int(gz), float(lx), float(ly), float(lz), float(dt), float(beta),
+                                          float(gamma), r.mem, r.stream))
+        else:
+            gz = 1
+            gy, gx = (r.obj.shape if rho_kind == RHO_GRID else (0, 0))
+            setup = _lib.sbfwi_set_model_lfe if lfe else _lib.sbfwi_set_model
+            _check(setup(ctypes.byref(h), mesh._h, float(c), r.ptr, int(rho_kind), int(gx), int(gy),
+                         float(lx), float(ly), float(dt), float(beta), float(gamma), r.mem, r.stream))
         self._h = h
         self.mesh = mesh                 # keeps the mesh alive for the model's lifetime
-        self.rho_kind, self.gx, self.gy, self.dt, self.lfe = rho_kind, int(gx), int(gy), float(dt), bool(lfe)
+        self.rho_kind, self.gx, self.gy, self.gz, self.dt, self.lfe = (rho_kind, int(gx), int(gy), int(gz), float(dt),
+                                                                       bool(lfe))
+
+    @property
+    def grad_shape(self):
+        """Shape of the gradient on the model's parameter layout."""
+        if self.rho_kind != RHO_GRID:
+            return (self.mesh.n_nodal,)
+        return (self.gz, self.gy, self.gx) if getattr(self.mesh, "dim", 2) == 3 else (self.gy, self.gx)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -287,7 +340,7 @@ class Session:
             out = torch.empty((self.rec.size, K), dtype=torch.float64, device=self.device)
         else:
             m = self.model
-            shape = (m.gy, m.gx) if m.rho_kind == RHO_GRID else (m.mesh.n_nodal,)
+            shape = m.grad_shape
             out = torch.zeros(shape, dtype=torch.float64, device=self.device)
         _check(_lib.sbfwi_session_collect(self._h, int(slot), ctypes.c_void_p(out.data_ptr()), MEM_DEVICE))
         return out
@@ -368,7 +421,7 @@ def adjoint_gradient(model: Model, state: FwdState, residual, mode=GRAD_KERNEL, 
         mode = int(mode) | GRAD_ACCUMULATE
     r = _Arr(residual)
     if grad_out is None:
-        shape = (model.gy, model.gx) if model.rho_kind == RHO_GRID else (model.mesh.n_nodal,)
+        shape = model.grad_shape
         if r.mem == MEM_DEVICE:
             import torch
             grad_out = torch.zeros(shape, dtype=torch.float64, device=r.obj.device)

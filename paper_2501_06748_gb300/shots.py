@@ -72,7 +72,7 @@ def misfit_and_gradient(model, src_nodes, wavelets, rec_nodes, observed, shots_p
     world = dist.get_world_size(group) if dist else 1
     src = np.asarray(src_nodes, dtype=np.int64)
     mine = shard(len(src), rank, world)
-    shape = (model.gy, model.gx) if model.rho_kind == sbfwi.RHO_GRID else (model.mesh.n_nodal,)
+    shape = model.grad_shape
     if hasattr(wavelets, "is_cuda") and wavelets.is_cuda:
         import torch
         grad = torch.zeros(shape, dtype=torch.float64, device=wavelets.device)

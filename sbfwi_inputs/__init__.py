@@ -19,11 +19,12 @@ from .mesh import (StructuredMesh, structured_mesh, boundary_nodes, nearest_node
 from .fields import flawed_density_circle, flawed_density_ellipses
 from .wavelet import ricker, sine_burst
 from .configs import (Workload, tiny_workload, size_workload, diff_workload, paper_workload, batching_workload,
-                      workload_by_name)
+                      solid_workload, workload_by_name)
 
 __all__ = [
     "StructuredMesh", "structured_mesh", "boundary_nodes", "nearest_node", "QuadtreeMesh", "quadtree_mesh",
     "min_spacing", "PolygonMesh", "voronoi_mesh", "batching_workload",
     "flawed_density_circle", "flawed_density_ellipses", "ricker", "sine_burst",
-    "Workload", "tiny_workload", "size_workload", "diff_workload", "paper_workload", "workload_by_name",
+    "Workload", "tiny_workload", "size_workload", "diff_workload", "paper_workload", "solid_workload",
+    "workload_by_name",
 ]

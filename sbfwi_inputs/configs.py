@@ -230,6 +230,38 @@ def batching_workload(index: int, seed: int = 4, base: int = 16, levels: int = 2
                     dt, K, f0, info={"flaws": finfo, "seed": seed + index, "base": base, "levels": levels})
 
 
+def solid_workload(nx: int = 16, p: int = 2, n_r: int = 16, n_shots: int = 8, K: int = 500, grid: int = 64,
+                   n_rec: int = 32, seed: int = 5, flaw_factor: float = FLAW_FACTOR) -> Workload:
+    """A 3-D recipe: the unit cube in nx^3 hexahedral S-elements with faces of order p
+    (n_b = 26 at p = 2), N_r radial points, one spherical flaw on a grid^3 density grid,
+    n_shots Ricker sources spread over the top face (z = 1), receivers on the bottom face
+    and the four sides (nearest nodes to seeded points), f0 and dt from the smallest node
+    spacing as in the 2-D recipes.  ``gx``/``gy`` hold the grid size; the density arrays are
+    [grid][grid][grid]."""
+    from .mesh3d import structured_mesh3d, boundary_nodes3d, nearest_node3d, flawed_density_sphere
+    mesh = structured_mesh3d(nx, nx, nx, p)
+    c = 1.0
+    s_min = 1.0 / (nx * p)
+    f0, dt = c / (10.0 * s_min), 0.5 * s_min / c
+    rho_true, finfo = flawed_density_sphere(grid, grid, grid, radius=0.15, factor=flaw_factor, seed=seed)
+    rho_start = np.ones_like(rho_true)
+    rng = np.random.default_rng(seed)
+    top = boundary_nodes3d(mesh, "z1")
+    k = int(np.ceil(np.sqrt(n_shots)))
+    pts = [((i + 0.5) / k, (j + 0.5) / k, 1.0) for j in range(k) for i in range(k)][:n_shots]
+    srcs = [nearest_node3d(mesh, top, q) for q in pts]
+    recs = []
+    for side in ("z0", "x0", "x1", "y0", "y1"):
+        ids = boundary_nodes3d(mesh, side)
+        for _ in range(max(1, n_rec // 5)):
+            q = mesh.node_xyz[rng.choice(ids)]
+            recs.append(int(nearest_node3d(mesh, ids, q)))
+    recs = [r for r in dict.fromkeys(recs) if r not in srcs]
+    wav = np.stack([ricker(f0, dt, K) for _ in srcs])
+    return Workload("solid", mesh, n_r, c, grid, grid, rho_true, rho_start, np.array(srcs, dtype=np.int64), wav,
+                    np.array(recs, dtype=np.int64), dt, K, f0, info={"flaw": finfo, "seed": seed, "grid": grid})
+
+
 def workload_by_name(name: str, **kw) -> Workload:
     if name == "tiny":
         return tiny_workload(**kw)
@@ -239,4 +271,6 @@ def workload_by_name(name: str, **kw) -> Workload:
         return diff_workload(**kw)
     if name == "paper":
         return paper_workload(**kw)
+    if name == "solid":
+        return solid_workload(**kw)
     raise KeyError(name)

@@ -176,3 +176,33 @@ def test_lfe_refuses_an_element_whose_stable_subspace_has_the_wrong_rank(binding
     with pytest.raises(binding.SbfwiError) as ei:
         binding.lfe_element_matrices(E0, E1, E2 + 0.1 * np.abs(E2).max() * np.eye(nb), M0)
     assert ei.value.code == binding.ESINGULAR and "n_b - 1" in str(ei.value)
+
+
+def test_mesh3d_info_and_validation(binding):
+    """sbfwi_build_mesh3d (host code): node and boundary-node counts of hexahedral
+    S-elements, and the checks on face orientation, closure and size."""
+    from sbfwi_inputs.mesh3d import structured_mesh3d
+    m = structured_mesh3d(3, 2, 2, 2)
+    M = binding.Mesh.from_inputs(m, 6)
+    assert (M.dim, M.n_elem, M.n_nodes, M.n_b) == (3, 12, 7 * 5 * 5 - 12, 26)
+    assert M.n_nodal == 5 * 26 * 12 + M.n_nodes and M.tree_levels >= 4
+    M1 = binding.Mesh.from_inputs(structured_mesh3d(2, 2, 2, 1), 5)
+    assert (M1.n_nodes, M1.n_b) == (27, 8)
+    args = dict(node_xy=m.node_xyz, elem_ptr=m.elem_ptr, line_nodes=m.face_nodes, centre_xy=m.centre_xyz, p=2, n_r=6)
+    # a face turned inward (eta and zeta swapped): det J_b < 0
+    bad = m.face_nodes.copy()
+    bad[0] = bad[0].reshape(3, 3).T.ravel()
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.Mesh(**{**args, "line_nodes": bad})
+    assert ei.value.code == binding.EINVAL and "det J_b" in str(ei.value)
+    # a missing face: the surface is not closed
+    ep = m.elem_ptr.copy()
+    ep[1:] -= 1
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.Mesh(**{**args, "line_nodes": m.face_nodes[1:], "elem_ptr": ep})
+    assert ei.value.code == binding.EINVAL and "close" in str(ei.value)
+    # p = 3 hexahedra have 56 boundary nodes, above the 40 the kernels take
+    m3 = structured_mesh3d(1, 1, 1, 3)
+    with pytest.raises(binding.SbfwiError) as ei:
+        binding.Mesh.from_inputs(m3, 5)
+    assert ei.value.code == binding.EUNSUPPORTED
