@@ -120,6 +120,9 @@ struct MeshDevice {
   DevBuf tree_nodes, sep_nodes, bnd_nodes, map0, map1, src0, src1, level_nodes;
   std::vector<int64_t> level_start;
   DevBuf F, U;                       // factorisation workspaces
+  DevBuf fgemm;                      // front product tiles {node, kind, r0, c0} (front_gemm_kernel)
+  std::vector<int64_t> fgemm_start;  // per level: first G/C tile, first U tile, end
+  std::vector<int8_t> fgemm_level;   // per level: products by tiles (1) or in front_factor_kernel (0)
   // bilinear map of one fine grid: base cell and clamping of every nodal point, and
   // the transpose as CSR grid cell -> (point*4 + corner) sorted by point
   // (3-D meshes: trilinear, point*8 + corner)

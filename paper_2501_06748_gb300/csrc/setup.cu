@@ -20,6 +20,7 @@
 
 #include "dd.cuh"
 #include "internal.h"
+#include "sync.cuh"
 #include "prof.h"
 
 namespace sbfwi {
@@ -841,6 +842,8 @@ struct FactorArgs {
   double* U;                    // workspace update matrices
   double* factors;
   int* status;
+  int products;                 // 1: front_factor_kernel also forms G, C and U (else front_gemm_kernel)
+  int big_s;                    // > 0: fronts with s >= big_s are inverted by front_invert_grid_kernel
 };
 
 __global__ void front_assemble_kernel(FactorArgs a) {
@@ -904,6 +907,7 @@ __global__ void front_factor_kernel(FactorArgs a) {
   double* C = G + (int64_t)s * b;              // b x s
   double* U = a.U + nd.U_off;                  // b x b
   const int tid = threadIdx.x, nt = blockDim.x;
+  if (a.big_s > 0 && s >= a.big_s) return;     // inverted over the whole grid; products by tiles
   if (s > 0) {
     // X = F11^{-1}: Gauss-Jordan on [F11 | I] with row pivoting inside F11
     for (int64_t t = tid; t < (int64_t)s * s; t += nt) X[t] = ((t / s) == (t % s)) ? 1.0 : 0.0;
@@ -944,6 +948,7 @@ __global__ void front_factor_kernel(FactorArgs a) {
         __syncthreads();
       }
     }
+    if (!a.products) return;
     // G = X F12 (s x b), C = F21 X (b x s)
     for (int64_t t = tid; t < (int64_t)s * b; t += nt) {
       const int r = (int)(t / b), c = (int)(t - (int64_t)r * b);
@@ -959,12 +964,165 @@ __global__ void front_factor_kernel(FactorArgs a) {
     }
     __syncthreads();
   }
+  if (!a.products) return;
   // update matrix U = F22 - C F12 (b x b)
   for (int64_t t = tid; t < (int64_t)b * b; t += nt) {
     const int r = (int)(t / b), c = (int)(t - (int64_t)r * b);
     double acc = F[(int64_t)(s + r) * f + s + c];
     for (int k = 0; k < s; ++k) acc = fma(-C[(int64_t)r * s + k], F[(int64_t)k * f + s + c], acc);
     U[t] = acc;
+  }
+}
+
+// X = F11^{-1} of one large front by the Gauss-Jordan elimination of front_factor_kernel
+// spread over the whole grid (cooperative launch, every block co-resident): per pivot, block
+// 0 picks the pivot row (largest |entry|, the smallest row on ties, as block_pivot),
+// swaps and normalises it; after a grid barrier every block eliminates the pivot column
+// from its rows (rows blockIdx.x + k gridDim.x), reading the column before any of its
+// entries change; a second barrier ends the step.  Each entry sees the operations of the
+// one-block elimination in the same order, so X is the same bits.  Values written by other
+// blocks are read through L2 (__ldcg).  Every barrier wait is bounded (status).
+struct InvertArgs {
+  FactorArgs f;
+  int32_t node;
+  unsigned* bar;              // [2] barrier count and generation, zero at launch
+  long long budget;           // clock cycles per barrier wait
+};
+
+__global__ void __launch_bounds__(512) front_invert_grid_kernel(InvertArgs ia) {
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ double colv[64];
+  const FactorArgs& a = ia.f;
+  const TreeNodeDev nd = a.nodes[ia.node];
+  const int s = nd.s, f = nd.s + nd.b;
+  double* F = a.F + nd.F_off;
+  double* X = a.factors + nd.X_off;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * nt + tid; t < (int64_t)s * s; t += (int64_t)gridDim.x * nt)
+    X[t] = ((t / s) == (t % s)) ? 1.0 : 0.0;
+  if (!grid_barrier(ia.bar, ia.bar + 1, a.status, ia.budget)) return;
+  for (int k = 0; k < s; ++k) {
+    if (blockIdx.x == 0) {
+      double bv = -1.0;
+      int bi = s;
+      for (int r = k + tid; r < s; r += nt) {
+        const double v = fabs(__ldcg(F + (int64_t)r * f + k));
+        if (v > bv) { bv = v; bi = r; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+      }
+      if ((tid & 31) == 0) { redv[tid >> 5] = bv; redi[tid >> 5] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        for (int j = 1; j < nt / 32; ++j)
+          if (redv[j] > redv[0] || (redv[j] == redv[0] && redi[j] < redi[0])) { redv[0] = redv[j]; redi[0] = redi[j]; }
+      }
+      __syncthreads();
+      const int pr = (redv[0] > 0.0 && isfinite(redv[0])) ? redi[0] : -1;
+      if (pr < 0) {
+        if (tid == 0) atomicCAS(a.status, 0, SBFWI_ESINGULAR);
+      } else {
+        if (pr != k)
+          for (int c = tid; c < s; c += nt) {
+            const double t1 = __ldcg(F + (int64_t)k * f + c), t2 = __ldcg(F + (int64_t)pr * f + c);
+            const double x1 = __ldcg(X + (int64_t)k * s + c), x2 = __ldcg(X + (int64_t)pr * s + c);
+            F[(int64_t)k * f + c] = t2; F[(int64_t)pr * f + c] = t1;
+            X[(int64_t)k * s + c] = x2; X[(int64_t)pr * s + c] = x1;
+          }
+        __syncthreads();
+        const double pinv = 1.0 / __ldcg(F + (int64_t)k * f + k);
+        __syncthreads();
+        for (int c = tid; c < s; c += nt) {
+          F[(int64_t)k * f + c] = __ldcg(F + (int64_t)k * f + c) * pinv;
+          X[(int64_t)k * s + c] = __ldcg(X + (int64_t)k * s + c) * pinv;
+        }
+      }
+    }
+    if (!grid_barrier(ia.bar, ia.bar + 1, a.status, ia.budget)) return;
+    if (*(volatile int*)a.status != 0) return;        // a singular pivot: every block stops here
+    // this block's rows, in groups of up to 64: the pivot-column entries first, then the rows
+    for (int g0 = blockIdx.x; g0 < s; g0 += 64 * gridDim.x) {
+      for (int i = tid; i < 64; i += nt) {
+        const int r = g0 + i * gridDim.x;
+        colv[i] = (r < s && r != k) ? __ldcg(F + (int64_t)r * f + k) : 0.0;
+      }
+      __syncthreads();
+      for (int i = 0; i < 64; ++i) {
+        const int r = g0 + i * gridDim.x;
+        if (r >= s) break;
+        const double fr = colv[i];
+        if (fr == 0.0) continue;
+        for (int c = tid; c < s; c += nt) {
+          F[(int64_t)r * f + c] -= fr * __ldcg(F + (int64_t)k * f + c);
+          X[(int64_t)r * s + c] -= fr * __ldcg(X + (int64_t)k * s + c);
+        }
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(ia.bar, ia.bar + 1, a.status, ia.budget)) return;
+  }
+}
+
+constexpr int kGridInvertS = 192;     // separators from this size up are inverted over the whole grid
+
+// The products of front_factor_kernel as 32 x 32 output tiles spread over many blocks (a
+// level's large fronts would otherwise each keep one SM busy): item {node, kind, r0, c0},
+// kind 0: G = X F12 (s x b), 1: C = F21 X (b x s), 2: U = F22 - C F12 (b x b).  Every
+// output sums its terms in increasing k with fma, as the one-block loops do, so the factors
+// are the same bits whichever kernel forms them.
+__global__ void __launch_bounds__(256) front_gemm_kernel(FactorArgs a, const int4* items) {
+  __shared__ double As[32][33];
+  __shared__ double Bs[32][33];
+  const int4 it = items[blockIdx.x];
+  const TreeNodeDev nd = a.nodes[it.x];
+  const int s = nd.s, b = nd.b, f = s + b;
+  const double* F = a.F + nd.F_off;
+  double* X = a.factors + nd.X_off;
+  double* G = X + (int64_t)s * s;
+  double* C = G + (int64_t)s * b;
+  double* U = a.U + nd.U_off;
+  const int kind = it.y, r0 = it.z, c0 = it.w;
+  const int M = kind == 0 ? s : b, N = kind == 1 ? s : b;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double acc[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + ty + 8 * j, c = c0 + tx;
+    acc[j] = (kind == 2 && r < M && c < N) ? F[(int64_t)(s + r) * f + s + c] : 0.0;
+  }
+  for (int k0 = 0; k0 < s; k0 += 32) {
+    for (int t = threadIdx.x; t < 32 * 32; t += 256) {
+      const int i = t >> 5, j = t & 31;
+      const int r = r0 + i, k = k0 + j;          // A(r, k)
+      double av = 0.0;
+      if (r < M && k < s)
+        av = kind == 0 ? X[(int64_t)r * s + k] : kind == 1 ? F[(int64_t)(s + r) * f + k] : -C[(int64_t)r * s + k];
+      As[i][j] = av;
+      const int kb = k0 + i, c = c0 + j;         // B(k, c)
+      double bv = 0.0;
+      if (kb < s && c < N) bv = kind == 1 ? X[(int64_t)kb * s + c] : F[(int64_t)kb * f + s + c];
+      Bs[i][j] = bv;
+    }
+    __syncthreads();
+    const int kn = min(32, s - k0);
+    for (int kk = 0; kk < kn; ++kk) {
+      const double bv = Bs[kk][tx];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] = fma(As[ty + 8 * j][kk], bv, acc[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + ty + 8 * j, c = c0 + tx;
+    if (r >= M || c >= N) continue;
+    if (kind == 0) G[(int64_t)r * b + c] = acc[j];
+    else if (kind == 1) C[(int64_t)r * s + c] = acc[j];
+    else U[(int64_t)r * b + c] = acc[j];
   }
 }
 
@@ -1094,6 +1252,38 @@ static int ensure_mesh_device(const Mesh& m, cudaStream_t st) {
     all.insert(all.end(), t.nodes_at_level[l].begin(), t.nodes_at_level[l].end());
   }
   if ((rc = upload(d->level_nodes, all, st))) return rc;
+  // tiles of the front products for the levels with fewer fronts than SMs: per level
+  // [G and C tiles | U tiles], offsets fgemm_start[3l .. 3l+2]
+  {
+    int sms = 152;
+    int dev_id = 0;
+    if (cudaGetDevice(&dev_id) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    std::vector<int4> items;
+    for (int l = 0; l < t.levels; ++l) {
+      const bool tiled = (int)t.nodes_at_level[l].size() < sms;
+      d->fgemm_level.push_back(tiled ? 1 : 0);
+      d->fgemm_start.push_back((int64_t)items.size());
+      if (tiled)
+        for (int32_t nd : t.nodes_at_level[l]) {
+          const TreeNodeDev& r = t.nodes[nd];
+          if (r.s == 0 || r.b == 0) continue;
+          for (int r0 = 0; r0 < r.s; r0 += 32)
+            for (int c0 = 0; c0 < r.b; c0 += 32) items.push_back(make_int4(nd, 0, r0, c0));
+          for (int r0 = 0; r0 < r.b; r0 += 32)
+            for (int c0 = 0; c0 < r.s; c0 += 32) items.push_back(make_int4(nd, 1, r0, c0));
+        }
+      d->fgemm_start.push_back((int64_t)items.size());
+      if (tiled)
+        for (int32_t nd : t.nodes_at_level[l]) {
+          const TreeNodeDev& r = t.nodes[nd];
+          for (int r0 = 0; r0 < r.b; r0 += 32)
+            for (int c0 = 0; c0 < r.b; c0 += 32) items.push_back(make_int4(nd, 2, r0, c0));
+        }
+      d->fgemm_start.push_back((int64_t)items.size());
+    }
+    if (items.empty()) items.push_back(make_int4(0, 0, 0, 0));
+    if ((rc = upload(d->fgemm, items, st))) return rc;
+  }
   SBFWI_CUDA(d->F.alloc(sizeof(double) * std::max<int64_t>(t.F_total, 1)));
   SBFWI_CUDA(d->U.alloc(sizeof(double) * std::max<int64_t>(t.U_total, 1)));
   SBFWI_CUDA(cudaStreamSynchronize(st));     // host vectors above go out of scope
@@ -1325,8 +1515,7 @@ static int launch_element_setup(Model& md, const Mesh& m, const double* rho_hi, 
 }
 
 int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream_t st) {
-  const int nb = m.nb, n = m.n, p = m.p, L = m.L, pp = p + 1;
-  const int ng = (3 * p + 2) / 2;
+  const int nb = m.nb, n = m.n;
   const int64_t E = m.n_elem, N = m.n_nodes, np = m.n_nodal;
   md.nb = nb; md.n = n; md.E = E; md.N = N;
   int rc;
@@ -1456,12 +1645,45 @@ int setup_model(Model& md, const Mesh& m, const double* rho, int mem, cudaStream
     a.nodes = d.tree_nodes.as<TreeNodeDev>(); a.map0 = d.map0.as<int32_t>(); a.map1 = d.map1.as<int32_t>();
     a.S = md.S.as<double>(); a.nb = nb; a.F = d.F.as<double>(); a.U = d.U.as<double>();
     a.factors = md.factors.as<double>(); a.status = status.as<int>();
+    // the grid of the cooperative inversion: one block of 512 threads per SM, as many as fit
+    DevBuf inv_bar;
+    SBFWI_CUDA(inv_bar.alloc(2 * sizeof(unsigned)));
+    int inv_grid = 0;
+    {
+      int dev_id = 0, sms = 0, per_sm = 0;
+      SBFWI_CUDA(cudaGetDevice(&dev_id));
+      SBFWI_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+      SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, front_invert_grid_kernel, 512, 0));
+      inv_grid = std::max(1, std::min(per_sm, 1) * sms);
+    }
     for (int l = 0; l < t.levels; ++l) {
       a.level_nodes = d.level_nodes.as<int32_t>() + d.level_start[l];
       const unsigned cnt = (unsigned)t.nodes_at_level[l].size();
+      // the products go to the tiled kernel on levels with fewer fronts than SMs (one block
+      // per front would leave most SMs idle); levels with many small fronts keep them in
+      // front_factor_kernel
+      const int64_t gc0 = d.fgemm_start[3 * l], u0 = d.fgemm_start[3 * l + 1], u1 = d.fgemm_start[3 * l + 2];
+      a.products = d.fgemm_level[l] ? 0 : 1;
+      a.big_s = d.fgemm_level[l] ? kGridInvertS : 0;
       front_assemble_kernel<<<cnt, 256, 0, st>>>(a);
       front_factor_kernel<<<cnt, 512, 0, st>>>(a);
       prof.count(kPhaseSetup, 2);
+      if (a.big_s > 0)
+        for (int32_t v : t.nodes_at_level[l]) {
+          if (t.nodes[v].s < kGridInvertS) continue;
+          InvertArgs ia;
+          ia.f = a; ia.node = v; ia.bar = inv_bar.as<unsigned>(); ia.budget = 4000000000LL;
+          SBFWI_CUDA(cudaMemsetAsync(inv_bar.p, 0, inv_bar.bytes, st));
+          void* kargs[] = {&ia};
+          SBFWI_CUDA(cudaLaunchCooperativeKernel((const void*)front_invert_grid_kernel, dim3(inv_grid), dim3(512), kargs,
+                                                 0, st));
+          prof.count(kPhaseSetup);
+        }
+      if (!a.products) {
+        const int4* items = d.fgemm.as<int4>();
+        if (u0 > gc0) { front_gemm_kernel<<<(unsigned)(u0 - gc0), 256, 0, st>>>(a, items + gc0); prof.count(kPhaseSetup); }
+        if (u1 > u0) { front_gemm_kernel<<<(unsigned)(u1 - u0), 256, 0, st>>>(a, items + u0); prof.count(kPhaseSetup); }
+      }
       SBFWI_CUDA(cudaGetLastError());
     }
   }
