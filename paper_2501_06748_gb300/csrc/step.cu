@@ -1125,7 +1125,9 @@ static size_t block_task_doubles(const Task& t, int B, bool fwd) {
 // no task (their parents read f_hat directly).  Warp tasks are grouped so that a
 // level's items about fill the grid.
 int build_level_tasks(const Model& md, LevelTasks& lt, int B, int grid) {
-  const int rows_max = std::max(1, 256 / B);
+  // rows x shots <= 256 outputs per block task (one per thread); 512 on levels whose separators
+  // are at most 32 nodes (their factor rows are short, so the staging stays small)
+  const int rows_max = std::max(1, 256 / B), rows_max_short = std::max(1, 512 / B);
   const Tree& t = md.mesh->tree;
   const int L = t.levels;
   std::vector<Task> fwd, bwd;
@@ -1142,9 +1144,9 @@ int build_level_tasks(const Model& md, LevelTasks& lt, int B, int grid) {
   };
   auto group_for = [&](int n) { return std::max(1, std::min(8, (n + grid - 1) / std::max(grid, 1))); };
   // rows per block task and lanes per output for a dot product of length len
-  auto rows_for = [&](int64_t level_rows) {
+  auto rows_for = [&](int64_t level_rows, int cap) {
     const int64_t per = (level_rows + grid - 1) / std::max(grid, 1);
-    return std::min(rows_max, pow2_ceil((int)std::max<int64_t>(1, per)));
+    return std::min(cap, pow2_ceil((int)std::max<int64_t>(1, per)));
   };
   auto lanes_for = [&](int rows, int len) {
     return std::max(1, std::min({32, pow2_floor(std::max(1, 256 / (B * rows))), pow2_ceil(std::max(1, len))}));
@@ -1153,11 +1155,12 @@ int build_level_tasks(const Model& md, LevelTasks& lt, int B, int grid) {
     lt.fwd_start[l] = (int32_t)fwd.size();
     lt.bwd_start[l] = (int32_t)bwd.size();
     int64_t rows_f = 0, rows_b = 0;
+    int s_max = 0;
     for (int32_t nd : t.nodes_at_level[l]) {
       const TreeNodeDev& r = t.nodes[nd];
-      if (!warp_front(r)) { rows_f += r.b; rows_b += r.s; }
+      if (!warp_front(r)) { rows_f += r.b; rows_b += r.s; s_max = std::max(s_max, (int)r.s); }
     }
-    const int rf = rows_for(rows_f), rb = rows_for(rows_b);
+    const int rf = rows_for(rows_f, s_max <= 32 ? rows_max_short : rows_max), rb = rows_for(rows_b, rows_max);
     for (int32_t nd : t.nodes_at_level[l]) {
       const TreeNodeDev& r = t.nodes[nd];
       if (warp_front(r)) continue;
