@@ -456,11 +456,13 @@ def points_to_grid3d(g_points, points, gx, gy, gz, lx, ly, lz):
     return out.reshape(gz, gy, gx)
 
 
-def build_model3d(mesh, n_r, c, rho, dt, beta=0.25, gamma=0.5, xi0=1e-3, rho_kind="grid", static=False) -> Model:
+def build_model3d(mesh, n_r, c, rho, dt, beta=0.25, gamma=0.5, xi0=1e-3, rho_kind="grid", static=False,
+                  rho_mass_nodal=None) -> Model:
     """``build_model`` for a mesh of 3-D S-elements (``sbfwi_inputs.mesh3d``): nodal
     densities (trilinear map of a rho[gz, gy, gx] grid, or nodal), the 3-D coefficient
     matrices, the blocks of the 3-D radial equation, condensation and the global matrix.
-    The time loop, misfit and velocity-kernel adjoint of this module apply unchanged."""
+    The time loop, misfit and velocity-kernel adjoint of this module apply unchanged.
+    ``rho_mass_nodal`` (tests only) gives M0 its own nodal densities, as in ``build_model``."""
     from . import sbfem3d
     XP = sbfem.XP
     n = n_r - 1
@@ -485,11 +487,17 @@ def build_model3d(mesh, n_r, c, rho, dt, beta=0.25, gamma=0.5, xi0=1e-3, rho_kin
     n_int = int(int_ptr[-1])
     E = len(elements)
     Es = [np.zeros((E, n + 1, nb, nb), dtype=XP) for _ in range(4)]
-    for e, el in enumerate(elements):
+    def local(rn, e, el):
         r = np.empty((n + 1, nb), dtype=XP)
-        r[:n] = rho_nodal[int_ptr[e]:int_ptr[e + 1]].reshape(n, nb)
-        r[n] = rho_nodal[n_int + el.dofs]
-        mats = sbfem3d.coefficient_matrices3d(el, mesh.node_xyz, mesh.p, c, r)
+        r[:n] = rn[int_ptr[e]:int_ptr[e + 1]].reshape(n, nb)
+        r[n] = rn[n_int + el.dofs]
+        return r
+
+    for e, el in enumerate(elements):
+        mats = sbfem3d.coefficient_matrices3d(el, mesh.node_xyz, mesh.p, c, local(rho_nodal, e, el))
+        if rho_mass_nodal is not None:
+            rm = local(np.asarray(rho_mass_nodal).astype(XP), e, el)
+            mats = mats[:3] + (sbfem3d.coefficient_matrices3d(el, mesh.node_xyz, mesh.p, c, rm)[3],)
         for k in range(4):
             Es[k][e] = mats[k]
     sys_ = sbfem.element_system(*Es, xi, dt, beta, static=static, dim=3)
