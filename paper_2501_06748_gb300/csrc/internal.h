@@ -198,6 +198,12 @@ struct LevelTasks {
   // child1 | nearest ancestor with backward tasks]
   DevBuf flow_items, node_info;
   int n_items = 0, nodes = 0;
+  // the dataflow in up to three launches: items [seg[0], seg[1]) are the lower forward
+  // levels, [seg[1], seg[2]) the upper levels of both passes, [seg[2], seg[3]) the lower
+  // backward levels; the lower levels' tasks fit small_doubles of staging (one launch when
+  // every level does: seg[1] == seg[3])
+  int flow_seg[4] = {0, 0, 0, 0};
+  size_t small_doubles = 0;
   int items(bool fwd, int l) const {
     const auto& st = fwd ? fwd_start : bwd_start;
     const auto& ws = fwd ? fwd_wstart : bwd_wstart;

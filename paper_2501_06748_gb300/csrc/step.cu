@@ -1200,8 +1200,31 @@ int build_level_tasks(const Model& md, LevelTasks& lt, int B, int grid) {
       for (int k = st[l]; k < ws[l]; ++k) items.push_back(make_int4(k, 1, 1, dir));
       for (int k = ws[l]; k < st[l + 1]; k += gr[l]) items.push_back(make_int4(k, std::min(gr[l], st[l + 1] - k), 0, dir));
     };
-    for (int l = 0; l < L; ++l) add_level(lt.fwd_start, lt.fwd_wstart, lt.fwd_group, l, 0);
-    for (int l = L - 1; l >= 0; --l) add_level(lt.bwd_start, lt.bwd_wstart, lt.bwd_group, l, 1);
+    // the lower levels whose block tasks fit the warp tasks' staging area run at full
+    // occupancy in their own launches; a few large fronts at the top (3-D separators are
+    // planes) then no longer hold the whole solve at one block per SM
+    lt.small_doubles = 8 * solve_warp_doubles(B);
+    int low = -1;                                  // levels 0..low fit
+    for (int l = 0; l < L; ++l) {
+      size_t dl = 0;
+      for (int k = lt.fwd_start[l]; k < lt.fwd_wstart[l]; ++k) dl = std::max(dl, block_task_doubles(fwd[k], B, true));
+      for (int k = lt.bwd_start[l]; k < lt.bwd_wstart[l]; ++k) dl = std::max(dl, block_task_doubles(bwd[k], B, false));
+      if (dl > lt.small_doubles) break;
+      low = l;
+    }
+    for (int l = 0; l < L; ++l) {
+      if (l == low + 1) lt.flow_seg[1] = (int)items.size();
+      add_level(lt.fwd_start, lt.fwd_wstart, lt.fwd_group, l, 0);
+    }
+    if (low + 1 >= L) lt.flow_seg[1] = (int)items.size();
+    for (int l = L - 1; l >= 0; --l) {
+      if (l == low) lt.flow_seg[2] = (int)items.size();
+      add_level(lt.bwd_start, lt.bwd_wstart, lt.bwd_group, l, 1);
+    }
+    lt.flow_seg[0] = 0;
+    lt.flow_seg[3] = (int)items.size();
+    if (low < 0) lt.flow_seg[2] = lt.flow_seg[3];                      // no level fits: one launch
+    if (low + 1 >= L) lt.flow_seg[1] = lt.flow_seg[2] = lt.flow_seg[3];   // every level fits: one launch
     const int T = (int)t.nodes.size();
     std::vector<int32_t> info(5 * (size_t)T, 0), parent(T, -1);
     for (const Task& tk : fwd) info[tk.node] += 1;
@@ -1352,7 +1375,9 @@ struct Stepper {
   DevBuf bar, pstatus;
   LevelTasks* lt = nullptr;
   bool flow = false;                 // dataflow solve (default) instead of level barriers
-  DevBuf flow_counters;              // done_f [nodes] | done_b [nodes] | item counter (u64)
+  DevBuf flow_counters;              // done_f [nodes] | done_b [nodes] | item counters (u64, one per launch segment)
+  int flow_grid[3] = {0, 0, 0};      // blocks of each dataflow launch segment
+  size_t flow_smem[3] = {0, 0, 0};   // and its staging area (bytes)
   FlowArgs fa;
   unsigned flow_gen = 0;
   ExactElemArgs xa;
@@ -1361,7 +1386,7 @@ struct Stepper {
   bool use_window = false;
   cudaAccessPolicyWindow window = {};
   int setup_l2_window(int device);
-  int launch_solve(const void* fn, unsigned grid, void** args, bool cooperative);
+  int launch_solve(const void* fn, unsigned grid, void** args, bool cooperative, size_t smem = 0);
   std::vector<DevBuf*> state_bufs() const;
   int element_launch(int down, int up, int64_t done_step);
   int solve();
@@ -1555,12 +1580,19 @@ int Stepper::init() {
     p_grid = std::max(1, std::min(std::min(per_sm, 4) * sms, lt->max_level_items));
   }
   if (flow) {
-    int per_sm_flow = 0;
-    SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, solve_flow_kernel<true>, 256, s_smem));
-    if (per_sm_flow < 1) return fail(SBFWI_EUNSUPPORTED, "the dataflow solve does not fit on an SM");
+    // segment 1 (upper levels) stages up to s_smem, segments 0 and 2 the warp tasks' area
+    const size_t small = std::min(s_smem, sizeof(double) * lt->small_doubles);
+    flow_smem[0] = flow_smem[2] = small;
+    flow_smem[1] = s_smem;
+    for (int g = 0; g < 3; ++g) {
+      int per_sm_flow = 0;
+      SBFWI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flow, solve_flow_kernel<true>, 256, flow_smem[g]));
+      if (per_sm_flow < 1) return fail(SBFWI_EUNSUPPORTED, "the dataflow solve does not fit on an SM");
+      flow_grid[g] = std::max(1, std::min(per_sm_flow, 4) * sms);   // every block co-resident (cooperative launch)
+    }
     const int T = lt->nodes;
     const size_t cb = ((sizeof(unsigned) * 2 * (size_t)T + 15) / 16) * 16;
-    SBFWI_CUDA(flow_counters.alloc(cb + sizeof(unsigned long long)));
+    SBFWI_CUDA(flow_counters.alloc(cb + 3 * sizeof(unsigned long long)));
     SBFWI_CUDA(cudaMemsetAsync(flow_counters.p, 0, flow_counters.bytes, st));
     fa.s = sa;
     fa.fwd = ftasks; fa.bwd = btasks;
@@ -1572,7 +1604,7 @@ int Stepper::init() {
     fa.budget = 4000000000LL;
     fa.levels = md.mesh->tree.levels;
     fa.trace = nullptr;
-    p_grid = std::max(1, std::min(per_sm_flow, 4) * sms);    // every block co-resident (cooperative launch)
+    p_grid = flow_grid[0];
     flow_gen = 0;
   }
 
@@ -1651,11 +1683,11 @@ int Stepper::setup_l2_window(int device) {
   return SBFWI_OK;
 }
 
-int Stepper::launch_solve(const void* fn, unsigned grid, void** args, bool cooperative) {
+int Stepper::launch_solve(const void* fn, unsigned grid, void** args, bool cooperative, size_t smem) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = s_smem;
+  cfg.dynamicSmemBytes = smem ? smem : s_smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   int na = 0;
@@ -1767,14 +1799,25 @@ int Stepper::solve() {
   prof.begin(kPhaseSolve, st);
   if (flow) {
     ++flow_gen;
-    fa.gen = flow_gen;
-    fa.trace = prof.flow_trace(2 * t.levels, st);
-    fa.base = (unsigned long long)(flow_gen - 1) * (unsigned long long)(fa.n_items + p_grid);
-    void* kargs[] = {&fa};
-    int rc = launch_solve(fa.trace ? (const void*)solve_flow_kernel<true> : (const void*)solve_flow_kernel<false>,
-                          (unsigned)p_grid, kargs, true);
-    if (rc) return rc;
-    prof.count(kPhaseSolve);
+    unsigned long long* trace = prof.flow_trace(2 * t.levels, st);
+    // up to three launches in stream order (lower forward levels, upper levels, lower backward
+    // levels), each claiming its own range of the topologically ordered items
+    for (int g = 0; g < 3; ++g) {
+      const int i0 = lt->flow_seg[g], i1 = lt->flow_seg[g + 1];
+      if (i1 <= i0) continue;
+      FlowArgs f = fa;
+      f.gen = flow_gen;
+      f.trace = trace;
+      f.items = lt->flow_items.as<int4>() + i0;
+      f.n_items = i1 - i0;
+      f.claim = fa.claim + g;
+      f.base = (unsigned long long)(flow_gen - 1) * (unsigned long long)(f.n_items + flow_grid[g]);
+      void* kargs[] = {&f};
+      int rc = launch_solve(trace ? (const void*)solve_flow_kernel<true> : (const void*)solve_flow_kernel<false>,
+                            (unsigned)flow_grid[g], kargs, true, flow_smem[g]);
+      if (rc) return rc;
+      prof.count(kPhaseSolve);
+    }
   } else if (persistent) {
     pa.trace = prof.level_trace(6 * t.levels, st);
     if (pa.trace) ++prof.level_steps;
