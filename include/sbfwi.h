@@ -486,8 +486,10 @@ int sbfwi_profile_solve_levels(double* us, int32_t cap, int32_t* n_slots, int64_
  * item, when the item's inputs are ready and when the item has finished (the last 64
  * solves are kept).  A phase is one tree level of one pass: phases 0..L-1 are the
  * forward levels (leaves -> root), L..2L-1 the backward levels (root -> leaves).  Fills
- * us[min(cap, 8L)] with, per phase: [0, 2L) the time from the launch's first block
- * start to the phase's last item finishing (the phase's completion time), [2L, 4L)
+ * us[min(cap, 8L)] with, per phase: [0, 2L) the time from the solve's first block start
+ * (the first of its launches: a solve whose upper levels need a large staging area runs as
+ * three launches in stream order) to the phase's last item finishing (the phase's
+ * completion time), [2L, 4L)
  * the mean execution time of an item (inputs ready -> finished), [4L, 6L) the mean
  * time an item waited for its inputs after being claimed, [6L, 8L) items per solve;
  * microseconds, averaged over the recorded solves.  *n_slots = 8L (0 if nothing was
